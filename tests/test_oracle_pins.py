@@ -1,0 +1,433 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, printed tables, theorems of Section 4, an independent formulation
+(the uncondensed hybrid system, the non-hybrid mixed system), physics
+(Terzaghi's undrained response, patch tests, macro-element mass balance).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import mhfp_inputs as mi
+import oracle
+from oracle import elements as el
+from oracle import fgmres, precond, system
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _box_element(hx, hy, hz, shear=0.0):
+    X = np.array([[o[0] * hx + shear * o[1] * hy, o[1] * hy, o[2] * hz]
+                  for o in [(a & 1, (a >> 1) & 1, (a >> 2) & 1) for a in range(8)]], float)
+    return X[None]
+
+
+# --------------------------------------------------------------- grid sizes
+def test_dof_counts_match_table_grids():
+    """Table tab:grids: n_u = 3(n+1)^3, n_q = n_pi = 3 n^2 (n+1), n_p = n^3."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "tab_grids.txt"), dtype=np.int64)
+    for n, nu, nq, npp, tot in rows:
+        nU = 3 * (n + 1) ** 3
+        nF = (n + 1) * n * n * 3
+        assert (nU, nF, n ** 3, nU + nF + n ** 3) == (nu, nq, npp, tot)
+    p = mi.terzaghi_cube(4)
+    B = oracle.assemble(p)
+    assert B.sizes == (3 * 125, 64, 3 * 16 * 5)
+
+
+# ------------------------------------------------------------- RT0 element
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.5, 0.25, 2.0)])
+def test_rt0_mass_closed_form_box(h):
+    """A_ww on an axis-aligned box: per axis d, (mu/kappa_d) h_d/(h_e h_f) *
+    [[1/3,-1/6],[-1/6,1/3]], so W = (kappa_d h_e h_f/(mu h_d)) [[4,2],[2,4]]."""
+    hx, hy, hz = h
+    mu, kap = 2e-3, np.array([[3e-12, 5e-13, 7e-11]])
+    A = el.rt0_element(_box_element(hx, hy, hz), np.array([mu]), kap)[0]
+    ref = np.zeros((6, 6))
+    hs = (hx, hy, hz)
+    for d in range(3):
+        e, f = [hs[i] for i in range(3) if i != d]
+        c = mu * hs[d] / (kap[0, d] * e * f)
+        ref[2 * d:2 * d + 2, 2 * d:2 * d + 2] = c * np.array([[1 / 3, -1 / 6], [-1 / 6, 1 / 3]])
+    assert np.allclose(A, ref, rtol=1e-13, atol=1e-15 * np.abs(ref).max())
+    W = np.linalg.inv(A)
+    if h == (1.0, 1.0, 1.0):
+        kiso = np.array([[1e-12] * 3])
+        Wi = np.linalg.inv(el.rt0_element(_box_element(1, 1, 1), np.array([mu]), kiso)[0])
+        assert np.allclose(Wi @ np.ones(6), 6 * 1e-12 / mu, rtol=1e-13)
+        assert np.isclose(np.ones(6) @ Wi @ np.ones(6), 36 * 1e-12 / mu, rtol=1e-13)
+    assert np.allclose(W, W.T, rtol=1e-14, atol=1e-15 * np.abs(W).max())
+    assert np.all(np.linalg.eigvalsh(W) > 0)
+
+
+def test_rt0_reproduces_linear_pressure_on_parallelepiped():
+    """RT0 is exact for a linear pressure on affine (parallelepiped) cells:
+    the recovered outward fluxes W (p_T 1 - pi) equal -(1/mu) K grad p . n |e|."""
+    X = _box_element(0.7, 0.4, 0.9, shear=0.3)
+    mu, kap = 1e-3, np.array([[2e-12, 2e-12, 2e-12]])
+    g = np.array([0.3, -1.1, 0.7])
+    W = np.linalg.inv(el.rt0_element(X, np.array([mu]), kap)[0])
+    x = X[0]
+    centroid = x.mean(axis=0)
+    faces = [[0, 2, 4, 6], [1, 3, 5, 7], [0, 1, 4, 5], [2, 3, 6, 7], [0, 1, 2, 3], [4, 5, 6, 7]]
+    pi, flux = np.zeros(6), np.zeros(6)
+    for lf, fn in enumerate(faces):
+        fc = x[fn].mean(axis=0)
+        pi[lf] = g @ fc
+        a, b, c = x[fn[0]], x[fn[1]], x[fn[2]]
+        nvec = np.cross(b - a, c - a)                  # area vector of the parallelogram
+        if nvec @ (fc - centroid) < 0:
+            nvec = -nvec
+        flux[lf] = -(kap[0, 0] / mu) * g @ nvec
+    w = W @ (g @ centroid * np.ones(6) - pi)
+    assert np.allclose(w, flux, rtol=1e-12, atol=1e-12 * np.abs(flux).max())
+
+
+# -------------------------------------------------------------- Q1 element
+def test_q1_constant_strain_energy_and_rigid_modes():
+    """u = eps x on a parallelepiped: u^T K u = |T| (lam tr(eps)^2 + 2G eps:eps);
+    the six rigid-body modes span the kernel (rank 18)."""
+    X = _box_element(0.8, 1.3, 0.6, shear=0.25)
+    E, nu = np.array([7e3]), np.array([0.3])
+    K, Aup, vol, _ = el.q1_element(X, E, nu, np.array([0.8]))
+    K = K[0]
+    lam, G = el.lame(E[0], nu[0])
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        M = rng.standard_normal((3, 3))
+        eps = 0.5 * (M + M.T)
+        u = (X[0] @ eps.T).ravel()
+        energy = vol[0] * (lam * np.trace(eps) ** 2 + 2 * G * np.sum(eps * eps))
+        assert np.isclose(u @ K @ u, energy, rtol=1e-12)
+    Wskew = np.array([[0, 1, -2], [-1, 0, 3], [2, -3, 0]], float)
+    for u in [(X[0] @ Wskew.T).ravel(), np.tile([1.0, -2.0, 0.5], 8)]:
+        assert np.linalg.norm(K @ u) <= 1e-12 * np.linalg.norm(K) * np.linalg.norm(u)
+    ev = np.linalg.eigvalsh(0.5 * (K + K.T))
+    assert np.allclose(K, K.T, rtol=0, atol=1e-12 * np.abs(K).max())
+    assert np.sum(ev > 1e-10 * ev.max()) == 18 and ev.min() > -1e-10 * ev.max()
+
+
+def test_q1_coupling_closed_form_cube():
+    """A_up,a = -b int div(N_a e_c) = -b * (+-h^2/4): the face integral of N_a."""
+    h, b = 0.5, 0.9
+    _, Aup, vol, _ = el.q1_element(_box_element(h, h, h), np.array([1e4]), np.array([0.25]),
+                                   np.array([b]))
+    ref = np.zeros(24)
+    for a in range(8):
+        o = [(a & 1), (a >> 1) & 1, (a >> 2) & 1]
+        for c in range(3):
+            ref[3 * a + c] = -b * (1 if o[c] else -1) * h * h / 4
+    assert np.allclose(Aup[0], ref, rtol=1e-13)
+    assert np.isclose(vol[0], h ** 3, rtol=1e-14)
+
+
+def test_q1_patch_test_jittered_mesh():
+    """Classical patch test: a linear displacement field on a distorted mesh
+    leaves zero nodal force at every interior node."""
+    p = mi.random_small(4, 3, 4, seed=5, jitter=0.25)
+    B = oracle.assemble(p)
+    mesh = B.mesh
+    # rebuild the stiffness without the Dirichlet treatment
+    Ke, _, _, _ = el.q1_element(mesh.element_coords(), p.E * 0 + 5e3, p.nu * 0 + 0.3, p.biot)
+    dofs = (3 * mesh.cell_nodes[:, :, None] + np.arange(3)).reshape(-1, 24)
+    K = sp.csr_matrix((Ke.ravel(), (np.repeat(dofs, 24, 1).ravel(), np.tile(dofs, (1, 24)).ravel())))
+    G = np.array([[0.1, -0.3, 0.2], [0.05, 0.4, -0.1], [0.3, 0.2, -0.25]])
+    u = (p.coords @ G.T).ravel()
+    f = (K @ u).reshape(-1, 3)
+    idx = np.arange(mesh.n_nodes)
+    i, j, k = idx % 5, (idx // 5) % 4, idx // 20
+    interior = (i > 0) & (i < 4) & (j > 0) & (j < 3) & (k > 0) & (k < 4)
+    assert np.abs(f[interior]).max() <= 1e-12 * np.abs(f).max()
+
+
+# ----------------------------------------------------------- stabilization
+def test_stabilization_macro_spectrum():
+    """A_stab of one full 2x2x2 macro-element is beta_M |M| times the
+    Laplacian of the cube graph Q3: eigenvalues {0,2,2,2,4,4,4,6};
+    beta_M = (3b)^2 / [32 (lambda + 4G)] (Section 3)."""
+    E, nu, b = 3e4, 0.2, 0.7
+    p = mi.terzaghi_cube(2, E=E, nu=nu, b=b)
+    B = oracle.assemble(p)
+    lam, G = el.lame(E, nu)
+    beta = (3 * b) ** 2 / (32 * (lam + 4 * G))
+    ev = np.sort(np.linalg.eigvalsh(B.Astab.toarray()))
+    assert np.allclose(ev, beta * 1.0 * np.array([0, 2, 2, 2, 4, 4, 4, 6]), rtol=1e-13, atol=1e-20)
+    # pattern of A_stab is inside pattern(A_ppi A_pip) (Section 3)
+    P = (abs(B.Appi) @ abs(B.Apip)).toarray() != 0
+    assert np.all(P[B.Astab.toarray() != 0])
+
+
+def test_stabilization_partial_macros():
+    """Odd n: trailing macro-elements are partial patches; every column of
+    A_stab still sums to zero (mass is conserved per macro-element)."""
+    p = mi.random_small(3, 5, 3, seed=2)
+    B = oracle.assemble(p)
+    S = B.Astab.toarray()
+    assert np.allclose(S.sum(axis=0), 0, atol=1e-14 * np.abs(S).max())
+    assert np.allclose(S, S.T)
+    k, l, m = B.mesh.internal_macro_faces()
+    nx, ny, nz = 3, 5, 3
+    assert len(k) == (nx // 2) * ny * nz + nx * (ny // 2) * nz + nx * ny * (nz // 2)
+
+
+# ------------------------------------------------------------ condensation
+def test_static_condensation_matches_uncondensed_hybrid():
+    """Eq. (hybridSys) solved with the broken fluxes w kept gives the same
+    (u, p, pi) as the condensed Eq. (A_33H), and w equals the cell-based
+    reconstruction of Section 2.2."""
+    p = mi.random_small(3, 2, 3, seed=11, jitter=0.2)
+    B = oracle.assemble(p)
+    rng = np.random.default_rng(1)
+    u0, p0 = rng.standard_normal(B.sizes[0]) * 1e-4, rng.standard_normal(B.sizes[1])
+    u0[B.u_fixed] = 0
+    b = system.rhs(B, u0, p0)
+    x = oracle.solve_direct(B, b)
+    A4, nW = system.hybrid_uncondensed(p, B)
+    nU, nP, nPi = B.sizes
+    b4 = np.concatenate([b[:nU], np.zeros(nW), b[nU:nU + nP], np.zeros(nPi)])
+    x4 = spla.spsolve(A4.tocsc(), b4)
+    u, pp, pi = system.split(B, x)
+    assert np.allclose(x4[:nU], u, rtol=0, atol=1e-10 * np.abs(u).max())
+    assert np.allclose(x4[nU + nW:nU + nW + nP], pp, rtol=0, atol=1e-10 * np.abs(pp).max())
+    assert np.allclose(x4[nU + nW + nP:], pi, rtol=0, atol=1e-10 * np.abs(pp).max())
+    w = system.reconstruct_fluxes(B, pp, pi)
+    assert np.allclose(x4[nU:nU + nW], w.ravel(), rtol=0, atol=1e-10 * np.abs(w).max())
+
+
+def _mixed_system(p, B):
+    """Eq. (mfeSys) with stabilization (Eq. stab_A): continuous RT0 fluxes
+    q, one per face not on a no-flow boundary, oriented along +axis."""
+    mesh = B.mesh
+    nU, nP, nPi = B.sizes
+    Aww = B.Aww_cells
+    nT = mesh.n_cells
+    # sign of the cell-local outward basis relative to the face's +axis
+    sgn = np.tile(np.array([-1.0, 1.0, -1.0, 1.0, -1.0, 1.0]), (nT, 1))
+    cf = mesh.cell_faces
+    R = np.repeat(cf, 6, axis=1).ravel()
+    C = np.tile(cf, (1, 6)).ravel()
+    V = (sgn[:, :, None] * Aww * sgn[:, None, :]).ravel()
+    Aqq = sp.csr_matrix((V, (R, C)), shape=(nPi, nPi))
+    Aqp = sp.csr_matrix((-sgn.ravel(), (cf.ravel(), np.repeat(np.arange(nT), 6))), shape=(nPi, nP))
+    Apq = (-Aqp.T).tocsr()
+    keep = np.flatnonzero(~((p.face_bc & 4) != 0))
+    Aqq, Aqp, Apq = Aqq[keep][:, keep], Aqp[keep], Apq[:, keep]
+    A = sp.bmat([[B.Auu, None, B.Aup], [None, Aqq, Aqp], [B.Apu, B.dt * Apq, B.App + B.Astab]],
+                format="csr")
+    return A, len(keep)
+
+
+def test_hybrid_equals_mixed_formulation():
+    """Hybridization is an algebraic reformulation of the mixed method:
+    (u, p) of Eq. (mfeSys)+stabilization equal those of Eq. (A_33H)."""
+    p = mi.random_small(4, 3, 2, seed=3, jitter=0.15)
+    B = oracle.assemble(p)
+    nU, nP, nPi = B.sizes
+    rng = np.random.default_rng(4)
+    u0 = rng.standard_normal(nU) * 1e-4
+    u0[B.u_fixed] = 0
+    p0 = rng.standard_normal(nP)
+    b = system.rhs(B, u0, p0)
+    x = oracle.solve_direct(B, b)
+    Am, nq = _mixed_system(p, B)
+    xm = spla.spsolve(Am.tocsc(), np.concatenate([b[:nU], np.zeros(nq), b[nU:nU + nP]]))
+    u, pp, _ = system.split(B, x)
+    assert np.allclose(xm[:nU], u, rtol=0, atol=1e-10 * np.abs(u).max())
+    assert np.allclose(xm[nU + nq:], pp, rtol=0, atol=1e-10 * np.abs(pp).max())
+
+
+def test_condensed_block_identities():
+    """Section 2: A_pu = -A_up^T; Abar_pp diagonal; A_pip = A_ppi^T;
+    pattern(A_pipi) = pattern(A_qq) (faces sharing a cell)."""
+    p = mi.random_small(3, 3, 2, seed=7)
+    B = oracle.assemble(p)
+    assert abs(B.Apu + B.Aup.T).max() == 0
+    assert abs(B.Apip - B.Appi.T).max() == 0
+    assert abs(B.Abar_pp - sp.diags(B.Abar_pp.diagonal())).max() == 0
+    mesh = B.mesh
+    share = np.zeros((mesh.n_faces, mesh.n_faces), bool)
+    for f6 in mesh.cell_faces:
+        share[np.ix_(f6, f6)] = True
+    fixed = B.pi_fixed
+    share[fixed, :] = False
+    share[:, fixed] = False
+    share[np.diag_indices_from(share)] = True
+    assert np.array_equal(B.Apipi.toarray() != 0, share)
+
+
+# ------------------------------------------------------- Section 4 theory
+def _spectral_case(seed, dims, dt):
+    p = mi.random_small(*dims, seed=seed, dt=dt)
+    B = oracle.assemble(p)
+    pc = precond.build(B, "exact")
+    return p, B, pc
+
+
+@pytest.mark.parametrize("seed,dims,dt", [(1, (2, 2, 2), 0.1), (2, (3, 2, 2), 1e-4)])
+def test_theorem_eigenvalues_of_preconditioned_matrix(seed, dims, dt):
+    """Theorem 1: A_H M^-1 has eigenvalue 1 with multiplicity
+    n_u + n_pi - n_p; Lemma 1 bounds the others, |mu| <= eps +
+    sqrt(eps^2 + 2 dt gamma eps) with 2-norms."""
+    p, B, pc = _spectral_case(seed, dims, dt)
+    A = system.system_matrix(B).toarray()
+    M = pc.matrix().toarray()
+    T = A @ np.linalg.inv(M)
+    ev = np.linalg.eigvals(T)
+    nU, nP, nPi = B.sizes
+    ones = np.sum(np.abs(ev - 1) < 1e-8)
+    assert ones >= nU + nPi - nP
+    Bp = (B.Abar_pp + B.Astab).toarray() - B.Apu.toarray() @ np.linalg.solve(B.Auu.toarray(), B.Aup.toarray())
+    Btinv = np.diag(1 / pc.Bt)
+    Ep = Bp @ Btinv - np.eye(nP)
+    eps = np.linalg.norm(Ep, 2) / 2
+    gam = np.linalg.norm(B.Appi.toarray() @ np.linalg.solve(pc.C.toarray(), B.Apip.toarray()) @ Btinv, 2)
+    bound = eps + np.sqrt(eps ** 2 + 2 * dt * gam * eps)
+    others = ev[np.abs(ev - 1) >= 1e-8]
+    assert np.all(np.abs(others - 1) <= bound * (1 + 1e-10))
+
+
+@pytest.mark.parametrize("dt", [1e-6, 1e-2, 1e2])
+def test_ctilde_spd_and_eigenvalue_bounds(dt):
+    """Theorem 2 / Remark: C~_pi is SPD for diagonal H~ > 0; Lemma 2: every
+    eigenvalue lies in [a - b^T D^-1 b, a] with a = v^T A_pipi v, b = A_ppi v."""
+    p = mi.random_small(3, 3, 3, seed=9, dt=dt)
+    B = oracle.assemble(p)
+    Bt = precond.btilde(B)
+    C = precond.ctilde(B, Bt).toarray()
+    assert np.allclose(C, C.T, rtol=0, atol=1e-14 * np.abs(C).max())
+    lam, V = np.linalg.eigh(C)
+    assert lam.min() > 0
+    App = B.Apipi.toarray()
+    Appi = B.Appi.toarray()
+    for i in range(0, len(lam), 7):
+        v = V[:, i]
+        a = v @ App @ v
+        bb = Appi @ v
+        lower = a - np.sum(bb ** 2 / B.Dw)
+        assert lower - 1e-12 * a <= lam[i] <= a * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- physics
+def test_terzaghi_undrained_response():
+    """One backward-Euler step of the consolidation column: away from the
+    drained top the cell pressure is the undrained p0 = b sigma / (b^2 +
+    S_eps K_v) with K_v = lambda + 2G, and the top settles by sigma H / K_u,
+    K_u = K_v + b^2 / S_eps (config: 8^3, E=1e4, nu=0.25, S=1e-4)."""
+    p = mi.terzaghi_cube(8)
+    B = oracle.assemble(p)
+    x = oracle.solve_direct(B, system.rhs(B))
+    u, pp, pi = system.split(B, x)
+    lam, G = el.lame(1e4, 0.25)
+    Kv = lam + 2 * G
+    p0 = 1.0 / (1.0 + 1e-4 * Kv)
+    assert np.isclose(p0, 1 / 2.2)
+    layers = pp.reshape(8, 64)
+    assert np.allclose(layers[:5], p0, rtol=2e-5)
+    assert np.all(layers[7] < p0)          # the drained top layer has lost pressure
+    uz_top = u[2::3].reshape(9, 81)[8]
+    assert np.allclose(uz_top, -1.0 / (Kv + 1.0 / 1e-4), rtol=2e-3)
+
+
+def test_macro_element_mass_balance():
+    """Section 3: with the jump stabilization the discrete mass balance holds
+    on every macro-element (not cell by cell), and reconstructed fluxes are
+    continuous across interior faces."""
+    p = mi.random_small(4, 3, 3, seed=21, S=1e-4)
+    B = oracle.assemble(p)
+    rng = np.random.default_rng(2)
+    u0 = rng.standard_normal(B.sizes[0]) * 1e-5
+    u0[B.u_fixed] = 0
+    p0 = rng.standard_normal(B.sizes[1])
+    x = oracle.solve_direct(B, system.rhs(B, u0, p0))
+    u, pp, pi = system.split(B, x)
+    w = system.reconstruct_fluxes(B, pp, pi)
+    cell_balance = B.Apu @ (u - u0) + B.App @ (pp - p0) + B.dt * w.sum(axis=1)
+    # per cell the balance is off by exactly the fictitious stabilization flux
+    assert np.allclose(cell_balance, -(B.Astab @ pp), rtol=0, atol=1e-9 * np.abs(cell_balance).max())
+    macro = np.bincount(B.mesh.cell_macro, weights=cell_balance)
+    assert np.abs(macro).max() <= 1e-9 * np.abs(cell_balance).max()
+    fc, fl = B.mesh.face_cells, B.mesh.face_local
+    inner = (fc[:, 0] >= 0) & (fc[:, 1] >= 0)
+    wsum = w[fc[inner, 0], fl[inner, 0]] + w[fc[inner, 1], fl[inner, 1]]
+    assert np.abs(wsum).max() <= 1e-10 * np.abs(w).max()
+
+
+def test_linearity_in_load():
+    """Scaling the load scales the solution (the batched workload's loads)."""
+    p = mi.random_small(2, 3, 2, seed=1)
+    B = oracle.assemble(p)
+    x1 = oracle.solve_direct(B, system.rhs(B, load_scale=1.0))
+    x4 = oracle.solve_direct(B, system.rhs(B, load_scale=4.0))
+    assert np.allclose(x4, 4 * x1, rtol=1e-12, atol=1e-14 * np.abs(x4).max())
+
+
+# ------------------------------------------------------------------ solver
+def test_fgmres_amg_converges_to_direct_solution():
+    """FGMRES + block-triangular preconditioner with the multigrid inner
+    solves reaches the direct solution: energy-norm error (block-diagonal
+    SPD norm of A_uu, B~_p, C~_pi) below 1e-8 at a 1e-10 tolerance."""
+    p = mi.random_small(7, 6, 7, seed=13, jitter=0.2)
+    B = oracle.assemble(p)
+    b = system.rhs(B)
+    x = oracle.solve_direct(B, b)
+    pc = precond.build(B, "amg")
+    assert len(pc.u_levels) >= 2 and len(pc.pi_levels) >= 2
+    A = system.system_matrix(B)
+    s = precond.equilibration(B, pc.Bt, pc.C)
+    xx, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=1e-10, scale=s)
+    assert info["converged"] and info["true_rel"] <= 1.05e-10
+    e = xx - x
+    nU, nP, nPi = B.sizes
+    def enorm(v):
+        return np.sqrt(v[:nU] @ (B.Auu @ v[:nU]) + v[nU:nU + nP] @ (pc.Bt * v[nU:nU + nP])
+                       + v[nU + nP:] @ (pc.C @ v[nU + nP:]))
+    assert enorm(e) <= 1e-8 * enorm(x)
+
+
+def test_table_can1_iteration_counts_exact_inner_solves():
+    """Table tab:can_1 (loose pin of the B~_p reading): cantilever, M_I^(h),
+    GMRES to tau = 1e-6.  The paper's counts (37/41 for dt = 0.1, 39/41 for
+    dt = 1e-5 on 10^3/20^3) are stable under refinement; with this oracle's
+    reading of B~_p and the equilibrated residual the counts are lower
+    (the load and scaling of the paper's runs are not stated), so the pin
+    is: never more iterations than the paper, and at most 25% growth from
+    10^3 to 20^3."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "tab_can1.txt"))
+    for dt in (0.1, 1e-5):
+        its = {}
+        for n in (10, 20):
+            p = mi.cantilever_cube(n, dt=dt)
+            B = oracle.assemble(p)
+            pc = precond.build(B, "exact")
+            A = system.system_matrix(B)
+            b = system.rhs(B)
+            s = precond.equilibration(B, pc.Bt, pc.C)
+            _, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=1e-6, restart=200, scale=s)
+            its[n] = info["iters"]
+            paper = rows[(rows[:, 0] == n) & np.isclose(rows[:, 1], dt), 2][0]
+            assert info["converged"] and its[n] <= paper, (n, dt, its[n], paper)
+        assert its[20] <= 1.25 * its[10], (dt, its)
+
+
+def test_vcycles_are_symmetric_contractions():
+    """The multigrid spec keeps each V-cycle a symmetric operator (Galerkin
+    coarse levels, R = P^T, identical pre/post Chebyshev polynomials), as the
+    transposed preconditioner needs, and each one reduces the error."""
+    p = mi.random_small(7, 5, 6, seed=17, jitter=0.2)
+    B = oracle.assemble(p)
+    pc = precond.build(B, "amg")
+    rng = np.random.default_rng(3)
+    for levels, A in ((pc.u_levels, B.Auu), (pc.pi_levels, pc.C)):
+        v, w = rng.standard_normal((2, A.shape[0]))
+        a = v @ precond.vcycle(levels, w)
+        b = w @ precond.vcycle(levels, v)
+        assert abs(a - b) <= 1e-10 * abs(a)
+        x = rng.standard_normal(A.shape[0])
+        e = x - precond.vcycle(levels, A @ x)
+        assert np.sqrt(e @ (A @ e)) < 0.9 * np.sqrt(x @ (A @ x))
+        for lev in levels[1:]:
+            assert abs(lev.A - lev.A.T).max() <= 1e-12 * abs(lev.A).max()
