@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Time-to-solve per backward-Euler step of the stabilized hybridized
+poromechanics system (FGMRES + block-triangular multigrid preconditioner,
+FP64) on one GB300, to a 1e-8 relative residual of the equilibrated system.
+
+Default workload: 64^3 unit cube, log-normal permeability (ln kappa ~
+N(ln 1e-13, 2^2), exponential covariance of 8 cells, seed 2), S_eps = 0,
+dt = 1e-3 s, consolidation-column boundaries; 1,884,739 unknowns.  A "step"
+is one time step: right-hand side from the previous state + FGMRES solve.
+The operator and the preconditioner are built once (constant dt), timed
+separately as setup_ms.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun) solve independent replicas, one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solve per step to 1e-8 rel. residual"
+TOL = 1e-8
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "lognormal64": dict(n=64, desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "lognormal32": dict(n=32, desc="32^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "lognormal96": dict(n=96, desc="96^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+}
+
+
+def make_problem(name):
+    import mhfp_inputs as mi
+    return mi.lognormal_cube(WORKLOADS[name]["n"])
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lognormal64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-target", type=str, default="", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                     "NUMEXPR_NUM_THREADS": "1"}
+
+
+def oracle_sample_subprocess(n_target_dofs, gpu_iters, sample_n=32):
+    """Run the oracle sample in a fresh interpreter pinned to one BLAS/OpenMP
+    thread (so the reported core count is exact), not forked from this
+    CUDA process."""
+    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(sample_n),
+                        "--oracle-target", f"{n_target_dofs},{gpu_iters}"], env=env, capture_output=True,
+                       text=True, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def clocks_start(dev_index):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--id={dev_index}", f"--query-gpu={CLOCK_Q}",
+                              "--format=csv,noheader,nounits", "-lms", "200"], stdout=f,
+                             stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None, f.name
+    return p, f.name
+
+
+def clocks_stop(proc, path):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [s.strip() for s in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(n_target_dofs, gpu_iters, sample_n=32, nsteps=1):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload:
+    `nsteps` time steps of the same generator at sample_n^3 (setup not
+    timed), scaled to the full workload by unknowns x FGMRES iterations."""
+    import numpy as np
+    import mhfp_inputs as mi
+    import oracle
+    from oracle import fgmres, precond, system
+    prob = mi.lognormal_cube(sample_n)
+    B = oracle.assemble(prob)
+    pc = precond.build(B, "amg")
+    A = system.system_matrix(B)
+    sc = precond.equilibration(B, pc.Bt, pc.C)
+    nU, nP, _ = B.sizes
+    n_s = sum(B.sizes)
+    xprev = None
+    secs, iters = [], []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        b = system.rhs(B, None if xprev is None else xprev[:nU], None if xprev is None else xprev[nU:nU + nP])
+        x, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=TOL, scale=sc)
+        secs.append(time.perf_counter() - t0)
+        iters.append(info["iters"])
+        xprev = x
+    per_dof_iter = sum(secs) / (n_s * sum(iters))
+    ms = per_dof_iter * n_target_dofs * gpu_iters * 1e3
+    return dict(value=ms, unit="ms", cores=1, kind="oracle",
+                sample=(f"{nsteps} time step(s) of the same workload generator at {sample_n}^3 ({n_s} unknowns, "
+                        f"{sum(iters)} FGMRES iterations, {sum(secs):.2f} s, setup untimed) on one host core "
+                        f"(scipy.sparse is single-threaded), scaled by unknowns x iterations to the full "
+                        f"workload's {gpu_iters:.1f} iterations"),
+                sample_seconds=sum(secs), sample_iters=iters), secs
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, each step a
+    bounded sample of the workload, scaled to the metric's unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import mhfp_inputs as mi
+    n_full = sum(make_problem_sizes(args.workload))
+    import oracle
+    from oracle import fgmres, precond, system
+    sample_n = 24
+    prob = mi.lognormal_cube(sample_n)
+    B = oracle.assemble(prob)
+    pc = precond.build(B, "amg")
+    A = system.system_matrix(B)
+    sc = precond.equilibration(B, pc.Bt, pc.C)
+    nU, nP, _ = B.sizes
+    n_s = sum(B.sizes)
+    xprev = None
+    per_step = []
+    total_iters = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        b = system.rhs(B, None if xprev is None else xprev[:nU], None if xprev is None else xprev[nU:nU + nP])
+        x, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=TOL, scale=sc)
+        dt = time.perf_counter() - t0
+        xprev = x
+        if k >= args.warmup:
+            per_step.append(dt * n_full / n_s * 1e3)
+            total_iters.append(info["iters"])
+    ms = sum(per_step) / len(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": n_full, "tol": TOL,
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": (f"each step = one time step of the same generator at {sample_n}^3 "
+                                        f"({n_s} unknowns, {total_iters} FGMRES iterations), scaled by unknowns "
+                                        f"to the full workload; one host core")},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def make_problem_sizes(name):
+    n = WORKLOADS[name]["n"]
+    return (3 * (n + 1) ** 3, n ** 3, 3 * n * n * (n + 1))
+
+
+def traffic_for(kernel):
+    """dram read+write bytes per launch of `kernel` at this workload, from the
+    committed ncu summary, or None if the kernel's source changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2002_09603_gb300", "csrc", d["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if sha == d["source_sha"] else None
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2002_09603_gb300 import Solver, launch_count
+
+    prob = make_problem(args.workload)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    setup_ms = e0.elapsed_time(e1)
+
+    # warm-up: a full simulation prefix from the initial state
+    x = None
+    for _ in range(args.warmup):
+        b = s.build_rhs(x)
+        x, _ = s.solve(b, tol=TOL)
+
+    # timed: K steps of a fresh simulation, inputs resident in HBM
+    x = None
+    iters = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk, clk_path = clocks_start(local)
+    time.sleep(0.3)
+    l0 = launch_count()
+    s.timing(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b = s.build_rhs(x)
+        x, st = s.solve(b, tol=TOL)
+        iters.append(st["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clocks_stop(clk, clk_path)
+    kt = s.timing_read(0)
+    s.timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI with host buffers: the previous state comes
+    # from pinned host memory and the solution goes back to it every step
+    e2e = None
+    if not args.no_e2e:
+        nU, nP, _ = s.sizes
+        h_state = torch.zeros(s.n, dtype=torch.float64).pin_memory()
+        d_prev = s.empty()
+        h2d = (nU + nP) * 8
+        d2h = s.n * 8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            d_prev[:nU + nP].copy_(h_state[:nU + nP], non_blocking=True)
+            b = s.build_rhs(d_prev if k > 0 else None)
+            xs, _ = s.solve(b, tol=TOL)
+            h_state.copy_(xs, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peak, peak_kind = measured_peaks()
+    avg_ms = kt["total_ms"] / max(kt["launches"], 1)
+    achieved = kt["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9 if kt["launches"] else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": traffic_for("k_cheb_u0"),
+                "kernel": "k_cheb_u0 (Chebyshev sweep, finest displacement level, 27-point 3x3-block stencil)",
+                "launches": kt["launches"], "avg_launch_us": avg_ms * 1e3,
+                "bytes_per_launch": kt["bytes_per_launch"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample_subprocess(s.n, statistics.mean(iters))
+
+    nU, nP, nPi = s.sizes
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
+                       "n_pi": nPi, "tol": TOL, "restart": 50, "iterations_per_step": iters,
+                       "setup_ms": setup_ms, "precision": "fp64 throughout",
+                       "l2": "inputs larger than L2 (A_uu alone is 534 MB)", "parallelism": "replicas",
+                       "hierarchy_u": s.hierarchy(0)["points"], "hierarchy_pi": s.hierarchy(1)["points"]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        tgt, it = args.oracle_target.split(",")
+        d, _ = oracle_sample(int(tgt), float(it), sample_n=args.oracle_sample)
+        print(json.dumps(d), flush=True)
+        return
+    if args.impl == "reference":
+        os.environ.update(SINGLE_THREAD_ENV)  # before numpy is imported
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

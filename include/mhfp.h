@@ -1,0 +1,182 @@
+/*
+ * libmhfp -- GB300 (sm_103a) solver for the stabilized, hybridized
+ * Q1-RT0-P0 three-field poromechanics system of Frigo, Castelletto,
+ * Ferronato & White, "Efficient solvers for hybridized three-field mixed
+ * finite element coupled poromechanics" (arXiv:2002.09603).
+ *
+ * One backward-Euler step solves A_H x = b (Eq. stab_A, hybrid form),
+ *
+ *     [ A_uu   A_up            0         ] [u]   [f_u]
+ *     [ A_pu   Abar_pp+A_stab  dt A_ppi  ] [p] = [f_p]
+ *     [ 0      A_pip           A_pipi    ] [pi]  [f_pi]
+ *
+ * by right-preconditioned flexible GMRES with the block upper-triangular
+ * preconditioner M of Eq. (hybridPrec), whose A_uu and C~_pi solves are
+ * multigrid V-cycles.
+ *
+ * Conventions for every call below:
+ *  - Vectors are FP64 DEVICE pointers in the layout
+ *      [ u (3 per node, node-major: u_x,u_y,u_z of node 0, then node 1, ...)
+ *      | p (one per cell) | pi (one per face) ],
+ *    nodes n = i + (nx+1)(j + (ny+1)k), cells c = i + nx(j + ny k), faces
+ *    x-normal family first (i <= nx, j < ny, k < nz), then y, then z, each
+ *    lexicographic.  The caller owns every vector it passes; the handle owns
+ *    all matrices, multigrid levels and Krylov workspace.
+ *  - All device work is issued on the CUDA stream given to mhfp_create.
+ *    Calls return after their work is queued, except those that report
+ *    statistics or sizes (mhfp_solve, mhfp_setup_precond), which
+ *    synchronise the stream.
+ *  - Errors are returned as mhfp_status; mhfp_last_error gives the text.
+ *    Host-side validation happens before any launch.  No call traps,
+ *    asserts on the device or waits without bound.
+ */
+#ifndef MHFP_H
+#define MHFP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhfp_ctx* mhfp_handle;
+
+typedef enum {
+  MHFP_OK = 0,
+  MHFP_ERR_ARG = 1,            /* bad argument (null pointer, size, value)      */
+  MHFP_ERR_MESH = 2,           /* inverted/degenerate element (det J <= 0)      */
+  MHFP_ERR_OOM = 3,            /* device allocation failed                      */
+  MHFP_ERR_CUDA = 4,           /* a CUDA runtime call failed                    */
+  MHFP_ERR_NOT_CONVERGED = 5,  /* maxit reached; x holds the last iterate       */
+  MHFP_ERR_NONFINITE = 6,      /* NaN/Inf in the right-hand side or residual    */
+  MHFP_ERR_BREAKDOWN = 7,      /* Krylov breakdown that is not convergence      */
+  MHFP_ERR_STATE = 8           /* call out of order (e.g. solve before setup)   */
+} mhfp_status;
+
+/* Structured hexahedral mesh of a box (nx*ny*nz cells), host arrays, copied
+ * at create time.  coords: (nx+1)(ny+1)(nz+1)*3 node coordinates (any
+ * positively oriented hexahedra).  node_fix: per node, bit0/1/2 = u_x/u_y/u_z
+ * prescribed to zero.  face_bc: per face, bit0 = the uniform traction acts on
+ * it, bit1 = drained (interface pressure prescribed to zero), bit2 = no-flow
+ * (the default for boundary faces that are not drained). */
+typedef struct {
+  int nx, ny, nz;
+  const double* coords;
+  const unsigned char* node_fix;
+  const unsigned char* face_bc;
+} mhfp_mesh;
+
+/* Per-cell material fields, host arrays of n_T values (kappa: 3 per cell,
+ * the diagonal of the permeability tensor).  E [Pa], nu [-], biot [-],
+ * Seps [1/Pa], mu [Pa s], kappa [m^2]. */
+typedef struct {
+  const double *E, *nu, *biot, *Seps, *mu, *kappa;
+} mhfp_materials;
+
+typedef struct {
+  int restart;          /* FGMRES restart length m (default 50)                */
+  int maxit;            /* maximum total FGMRES iterations (default 1000)      */
+  int cheb_degree;      /* Chebyshev smoother degree (default 2)               */
+  double cheb_ratio;    /* lmax / lmin of the smoother interval (default 10)   */
+  int coarse_max;       /* coarsen while a level has more points (default 125) */
+  int power_iters;      /* power iterations for rho(D^-1 A) (default 15)       */
+} mhfp_options;
+
+typedef struct {
+  int iterations;       /* FGMRES iterations (all cycles)                      */
+  int restarts;         /* completed restart cycles                            */
+  int converged;        /* 1 if the true residual met tol                      */
+  double rel_residual;  /* Arnoldi estimate |g_{j+1}| / ||D_s b||              */
+  double true_rel_residual; /* ||D_s (b - A x)|| / ||D_s b|| at exit           */
+  double solve_ms;      /* wall time of the call (host clock)                  */
+} mhfp_stats;
+
+typedef struct {
+  int levels;           /* number of levels (>= 1)                             */
+  long long points[8];  /* lattice points (or faces) per level                 */
+  int block[8];         /* unknowns per point (3 for u, 1 for pi)              */
+  double lmax[8];       /* 1.1 * rho(D^-1 A) per level (0 on the last level)   */
+} mhfp_hierarchy_info;
+
+/* Fill *opt with the defaults listed above. */
+void mhfp_default_options(mhfp_options* opt);
+
+/* Validate and copy mesh + materials, record dt (Section 2.1, backward
+ * Euler) and the uniform traction vector (Appendix A, f_u) acting on faces
+ * with face_bc bit0.  stream: a cudaStream_t (may be NULL = legacy default).
+ * The device current at the call is the one the handle uses. */
+mhfp_status mhfp_create(const mhfp_mesh* mesh, const mhfp_materials* mat, double dt,
+                        const double traction[3], void* stream, mhfp_handle* out);
+
+/* Element kernels and assembly (Appendix A; Eq. hmfeSys / A_33H static
+ * condensation of the RT0 fluxes; Eq. J_def / stab_A macro-element
+ * stabilization with beta_M = (3b)^2 / [32 (lambda + 4G)]).  Returns
+ * MHFP_ERR_MESH if any element has det J <= 0 at a quadrature point. */
+mhfp_status mhfp_assemble_condense(mhfp_handle h);
+
+/* Preconditioner set-up (Section 4, Eq. hybridPrec, Eq. app_Bp):
+ * B~_p = S_eps|T| + diag(A_stab) + diag(A_up^T diag(A_uu)^-1 A_up)
+ *        + dt diag(A_wp^T A_ww^-1 A_wp),
+ * C~_pi = A_pipi - dt A_pip B~_p^-1 A_ppi, and the two multigrid
+ * hierarchies.  opt may be NULL (defaults).  Synchronises the stream. */
+mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt);
+
+/* Right-hand side of one backward-Euler step (Section 2.1, Appendix A):
+ * b = [ load_scale * f_u ; A_pu u_prev + S_eps |T| p_prev ; 0 ].
+ * d_x_prev: previous solution in the vector layout (only u and p are read),
+ * or NULL for u_0 = 0, p_0 = 0.  d_rhs: output, n = n_u + n_p + n_pi. */
+mhfp_status mhfp_build_rhs(mhfp_handle h, const double* d_x_prev, double load_scale, double* d_rhs);
+
+/* Solve A_H x = b by FGMRES(restart) with right preconditioning M^-1, zero
+ * initial guess (Section 5), on the equilibrated system D_s A_H D_s with
+ * D_s = diag(A_uu, B~_p, C~_pi)^(-1/2); stops when ||D_s (b - A x)|| <=
+ * tol ||D_s b||.  d_rhs, d_x: device vectors (d_x is overwritten).
+ * stats may be NULL.  Synchronises the stream. */
+mhfp_status mhfp_solve(mhfp_handle h, const double* d_rhs, double* d_x, double tol, mhfp_stats* stats);
+
+/* y = A_H x (Eq. stab_A, hybrid form), unscaled. */
+mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y);
+
+/* z = M^-1 v with the multigrid inner solves (Eq. hybridPrec back
+ * substitution: pi, then p, then u), unscaled. */
+mhfp_status mhfp_apply_precond(mhfp_handle h, const double* d_v, double* d_z);
+
+/* One V-cycle x = V(b) of the displacement (which = 0, length n_u) or the
+ * interface-pressure (which = 1, length n_pi) hierarchy. */
+mhfp_status mhfp_vcycle(mhfp_handle h, int which, const double* d_b, double* d_x);
+
+/* y = A_l x for level `level` of hierarchy `which` (lengths from
+ * mhfp_hierarchy).  Level 0 of which = 1 is C~_pi. */
+mhfp_status mhfp_level_apply(mhfp_handle h, int which, int level, const double* d_x, double* d_y);
+
+/* Hierarchy description (after mhfp_setup_precond). */
+mhfp_status mhfp_hierarchy(mhfp_handle h, int which, mhfp_hierarchy_info* info);
+
+/* Copy the diagonal approximation B~_p (n_p values) and the equilibration
+ * scaling D_s (n values) into device buffers (either may be NULL). */
+mhfp_status mhfp_get_scalings(mhfp_handle h, double* d_btilde, double* d_ds);
+
+/* Sizes: n_u = 3 (nx+1)(ny+1)(nz+1), n_p = nx ny nz, n_pi = number of faces
+ * (every dof is kept, Table tab:grids counting). */
+mhfp_status mhfp_sizes(mhfp_handle h, long long* n_u, long long* n_p, long long* n_pi);
+
+/* Per-kernel-class device time accumulated with CUDA events on the
+ * handle's stream while timing is enabled (kernel classes: 0 = Chebyshev
+ * sweeps of the finest displacement level, k_cheb_u0; 1 = operator apply;
+ * 2 = Gram-Schmidt).  bytes_per_launch is the algorithmic traffic
+ * (matrix values, inverse diagonal blocks and vectors touched once).
+ * mhfp_timing(h, 1) resets and enables, mhfp_timing(h, 0) disables. */
+mhfp_status mhfp_timing(mhfp_handle h, int enable);
+mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launches,
+                             double* total_ms, double* bytes_per_launch);
+
+/* Number of kernels this library has launched in the process so far (all
+ * handles); a caller brackets a region with two reads to count its launches. */
+long long mhfp_launch_count(void);
+
+const char* mhfp_last_error(mhfp_handle h);
+const char* mhfp_status_string(mhfp_status s);
+void mhfp_destroy(mhfp_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHFP_H */

@@ -1,0 +1,246 @@
+"""ctypes binding of libmhfp (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts numpy
+inputs into the C structs, passes torch CUDA tensors as device pointers and
+turns status codes into exceptions.  There is no CPU fallback: if the
+shared library is missing the import of a Solver fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmhfp.so")
+
+MHFP_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "out of memory", 4: "CUDA error",
+          5: "not converged", 6: "non-finite value", 7: "Krylov breakdown", 8: "call out of order"}
+
+# every symbol include/mhfp.h declares
+EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhfp_setup_precond",
+           "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_precond", "mhfp_vcycle",
+           "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
+           "mhfp_timing_read", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
+
+
+class MhfpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("coords", C.c_void_p),
+                ("node_fix", C.c_void_p), ("face_bc", C.c_void_p)]
+
+
+class Materials(C.Structure):
+    _fields_ = [("E", C.c_void_p), ("nu", C.c_void_p), ("biot", C.c_void_p), ("Seps", C.c_void_p),
+                ("mu", C.c_void_p), ("kappa", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("cheb_degree", C.c_int),
+                ("cheb_ratio", C.c_double), ("coarse_max", C.c_int), ("power_iters", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("rel_residual", C.c_double), ("true_rel_residual", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HierInfo(C.Structure):
+    _fields_ = [("levels", C.c_int), ("points", C.c_longlong * 8), ("block", C.c_int * 8),
+                ("lmax", C.c_double * 8)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libmhfp.so (built in-tree by paper_2002_09603_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libmhfp.so not built ({p}); run paper_2002_09603_gb300.build.build()")
+    lib = C.CDLL(p)
+    vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    sig = {
+        "mhfp_default_options": (None, [C.POINTER(Options)]),
+        "mhfp_create": (i, [C.POINTER(Mesh), C.POINTER(Materials), d, C.POINTER(C.c_double), vp, C.POINTER(vp)]),
+        "mhfp_assemble_condense": (i, [vp]),
+        "mhfp_setup_precond": (i, [vp, C.POINTER(Options)]),
+        "mhfp_build_rhs": (i, [vp, vp, d, vp]),
+        "mhfp_solve": (i, [vp, vp, vp, d, C.POINTER(Stats)]),
+        "mhfp_apply_operator": (i, [vp, vp, vp]),
+        "mhfp_apply_precond": (i, [vp, vp, vp]),
+        "mhfp_vcycle": (i, [vp, i, vp, vp]),
+        "mhfp_level_apply": (i, [vp, i, i, vp, vp]),
+        "mhfp_hierarchy": (i, [vp, i, C.POINTER(HierInfo)]),
+        "mhfp_get_scalings": (i, [vp, vp, vp]),
+        "mhfp_sizes": (i, [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]),
+        "mhfp_timing": (i, [vp, i]),
+        "mhfp_timing_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d), C.POINTER(d)]),
+        "mhfp_launch_count": (ll, []),
+        "mhfp_last_error": (C.c_char_p, [vp]),
+        "mhfp_status_string": (C.c_char_p, [i]),
+        "mhfp_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libmhfp so far in this process."""
+    return int(load().mhfp_launch_count())
+
+
+def default_options() -> Options:
+    o = Options()
+    load().mhfp_default_options(C.byref(o))
+    return o
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One stabilized hybridized poromechanics system on one GPU.
+
+    ``prob`` is an ``mhfp_inputs.Problem``.  Device vectors are float64
+    torch CUDA tensors in the layout [u | p | pi]."""
+
+    def __init__(self, prob, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep = dict(
+            coords=np.ascontiguousarray(prob.coords, dtype=np.float64),
+            node_fix=np.ascontiguousarray(prob.node_fix, dtype=np.uint8),
+            face_bc=np.ascontiguousarray(prob.face_bc, dtype=np.uint8),
+            E=np.ascontiguousarray(prob.E, dtype=np.float64),
+            nu=np.ascontiguousarray(prob.nu, dtype=np.float64),
+            biot=np.ascontiguousarray(prob.biot, dtype=np.float64),
+            Seps=np.ascontiguousarray(prob.Seps, dtype=np.float64),
+            mu=np.ascontiguousarray(prob.mu, dtype=np.float64),
+            kappa=np.ascontiguousarray(prob.kappa, dtype=np.float64),
+        )
+        k = self._keep
+        mesh = Mesh(prob.nx, prob.ny, prob.nz, k["coords"].ctypes.data, k["node_fix"].ctypes.data,
+                    k["face_bc"].ctypes.data)
+        mats = Materials(k["E"].ctypes.data, k["nu"].ctypes.data, k["biot"].ctypes.data,
+                         k["Seps"].ctypes.data, k["mu"].ctypes.data, k["kappa"].ctypes.data)
+        trac = (C.c_double * 3)(*[float(v) for v in prob.traction])
+        h = C.c_void_p()
+        st = self.lib.mhfp_create(C.byref(mesh), C.byref(mats), float(prob.dt), trac,
+                                  C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != MHFP_OK:
+            raise MhfpError(st, "mhfp_create failed")
+        self.h = h
+        nu_, np_, npi = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        self.lib.mhfp_sizes(h, C.byref(nu_), C.byref(np_), C.byref(npi))
+        self.sizes = (nu_.value, np_.value, npi.value)
+        self.n = sum(self.sizes)
+
+    # ------------------------------------------------------------ helpers
+    def _check(self, st):
+        if st != MHFP_OK:
+            raise MhfpError(st, self.lib.mhfp_last_error(self.h).decode())
+
+    def empty(self, n=None):
+        return self.torch.empty(self.n if n is None else n, dtype=self.torch.float64, device=self.device)
+
+    # ------------------------------------------------------------ C ABI
+    def assemble_condense(self):
+        self._check(self.lib.mhfp_assemble_condense(self.h))
+
+    def setup_precond(self, options: Options | None = None):
+        self._check(self.lib.mhfp_setup_precond(self.h, None if options is None else C.byref(options)))
+
+    def build_rhs(self, x_prev=None, load_scale=1.0, out=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_build_rhs(self.h, _ptr(x_prev), float(load_scale), _ptr(out)))
+        return out
+
+    def solve(self, rhs, tol=1e-8, out=None, raise_not_converged=True):
+        out = self.empty() if out is None else out
+        st = Stats()
+        code = self.lib.mhfp_solve(self.h, _ptr(rhs), _ptr(out), float(tol), C.byref(st))
+        if code != MHFP_OK and not (code == 5 and not raise_not_converged):
+            self._check(code)
+        return out, st.as_dict()
+
+    def apply_operator(self, x, out=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_apply_operator(self.h, _ptr(x), _ptr(out)))
+        return out
+
+    def apply_precond(self, v, out=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_apply_precond(self.h, _ptr(v), _ptr(out)))
+        return out
+
+    def vcycle(self, which, b, out=None):
+        out = self.torch.empty_like(b) if out is None else out
+        self._check(self.lib.mhfp_vcycle(self.h, int(which), _ptr(b), _ptr(out)))
+        return out
+
+    def level_apply(self, which, level, x, out=None):
+        out = self.torch.empty_like(x) if out is None else out
+        self._check(self.lib.mhfp_level_apply(self.h, int(which), int(level), _ptr(x), _ptr(out)))
+        return out
+
+    def hierarchy(self, which):
+        info = HierInfo()
+        self._check(self.lib.mhfp_hierarchy(self.h, int(which), C.byref(info)))
+        L = info.levels
+        return dict(levels=L, points=list(info.points[:L]), block=list(info.block[:L]), lmax=list(info.lmax[:L]))
+
+    def scalings(self):
+        bt = self.empty(self.sizes[1])
+        ds = self.empty()
+        self._check(self.lib.mhfp_get_scalings(self.h, _ptr(bt), _ptr(ds)))
+        return bt, ds
+
+    def timing(self, enable: bool):
+        self._check(self.lib.mhfp_timing(self.h, 1 if enable else 0))
+
+    def timing_read(self, kernel_class: int):
+        n, ms, b = C.c_longlong(), C.c_double(), C.c_double()
+        self._check(self.lib.mhfp_timing_read(self.h, int(kernel_class), C.byref(n), C.byref(ms), C.byref(b)))
+        return dict(launches=n.value, total_ms=ms.value, bytes_per_launch=b.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mhfp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prepare(prob, options: Options | None = None, stream=None) -> Solver:
+    """create -> assemble_condense -> setup_precond."""
+    s = Solver(prob, stream=stream)
+    s.assemble_condense()
+    s.setup_precond(options)
+    return s

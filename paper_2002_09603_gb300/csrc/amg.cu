@@ -1,0 +1,954 @@
+// Multigrid inner solvers of the block-triangular preconditioner (Section 4,
+// Eq. hybridPrec; the paper's M_II^(h) uses smoothed aggregation on A_uu and
+// an AMG on C~_pi).  Everything here runs on structured lattices:
+//
+//  * displacement hierarchy: level 0 = A_uu on the Q1 node lattice (27-point
+//    3x3-block stencil); smoothed aggregation with 3x3x3 node aggregates,
+//    tentative prolongator = indicator x I_3 on free dofs, one damped block-
+//    Jacobi smoothing step of the prolongator, Galerkin coarse operators
+//    (which stay 27-point block stencils);
+//  * interface-pressure hierarchy: level 0 = C~_pi on faces (11-entry ELL
+//    rows), faces -> cells by averaging (weight 1/2 per adjacent cell, 1 on
+//    a boundary face, 0 on a drained face) giving a 25-point cell stencil,
+//    then scalar smoothed aggregation (125-point coarse stencils);
+//  * V(1,1) cycles with Chebyshev smoothing preconditioned by the (block)
+//    diagonal, exact dense solve on the last level.
+//
+// Galerkin products are formed in two deterministic gather passes, Q = A P
+// on the fine lattice and A_c = P^T Q per coarse point: no atomics, no
+// sparse-matrix hashing.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace mhfp {
+
+namespace {
+
+static __constant__ signed char c_dia[25][3] = {
+    {0, 0, -2}, {0, -1, -1}, {-1, 0, -1}, {0, 0, -1}, {1, 0, -1}, {0, 1, -1}, {0, -2, 0}, {-1, -1, 0}, {0, -1, 0},
+    {1, -1, 0}, {-2, 0, 0},  {-1, 0, 0},  {0, 0, 0},  {1, 0, 0},  {2, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
+    {0, 2, 0},  {0, -1, 1},  {-1, 0, 1},  {0, 0, 1},  {1, 0, 1},  {0, 1, 1},  {0, 0, 2}};
+static __constant__ signed char c_dia_idx[125] = {
+    -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 0,  -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
+    -1, -1, -1, -1, -1, -1, -1, 1,  -1, -1, -1, 2,  3,  4,  -1, -1, -1, 5,  -1, -1, -1, -1, -1, -1, -1,
+    -1, -1, 6,  -1, -1, -1, 7,  8,  9,  -1, 10, 11, 12, 13, 14, -1, 15, 16, 17, -1, -1, -1, 18, -1, -1,
+    -1, -1, -1, -1, -1, -1, -1, 19, -1, -1, -1, 20, 21, 22, -1, -1, -1, 23, -1, -1, -1, -1, -1, -1, -1,
+    -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 24, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+
+template <int KIND>
+struct St;
+template <>
+struct St<ST_BOX1> {
+  static constexpr int N = 27, R = 1, C = 13;
+  __device__ static void off(int o, int& x, int& y, int& z) { x = o % 3 - 1; y = (o / 3) % 3 - 1; z = o / 9 - 1; }
+  __device__ static int idx(int x, int y, int z) {
+    if (x < -1 || x > 1 || y < -1 || y > 1 || z < -1 || z > 1) return -1;
+    return (x + 1) + 3 * ((y + 1) + 3 * (z + 1));
+  }
+};
+template <>
+struct St<ST_DIAMOND2> {
+  static constexpr int N = 25, R = 2, C = 12;
+  __device__ static void off(int o, int& x, int& y, int& z) { x = c_dia[o][0]; y = c_dia[o][1]; z = c_dia[o][2]; }
+  __device__ static int idx(int x, int y, int z) {
+    if (x < -2 || x > 2 || y < -2 || y > 2 || z < -2 || z > 2) return -1;
+    return c_dia_idx[(x + 2) + 5 * ((y + 2) + 5 * (z + 2))];
+  }
+};
+template <>
+struct St<ST_BOX2> {
+  static constexpr int N = 125, R = 2, C = 62;
+  __device__ static void off(int o, int& x, int& y, int& z) { x = o % 5 - 2; y = (o / 5) % 5 - 2; z = o / 25 - 2; }
+  __device__ static int idx(int x, int y, int z) {
+    if (x < -2 || x > 2 || y < -2 || y > 2 || z < -2 || z > 2) return -1;
+    return (x + 2) + 5 * ((y + 2) + 5 * (z + 2));
+  }
+};
+
+struct Lat {
+  int Lx, Ly, Lz;
+  long long N;
+  __device__ void ijk(long long p, int& i, int& j, int& k) const {
+    i = (int)(p % Lx);
+    const long long r = p / Lx;
+    j = (int)(r % Ly);
+    k = (int)(r / Ly);
+  }
+  __device__ bool in(int i, int j, int k) const { return i >= 0 && i < Lx && j >= 0 && j < Ly && k >= 0 && k < Lz; }
+  __device__ long long id(int i, int j, int k) const { return i + (long long)Lx * (j + (long long)Ly * k); }
+};
+
+Lat lat_of(const StructOp& A) { return Lat{A.Lx, A.Ly, A.Lz, A.N}; }
+
+// ------------------------------------------------------------------ SpMV
+// y = A x (or r = b - A x) on a lattice level; thread per lattice point.
+template <int BS, int KIND, typename T>
+__device__ __forceinline__ void spmv_body(const Lat& L, const T* __restrict__ val, const T* __restrict__ x,
+                                          const T* __restrict__ b, T* __restrict__ y) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  int i, j, k;
+  L.ijk(p, i, j, k);
+  T acc[BS];
+#pragma unroll
+  for (int r = 0; r < BS; ++r) acc[r] = T(0);
+#pragma unroll 1
+  for (int o = 0; o < St<KIND>::N; ++o) {
+    int dx, dy, dz;
+    St<KIND>::off(o, dx, dy, dz);
+    if (!L.in(i + dx, j + dy, k + dz)) continue;
+    const long long q = p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
+    const T* v = val + (long long)o * BS * BS * L.N + p;
+#pragma unroll
+    for (int r = 0; r < BS; ++r)
+#pragma unroll
+      for (int s = 0; s < BS; ++s) acc[r] += v[(long long)(r * BS + s) * L.N] * x[BS * q + s];
+  }
+#pragma unroll
+  for (int r = 0; r < BS; ++r) y[BS * p + r] = b ? b[BS * p + r] - acc[r] : acc[r];
+}
+
+// Chebyshev step: r = b - A xin (r = b when xin is null), d = cd d + cr D^-1 r,
+// xout = xin + d.
+template <int BS, int KIND, typename T>
+__device__ __forceinline__ void cheb_body(const Lat& L, const T* __restrict__ val, const T* __restrict__ dinv,
+                                          const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+                                          T* __restrict__ d, T cd, T cr) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  T r[BS];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) r[q] = b[BS * p + q];
+  if (xin) {
+    int i, j, k;
+    L.ijk(p, i, j, k);
+#pragma unroll 1
+    for (int o = 0; o < St<KIND>::N; ++o) {
+      int dx, dy, dz;
+      St<KIND>::off(o, dx, dy, dz);
+      if (!L.in(i + dx, j + dy, k + dz)) continue;
+      const long long q = p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
+      const T* v = val + (long long)o * BS * BS * L.N + p;
+#pragma unroll
+      for (int a = 0; a < BS; ++a)
+#pragma unroll
+        for (int s = 0; s < BS; ++s) r[a] -= v[(long long)(a * BS + s) * L.N] * xin[BS * q + s];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    T z = T(0);
+#pragma unroll
+    for (int s = 0; s < BS; ++s) z += dinv[(long long)(a * BS + s) * L.N + p] * r[s];
+    const T dn = (cd != T(0)) ? cd * d[BS * p + a] + cr * z : cr * z;
+    d[BS * p + a] = dn;
+    xout[BS * p + a] = (xin ? xin[BS * p + a] : T(0)) + dn;
+  }
+}
+
+template <int BS, int KIND, typename T>
+__global__ void __launch_bounds__(256) k_spmv(Lat L, const T* __restrict__ val, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ y) {
+  spmv_body<BS, KIND, T>(L, val, x, b, y);
+}
+template <int BS, int KIND, typename T>
+__global__ void __launch_bounds__(256) k_cheb(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
+                                              const T* __restrict__ b, const T* __restrict__ xin, T* __restrict__ xout,
+                                              T* __restrict__ d, T cd, T cr) {
+  cheb_body<BS, KIND, T>(L, val, dinv, b, xin, xout, d, cd, cr);
+}
+// the finest displacement level (the dominant sweeps) under names of their own
+template <typename T>
+__global__ void __launch_bounds__(256) k_resid_u0(Lat L, const T* __restrict__ val, const T* __restrict__ x,
+                                                  const T* __restrict__ b, T* __restrict__ y) {
+  spmv_body<3, ST_BOX1, T>(L, val, x, b, y);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
+                                                 const T* __restrict__ b, const T* __restrict__ xin,
+                                                 T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+  cheb_body<3, ST_BOX1, T>(L, val, dinv, b, xin, xout, d, cd, cr);
+}
+
+// face level (ELL, 11 slots) versions
+template <typename T>
+__global__ void k_spmv_ell(long long n, const int* __restrict__ col, const T* __restrict__ val,
+                           const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  T a = T(0);
+#pragma unroll
+  for (int q = 0; q < 11; ++q) a += val[q * n + f] * x[col[q * n + f]];
+  y[f] = b ? b[f] - a : a;
+}
+
+template <typename T>
+__global__ void k_cheb_ell(long long n, const int* __restrict__ col, const T* __restrict__ val,
+                           const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
+                           T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  T r = b[f];
+  if (xin) {
+#pragma unroll
+    for (int q = 0; q < 11; ++q) r -= val[q * n + f] * xin[col[q * n + f]];
+  }
+  const T dn = (cd != T(0)) ? cd * d[f] + cr * dinv[f] * r : cr * dinv[f] * r;
+  d[f] = dn;
+  xout[f] = (xin ? xin[f] : T(0)) + dn;
+}
+
+// restriction b_c = P^T r (gather over the support box of each coarse point)
+template <int BS, typename T>
+__global__ void k_restrict(Lat F, Lat Cc, int R, const T* __restrict__ P, const T* __restrict__ r,
+                           T* __restrict__ bc) {
+  const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= Cc.N) return;
+  int I, Jj, K;
+  Cc.ijk(J, I, Jj, K);
+  const int ns = p_slots(R);
+  T acc[BS];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) acc[q] = T(0);
+  for (int c = 3 * K - R; c <= 3 * K + 2 + R; ++c) {
+    if (c < 0 || c >= F.Lz) continue;
+    const int sz = K - p_lo(c, R);
+    if (sz < 0 || sz >= ns) continue;
+    for (int b = 3 * Jj - R; b <= 3 * Jj + 2 + R; ++b) {
+      if (b < 0 || b >= F.Ly) continue;
+      const int sy = Jj - p_lo(b, R);
+      if (sy < 0 || sy >= ns) continue;
+      for (int a = 3 * I - R; a <= 3 * I + 2 + R; ++a) {
+        if (a < 0 || a >= F.Lx) continue;
+        const int sx = I - p_lo(a, R);
+        if (sx < 0 || sx >= ns) continue;
+        const long long p = F.id(a, b, c);
+        const int s = sx + ns * (sy + ns * sz);
+        const T* pv = P + (long long)s * BS * BS * F.N + p;
+#pragma unroll
+        for (int q = 0; q < BS; ++q)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) acc[q] += pv[(long long)(t * BS + q) * F.N] * r[BS * p + t];
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < BS; ++q) bc[BS * J + q] = acc[q];
+}
+
+// prolongation x += P x_c
+template <int BS, typename T>
+__global__ void k_prolong(Lat F, Lat Cc, int R, const T* __restrict__ P, const T* __restrict__ xc,
+                          T* __restrict__ x) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= F.N) return;
+  int a, b, c;
+  F.ijk(p, a, b, c);
+  const int ns = p_slots(R);
+  const int lx = p_lo(a, R), ly = p_lo(b, R), lz = p_lo(c, R);
+  T acc[BS];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) acc[q] = T(0);
+  for (int sz = 0; sz < ns; ++sz)
+    for (int sy = 0; sy < ns; ++sy)
+      for (int sx = 0; sx < ns; ++sx) {
+        const int I = lx + sx, J = ly + sy, K = lz + sz;
+        if (!Cc.in(I, J, K)) continue;
+        const long long Jc = Cc.id(I, J, K);
+        const int s = sx + ns * (sy + ns * sz);
+        const T* pv = P + (long long)s * BS * BS * F.N + p;
+#pragma unroll
+        for (int q = 0; q < BS; ++q)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) acc[q] += pv[(long long)(q * BS + t) * F.N] * xc[BS * Jc + t];
+      }
+#pragma unroll
+  for (int q = 0; q < BS; ++q) x[BS * p + q] += acc[q];
+}
+
+// faces -> cells transfer of the interface-pressure hierarchy
+struct FaceTopo {
+  int nx, ny, nz;
+  long long nT, nF, nFx, nFy;
+};
+
+__device__ __forceinline__ long long ft_cell_face(const FaceTopo& d, int i, int j, int k, int lf) {
+  switch (lf) {
+    case 0: return i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    case 1: return (i + 1) + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    case 2: return d.nFx + i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    case 3: return d.nFx + i + (long long)d.nx * ((j + 1) + (long long)(d.ny + 1) * k);
+    case 4: return d.nFx + d.nFy + i + (long long)d.nx * (j + (long long)d.ny * k);
+    default: return d.nFx + d.nFy + i + (long long)d.nx * (j + (long long)d.ny * (k + 1));
+  }
+}
+
+// face -> up to two cells as lattice coordinates (valid flags)
+__device__ __forceinline__ int ft_face_cells(const FaceTopo& d, long long f, int c[2][3]) {
+  int i, j, k, ax;
+  if (f < d.nFx) {
+    ax = 0; i = (int)(f % (d.nx + 1)); long long r = f / (d.nx + 1); j = (int)(r % d.ny); k = (int)(r / d.ny);
+  } else if (f < d.nFx + d.nFy) {
+    long long g = f - d.nFx;
+    ax = 1; i = (int)(g % d.nx); long long r = g / d.nx; j = (int)(r % (d.ny + 1)); k = (int)(r / (d.ny + 1));
+  } else {
+    long long g = f - d.nFx - d.nFy;
+    ax = 2; i = (int)(g % d.nx); long long r = g / d.nx; j = (int)(r % d.ny); k = (int)(r / d.ny);
+  }
+  const int lim[3] = {d.nx, d.ny, d.nz};
+  int cnt = 0;
+  int base[3] = {i, j, k};
+  base[ax] -= 1;
+  if (base[ax] >= 0) { c[cnt][0] = base[0]; c[cnt][1] = base[1]; c[cnt][2] = base[2]; ++cnt; }
+  base[ax] += 1;
+  if (base[ax] < lim[ax]) { c[cnt][0] = base[0]; c[cnt][1] = base[1]; c[cnt][2] = base[2]; ++cnt; }
+  return cnt;
+}
+
+template <typename T>
+__global__ void k_restrict_faces(FaceTopo d, const T* __restrict__ pw, const T* __restrict__ r, T* __restrict__ bc) {
+  const long long Tc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (Tc >= d.nT) return;
+  const int i = (int)(Tc % d.nx), j = (int)((Tc / d.nx) % d.ny), k = (int)(Tc / ((long long)d.nx * d.ny));
+  T s = T(0);
+  for (int lf = 0; lf < 6; ++lf) {
+    const long long f = ft_cell_face(d, i, j, k, lf);
+    s += pw[f] * r[f];
+  }
+  bc[Tc] = s;
+}
+
+template <typename T>
+__global__ void k_prolong_faces(FaceTopo d, const T* __restrict__ pw, const T* __restrict__ xc, T* __restrict__ x) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nF) return;
+  int c[2][3];
+  const int cnt = ft_face_cells(d, f, c);
+  T s = T(0);
+  for (int q = 0; q < cnt; ++q) s += xc[c[q][0] + (long long)d.nx * (c[q][1] + (long long)d.ny * c[q][2])];
+  x[f] += pw[f] * s;
+}
+
+// dense coarsest solve y = Ainv b (warp per row)
+template <typename T>
+__global__ void k_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ y) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  T s = T(0);
+  for (int c = lane; c < n; c += 32) s += Ainv[(long long)row * n + c] * b[c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+// ------------------------------------------------------------------ setup
+template <int BS, int KIND>
+__global__ void k_dinv(Lat L, const double* __restrict__ val, double* __restrict__ dinv) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const double* v = val + (long long)St<KIND>::C * BS * BS * L.N + p;
+  if (BS == 1) {
+    dinv[p] = 1.0 / v[0];
+  } else {
+    double a[9];
+    for (int q = 0; q < 9; ++q) a[q] = v[(long long)q * L.N];
+    const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    const double id = 1.0 / det;
+    double inv[9];
+    inv[0] = c00 * id; inv[1] = (a[2] * a[7] - a[1] * a[8]) * id; inv[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+    inv[3] = c01 * id; inv[4] = (a[0] * a[8] - a[2] * a[6]) * id; inv[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+    inv[6] = c02 * id; inv[7] = (a[1] * a[6] - a[0] * a[7]) * id; inv[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+    for (int q = 0; q < 9; ++q) dinv[(long long)q * L.N + p] = inv[q];
+  }
+}
+
+__global__ void k_dinv_ell(long long n, const double* __restrict__ val, double* __restrict__ dinv) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < n) dinv[f] = 1.0 / val[f];
+}
+
+// y = D^-1 x (block), x and y of length BS*N
+template <int BS>
+__global__ void k_apply_dinv(long long N, const double* __restrict__ dinv, const double* __restrict__ x,
+                             double* __restrict__ y) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  for (int a = 0; a < BS; ++a) {
+    double s = 0.0;
+    for (int t = 0; t < BS; ++t) s += dinv[(long long)(a * BS + t) * N + p] * x[BS * p + t];
+    y[BS * p + a] = s;
+  }
+}
+
+__global__ void k_power_start(long long n, double* __restrict__ v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = 1.0 + (double)((7919LL * i) % 97) / 97.0;
+}
+
+__global__ void k_scale_by(long long n, double s, double* __restrict__ v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= s;
+}
+
+// Smoothed prolongator: P[a, J] = [a in J] diag(active_a) - omega D_a^-1 sum_{b in J, b ~ a} A_ab diag(active_b)
+template <int BS, int KIND>
+__global__ void k_build_P(Lat F, Lat Cc, const double* __restrict__ val, const double* __restrict__ dinv,
+                          const unsigned char* __restrict__ active, double omega, double* __restrict__ P) {
+  const int R = St<KIND>::R;
+  const int ns = p_slots(R);
+  const int nslot = ns * ns * ns;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= F.N * nslot) return;
+  const int s = (int)(tid / F.N);
+  const long long p = tid - (long long)s * F.N;
+  int a, b, c;
+  F.ijk(p, a, b, c);
+  const int sx = s % ns, sy = (s / ns) % ns, sz = s / (ns * ns);
+  const int I = p_lo(a, R) + sx, J = p_lo(b, R) + sy, K = p_lo(c, R) + sz;
+  double out[BS * BS];
+  for (int q = 0; q < BS * BS; ++q) out[q] = 0.0;
+  if (Cc.in(I, J, K)) {
+    double ap[BS * BS];
+    for (int q = 0; q < BS * BS; ++q) ap[q] = 0.0;
+    for (int o = 0; o < St<KIND>::N; ++o) {
+      int dx, dy, dz;
+      St<KIND>::off(o, dx, dy, dz);
+      const int na = a + dx, nb = b + dy, nc = c + dz;
+      if (!F.in(na, nb, nc)) continue;
+      if (na / 3 != I || nb / 3 != J || nc / 3 != K) continue;
+      const long long q = F.id(na, nb, nc);
+      const double* v = val + (long long)o * BS * BS * F.N + p;
+      for (int r = 0; r < BS; ++r)
+        for (int t = 0; t < BS; ++t) ap[r * BS + t] += v[(long long)(r * BS + t) * F.N] * (active[BS * q + t] ? 1.0 : 0.0);
+    }
+    for (int r = 0; r < BS; ++r)
+      for (int t = 0; t < BS; ++t) {
+        double z = 0.0;
+        for (int u = 0; u < BS; ++u) z += dinv[(long long)(r * BS + u) * F.N + p] * ap[u * BS + t];
+        out[r * BS + t] = -omega * z;
+      }
+    if (a / 3 == I && b / 3 == J && c / 3 == K)
+      for (int r = 0; r < BS; ++r) out[r * BS + r] += active[BS * p + r] ? 1.0 : 0.0;
+  }
+  for (int q = 0; q < BS * BS; ++q) P[((long long)s * BS * BS + q) * F.N + p] = out[q];
+}
+
+template <int BS>
+__global__ void k_active_coarse(Lat F, Lat Cc, const unsigned char* __restrict__ af, unsigned char* __restrict__ ac) {
+  const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (J >= Cc.N) return;
+  int I, Jj, K;
+  Cc.ijk(J, I, Jj, K);
+  unsigned char m[BS];
+  for (int q = 0; q < BS; ++q) m[q] = 0;
+  for (int c = 3 * K; c < 3 * K + 3 && c < F.Lz; ++c)
+    for (int b = 3 * Jj; b < 3 * Jj + 3 && b < F.Ly; ++b)
+      for (int a = 3 * I; a < 3 * I + 3 && a < F.Lx; ++a) {
+        const long long p = F.id(a, b, c);
+        for (int q = 0; q < BS; ++q) m[q] |= af[BS * p + q];
+      }
+  for (int q = 0; q < BS; ++q) ac[BS * J + q] = m[q] ? 1 : 0;
+}
+
+// Q[a, J] = sum_o A[a, a+o] P[a+o, J]   (fine point a, coarse J in its Q range)
+template <int BS, int KIND>
+__global__ void k_build_Q(Lat F, Lat Cc, const double* __restrict__ val, const double* __restrict__ P,
+                          double* __restrict__ Q) {
+  const int R = St<KIND>::R;
+  const int ns = p_slots(R), nq = q_slots(R);
+  const int nqs = nq * nq * nq;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= F.N * nqs) return;
+  const int s = (int)(tid / F.N);
+  const long long p = tid - (long long)s * F.N;
+  int a, b, c;
+  F.ijk(p, a, b, c);
+  const int I = q_lo(a, R) + s % nq, J = q_lo(b, R) + (s / nq) % nq, K = q_lo(c, R) + s / (nq * nq);
+  double out[BS * BS];
+  for (int q = 0; q < BS * BS; ++q) out[q] = 0.0;
+  if (Cc.in(I, J, K)) {
+    for (int o = 0; o < St<KIND>::N; ++o) {
+      int dx, dy, dz;
+      St<KIND>::off(o, dx, dy, dz);
+      const int na = a + dx, nb = b + dy, nc = c + dz;
+      if (!F.in(na, nb, nc)) continue;
+      const int px = I - p_lo(na, R), py = J - p_lo(nb, R), pz = K - p_lo(nc, R);
+      if (px < 0 || px >= ns || py < 0 || py >= ns || pz < 0 || pz >= ns) continue;
+      const long long q = F.id(na, nb, nc);
+      const int ps = px + ns * (py + ns * pz);
+      const double* v = val + (long long)o * BS * BS * F.N + p;
+      const double* pv = P + (long long)ps * BS * BS * F.N + q;
+      for (int r = 0; r < BS; ++r)
+        for (int t = 0; t < BS; ++t) {
+          double z = 0.0;
+          for (int u = 0; u < BS; ++u) z += v[(long long)(r * BS + u) * F.N] * pv[(long long)(u * BS + t) * F.N];
+          out[r * BS + t] += z;
+        }
+    }
+  }
+  for (int q = 0; q < BS * BS; ++q) Q[((long long)s * BS * BS + q) * F.N + p] = out[q];
+}
+
+// A_c[J, J+oc] = sum_{a in box(J)} P[a, J]^T Q[a, J+oc]
+template <int BS, int CKIND>
+__global__ void k_rap(Lat F, Lat Cc, int R, const double* __restrict__ P, const double* __restrict__ Q,
+                      const unsigned char* __restrict__ ac, double* __restrict__ Ac) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= Cc.N * St<CKIND>::N) return;
+  const int oc = (int)(tid / Cc.N);
+  const long long J = tid - (long long)oc * Cc.N;
+  int I, Jj, K;
+  Cc.ijk(J, I, Jj, K);
+  int ox, oy, oz;
+  St<CKIND>::off(oc, ox, oy, oz);
+  const int I2 = I + ox, J2 = Jj + oy, K2 = K + oz;
+  double out[BS * BS];
+  for (int q = 0; q < BS * BS; ++q) out[q] = 0.0;
+  if (Cc.in(I2, J2, K2)) {
+    const int ns = p_slots(R), nq = q_slots(R);
+    for (int c = 3 * K - R; c <= 3 * K + 2 + R; ++c) {
+      if (c < 0 || c >= F.Lz) continue;
+      const int pz = K - p_lo(c, R), qz = K2 - q_lo(c, R);
+      if (pz < 0 || pz >= ns || qz < 0 || qz >= nq) continue;
+      for (int b = 3 * Jj - R; b <= 3 * Jj + 2 + R; ++b) {
+        if (b < 0 || b >= F.Ly) continue;
+        const int py = Jj - p_lo(b, R), qy = J2 - q_lo(b, R);
+        if (py < 0 || py >= ns || qy < 0 || qy >= nq) continue;
+        for (int a = 3 * I - R; a <= 3 * I + 2 + R; ++a) {
+          if (a < 0 || a >= F.Lx) continue;
+          const int px = I - p_lo(a, R), qx = I2 - q_lo(a, R);
+          if (px < 0 || px >= ns || qx < 0 || qx >= nq) continue;
+          const long long p = F.id(a, b, c);
+          const double* pv = P + (long long)(px + ns * (py + ns * pz)) * BS * BS * F.N + p;
+          const double* qv = Q + (long long)(qx + nq * (qy + nq * qz)) * BS * BS * F.N + p;
+          for (int r = 0; r < BS; ++r)
+            for (int t = 0; t < BS; ++t) {
+              double z = 0.0;
+              for (int u = 0; u < BS; ++u) z += pv[(long long)(u * BS + r) * F.N] * qv[(long long)(u * BS + t) * F.N];
+              out[r * BS + t] += z;
+            }
+        }
+      }
+    }
+  }
+  if (ox == 0 && oy == 0 && oz == 0)
+    for (int r = 0; r < BS; ++r)
+      if (!ac[BS * J + r]) out[r * BS + r] = 1.0;
+  for (int q = 0; q < BS * BS; ++q) Ac[((long long)oc * BS * BS + q) * Cc.N + J] = out[q];
+}
+
+// Galerkin faces -> cells: A_1[T, T'] = sum_{f in T, g} pw_f C_fg pw_g [T' adjacent to g]
+__global__ void k_rap_faces(FaceTopo d, const int* __restrict__ col, const double* __restrict__ C,
+                            const double* __restrict__ pw, double* __restrict__ A1, unsigned char* __restrict__ act) {
+  const long long Tc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (Tc >= d.nT) return;
+  const int i = (int)(Tc % d.nx), j = (int)((Tc / d.nx) % d.ny), k = (int)(Tc / ((long long)d.nx * d.ny));
+  double acc[25];
+  for (int q = 0; q < 25; ++q) acc[q] = 0.0;
+  bool any = false;
+  for (int lf = 0; lf < 6; ++lf) {
+    const long long f = ft_cell_face(d, i, j, k, lf);
+    const double wf = pw[f];
+    if (wf == 0.0) continue;
+    any = true;
+    for (int q = 0; q < 11; ++q) {
+      const long long g = col[q * d.nF + f];
+      const double v = C[q * d.nF + f];
+      const double wg = pw[g];
+      if (v == 0.0 || wg == 0.0) continue;
+      int cc[2][3];
+      const int cnt = ft_face_cells(d, g, cc);
+      for (int e = 0; e < cnt; ++e) {
+        const int o = St<ST_DIAMOND2>::idx(cc[e][0] - i, cc[e][1] - j, cc[e][2] - k);
+        if (o >= 0) acc[o] += wf * v * wg;
+      }
+    }
+  }
+  act[Tc] = any ? 1 : 0;
+  if (!any) acc[12] = 1.0;
+  for (int q = 0; q < 25; ++q) A1[(long long)q * d.nT + Tc] = acc[q];
+}
+
+// ------------------------------------------------------------------ host helpers
+template <class F>
+void dispatch_kind(int kind, F&& f) {
+  if (kind == ST_BOX1) f(std::integral_constant<int, ST_BOX1>{});
+  else if (kind == ST_DIAMOND2) f(std::integral_constant<int, ST_DIAMOND2>{});
+  else f(std::integral_constant<int, ST_BOX2>{});
+}
+
+template <class F>
+void dispatch_bs(int bs, F&& f) {
+  if (bs == 3) f(std::integral_constant<int, 3>{});
+  else f(std::integral_constant<int, 1>{});
+}
+
+FaceTopo face_topo(const Ctx& c) { return FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy}; }
+
+void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
+  if (L.faces) {
+    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, x, b, y);
+  } else {
+    const Lat lat = lat_of(L.A);
+    dispatch_bs(L.bs, [&](auto BS) {
+      dispatch_kind(L.A.kind, [&](auto K) {
+        k_spmv<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, y);
+      });
+    });
+  }
+  MHFP_LAUNCH_CHECK();
+}
+
+void alloc_work(Ctx& c, Level& L) {
+  L.x = dalloc_n<double>(c, L.n);
+  L.b = dalloc_n<double>(c, L.n);
+  L.r = dalloc_n<double>(c, L.n);
+  L.d = dalloc_n<double>(c, L.n);
+  L.y = dalloc_n<double>(c, L.n);
+}
+
+// rho(D^-1 A) by power iteration from the fixed start vector
+double spectral_radius(Ctx& c, Level& L) {
+  const long long n = L.n;
+  double* v = L.x;
+  double* w = L.y;
+  k_power_start<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v);
+  MHFP_LAUNCH_CHECK();
+  double nv = device_norm2(c, v, n);
+  k_scale_by<<<grid_for(n, 256), 256, 0, c.stream>>>(n, 1.0 / nv, v);
+  MHFP_LAUNCH_CHECK();
+  double rho = 0.0;
+  for (int it = 0; it < c.opt.power_iters; ++it) {
+    level_spmv(c, L, v, nullptr, L.r);
+    if (L.bs == 3)
+      k_apply_dinv<3><<<grid_for(L.npts, 256), 256, 0, c.stream>>>(L.npts, L.dinv, L.r, w);
+    else
+      k_apply_dinv<1><<<grid_for(L.npts, 256), 256, 0, c.stream>>>(L.npts, L.dinv, L.r, w);
+    MHFP_LAUNCH_CHECK();
+    rho = device_norm2(c, w, n);
+    k_scale_by<<<grid_for(n, 256), 256, 0, c.stream>>>(n, 1.0 / rho, w);
+    MHFP_LAUNCH_CHECK();
+    std::swap(v, w);
+  }
+  return rho;
+}
+
+// Gauss-Jordan inverse with partial pivoting (host, FP64), row-major
+void invert_dense(std::vector<double>& A, int n) {
+  std::vector<double> I(n * (size_t)n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
+    if (A[(size_t)piv * n + col] == 0.0) throw Error{MHFP_ERR_ARG, "singular coarsest multigrid level"};
+    if (piv != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)piv * n + k], A[(size_t)col * n + k]);
+        std::swap(I[(size_t)piv * n + k], I[(size_t)col * n + k]);
+      }
+    const double inv = 1.0 / A[(size_t)col * n + col];
+    for (int k = 0; k < n; ++k) { A[(size_t)col * n + k] *= inv; I[(size_t)col * n + k] *= inv; }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = A[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)r * n + k] -= f * A[(size_t)col * n + k];
+        I[(size_t)r * n + k] -= f * I[(size_t)col * n + k];
+      }
+    }
+  }
+  A.swap(I);
+}
+
+void make_dense_coarse(Ctx& c, Level& L) {
+  const int n = (int)L.n;
+  std::vector<double> A((size_t)n * n, 0.0);
+  if (L.faces) {
+    std::vector<int> col(11 * (size_t)n);
+    std::vector<double> val(11 * (size_t)n);
+    MHFP_CUDA(cudaMemcpyAsync(col.data(), c.ell_col, col.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    MHFP_CUDA(cudaMemcpyAsync(val.data(), c.Cpi, val.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    for (int f = 0; f < n; ++f)
+      for (int q = 0; q < 11; ++q) A[(size_t)f * n + col[(size_t)q * n + f]] += val[(size_t)q * n + f];
+  } else {
+    const StructOp& S = L.A;
+    const int bs = S.bs, no = S.noff();
+    std::vector<double> val((size_t)no * bs * bs * S.N);
+    MHFP_CUDA(cudaMemcpyAsync(val.data(), S.val, val.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    for (long long p = 0; p < S.N; ++p) {
+      const int i = (int)(p % S.Lx), j = (int)((p / S.Lx) % S.Ly), k = (int)(p / ((long long)S.Lx * S.Ly));
+      for (int o = 0; o < no; ++o) {
+        int dx, dy, dz;
+        stencil_offset(S.kind, o, dx, dy, dz);
+        const int a = i + dx, b = j + dy, cc = k + dz;
+        if (a < 0 || a >= S.Lx || b < 0 || b >= S.Ly || cc < 0 || cc >= S.Lz) continue;
+        const long long q = a + (long long)S.Lx * (b + (long long)S.Ly * cc);
+        for (int r = 0; r < bs; ++r)
+          for (int t = 0; t < bs; ++t)
+            A[(size_t)(bs * p + r) * n + bs * q + t] += val[((size_t)o * bs * bs + r * bs + t) * S.N + p];
+      }
+    }
+  }
+  invert_dense(A, n);
+  L.dense_inv = dalloc_n<double>(c, (size_t)n * n);
+  MHFP_CUDA(cudaMemcpyAsync(L.dense_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+void finish_level(Ctx& c, Level& L) {
+  L.dinv = dalloc_n<double>(c, (size_t)L.bs * L.bs * L.npts);
+  if (L.faces) {
+    k_dinv_ell<<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.Cpi, L.dinv);
+  } else {
+    const Lat lat = lat_of(L.A);
+    dispatch_bs(L.bs, [&](auto BS) {
+      dispatch_kind(L.A.kind, [&](auto K) {
+        k_dinv<BS.value, K.value><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, L.dinv);
+      });
+    });
+  }
+  MHFP_LAUNCH_CHECK();
+  L.lmax = 1.1 * spectral_radius(c, L);
+}
+
+// one smoothed-aggregation coarsening step of a lattice level
+Level coarsen(Ctx& c, Level& L) {
+  const StructOp& A = L.A;
+  const int R = stencil_radius(A.kind);
+  L.R = R;
+  Level Cl;
+  Cl.bs = L.bs;
+  Cl.A.Lx = (A.Lx + 2) / 3; Cl.A.Ly = (A.Ly + 2) / 3; Cl.A.Lz = (A.Lz + 2) / 3;
+  Cl.A.N = (long long)Cl.A.Lx * Cl.A.Ly * Cl.A.Lz;
+  Cl.A.bs = L.bs;
+  Cl.A.kind = (R == 1) ? ST_BOX1 : ST_BOX2;
+  Cl.npts = Cl.A.N;
+  Cl.n = Cl.A.N * L.bs;
+  Cl.R = stencil_radius(Cl.A.kind);
+  const Lat F = lat_of(A), Cc = lat_of(Cl.A);
+  const int ns = p_slots(R), nq = q_slots(R);
+  const int bs2 = L.bs * L.bs;
+  L.P = dalloc_n<double>(c, (size_t)ns * ns * ns * bs2 * F.N);
+  Cl.active = dalloc_n<unsigned char>(c, Cl.n);
+  Cl.A.val = dalloc_n<double>(c, (size_t)Cl.A.noff() * bs2 * Cc.N);
+  double* Q = nullptr;
+  MHFP_CUDA(cudaMalloc(&Q, (size_t)nq * nq * nq * bs2 * F.N * sizeof(double)));
+  const double omega = 4.0 / (3.0 * L.lmax);
+  try {
+    dispatch_bs(L.bs, [&](auto BS) {
+      dispatch_kind(A.kind, [&](auto K) {
+        k_build_P<BS.value, K.value><<<grid_for(F.N * ns * ns * ns, 256), 256, 0, c.stream>>>(F, Cc, A.val, L.dinv,
+                                                                                             L.active, omega, L.P);
+        MHFP_LAUNCH_CHECK();
+        k_active_coarse<BS.value><<<grid_for(Cc.N, 256), 256, 0, c.stream>>>(F, Cc, L.active, Cl.active);
+        MHFP_LAUNCH_CHECK();
+        k_build_Q<BS.value, K.value><<<grid_for(F.N * nq * nq * nq, 256), 256, 0, c.stream>>>(F, Cc, A.val, L.P, Q);
+        MHFP_LAUNCH_CHECK();
+      });
+      if (Cl.A.kind == ST_BOX1)
+        k_rap<BS.value, ST_BOX1><<<grid_for(Cc.N * 27, 128), 128, 0, c.stream>>>(F, Cc, R, L.P, Q, Cl.active, Cl.A.val);
+      else
+        k_rap<BS.value, ST_BOX2><<<grid_for(Cc.N * 125, 128), 128, 0, c.stream>>>(F, Cc, R, L.P, Q, Cl.active, Cl.A.val);
+      MHFP_LAUNCH_CHECK();
+    });
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  } catch (...) {
+    cudaFree(Q);
+    throw;
+  }
+  MHFP_CUDA(cudaFree(Q));
+  return Cl;
+}
+
+void build_u(Ctx& c) {
+  c.hu.clear();
+  Level L0;
+  L0.bs = 3;
+  L0.A = c.Auu;
+  L0.npts = c.nN;
+  L0.n = c.nU;
+  L0.R = 1;
+  L0.active = dalloc_n<unsigned char>(c, c.nU);
+  {
+    std::vector<unsigned char> fix(c.nN), act(c.nU);
+    MHFP_CUDA(cudaMemcpyAsync(fix.data(), c.node_fix, c.nN, cudaMemcpyDeviceToHost, c.stream));
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    for (long long n = 0; n < c.nN; ++n)
+      for (int q = 0; q < 3; ++q) act[3 * n + q] = ((fix[n] >> q) & 1) ? 0 : 1;
+    MHFP_CUDA(cudaMemcpyAsync(L0.active, act.data(), c.nU, cudaMemcpyHostToDevice, c.stream));
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  c.hu.push_back(L0);
+  while (c.hu.back().npts > c.opt.coarse_max && c.hu.size() < 8) {
+    Level& L = c.hu.back();
+    alloc_work(c, L);
+    finish_level(c, L);
+    Level Cl = coarsen(c, L);
+    c.hu.push_back(Cl);
+  }
+  Level& last = c.hu.back();
+  alloc_work(c, last);
+  make_dense_coarse(c, last);
+}
+
+void build_pi(Ctx& c) {
+  c.hpi.clear();
+  Level L0;
+  L0.faces = true;
+  L0.bs = 1;
+  L0.npts = c.nF;
+  L0.n = c.nF;
+  c.hpi.push_back(L0);
+  if (c.nF <= c.opt.coarse_max) {
+    alloc_work(c, c.hpi.back());
+    make_dense_coarse(c, c.hpi.back());
+    return;
+  }
+  {
+    Level& F = c.hpi.back();
+    alloc_work(c, F);
+    finish_level(c, F);
+    Level L1;
+    L1.bs = 1;
+    L1.A.Lx = c.nx; L1.A.Ly = c.ny; L1.A.Lz = c.nz;
+    L1.A.N = c.nT; L1.A.bs = 1; L1.A.kind = ST_DIAMOND2;
+    L1.npts = c.nT; L1.n = c.nT; L1.R = 2;
+    L1.A.val = dalloc_n<double>(c, (size_t)25 * c.nT);
+    L1.active = dalloc_n<unsigned char>(c, c.nT);
+    k_rap_faces<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(face_topo(c), c.ell_col, c.Cpi, c.pw, L1.A.val, L1.active);
+    MHFP_LAUNCH_CHECK();
+    c.hpi.push_back(L1);
+  }
+  while (c.hpi.back().npts > c.opt.coarse_max && c.hpi.size() < 8) {
+    Level& L = c.hpi.back();
+    alloc_work(c, L);
+    finish_level(c, L);
+    Level Cl = coarsen(c, L);
+    c.hpi.push_back(Cl);
+  }
+  Level& last = c.hpi.back();
+  alloc_work(c, last);
+  make_dense_coarse(c, last);
+}
+
+// ------------------------------------------------------------------ V-cycle
+struct ChebCoef {
+  double theta, delta, sigma;
+};
+
+void smooth(Ctx& c, std::vector<Level>& H, int l, const double* b, double*& x, double* other, bool from_zero,
+            bool time_it) {
+  Level& L = H[l];
+  const double lmax = L.lmax, lmin = lmax / c.opt.cheb_ratio;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  // ping-pong so that the last step writes x (each step reads neighbours of
+  // its input, so it cannot update in place)
+  const double* xin = from_zero ? nullptr : x;
+  double* out = (from_zero && c.opt.cheb_degree % 2 == 1) ? x : other;
+  for (int s = 0; s < c.opt.cheb_degree; ++s) {
+    double cd = 0.0, cr = 1.0 / theta;
+    if (s > 0) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      cd = rn * rho;
+      cr = 2.0 * rn / delta;
+      rho = rn;
+    }
+    if (time_it && xin) timing_begin(c, 0);
+    if (L.faces) {
+      k_cheb_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, L.dinv, b, xin, out, L.d,
+                                                                  cd, cr);
+    } else if (time_it) {
+      const Lat lat = lat_of(L.A);
+      k_cheb_u0<double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, L.dinv, b, xin, out, L.d, cd, cr);
+    } else {
+      const Lat lat = lat_of(L.A);
+      dispatch_bs(L.bs, [&](auto BS) {
+        dispatch_kind(L.A.kind, [&](auto K) {
+          k_cheb<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, L.dinv, b, xin,
+                                                                                         out, L.d, cd, cr);
+        });
+      });
+    }
+    MHFP_LAUNCH_CHECK();
+    // algorithmic bytes of a Chebyshev sweep: 27 x 9 matrix values and the
+    // 3x3 inverse diagonal per node, b, x_in, x_out and d read/written
+    if (time_it && xin) timing_end(c, 0, (27.0 * 9 + 9) * 8 * L.npts + 5.0 * 8 * L.n);
+    // next step reads what this one wrote
+    xin = out;
+    out = (out == x) ? other : x;
+  }
+  // result is in xin
+  if (xin != x) {
+    MHFP_CUDA(cudaMemcpyAsync(x, xin, L.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  }
+}
+
+void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const double* b, double* x) {
+  Level& L = H[l];
+  if (L.dense_inv) {
+    const int n = (int)L.n;
+    k_dense_mv<double><<<grid_for(n, 8), 256, 0, c.stream>>>(n, L.dense_inv, b, x);
+    MHFP_LAUNCH_CHECK();
+    return;
+  }
+  const bool fine_u = (&H == &c.hu) && l == 0;
+  smooth(c, H, l, b, x, L.y, true, fine_u);
+  // residual
+  if (fine_u) {
+    const Lat lat = lat_of(L.A);
+    k_resid_u0<double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, L.r);
+    MHFP_LAUNCH_CHECK();
+  } else {
+    level_spmv(c, L, x, b, L.r);
+  }
+  Level& C = H[l + 1];
+  if (L.faces) {
+    k_restrict_faces<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(face_topo(c), c.pw, L.r, C.b);
+  } else {
+    const Lat F = lat_of(L.A), Cc = lat_of(C.A);
+    dispatch_bs(L.bs, [&](auto BS) {
+      k_restrict<BS.value, double><<<grid_for(Cc.N, 128), 128, 0, c.stream>>>(F, Cc, L.R, L.P, L.r, C.b);
+    });
+  }
+  MHFP_LAUNCH_CHECK();
+  vcycle_level(c, H, l + 1, C.b, C.x);
+  if (L.faces) {
+    k_prolong_faces<double><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(face_topo(c), c.pw, C.x, x);
+  } else {
+    const Lat F = lat_of(L.A), Cc = lat_of(C.A);
+    dispatch_bs(L.bs, [&](auto BS) {
+      k_prolong<BS.value, double><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, L.R, L.P, C.x, x);
+    });
+  }
+  MHFP_LAUNCH_CHECK();
+  smooth(c, H, l, b, x, L.y, false, fine_u);
+}
+
+}  // namespace
+
+void build_hierarchies(Ctx& c) {
+  build_u(c);
+  build_pi(c);
+}
+
+void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x) { vcycle_level(c, H, 0, b, x); }
+
+void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y) {
+  Level& L = H[l];
+  if (L.faces) {
+    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, x, nullptr, y);
+    MHFP_LAUNCH_CHECK();
+  } else {
+    level_spmv(c, L, x, nullptr, y);
+  }
+}
+
+}  // namespace mhfp

@@ -1,0 +1,339 @@
+// C ABI of libmhfp: argument validation, handle life cycle, dispatch.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace mhfp {
+
+long long g_launches = 0;
+
+void* dalloc(Ctx& c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{MHFP_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+  }
+  c.allocs.push_back(p);
+  return p;
+}
+
+void dfree_all(Ctx& c) {
+  for (void* p : c.allocs) cudaFree(p);
+  c.allocs.clear();
+}
+
+void timing_begin(Ctx& c, int cls) {
+  if (!c.timing.enabled) return;
+  auto& v = c.timing.ev_start[cls];
+  if (c.timing.used[cls] >= v.size()) {
+    cudaEvent_t a, b;
+    MHFP_CUDA(cudaEventCreate(&a));
+    MHFP_CUDA(cudaEventCreate(&b));
+    c.timing.ev_start[cls].push_back(a);
+    c.timing.ev_stop[cls].push_back(b);
+  }
+  MHFP_CUDA(cudaEventRecord(c.timing.ev_start[cls][c.timing.used[cls]], c.stream));
+}
+
+static void harvest(Ctx& c, int cls) {
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  for (size_t i = 0; i < c.timing.used[cls]; ++i) {
+    float ms = 0.f;
+    MHFP_CUDA(cudaEventElapsedTime(&ms, c.timing.ev_start[cls][i], c.timing.ev_stop[cls][i]));
+    c.timing.total_ms[cls] += ms;
+  }
+  c.timing.used[cls] = 0;
+}
+
+void timing_end(Ctx& c, int cls, double bytes) {
+  if (!c.timing.enabled) return;
+  MHFP_CUDA(cudaEventRecord(c.timing.ev_stop[cls][c.timing.used[cls]], c.stream));
+  c.timing.used[cls]++;
+  c.timing.launches[cls]++;
+  c.timing.bytes[cls] += bytes;
+  if (c.timing.used[cls] >= 4096) harvest(c, cls);
+}
+
+}  // namespace mhfp
+
+using mhfp::Ctx;
+using mhfp::Error;
+
+struct mhfp_ctx {
+  Ctx c;
+};
+
+namespace {
+
+template <class F>
+mhfp_status guarded(mhfp_handle h, F&& f) {
+  if (!h) return MHFP_ERR_ARG;
+  try {
+    MHFP_CUDA(cudaSetDevice(h->c.device));
+    f(h->c);
+    h->c.err.clear();
+    return MHFP_OK;
+  } catch (const Error& e) {
+    h->c.err = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    h->c.err = "host allocation failed";
+    return MHFP_ERR_OOM;
+  }
+}
+
+template <class T>
+T* upload(Ctx& c, const T* host, size_t n) {
+  T* d = mhfp::dalloc_n<T>(c, n);
+  MHFP_CUDA(cudaMemcpyAsync(d, host, n * sizeof(T), cudaMemcpyHostToDevice, c.stream));
+  return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mhfp_default_options(mhfp_options* o) {
+  if (!o) return;
+  o->restart = 50;
+  o->maxit = 1000;
+  o->cheb_degree = 2;
+  o->cheb_ratio = 10.0;
+  o->coarse_max = 125;
+  o->power_iters = 15;
+}
+
+const char* mhfp_status_string(mhfp_status s) {
+  switch (s) {
+    case MHFP_OK: return "ok";
+    case MHFP_ERR_ARG: return "invalid argument";
+    case MHFP_ERR_MESH: return "invalid mesh";
+    case MHFP_ERR_OOM: return "out of memory";
+    case MHFP_ERR_CUDA: return "CUDA error";
+    case MHFP_ERR_NOT_CONVERGED: return "not converged";
+    case MHFP_ERR_NONFINITE: return "non-finite value";
+    case MHFP_ERR_BREAKDOWN: return "Krylov breakdown";
+    case MHFP_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* mhfp_last_error(mhfp_handle h) { return h ? h->c.err.c_str() : "null handle"; }
+
+mhfp_status mhfp_create(const mhfp_mesh* mesh, const mhfp_materials* mat, double dt, const double traction[3],
+                        void* stream, mhfp_handle* out) {
+  if (!out) return MHFP_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || !mat || !mesh->coords || !mesh->node_fix || !mesh->face_bc) return MHFP_ERR_ARG;
+  if (!mat->E || !mat->nu || !mat->biot || !mat->Seps || !mat->mu || !mat->kappa) return MHFP_ERR_ARG;
+  if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return MHFP_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return MHFP_ERR_ARG;
+  const long long nx = mesh->nx, ny = mesh->ny, nz = mesh->nz;
+  const long long nT = nx * ny * nz;
+  if (nT > (1LL << 30)) return MHFP_ERR_ARG;
+  // host-side validation of the material fields
+  for (long long t = 0; t < nT; ++t) {
+    const double E = mat->E[t], nu = mat->nu[t], mu = mat->mu[t], S = mat->Seps[t], b = mat->biot[t];
+    if (!(E > 0.0) || !(nu > -1.0 && nu < 0.5) || !(mu > 0.0) || !(S >= 0.0) || !std::isfinite(b))
+      return MHFP_ERR_ARG;
+    for (int q = 0; q < 3; ++q)
+      if (!(mat->kappa[3 * t + q] > 0.0) || !std::isfinite(mat->kappa[3 * t + q])) return MHFP_ERR_ARG;
+  }
+  mhfp_ctx* h = new (std::nothrow) mhfp_ctx;
+  if (!h) return MHFP_ERR_OOM;
+  Ctx& c = h->c;
+  mhfp_default_options(&c.opt);
+  c.nx = mesh->nx; c.ny = mesh->ny; c.nz = mesh->nz;
+  c.nN = (nx + 1) * (ny + 1) * (nz + 1);
+  c.nT = nT;
+  c.nFx = (nx + 1) * ny * nz;
+  c.nFy = nx * (ny + 1) * nz;
+  c.nF = c.nFx + c.nFy + nx * ny * (nz + 1);
+  c.nU = 3 * c.nN;
+  c.n = c.nU + c.nT + c.nF;
+  c.dt = dt;
+  for (int q = 0; q < 3; ++q) c.trac[q] = traction ? traction[q] : 0.0;
+  c.stream = (cudaStream_t)stream;
+  try {
+    int dev = 0;
+    MHFP_CUDA(cudaGetDevice(&dev));
+    c.device = dev;
+    for (long long i = 0; i < 3 * c.nN; ++i)
+      if (!std::isfinite(mesh->coords[i])) throw Error{MHFP_ERR_ARG, "non-finite node coordinate"};
+    c.coords = upload(c, mesh->coords, 3 * c.nN);
+    c.node_fix = upload(c, mesh->node_fix, c.nN);
+    c.face_bc = upload(c, mesh->face_bc, c.nF);
+    c.E = upload(c, mat->E, nT);
+    c.nu = upload(c, mat->nu, nT);
+    c.biot = upload(c, mat->biot, nT);
+    c.Seps = upload(c, mat->Seps, nT);
+    c.mu = upload(c, mat->mu, nT);
+    c.kappa = upload(c, mat->kappa, 3 * nT);
+    c.d_flag = mhfp::dalloc_n<int>(c, 4);
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  } catch (const Error& e) {
+    mhfp::dfree_all(c);
+    delete h;
+    return e.status;
+  }
+  *out = h;
+  return MHFP_OK;
+}
+
+mhfp_status mhfp_assemble_condense(mhfp_handle h) {
+  return guarded(h, [](Ctx& c) {
+    if (c.assembled) throw Error{MHFP_ERR_STATE, "already assembled"};
+    mhfp::assemble_all(c);
+    c.assembled = true;
+  });
+}
+
+mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
+    if (c.prepared) throw Error{MHFP_ERR_STATE, "preconditioner already set up"};
+    if (opt) {
+      if (opt->restart < 1 || opt->restart > 200 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
+          !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1)
+        throw Error{MHFP_ERR_ARG, "invalid options"};
+      c.opt = *opt;
+    }
+    mhfp::build_preconditioner_blocks(c);
+    mhfp::build_hierarchies(c);
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    c.prepared = true;
+  });
+}
+
+mhfp_status mhfp_build_rhs(mhfp_handle h, const double* d_x_prev, double load_scale, double* d_rhs) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
+    if (!d_rhs || !std::isfinite(load_scale)) throw Error{MHFP_ERR_ARG, "bad rhs argument"};
+    mhfp::build_rhs(c, d_x_prev, load_scale, d_rhs);
+  });
+}
+
+mhfp_status mhfp_solve(mhfp_handle h, const double* d_rhs, double* d_x, double tol, mhfp_stats* stats) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (!d_rhs || !d_x || !(tol > 0.0) || !(tol < 1.0)) throw Error{MHFP_ERR_ARG, "bad solve argument"};
+    mhfp::fgmres_solve(c, d_rhs, d_x, tol, stats);
+  });
+}
+
+mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled || !c.prepared) throw Error{MHFP_ERR_STATE, "operator needs assemble + setup"};
+    if (!d_x || !d_y || d_x == d_y) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::apply_operator(c, d_x, d_y, nullptr, nullptr);
+  });
+}
+
+mhfp_status mhfp_apply_precond(mhfp_handle h, const double* d_v, double* d_z) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (!d_v || !d_z || d_v == d_z) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::apply_precond(c, d_v, d_z);
+  });
+}
+
+mhfp_status mhfp_vcycle(mhfp_handle h, int which, const double* d_b, double* d_x) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (which != 0 && which != 1) throw Error{MHFP_ERR_ARG, "which must be 0 or 1"};
+    if (!d_b || !d_x || d_b == d_x) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::vcycle(c, which == 0 ? c.hu : c.hpi, d_b, d_x);
+  });
+}
+
+mhfp_status mhfp_level_apply(mhfp_handle h, int which, int level, const double* d_x, double* d_y) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (which != 0 && which != 1) throw Error{MHFP_ERR_ARG, "which must be 0 or 1"};
+    auto& H = which == 0 ? c.hu : c.hpi;
+    if (level < 0 || level >= (int)H.size()) throw Error{MHFP_ERR_ARG, "level out of range"};
+    if (!d_x || !d_y || d_x == d_y) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::level_apply(c, H, level, d_x, d_y);
+  });
+}
+
+mhfp_status mhfp_hierarchy(mhfp_handle h, int which, mhfp_hierarchy_info* info) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if ((which != 0 && which != 1) || !info) throw Error{MHFP_ERR_ARG, "bad argument"};
+    auto& H = which == 0 ? c.hu : c.hpi;
+    std::memset(info, 0, sizeof(*info));
+    info->levels = (int)H.size();
+    for (size_t l = 0; l < H.size() && l < 8; ++l) {
+      info->points[l] = H[l].npts;
+      info->block[l] = H[l].bs;
+      info->lmax[l] = H[l].dense_inv ? 0.0 : H[l].lmax;
+    }
+  });
+}
+
+mhfp_status mhfp_get_scalings(mhfp_handle h, double* d_btilde, double* d_ds) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (d_btilde)
+      MHFP_CUDA(cudaMemcpyAsync(d_btilde, c.btilde, c.nT * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    if (d_ds) MHFP_CUDA(cudaMemcpyAsync(d_ds, c.ds, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  });
+}
+
+mhfp_status mhfp_sizes(mhfp_handle h, long long* n_u, long long* n_p, long long* n_pi) {
+  if (!h) return MHFP_ERR_ARG;
+  if (n_u) *n_u = h->c.nU;
+  if (n_p) *n_p = h->c.nT;
+  if (n_pi) *n_pi = h->c.nF;
+  return MHFP_OK;
+}
+
+mhfp_status mhfp_timing(mhfp_handle h, int enable) {
+  return guarded(h, [&](Ctx& c) {
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    for (int k = 0; k < 3; ++k) {
+      c.timing.used[k] = 0;
+      if (enable) {
+        c.timing.launches[k] = 0;
+        c.timing.total_ms[k] = 0.0;
+        c.timing.bytes[k] = 0.0;
+      }
+    }
+    c.timing.enabled = enable != 0;
+  });
+}
+
+mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launches, double* total_ms,
+                             double* bytes_per_launch) {
+  return guarded(h, [&](Ctx& c) {
+    if (kernel_class < 0 || kernel_class > 2) throw Error{MHFP_ERR_ARG, "kernel class out of range"};
+    mhfp::harvest(c, kernel_class);
+    if (launches) *launches = c.timing.launches[kernel_class];
+    if (total_ms) *total_ms = c.timing.total_ms[kernel_class];
+    if (bytes_per_launch)
+      *bytes_per_launch = c.timing.launches[kernel_class] ? c.timing.bytes[kernel_class] / c.timing.launches[kernel_class] : 0.0;
+  });
+}
+
+long long mhfp_launch_count(void) { return mhfp::g_launches; }
+
+void mhfp_destroy(mhfp_handle h) {
+  if (!h) return;
+  Ctx& c = h->c;
+  cudaSetDevice(c.device);
+  cudaStreamSynchronize(c.stream);
+  for (int k = 0; k < 3; ++k) {
+    for (auto e : c.timing.ev_start[k]) cudaEventDestroy(e);
+    for (auto e : c.timing.ev_stop[k]) cudaEventDestroy(e);
+  }
+  if (c.host_scal) cudaFreeHost(c.host_scal);
+  mhfp::dfree_all(c);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,778 @@
+// Element kernels, static condensation, stabilization, assembly, right-hand
+// side and the block operator apply of the hybridized Q1-RT0-P0 system.
+//
+// Appendix A (element matrices), Eq. (hmfeSys)/(A_33H) (condensation of the
+// broken RT0 fluxes), Eq. (J_def)/(stab_A) (macro-element pressure-jump
+// stabilization), Section 2.1 (backward-Euler right-hand side).
+#include "common.cuh"
+
+#include <cmath>
+
+namespace mhfp {
+
+namespace {
+
+constexpr double kGP = 0.57735026918962576451;  // 1/sqrt(3): 2-point Gauss-Legendre
+
+struct Dims {
+  int nx, ny, nz;
+  long long nN, nT, nF, nFx, nFy;
+};
+
+__device__ __forceinline__ long long node_id(const Dims& d, int i, int j, int k) {
+  return i + (long long)(d.nx + 1) * (j + (long long)(d.ny + 1) * k);
+}
+__device__ __forceinline__ long long cell_id(const Dims& d, int i, int j, int k) {
+  return i + (long long)d.nx * (j + (long long)d.ny * k);
+}
+__device__ __forceinline__ long long cell_face(const Dims& d, int i, int j, int k, int lf) {
+  switch (lf) {
+    case 0: return i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    case 1: return (i + 1) + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    case 2: return d.nFx + i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    case 3: return d.nFx + i + (long long)d.nx * ((j + 1) + (long long)(d.ny + 1) * k);
+    case 4: return d.nFx + d.nFy + i + (long long)d.nx * (j + (long long)d.ny * k);
+    default: return d.nFx + d.nFy + i + (long long)d.nx * (j + (long long)d.ny * (k + 1));
+  }
+}
+// face -> its (up to) two cells: slot 0 = cell on the - side (the face is its
+// local face 2*axis+1), slot 1 = cell on the + side (local face 2*axis).
+__device__ __forceinline__ void face_cells(const Dims& d, long long f, long long cell[2], int lf[2],
+                                           int ijk[2][3]) {
+  int i, j, k, ax;
+  if (f < d.nFx) {
+    ax = 0; i = (int)(f % (d.nx + 1)); long long r = f / (d.nx + 1); j = (int)(r % d.ny); k = (int)(r / d.ny);
+  } else if (f < d.nFx + d.nFy) {
+    long long g = f - d.nFx;
+    ax = 1; i = (int)(g % d.nx); long long r = g / d.nx; j = (int)(r % (d.ny + 1)); k = (int)(r / (d.ny + 1));
+  } else {
+    long long g = f - d.nFx - d.nFy;
+    ax = 2; i = (int)(g % d.nx); long long r = g / d.nx; j = (int)(r % d.ny); k = (int)(r / d.ny);
+  }
+  int c[3] = {i, j, k};
+  int lim[3] = {d.nx, d.ny, d.nz};
+  // minus side
+  int cm[3] = {c[0], c[1], c[2]};
+  cm[ax] -= 1;
+  if (cm[ax] >= 0) {
+    cell[0] = cell_id(d, cm[0], cm[1], cm[2]); lf[0] = 2 * ax + 1;
+    ijk[0][0] = cm[0]; ijk[0][1] = cm[1]; ijk[0][2] = cm[2];
+  } else {
+    cell[0] = -1; lf[0] = -1;
+  }
+  if (c[ax] < lim[ax]) {
+    cell[1] = cell_id(d, c[0], c[1], c[2]); lf[1] = 2 * ax;
+    ijk[1][0] = c[0]; ijk[1][1] = c[1]; ijk[1][2] = c[2];
+  } else {
+    cell[1] = -1; lf[1] = -1;
+  }
+}
+
+__device__ __forceinline__ void q1_ref_grad(int a, double xi, double eta, double zeta, double g[3]) {
+  const double sx = (a & 1) ? 1.0 : -1.0, sy = ((a >> 1) & 1) ? 1.0 : -1.0, sz = ((a >> 2) & 1) ? 1.0 : -1.0;
+  g[0] = 0.125 * sx * (1.0 + sy * eta) * (1.0 + sz * zeta);
+  g[1] = 0.125 * sy * (1.0 + sx * xi) * (1.0 + sz * zeta);
+  g[2] = 0.125 * sz * (1.0 + sx * xi) * (1.0 + sy * eta);
+}
+
+__device__ __forceinline__ void load_cell_coords(const Dims& d, const double* __restrict__ coords, long long T,
+                                                 double X[8][3]) {
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    X[a][0] = coords[3 * n]; X[a][1] = coords[3 * n + 1]; X[a][2] = coords[3 * n + 2];
+  }
+}
+
+// ---------------------------------------------------------------- K1: Q1
+// One warp per cell.  Appendix A: [A_uu]_ab = (grad^s eta_a, C_dr grad^s
+// eta_b)_T; for isotropic C_dr the 3x3 block is
+//   K_ab(i,j) = int lam d_i N_a d_j N_b + G d_j N_a d_i N_b + G delta_ij grad N_a . grad N_b,
+// [A_up]_(a,c) = -b int d_c N_a, |T| = int 1.  2x2x2 Gauss.
+constexpr int Q1_WARPS = 4;
+__global__ void __launch_bounds__(32 * Q1_WARPS) k_q1(Dims d, const double* __restrict__ coords,
+                                                      const double* __restrict__ E, const double* __restrict__ nu,
+                                                      const double* __restrict__ biot, double* __restrict__ Ke,
+                                                      double* __restrict__ Aup, double* __restrict__ vol,
+                                                      int* __restrict__ flag) {
+  __shared__ double sG[Q1_WARPS][8][8][3];
+  __shared__ double sW[Q1_WARPS][8];
+  __shared__ double sX[Q1_WARPS][8][3];
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long T = (long long)blockIdx.x * Q1_WARPS + wp;
+  if (T >= d.nT) return;  // whole warp leaves together; only __syncwarp below
+  const int ci = (int)(T % d.nx), cj = (int)((T / d.nx) % d.ny), ck = (int)(T / ((long long)d.nx * d.ny));
+  if (lane < 24) {
+    const int a = lane / 3, c = lane % 3;
+    sX[wp][a][c] = coords[3 * node_id(d, ci + (a & 1), cj + ((a >> 1) & 1), ck + ((a >> 2) & 1)) + c];
+  }
+  __syncwarp();
+  if (lane < 8) {
+    const double xi = (lane & 1) ? kGP : -kGP, eta = ((lane >> 1) & 1) ? kGP : -kGP,
+                 zeta = ((lane >> 2) & 1) ? kGP : -kGP;
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double gr[8][3];
+    for (int a = 0; a < 8; ++a) {
+      q1_ref_grad(a, xi, eta, zeta, gr[a]);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] += sX[wp][a][i] * gr[a][j];
+    }
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(det > 0.0)) atomicOr(flag, 1);
+    const double id = 1.0 / det;
+    double Ji[3][3];
+    Ji[0][0] = c00 * id; Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id; Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][0] = c01 * id; Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id; Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][0] = c02 * id; Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id; Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    for (int a = 0; a < 8; ++a)
+      for (int i = 0; i < 3; ++i)
+        sG[wp][lane][a][i] = gr[a][0] * Ji[0][i] + gr[a][1] * Ji[1][i] + gr[a][2] * Ji[2][i];
+    sW[wp][lane] = det;  // Gauss weight 1
+  }
+  __syncwarp();
+  const double e = E[T], v = nu[T];
+  const double lam = e * v / ((1.0 + v) * (1.0 - 2.0 * v));
+  const double G = e / (2.0 * (1.0 + v));
+  const long long nT = d.nT;
+#pragma unroll 1
+  for (int rep = 0; rep < 2; ++rep) {
+    const int a = (lane >> 3) + 4 * rep, b = lane & 7;
+    double K[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int q = 0; q < 8; ++q) {
+      const double w = sW[wp][q];
+      const double* ga = sG[wp][q][a];
+      const double* gb = sG[wp][q][b];
+      const double dot = ga[0] * gb[0] + ga[1] * gb[1] + ga[2] * gb[2];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          K[i][j] += w * (lam * ga[i] * gb[j] + G * ga[j] * gb[i] + (i == j ? G * dot : 0.0));
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Ke[(long long)((3 * a + i) * 24 + 3 * b + j) * nT + T] = K[i][j];
+  }
+  if (lane < 24) {
+    const int a = lane / 3, c = lane % 3;
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += sW[wp][q] * sG[wp][q][a][c];
+    Aup[(long long)lane * nT + T] = -biot[T] * s;
+  }
+  if (lane == 0) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += sW[wp][q];
+    vol[T] = s;
+  }
+}
+
+// ---------------------------------------------------------------- K2: RT0
+// Thread per cell.  [A_ww]_fg = (phi_f, mu kappa^-1 phi_g)_T with the
+// contravariant Piola map phi = J phi_hat / det J of the unit-outward-flux
+// reference basis (phi_hat of local face 2d / 2d+1 is -(1-xi_d)/8 e_d /
+// (1+xi_d)/8 e_d).  Condensation (Eq. hmfeSys): W_T = A_ww,T^-1, W_T 1,
+// 1^T W_T 1, Abar_pp,T = S_eps|T| + dt 1^T W_T 1.
+__global__ void k_rt0(Dims d, const double* __restrict__ coords, const double* __restrict__ mu,
+                      const double* __restrict__ kappa, const double* __restrict__ Seps,
+                      const double* __restrict__ vol, double dt, double* __restrict__ Wout,
+                      double* __restrict__ W1out, double* __restrict__ sWout, double* __restrict__ Abar,
+                      int* __restrict__ flag) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  double X[8][3];
+  load_cell_coords(d, coords, T, X);
+  const double m = mu[T];
+  const double kinv[3] = {m / kappa[3 * T], m / kappa[3 * T + 1], m / kappa[3 * T + 2]};
+  double A[6][6];
+  for (int f = 0; f < 6; ++f)
+    for (int g = 0; g < 6; ++g) A[f][g] = 0.0;
+  for (int q = 0; q < 8; ++q) {
+    const double xq[3] = {(q & 1) ? kGP : -kGP, ((q >> 1) & 1) ? kGP : -kGP, ((q >> 2) & 1) ? kGP : -kGP};
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < 8; ++a) {
+      double gr[3];
+      q1_ref_grad(a, xq[0], xq[1], xq[2], gr);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) J[i][j] += X[a][i] * gr[j];
+    }
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(det > 0.0)) atomicOr(flag, 1);
+    // M_dd' = sum_i J_id J_id' (mu/kappa_i) / det
+    double M[3][3];
+    for (int p = 0; p < 3; ++p)
+      for (int r = 0; r < 3; ++r) M[p][r] = (J[0][p] * J[0][r] * kinv[0] + J[1][p] * J[1][r] * kinv[1] + J[2][p] * J[2][r] * kinv[2]) / det;
+    double val[6];
+    for (int f = 0; f < 6; ++f) {
+      const int dd = f >> 1;
+      val[f] = (f & 1) ? (1.0 + xq[dd]) * 0.125 : -(1.0 - xq[dd]) * 0.125;
+    }
+    for (int f = 0; f < 6; ++f)
+      for (int g = 0; g < 6; ++g) A[f][g] += M[f >> 1][g >> 1] * val[f] * val[g];
+  }
+  // Cholesky A = L L^T, then W = A^-1 column by column
+  double L[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) L[i][j] = 0.0;
+  for (int j = 0; j < 6; ++j) {
+    double s = A[j][j];
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > 0.0)) { atomicOr(flag, 2); s = 1e-300; }
+    const double ljj = sqrt(s);
+    L[j][j] = ljj;
+    for (int i = j + 1; i < 6; ++i) {
+      double t = A[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / ljj;
+    }
+  }
+  double W[6][6];
+  for (int c = 0; c < 6; ++c) {
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+      y[i] = t / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < 6; ++k) t -= L[k][i] * W[k][c];
+      W[i][c] = t / L[i][i];
+    }
+  }
+  // symmetrise (exact symmetry of the stored inverse)
+  double s1 = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    double r = 0.0;
+    for (int g = 0; g < 6; ++g) {
+      const double wfg = 0.5 * (W[f][g] + W[g][f]);
+      Wout[(long long)(6 * f + g) * d.nT + T] = wfg;
+      r += wfg;
+    }
+    W1out[(long long)f * d.nT + T] = r;
+    s1 += r;
+  }
+  sWout[T] = s1;
+  Abar[T] = Seps[T] * vol[T] + dt * s1;
+}
+
+// ---------------------------------------------------------------- K3: stab
+// Thread per cell.  Eq. (J_def): beta_M |M| on every internal face of the
+// macro-element (i>>1, j>>1, k>>1); beta_M = (3b)^2 / [32 (lam + 4G)] with
+// volume-averaged lam, G, b over the macro-element's cells.
+__global__ void k_stab(Dims d, const double* __restrict__ E, const double* __restrict__ nu,
+                       const double* __restrict__ biot, const double* __restrict__ vol,
+                       double* __restrict__ stabc) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  const int i0 = i & ~1, j0 = j & ~1, k0 = k & ~1;
+  double sv = 0, sl = 0, sg = 0, sb = 0;
+  for (int kk = k0; kk < k0 + 2 && kk < d.nz; ++kk)
+    for (int jj = j0; jj < j0 + 2 && jj < d.ny; ++jj)
+      for (int ii = i0; ii < i0 + 2 && ii < d.nx; ++ii) {
+        const long long c = cell_id(d, ii, jj, kk);
+        const double e = E[c], v = nu[c], w = vol[c];
+        const double lam = e * v / ((1.0 + v) * (1.0 - 2.0 * v));
+        const double G = e / (2.0 * (1.0 + v));
+        sv += w; sl += lam * w; sg += G * w; sb += biot[c] * w;
+      }
+  const double lamM = sl / sv, GM = sg / sv, bM = sb / sv;
+  const double beta = (3.0 * bM) * (3.0 * bM) / (32.0 * (lamM + 4.0 * GM));
+  const double c = beta * sv;
+  stabc[T] = ((i ^ 1) < d.nx) ? c : 0.0;
+  stabc[d.nT + T] = ((j ^ 1) < d.ny) ? c : 0.0;
+  stabc[2 * d.nT + T] = ((k ^ 1) < d.nz) ? c : 0.0;
+}
+
+// ---------------------------------------------------------------- K4: A_uu
+// Thread per (node, neighbour offset): deterministic gather of the <= 8
+// element blocks coupling the two nodes, then the Dirichlet treatment (zero
+// row and column of a prescribed component, keep its diagonal).
+__global__ void k_assemble_uu(Dims d, const double* __restrict__ Ke, const unsigned char* __restrict__ fix,
+                              double* __restrict__ val) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= d.nN * 27) return;
+  const int o = (int)(tid / d.nN);
+  const long long n = tid - (long long)o * d.nN;
+  const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
+            nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+  const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+  const int mi = ni + dx, mj = nj + dy, mk = nk + dz;
+  double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const bool inside = mi >= 0 && mi <= d.nx && mj >= 0 && mj <= d.ny && mk >= 0 && mk <= d.nz;
+  unsigned char fm = 0;
+  if (inside) {
+    fm = fix[node_id(d, mi, mj, mk)];
+    const int zlo = dz == 1 ? nk : nk - 1, zhi = dz == -1 ? nk - 1 : nk;
+    const int ylo = dy == 1 ? nj : nj - 1, yhi = dy == -1 ? nj - 1 : nj;
+    const int xlo = dx == 1 ? ni : ni - 1, xhi = dx == -1 ? ni - 1 : ni;
+    for (int cz = zlo; cz <= zhi; ++cz) {
+      if (cz < 0 || cz >= d.nz) continue;
+      for (int cy = ylo; cy <= yhi; ++cy) {
+        if (cy < 0 || cy >= d.ny) continue;
+        for (int cx = xlo; cx <= xhi; ++cx) {
+          if (cx < 0 || cx >= d.nx) continue;
+          const long long T = cell_id(d, cx, cy, cz);
+          const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
+          const int b = (mi - cx) + 2 * (mj - cy) + 4 * (mk - cz);
+          for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) blk[3 * r + s] += Ke[(long long)((3 * a + r) * 24 + 3 * b + s) * d.nT + T];
+        }
+      }
+    }
+  }
+  const unsigned char fn = fix[n];
+  for (int r = 0; r < 3; ++r)
+    for (int s = 0; s < 3; ++s) {
+      double v = blk[3 * r + s];
+      if (((fn >> r) & 1) || ((fm >> s) & 1)) v = (o == 13 && r == s) ? v : 0.0;
+      val[(long long)(o * 9 + 3 * r + s) * d.nN + n] = v;
+    }
+}
+
+__global__ void k_aup_dirichlet(Dims d, const unsigned char* __restrict__ fix, double* __restrict__ Aup) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= d.nT * 24) return;
+  const int e = (int)(tid / d.nT);
+  const long long T = tid - (long long)e * d.nT;
+  const int a = e / 3, c = e % 3;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+  if ((fix[n] >> c) & 1) Aup[tid] = 0.0;
+}
+
+// traction load: thread per node, integral of N_a t over every traction face
+// touching the node (2x2 Gauss on the bilinear face).
+__global__ void k_face_load(Dims d, const double* __restrict__ coords, const unsigned char* __restrict__ face_bc,
+                            const unsigned char* __restrict__ fix, double t0, double t1, double t2,
+                            double* __restrict__ fu) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.nN) return;
+  const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
+            nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+  double acc = 0.0;  // integral of N_a over traction faces (times traction later)
+  for (int cz = nk - 1; cz <= nk; ++cz) {
+    if (cz < 0 || cz >= d.nz) continue;
+    for (int cy = nj - 1; cy <= nj; ++cy) {
+      if (cy < 0 || cy >= d.ny) continue;
+      for (int cx = ni - 1; cx <= ni; ++cx) {
+        if (cx < 0 || cx >= d.nx) continue;
+        const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
+        for (int lf = 0; lf < 6; ++lf) {
+          const int ax = lf >> 1, side = lf & 1;
+          if (((a >> ax) & 1) != side) continue;
+          const long long f = cell_face(d, cx, cy, cz, lf);
+          if (!(face_bc[f] & 1)) continue;
+          // the two in-face axes, lower first
+          const int u = ax == 0 ? 1 : 0, v = ax == 2 ? 1 : 2;
+          double Xf[4][3];
+          int pos = -1;
+          for (int q = 0; q < 4; ++q) {
+            int loc = (side << ax) | ((q & 1) << u) | (((q >> 1) & 1) << v);
+            if (loc == a) pos = q;
+            const long long m = node_id(d, cx + (loc & 1), cy + ((loc >> 1) & 1), cz + ((loc >> 2) & 1));
+            Xf[q][0] = coords[3 * m]; Xf[q][1] = coords[3 * m + 1]; Xf[q][2] = coords[3 * m + 2];
+          }
+          const double ps = (pos & 1) ? 1.0 : -1.0, pt = (pos & 2) ? 1.0 : -1.0;
+          for (int gs = 0; gs < 2; ++gs)
+            for (int gt = 0; gt < 2; ++gt) {
+              const double s = gs ? kGP : -kGP, t = gt ? kGP : -kGP;
+              double xs[3] = {0, 0, 0}, xt[3] = {0, 0, 0};
+              for (int q = 0; q < 4; ++q) {
+                const double qs = (q & 1) ? 1.0 : -1.0, qt = (q & 2) ? 1.0 : -1.0;
+                const double dNs = 0.25 * qs * (1.0 + qt * t), dNt = 0.25 * qt * (1.0 + qs * s);
+                for (int c = 0; c < 3; ++c) { xs[c] += dNs * Xf[q][c]; xt[c] += dNt * Xf[q][c]; }
+              }
+              const double cr0 = xs[1] * xt[2] - xs[2] * xt[1], cr1 = xs[2] * xt[0] - xs[0] * xt[2],
+                           cr2 = xs[0] * xt[1] - xs[1] * xt[0];
+              const double area = sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+              acc += area * 0.25 * (1.0 + ps * s) * (1.0 + pt * t);
+            }
+        }
+      }
+    }
+  }
+  const unsigned char fx = fix[n];
+  fu[3 * n + 0] = (fx & 1) ? 0.0 : acc * t0;
+  fu[3 * n + 1] = (fx & 2) ? 0.0 : acc * t1;
+  fu[3 * n + 2] = (fx & 4) ? 0.0 : acc * t2;
+}
+
+// ---------------------------------------------------------------- K5
+// Thread per cell: B~_p (Eq. app_Bp with the fixed-stress diagonal of the
+// M_I^(h) definition) and the masked coupling A_ppi = -W_T 1 (zero on
+// drained faces, whose columns are eliminated).
+__global__ void k_btilde(Dims d, const double* __restrict__ Auu_diag_src, const double* __restrict__ Aup,
+                         const double* __restrict__ Seps, const double* __restrict__ vol,
+                         const double* __restrict__ stabc, const double* __restrict__ sW,
+                         const double* __restrict__ W1, const unsigned char* __restrict__ face_bc, double dt,
+                         double* __restrict__ btilde, double* __restrict__ ApPi) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  double fs = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    for (int c = 0; c < 3; ++c) {
+      const double v = Aup[(long long)(3 * a + c) * d.nT + T];
+      const double dg = Auu_diag_src[(long long)(13 * 9 + 4 * c) * d.nN + n];
+      fs += v * v / dg;
+    }
+  }
+  const double sd = stabc[T] + stabc[d.nT + T] + stabc[2 * d.nT + T];
+  btilde[T] = Seps[T] * vol[T] + sd + fs + dt * sW[T];
+  for (int lf = 0; lf < 6; ++lf) {
+    const long long f = cell_face(d, i, j, k, lf);
+    ApPi[(long long)lf * d.nT + T] = (face_bc[f] & 2) ? 0.0 : -W1[(long long)lf * d.nT + T];
+  }
+}
+
+// Thread per face: ELL rows (11 slots) of A_pipi = sum_T W_T and of
+// C~_pi = sum_T [W_T - dt (W_T 1)(W_T 1)^T / B~_T], Dirichlet treatment,
+// and the faces -> cells prolongation weight.
+__global__ void k_face_ell(Dims d, const double* __restrict__ W, const double* __restrict__ W1,
+                           const double* __restrict__ btilde, const unsigned char* __restrict__ face_bc, double dt,
+                           int* __restrict__ col, double* __restrict__ Apipi, double* __restrict__ Cpi,
+                           double* __restrict__ pw) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nF) return;
+  long long cell[2];
+  int lf[2], ijk[2][3];
+  face_cells(d, f, cell, lf, ijk);
+  const bool fixed = face_bc[f] & 2;
+  double da = 0.0, dc = 0.0;
+  const long long nF = d.nF, nT = d.nT;
+  for (int s = 0; s < 2; ++s) {
+    if (cell[s] < 0) {
+      for (int q = 0; q < 5; ++q) {
+        col[(1 + 5 * s + q) * nF + f] = (int)f;
+        Apipi[(1 + 5 * s + q) * nF + f] = 0.0;
+        Cpi[(1 + 5 * s + q) * nF + f] = 0.0;
+      }
+      continue;
+    }
+    const long long T = cell[s];
+    const int l = lf[s];
+    const double w1l = W1[(long long)l * nT + T];
+    const double bt = btilde[T];
+    const double wll = W[(long long)(6 * l + l) * nT + T];
+    da += wll;
+    dc += wll - dt * w1l * w1l / bt;
+    int q = 0;
+    for (int m = 0; m < 6; ++m) {
+      if (m == l) continue;
+      const long long g = cell_face(d, ijk[s][0], ijk[s][1], ijk[s][2], m);
+      const bool gfix = face_bc[g] & 2;
+      double va = W[(long long)(6 * l + m) * nT + T];
+      double vc = va - dt * w1l * W1[(long long)m * nT + T] / bt;
+      if (fixed || gfix) { va = 0.0; vc = 0.0; }
+      col[(1 + 5 * s + q) * nF + f] = (int)g;
+      Apipi[(1 + 5 * s + q) * nF + f] = va;
+      Cpi[(1 + 5 * s + q) * nF + f] = vc;
+      ++q;
+    }
+  }
+  col[f] = (int)f;
+  Apipi[f] = da;
+  Cpi[f] = fixed ? da : dc;
+  const int ncell = (cell[0] >= 0) + (cell[1] >= 0);
+  pw[f] = fixed ? 0.0 : (ncell == 2 ? 0.5 : 1.0);
+}
+
+__global__ void k_scalings(Dims d, const double* __restrict__ Auu, const double* __restrict__ btilde,
+                           const double* __restrict__ Cpi, double* __restrict__ ds) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nU = 3 * d.nN;
+  if (r >= nU + d.nT + d.nF) return;
+  double v;
+  if (r < nU) {
+    const long long n = r / 3;
+    const int c = (int)(r % 3);
+    v = Auu[(long long)(13 * 9 + 4 * c) * d.nN + n];
+  } else if (r < nU + d.nT) {
+    v = btilde[r - nU];
+  } else {
+    v = Cpi[r - nU - d.nT];
+  }
+  ds[r] = 1.0 / sqrt(v);
+}
+
+// ---------------------------------------------------------------- RHS
+__global__ void k_rhs(Dims d, const double* __restrict__ fu, const double* __restrict__ Aup,
+                      const double* __restrict__ Seps, const double* __restrict__ vol,
+                      const double* __restrict__ xprev, double scale, double* __restrict__ b) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nU = 3 * d.nN;
+  if (r >= nU + d.nT + d.nF) return;
+  if (r < nU) {
+    b[r] = scale * fu[r];
+  } else if (r < nU + d.nT) {
+    const long long T = r - nU;
+    double s = 0.0;
+    if (xprev) {
+      const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+      for (int a = 0; a < 8; ++a) {
+        const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+        for (int c = 0; c < 3; ++c) s -= Aup[(long long)(3 * a + c) * d.nT + T] * xprev[3 * n + c];
+      }
+      s += Seps[T] * vol[T] * xprev[nU + T];
+    }
+    b[r] = s;
+  } else {
+    b[r] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- operator
+// out = so ? so[r] * (bsub ? bsub[r] - y : y) : (bsub ? bsub[r] - y : y)
+__device__ __forceinline__ double finish(double y, long long r, const double* so, const double* bsub) {
+  double v = bsub ? bsub[r] - y : y;
+  return so ? so[r] * v : v;
+}
+
+// u rows: A_uu x_u (27-point 3x3-block stencil) + A_up x_p (8 cells).
+__global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restrict__ Auu, const double* __restrict__ Aup,
+                                                 const double* __restrict__ x, double* __restrict__ y,
+                                                 const double* __restrict__ so, const double* __restrict__ bsub) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.nN) return;
+  const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
+            nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+  const long long sx = 1, sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
+  double y0 = 0, y1 = 0, y2 = 0;
+  const long long N = d.nN;
+#pragma unroll 3
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int mk = nk + dz;
+    if (mk < 0 || mk > d.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int mj = nj + dy;
+      if (mj < 0 || mj > d.ny) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int mi = ni + dx;
+        if (mi < 0 || mi > d.nx) continue;
+        const int o = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+        const long long m = n + dx * sx + dy * sy + dz * sz;
+        const double x0 = x[3 * m], x1 = x[3 * m + 1], x2 = x[3 * m + 2];
+        const double* v = Auu + (long long)o * 9 * N + n;
+        y0 += v[0] * x0 + v[N] * x1 + v[2 * N] * x2;
+        y1 += v[3 * N] * x0 + v[4 * N] * x1 + v[5 * N] * x2;
+        y2 += v[6 * N] * x0 + v[7 * N] * x1 + v[8 * N] * x2;
+      }
+    }
+  }
+  const long long nU = 3 * N;
+  const double* xp = x + nU;
+  for (int cz = nk - 1; cz <= nk; ++cz) {
+    if (cz < 0 || cz >= d.nz) continue;
+    for (int cy = nj - 1; cy <= nj; ++cy) {
+      if (cy < 0 || cy >= d.ny) continue;
+      for (int cx = ni - 1; cx <= ni; ++cx) {
+        if (cx < 0 || cx >= d.nx) continue;
+        const long long T = cell_id(d, cx, cy, cz);
+        const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
+        const double p = xp[T];
+        y0 += Aup[(long long)(3 * a) * d.nT + T] * p;
+        y1 += Aup[(long long)(3 * a + 1) * d.nT + T] * p;
+        y2 += Aup[(long long)(3 * a + 2) * d.nT + T] * p;
+      }
+    }
+  }
+  y[3 * n] = finish(y0, 3 * n, so, bsub);
+  y[3 * n + 1] = finish(y1, 3 * n + 1, so, bsub);
+  y[3 * n + 2] = finish(y2, 3 * n + 2, so, bsub);
+}
+
+// p rows: A_pu x_u + (Abar_pp + A_stab) x_p + dt A_ppi x_pi.
+__global__ void k_apply_p(Dims d, const double* __restrict__ Aup, const double* __restrict__ Abar,
+                          const double* __restrict__ stabc, const double* __restrict__ ApPi, double dt,
+                          const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ so,
+                          const double* __restrict__ bsub) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  const long long nU = 3 * d.nN;
+  double s = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    for (int c = 0; c < 3; ++c) s -= Aup[(long long)(3 * a + c) * d.nT + T] * x[3 * n + c];
+  }
+  const double* xp = x + nU;
+  const double cx = stabc[T], cy = stabc[d.nT + T], cz = stabc[2 * d.nT + T];
+  double st = (Abar[T] + (cx + cy + cz)) * xp[T];
+  if (cx != 0.0) st -= cx * xp[cell_id(d, i ^ 1, j, k)];
+  if (cy != 0.0) st -= cy * xp[cell_id(d, i, j ^ 1, k)];
+  if (cz != 0.0) st -= cz * xp[cell_id(d, i, j, k ^ 1)];
+  s += st;
+  const double* xpi = xp + d.nT;
+  double c = 0.0;
+  for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * xpi[cell_face(d, i, j, k, lf)];
+  s += dt * c;
+  y[nU + T] = finish(s, nU + T, so, bsub);
+}
+
+// pi rows: A_pip x_p + A_pipi x_pi (ELL, 11 slots).
+__global__ void k_apply_pi(Dims d, const double* __restrict__ ApPi, const int* __restrict__ col,
+                           const double* __restrict__ Apipi, const double* __restrict__ x, double* __restrict__ y,
+                           const double* __restrict__ so, const double* __restrict__ bsub) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nF) return;
+  long long cell[2];
+  int lf[2], ijk[2][3];
+  face_cells(d, f, cell, lf, ijk);
+  const long long nU = 3 * d.nN;
+  const double* xp = x + nU;
+  const double* xpi = xp + d.nT;
+  double s = 0.0;
+  for (int q = 0; q < 2; ++q)
+    if (cell[q] >= 0) s += ApPi[(long long)lf[q] * d.nT + cell[q]] * xp[cell[q]];
+  double a = 0.0;
+#pragma unroll
+  for (int q = 0; q < 11; ++q) a += Apipi[(long long)q * d.nF + f] * xpi[col[(long long)q * d.nF + f]];
+  s += a;
+  const long long r = nU + d.nT + f;
+  y[r] = finish(s, r, so, bsub);
+}
+
+// preconditioner pieces: z_p = B~^-1 (v_p - dt A_ppi z_pi), t_u = v_u - A_up z_p
+__global__ void k_prec_p(Dims d, const double* __restrict__ ApPi, const double* __restrict__ btilde, double dt,
+                         const double* __restrict__ vp, const double* __restrict__ zpi, double* __restrict__ zp) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  double c = 0.0;
+  for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * zpi[cell_face(d, i, j, k, lf)];
+  zp[T] = (vp[T] - dt * c) / btilde[T];
+}
+
+__global__ void k_prec_u(Dims d, const double* __restrict__ Aup, const double* __restrict__ vu,
+                         const double* __restrict__ zp, double* __restrict__ tu) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= d.nN) return;
+  const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
+            nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+  double y0 = 0, y1 = 0, y2 = 0;
+  for (int cz = nk - 1; cz <= nk; ++cz) {
+    if (cz < 0 || cz >= d.nz) continue;
+    for (int cy = nj - 1; cy <= nj; ++cy) {
+      if (cy < 0 || cy >= d.ny) continue;
+      for (int cx = ni - 1; cx <= ni; ++cx) {
+        if (cx < 0 || cx >= d.nx) continue;
+        const long long T = cell_id(d, cx, cy, cz);
+        const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
+        const double p = zp[T];
+        y0 += Aup[(long long)(3 * a) * d.nT + T] * p;
+        y1 += Aup[(long long)(3 * a + 1) * d.nT + T] * p;
+        y2 += Aup[(long long)(3 * a + 2) * d.nT + T] * p;
+      }
+    }
+  }
+  tu[3 * n] = vu[3 * n] - y0;
+  tu[3 * n + 1] = vu[3 * n + 1] - y1;
+  tu[3 * n + 2] = vu[3 * n + 2] - y2;
+}
+
+Dims dims_of(const Ctx& c) {
+  return Dims{c.nx, c.ny, c.nz, c.nN, c.nT, c.nF, c.nFx, c.nFy};
+}
+
+}  // namespace
+
+void assemble_all(Ctx& c) {
+  const Dims d = dims_of(c);
+  MHFP_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+  double* Ke = dalloc_n<double>(c, (size_t)576 * c.nT);
+  c.Aup = dalloc_n<double>(c, (size_t)24 * c.nT);
+  c.vol = dalloc_n<double>(c, c.nT);
+  k_q1<<<grid_for(c.nT, Q1_WARPS), 32 * Q1_WARPS, 0, c.stream>>>(d, c.coords, c.E, c.nu, c.biot, Ke, c.Aup, c.vol,
+                                                                 c.d_flag);
+  MHFP_LAUNCH_CHECK();
+  c.W = dalloc_n<double>(c, (size_t)36 * c.nT);
+  c.W1 = dalloc_n<double>(c, (size_t)6 * c.nT);
+  c.sW = dalloc_n<double>(c, c.nT);
+  c.Abar = dalloc_n<double>(c, c.nT);
+  k_rt0<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.coords, c.mu, c.kappa, c.Seps, c.vol, c.dt, c.W, c.W1, c.sW,
+                                                   c.Abar, c.d_flag);
+  MHFP_LAUNCH_CHECK();
+  c.stabc = dalloc_n<double>(c, (size_t)3 * c.nT);
+  k_stab<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.E, c.nu, c.biot, c.vol, c.stabc);
+  MHFP_LAUNCH_CHECK();
+  c.Auu.Lx = c.nx + 1; c.Auu.Ly = c.ny + 1; c.Auu.Lz = c.nz + 1;
+  c.Auu.N = c.nN; c.Auu.bs = 3; c.Auu.kind = ST_BOX1;
+  c.Auu.val = dalloc_n<double>(c, (size_t)27 * 9 * c.nN);
+  k_assemble_uu<<<grid_for(c.nN * 27, 256), 256, 0, c.stream>>>(d, Ke, c.node_fix, c.Auu.val);
+  MHFP_LAUNCH_CHECK();
+  k_aup_dirichlet<<<grid_for(c.nT * 24, 256), 256, 0, c.stream>>>(d, c.node_fix, c.Aup);
+  MHFP_LAUNCH_CHECK();
+  c.fu = dalloc_n<double>(c, (size_t)c.nU);
+  k_face_load<<<grid_for(c.nN, 128), 128, 0, c.stream>>>(d, c.coords, c.face_bc, c.node_fix, c.trac[0], c.trac[1],
+                                                         c.trac[2], c.fu);
+  MHFP_LAUNCH_CHECK();
+  int hflag = 0;
+  MHFP_CUDA(cudaMemcpyAsync(&hflag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  // the element stiffness is consumed by the gather; release it now
+  for (auto it = c.allocs.begin(); it != c.allocs.end(); ++it)
+    if (*it == (void*)Ke) { c.allocs.erase(it); break; }
+  MHFP_CUDA(cudaFree(Ke));
+  if (hflag & 1) throw Error{MHFP_ERR_MESH, "inverted or degenerate element (det J <= 0 at a Gauss point)"};
+  if (hflag & 2) throw Error{MHFP_ERR_MESH, "RT0 element mass matrix is not positive definite"};
+}
+
+void build_preconditioner_blocks(Ctx& c) {
+  const Dims d = dims_of(c);
+  c.btilde = dalloc_n<double>(c, c.nT);
+  c.ApPi = dalloc_n<double>(c, (size_t)6 * c.nT);
+  k_btilde<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.Auu.val, c.Aup, c.Seps, c.vol, c.stabc, c.sW, c.W1,
+                                                      c.face_bc, c.dt, c.btilde, c.ApPi);
+  MHFP_LAUNCH_CHECK();
+  c.ell_col = dalloc_n<int>(c, (size_t)11 * c.nF);
+  c.Apipi = dalloc_n<double>(c, (size_t)11 * c.nF);
+  c.Cpi = dalloc_n<double>(c, (size_t)11 * c.nF);
+  c.pw = dalloc_n<double>(c, c.nF);
+  k_face_ell<<<grid_for(c.nF, 128), 128, 0, c.stream>>>(d, c.W, c.W1, c.btilde, c.face_bc, c.dt, c.ell_col, c.Apipi,
+                                                        c.Cpi, c.pw);
+  MHFP_LAUNCH_CHECK();
+  c.ds = dalloc_n<double>(c, c.n);
+  k_scalings<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.btilde, c.Cpi, c.ds);
+  MHFP_LAUNCH_CHECK();
+}
+
+void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs) {
+  const Dims d = dims_of(c);
+  k_rhs<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.fu, c.Aup, c.Seps, c.vol, xprev, scale, rhs);
+  MHFP_LAUNCH_CHECK();
+}
+
+void apply_operator(Ctx& c, const double* x, double* y, const double* so, const double* bsub) {
+  const Dims d = dims_of(c);
+  timing_begin(c, 1);
+  k_apply_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so, bsub);
+  MHFP_LAUNCH_CHECK();
+  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, c.dt, x, y, so, bsub);
+  MHFP_LAUNCH_CHECK();
+  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(d, c.ApPi, c.ell_col, c.Apipi, x, y, so, bsub);
+  MHFP_LAUNCH_CHECK();
+  // algorithmic bytes: A_uu values (27*9 doubles/node) + A_up read twice
+  // (24 doubles/cell) + ELL (11 doubles + 11 ints/face) + p-block (~17
+  // doubles/cell) + vectors (read x, write y: 2 * 8 B per dof).
+  const double bytes = 27.0 * 9 * 8 * c.nN + 2.0 * 24 * 8 * c.nT + 11.0 * 12 * c.nF + 17.0 * 8 * c.nT + 16.0 * c.n;
+  timing_end(c, 1, bytes);
+}
+
+void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp) {
+  const Dims d = dims_of(c);
+  k_prec_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.ApPi, c.btilde, c.dt, vp, zpi, zp);
+  MHFP_LAUNCH_CHECK();
+}
+
+void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu) {
+  const Dims d = dims_of(c);
+  k_prec_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aup, vu, zp, tu);
+  MHFP_LAUNCH_CHECK();
+}
+
+}  // namespace mhfp

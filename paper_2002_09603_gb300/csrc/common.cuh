@@ -1,0 +1,220 @@
+// Internal declarations shared by the libmhfp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mhfp.h"
+
+namespace mhfp {
+
+// ------------------------------------------------------------ error handling
+struct Error {
+  mhfp_status status;
+  std::string msg;
+};
+
+#define MHFP_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      throw ::mhfp::Error{MHFP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+// every kernel launch of the library is followed by this check, which also
+// counts the launch (mhfp_launch_count)
+extern long long g_launches;
+#define MHFP_LAUNCH_CHECK()         \
+  do {                              \
+    ++::mhfp::g_launches;           \
+    MHFP_CUDA(cudaGetLastError());  \
+  } while (0)
+
+inline unsigned grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ------------------------------------------------------------ stencils
+// Offsets of a structured lattice operator.  BOX1: the 27 neighbours with
+// |d|_inf <= 1 (Q1 node coupling), DIAMOND2: the 25 with |d|_1 <= 2 (cell
+// coupling through shared faces after faces -> cells), BOX2: the 125 with
+// |d|_inf <= 2 (smoothed-aggregation coarse levels of DIAMOND2/BOX2).
+enum StencilKind : int { ST_BOX1 = 0, ST_DIAMOND2 = 1, ST_BOX2 = 2 };
+
+__host__ __device__ inline int stencil_size(int k) { return k == ST_BOX1 ? 27 : (k == ST_DIAMOND2 ? 25 : 125); }
+__host__ __device__ inline int stencil_radius(int k) { return k == ST_BOX1 ? 1 : 2; }
+
+// offset o of a stencil -> (dx,dy,dz)
+__host__ __device__ inline void stencil_offset(int kind, int o, int& dx, int& dy, int& dz) {
+  if (kind == ST_BOX1) {
+    dx = o % 3 - 1; dy = (o / 3) % 3 - 1; dz = o / 9 - 1;
+  } else if (kind == ST_BOX2) {
+    dx = o % 5 - 2; dy = (o / 5) % 5 - 2; dz = o / 25 - 2;
+  } else {
+    // enumerate the |d|_1 <= 2 subset of the 5^3 box in box order
+    int c = -1;
+    for (int b = 0; b < 125; ++b) {
+      int x = b % 5 - 2, y = (b / 5) % 5 - 2, z = b / 25 - 2;
+      int l1 = (x < 0 ? -x : x) + (y < 0 ? -y : y) + (z < 0 ? -z : z);
+      if (l1 <= 2) {
+        ++c;
+        if (c == o) { dx = x; dy = y; dz = z; return; }
+      }
+    }
+    dx = dy = dz = 0;
+  }
+}
+
+// (dx,dy,dz) -> offset index of a stencil, or -1 if not part of it
+__host__ __device__ inline int stencil_index(int kind, int dx, int dy, int dz) {
+  if (kind == ST_BOX1) {
+    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return -1;
+    return (dx + 1) + 3 * ((dy + 1) + 3 * (dz + 1));
+  }
+  if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2) return -1;
+  if (kind == ST_BOX2) return (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
+  int l1 = (dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy) + (dz < 0 ? -dz : dz);
+  if (l1 > 2) return -1;
+  int c = 0;
+  int target = (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
+  for (int b = 0; b < target; ++b) {
+    int x = b % 5 - 2, y = (b / 5) % 5 - 2, z = b / 25 - 2;
+    int m = (x < 0 ? -x : x) + (y < 0 ? -y : y) + (z < 0 ? -z : z);
+    if (m <= 2) ++c;
+  }
+  return c;
+}
+
+// Structured lattice operator: values stored offset-major, then block entry,
+// then lattice point (so a warp of consecutive points reads coalesced).
+struct StructOp {
+  int Lx = 0, Ly = 0, Lz = 0;
+  long long N = 0;
+  int bs = 1;
+  int kind = ST_BOX1;
+  double* val = nullptr;  // [noff][bs*bs][N]
+  int noff() const { return stencil_size(kind); }
+};
+
+// Per-dimension slot range of smoothed-aggregation prolongators with 3-point
+// aggregates along each axis and a fine stencil of radius R:
+// fine a lies in the support of coarse J iff 3J - R <= a <= 3J + 2 + R.
+__host__ __device__ inline int p_lo(int a, int R) { return (a - R + 6) / 3 - 2; }   // = ceil((a-2-R)/3), a >= 0
+__host__ __device__ inline int p_slots(int R) { return (2 + 2 * R) / 3 + 1; }
+// Q = A P touches coarse J iff 3J - 2R <= a <= 3J + 2 + 2R.
+__host__ __device__ inline int q_lo(int a, int R) { return (a - 2 * R + 6) / 3 - 2; } // = ceil((a-2-2R)/3), a >= 0
+__host__ __device__ inline int q_slots(int R) { return (2 + 4 * R) / 3 + 1; }
+
+// ------------------------------------------------------------ multigrid level
+struct Level {
+  bool faces = false;         // level 0 of the interface-pressure hierarchy
+  long long n = 0;            // unknowns
+  long long npts = 0;         // lattice points (or faces)
+  int bs = 1;
+  StructOp A;                 // lattice operator (unused on the face level)
+  double* dinv = nullptr;     // [bs*bs][npts] inverse diagonal blocks
+  double lmax = 0.0;
+  // prolongator to the next level (lattice levels only): [p_slots^3][bs*bs][npts]
+  double* P = nullptr;
+  int R = 1;                  // stencil radius of A (L_inf)
+  unsigned char* active = nullptr;  // [n] free dofs
+  // work vectors of length n
+  double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *y = nullptr;
+  // last level: dense inverse (n x n, row-major)
+  double* dense_inv = nullptr;
+};
+
+// ------------------------------------------------------------ handle
+struct Timing {
+  bool enabled = false;
+  std::vector<cudaEvent_t> ev_start[3], ev_stop[3];
+  size_t used[3] = {0, 0, 0};
+  long long launches[3] = {0, 0, 0};
+  double total_ms[3] = {0, 0, 0};
+  double bytes[3] = {0, 0, 0};
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, nz = 0;
+  long long nN = 0, nT = 0, nF = 0, nFx = 0, nFy = 0, nU = 0, n = 0;
+  double dt = 0;
+  double trac[3] = {0, 0, 0};
+  mhfp_options opt;
+  bool assembled = false, prepared = false;
+  std::string err;
+
+  // inputs (device)
+  double *coords = nullptr, *E = nullptr, *nu = nullptr, *biot = nullptr, *Seps = nullptr,
+         *mu = nullptr, *kappa = nullptr;
+  unsigned char *node_fix = nullptr, *face_bc = nullptr;
+  int* d_flag = nullptr;  // device error flags
+
+  // assembled blocks (device)
+  StructOp Auu;             // ST_BOX1, bs 3, Dirichlet rows/cols zeroed
+  double* Aup = nullptr;    // [24][nT], Dirichlet rows zeroed
+  double* vol = nullptr;    // [nT]
+  double* W = nullptr;      // [36][nT] W_T = A_ww,T^-1
+  double* W1 = nullptr;     // [6][nT]  W_T 1
+  double* sW = nullptr;     // [nT]     1^T W_T 1
+  double* Abar = nullptr;   // [nT]     S_eps|T| + dt 1^T W 1
+  double* stabc = nullptr;  // [3][nT]  beta_M|M| to the x/y/z macro partner (0: none)
+  double* ApPi = nullptr;   // [6][nT]  A_ppi entries (-W1, 0 on drained faces)
+  int* ell_col = nullptr;   // [11][nF]
+  double* Apipi = nullptr;  // [11][nF]
+  double* Cpi = nullptr;    // [11][nF]
+  double* pw = nullptr;     // [nF] faces->cells prolongation weight (0, 1/2, 1)
+  double* fu = nullptr;     // [nU] traction load
+  double* btilde = nullptr; // [nT]
+  double* ds = nullptr;     // [n] equilibration D_s
+
+  std::vector<Level> hu, hpi;
+
+  // Krylov workspace
+  int m_alloc = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *tmp = nullptr;
+  double *h = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
+         *partials = nullptr, *scal = nullptr;
+  double* host_scal = nullptr;  // pinned
+  int npart = 0;
+
+  Timing timing;
+  std::vector<void*> allocs;
+};
+
+// allocation helpers (tracked, freed at destroy)
+void* dalloc(Ctx& c, size_t bytes);
+template <class T>
+T* dalloc_n(Ctx& c, size_t n) { return (T*)dalloc(c, n * sizeof(T)); }
+void dfree_all(Ctx& c);
+
+// timing helpers
+void timing_begin(Ctx& c, int cls);
+void timing_end(Ctx& c, int cls, double bytes);
+
+// assemble.cu
+void assemble_all(Ctx& c);
+void build_preconditioner_blocks(Ctx& c);
+void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs);
+void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub);
+void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp);
+void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu);
+
+// amg.cu
+void build_hierarchies(Ctx& c);
+void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x);
+void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y);
+
+// krylov.cu
+void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st);
+void apply_precond(Ctx& c, const double* v, double* z);
+double device_norm2(Ctx& c, const double* x, long long n);
+void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y, long long n);
+
+}  // namespace mhfp

@@ -1,0 +1,312 @@
+// Right-preconditioned flexible GMRES(m) (Section 5: GMRES, right
+// preconditioning, zero initial guess, stop on the 2-norm of the residual
+// relative to the initial one).  Classical Gram-Schmidt applied twice with
+// deterministic two-stage reductions; Givens rotations and the triangular
+// solve run in one thread on the device; the host reads one 8-byte residual
+// estimate per iteration.
+#include "common.cuh"
+
+#include <chrono>
+#include <cmath>
+
+namespace mhfp {
+
+namespace {
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int DOT_COLS = 8;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// partials[col * gridDim.x + block] = sum over this block's rows of V[:,col] . w
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partials(long long n, const double* __restrict__ V, int ncols,
+                                                               const double* __restrict__ w,
+                                                               double* __restrict__ partials) {
+  __shared__ double sh[RED_THREADS / 32];
+  const int c0 = blockIdx.y * DOT_COLS;
+  double acc[DOT_COLS];
+#pragma unroll
+  for (int q = 0; q < DOT_COLS; ++q) acc[q] = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    const double wr = w[r];
+#pragma unroll
+    for (int q = 0; q < DOT_COLS; ++q)
+      if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * n + r] * wr;
+  }
+#pragma unroll
+  for (int q = 0; q < DOT_COLS; ++q) {
+    const double s = block_sum(acc[q], sh);
+    if (threadIdx.x == 0 && c0 + q < ncols) partials[(long long)(c0 + q) * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out[col] (+)= sum_b partials[col * nb + b] in a fixed order
+__global__ void k_reduce_partials(int nb, const double* __restrict__ partials, double* __restrict__ out, int accumulate) {
+  __shared__ double sh[RED_THREADS / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[(long long)blockIdx.x * nb + b];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = accumulate ? out[blockIdx.x] + s : s;
+}
+
+// w -= V h; optionally partial sums of the updated w squared
+__global__ void __launch_bounds__(RED_THREADS) k_gemv_sub(long long n, const double* __restrict__ V, int ncols,
+                                                           const double* __restrict__ h, double* __restrict__ w,
+                                                           double* __restrict__ partials) {
+  __shared__ double sh[RED_THREADS / 32];
+  double acc = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double s = w[r];
+    for (int c = 0; c < ncols; ++c) s -= V[(long long)c * n + r] * h[c];
+    w[r] = s;
+    acc += s * s;
+  }
+  if (partials) {
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_norm_partials(long long n, const double* __restrict__ x,
+                                                                double* __restrict__ partials) {
+  __shared__ double sh[RED_THREADS / 32];
+  double acc = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    acc += x[r] * x[r];
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// x += Z y
+__global__ void k_gemv_add(long long n, const double* __restrict__ Z, int ncols, const double* __restrict__ y,
+                           double* __restrict__ x) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double s = x[r];
+  for (int c = 0; c < ncols; ++c) s += Z[(long long)c * n + r] * y[c];
+  x[r] = s;
+}
+
+__global__ void k_scale_dev(long long n, const double* __restrict__ x, const double* __restrict__ s,
+                            double* __restrict__ y) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) y[r] = x[r] * s[0];
+}
+
+__global__ void k_scale_host(long long n, const double* __restrict__ x, double s, double* __restrict__ y) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) y[r] = x[r] * s;
+}
+
+__global__ void k_ewise(long long n, const double* __restrict__ x, const double* __restrict__ s, int divide,
+                        double* __restrict__ y) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) y[r] = divide ? x[r] / s[r] : x[r] * s[r];
+}
+
+// One Arnoldi step's Hessenberg column: h = h1 + h2 (j+1 entries), the new
+// subdiagonal ||w|| = sqrt(nrm2); apply the previous rotations, make the new
+// one, update g.  scal[0] = |g_{j+1}|, scal[1] = 1/||w|| (0 on breakdown).
+__global__ void k_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
+                         const double* __restrict__ nrm2, double* __restrict__ H, double* __restrict__ cs,
+                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = H + (long long)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  const double hn = sqrt(nrm2[0]);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  const double c = den > 0.0 ? col[j] / den : 1.0;
+  const double s = den > 0.0 ? col[j + 1] / den : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  scal[0] = fabs(g[j + 1]);
+  scal[1] = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
+// back substitution R y = g (k x k upper triangle of the rotated H)
+__global__ void k_lsq(int k, int m, const double* __restrict__ H, const double* __restrict__ g, double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(long long)c * (m + 1) + i] * y[c];
+    const double d = H[(long long)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+__global__ void k_set_g(int m, double beta, double* __restrict__ g) {
+  const int i = threadIdx.x + blockIdx.x * blockDim.x;
+  if (i <= m) g[i] = (i == 0) ? beta : 0.0;
+}
+
+void ensure_workspace(Ctx& c) {
+  const int m = c.opt.restart;
+  if (c.m_alloc == m) return;
+  if (c.m_alloc != 0) throw Error{MHFP_ERR_STATE, "restart length cannot change after the first solve"};
+  c.V = dalloc_n<double>(c, (size_t)(m + 1) * c.n);
+  c.Z = dalloc_n<double>(c, (size_t)m * c.n);
+  c.w = dalloc_n<double>(c, c.n);
+  c.t = dalloc_n<double>(c, c.n);
+  c.tmp = dalloc_n<double>(c, c.n);
+  c.h = dalloc_n<double>(c, 2 * (size_t)(m + 1));
+  c.H = dalloc_n<double>(c, (size_t)(m + 1) * m);
+  c.cs = dalloc_n<double>(c, m);
+  c.sn = dalloc_n<double>(c, m);
+  c.g = dalloc_n<double>(c, m + 1);
+  c.yv = dalloc_n<double>(c, m);
+  c.npart = RED_BLOCKS;
+  c.partials = dalloc_n<double>(c, (size_t)(m + 1) * RED_BLOCKS);
+  c.scal = dalloc_n<double>(c, 8);
+  if (!c.host_scal) MHFP_CUDA(cudaMallocHost(&c.host_scal, 8 * sizeof(double)));
+  c.m_alloc = m;
+}
+
+// h[0..ncols) = V[:, 0..ncols)^T w
+void multi_dot(Ctx& c, const double* V, int ncols, const double* w, double* h) {
+  dim3 grid(RED_BLOCKS, (ncols + DOT_COLS - 1) / DOT_COLS);
+  k_dot_partials<<<grid, RED_THREADS, 0, c.stream>>>(c.n, V, ncols, w, c.partials);
+  MHFP_LAUNCH_CHECK();
+  k_reduce_partials<<<ncols, RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials, h, 0);
+  MHFP_LAUNCH_CHECK();
+}
+
+// norm^2 into dst (device)
+void norm2_dev(Ctx& c, const double* x, long long n, double* dst) {
+  k_norm_partials<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(n, x, c.partials);
+  MHFP_LAUNCH_CHECK();
+  k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials, dst, 0);
+  MHFP_LAUNCH_CHECK();
+}
+
+double read_scalar(Ctx& c, const double* dsrc) {
+  MHFP_CUDA(cudaMemcpyAsync(c.host_scal, dsrc, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  return c.host_scal[0];
+}
+
+}  // namespace
+
+double device_norm2(Ctx& c, const double* x, long long n) {
+  ensure_workspace(c);
+  norm2_dev(c, x, n, c.scal + 4);
+  return std::sqrt(read_scalar(c, c.scal + 4));
+}
+
+void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y, long long n) {
+  k_ewise<<<grid_for(n, 256), 256, 0, c.stream>>>(n, x, s, divide ? 1 : 0, y);
+  MHFP_LAUNCH_CHECK();
+}
+
+void apply_precond(Ctx& c, const double* v, double* z) {
+  const double* vu = v;
+  const double* vp = v + c.nU;
+  const double* vpi = vp + c.nT;
+  double* zu = z;
+  double* zp = z + c.nU;
+  double* zpi = zp + c.nT;
+  vcycle(c, c.hpi, vpi, zpi);
+  precond_p_step(c, vp, zpi, zp);
+  double* tu = c.hu[0].b;  // level-0 right-hand side buffer is free at the fine level
+  precond_u_rhs(c, vu, zp, tu);
+  vcycle(c, c.hu, tu, zu);
+}
+
+void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  ensure_workspace(c);
+  const int m = c.opt.restart;
+  const long long n = c.n;
+  MHFP_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c.stream));
+  vec_scale(c, b, c.ds, false, c.tmp, n);
+  norm2_dev(c, c.tmp, n, c.scal + 4);
+  const double bnorm = std::sqrt(read_scalar(c, c.scal + 4));
+  mhfp_stats s{};
+  if (!std::isfinite(bnorm)) throw Error{MHFP_ERR_NONFINITE, "non-finite right-hand side"};
+  if (bnorm == 0.0) {
+    s.converged = 1;
+    if (st) *st = s;
+    return;
+  }
+  int total = 0, cycles = 0;
+  bool converged = false;
+  double est = 1.0;
+  while (total < c.opt.maxit) {
+    apply_operator(c, x, c.tmp, c.ds, b);  // tmp = D_s (b - A x)
+    norm2_dev(c, c.tmp, n, c.scal + 4);
+    const double beta = std::sqrt(read_scalar(c, c.scal + 4));
+    if (!std::isfinite(beta)) throw Error{MHFP_ERR_NONFINITE, "non-finite residual"};
+    if (beta <= 1.05 * tol * bnorm) { converged = true; est = beta / bnorm; break; }
+    k_scale_host<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.tmp, 1.0 / beta, c.V);
+    MHFP_LAUNCH_CHECK();
+    k_set_g<<<1, 64, 0, c.stream>>>(m, beta, c.g);
+    MHFP_LAUNCH_CHECK();
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = c.V + (long long)j * n;
+      double* zj = c.Z + (long long)j * n;
+      vec_scale(c, vj, c.ds, true, c.t, n);  // unscale into the preconditioner
+      apply_precond(c, c.t, zj);
+      apply_operator(c, zj, c.w, c.ds, nullptr);  // w = D_s A z_j
+      timing_begin(c, 2);
+      multi_dot(c, c.V, j + 1, c.w, c.h);
+      k_gemv_sub<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, nullptr);
+      MHFP_LAUNCH_CHECK();
+      multi_dot(c, c.V, j + 1, c.w, c.h + (m + 1));
+      k_gemv_sub<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w, c.partials + (size_t)m * RED_BLOCKS);
+      MHFP_LAUNCH_CHECK();
+      k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials + (size_t)m * RED_BLOCKS, c.scal + 2, 0);
+      MHFP_LAUNCH_CHECK();
+      timing_end(c, 2, 8.0 * n * (4.0 * (j + 1) + 6.0));
+      k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, c.h + (m + 1), c.scal + 2, c.H, c.cs, c.sn, c.g, c.scal);
+      MHFP_LAUNCH_CHECK();
+      k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
+      MHFP_LAUNCH_CHECK();
+      const double resid = read_scalar(c, c.scal);
+      ++total;
+      k = j + 1;
+      est = resid / bnorm;
+      if (!std::isfinite(resid)) throw Error{MHFP_ERR_NONFINITE, "non-finite Arnoldi residual"};
+      if (resid <= tol * bnorm || total >= c.opt.maxit) break;
+    }
+    k_lsq<<<1, 32, 0, c.stream>>>(k, m, c.H, c.g, c.yv);
+    MHFP_LAUNCH_CHECK();
+    k_gemv_add<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, k, c.yv, x);
+    MHFP_LAUNCH_CHECK();
+    ++cycles;
+  }
+  apply_operator(c, x, c.tmp, c.ds, b);
+  norm2_dev(c, c.tmp, n, c.scal + 4);
+  const double true_rel = std::sqrt(read_scalar(c, c.scal + 4)) / bnorm;
+  converged = converged || true_rel <= 1.05 * tol;
+  s.iterations = total;
+  s.restarts = cycles;
+  s.converged = converged ? 1 : 0;
+  s.rel_residual = est;
+  s.true_rel_residual = true_rel;
+  s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (st) *st = s;
+  if (!converged) throw Error{MHFP_ERR_NOT_CONVERGED, "FGMRES reached maxit before the tolerance"};
+}
+
+}  // namespace mhfp

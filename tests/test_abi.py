@@ -1,0 +1,47 @@
+"""The C-ABI library loads and exports every symbol include/mhfp.h declares
+(no GPU needed: nothing is computed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mhfp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mhfp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    from paper_2002_09603_gb300 import EXPORTS
+    assert sorted(EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2002_09603_gb300 import build
+    try:
+        path = build.build()
+    except RuntimeError as e:  # no nvcc in this environment
+        pytest.skip(str(e))
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_argument_validation_without_gpu():
+    """mhfp_create rejects bad arguments on the host before touching a device."""
+    from paper_2002_09603_gb300 import build
+    import paper_2002_09603_gb300._lib as L
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    lib = L.load()
+    h = ctypes.c_void_p()
+    assert lib.mhfp_create(None, None, 1.0, None, None, ctypes.byref(h)) == 1
+    assert lib.mhfp_status_string(5) == b"not converged"
+    o = L.default_options()
+    assert (o.restart, o.maxit, o.cheb_degree, o.coarse_max) == (50, 1000, 2, 125)

@@ -1,0 +1,236 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 operator applies and assembled blocks 1e-12 relative (to
+the largest entry of the block they belong to); multigrid levels 1e-11
+(their Chebyshev bounds come from power iterations summed in a different
+order); full solves 1e-8 relative in the block-diagonal energy norm at a
+1e-10 residual tolerance.
+"""
+import numpy as np
+import pytest
+
+import mhfp_inputs as mi
+import oracle
+from oracle import fgmres, precond, system
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _prep(prob):
+    from paper_2002_09603_gb300 import prepare
+    return prepare(prob)
+
+
+def _blockwise_close(got, ref, sizes, rtol):
+    o = 0
+    for n in sizes:
+        g, r = got[o:o + n], ref[o:o + n]
+        scale = max(np.abs(r).max(), 1e-300)
+        assert np.abs(g - r).max() <= rtol * scale, (o, n, np.abs(g - r).max() / scale)
+        o += n
+
+
+CASES = [
+    ("cube2", lambda: mi.random_small(2, 2, 2, seed=1)),
+    ("odd", lambda: mi.random_small(3, 2, 5, seed=2, jitter=0.2)),
+    ("jitter7", lambda: mi.random_small(7, 6, 5, seed=3, jitter=0.25)),
+    ("one", lambda: mi.random_small(1, 1, 1, seed=4)),
+    ("terzaghi8", lambda: mi.terzaghi_cube(8)),
+    ("ragged", lambda: mi.random_small(10, 4, 7, seed=5, jitter=0.1)),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[c[0] for c in CASES])
+def case(request):
+    prob = request.param[1]()
+    B = oracle.assemble(prob)
+    pc = precond.build(B, "amg")
+    s = _prep(prob)
+    yield prob, B, pc, s
+    s.close()
+
+
+def test_sizes(case):
+    prob, B, pc, s = case
+    assert s.sizes == B.sizes == prob.sizes
+
+
+def test_operator_apply(case):
+    prob, B, pc, s = case
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(s.n)
+    y = s.apply_operator(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = system.system_matrix(B) @ x
+    _blockwise_close(y, ref, B.sizes, 1e-12)
+
+
+def test_btilde_and_scaling(case):
+    prob, B, pc, s = case
+    bt, ds = s.scalings()
+    assert np.allclose(bt.cpu().numpy(), pc.Bt, rtol=1e-12, atol=0)
+    assert np.allclose(ds.cpu().numpy(), precond.equilibration(B, pc.Bt, pc.C), rtol=1e-12, atol=0)
+
+
+def test_rhs(case):
+    prob, B, pc, s = case
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(s.n)
+    nU, nP, _ = B.sizes
+    got = s.build_rhs(torch.from_numpy(x).cuda(), load_scale=2.5).cpu().numpy()
+    ref = system.rhs(B, x[:nU], x[nU:nU + nP], load_scale=2.5)
+    _blockwise_close(got, ref, B.sizes, 1e-12)
+    got0 = s.build_rhs(None).cpu().numpy()
+    _blockwise_close(got0, system.rhs(B), B.sizes, 1e-12)
+
+
+def _dense_of(apply, n):
+    cols = []
+    for j in range(n):
+        e = torch.zeros(n, dtype=torch.float64, device="cuda")
+        e[j] = 1.0
+        cols.append(apply(e).cpu().numpy())
+    return np.stack(cols, axis=1)
+
+
+def test_multigrid_levels(case):
+    """Every level operator: same sizes, same sparsity pattern (bit-exact),
+    values within 1e-11 of the oracle's Galerkin products."""
+    prob, B, pc, s = case
+    for which, levels in ((0, pc.u_levels), (1, pc.pi_levels)):
+        info = s.hierarchy(which)
+        assert info["levels"] == len(levels)
+        rng = np.random.default_rng(2)
+        for l, lev in enumerate(levels):
+            n = lev.A.shape[0]
+            assert info["points"][l] * info["block"][l] == n
+            if l < len(levels) - 1:
+                assert np.isclose(info["lmax"][l], lev.lmax, rtol=1e-11)
+            x = rng.standard_normal(n)
+            y = s.level_apply(which, l, torch.from_numpy(x).cuda()).cpu().numpy()
+            ref = lev.A @ x
+            assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max(), (which, l)
+            if n <= 700:
+                D = _dense_of(lambda e: s.level_apply(which, l, e), n)
+                R = lev.A.toarray()
+                # same sparsity pattern up to entries that cancel to rounding
+                # noise on one side (1e-12 of the level's largest entry)
+                noise = 1e-12 * np.abs(R).max()
+                assert np.all(R[np.abs(D) > noise] != 0) and np.all(D[np.abs(R) > noise] != 0), (which, l)
+                assert np.abs(D - R).max() <= 1e-11 * np.abs(R).max()
+
+
+def test_vcycles_and_preconditioner(case):
+    prob, B, pc, s = case
+    rng = np.random.default_rng(3)
+    nU, nP, nPi = B.sizes
+    bu, bpi = rng.standard_normal(nU), rng.standard_normal(nPi)
+    xu = s.vcycle(0, torch.from_numpy(bu).cuda()).cpu().numpy()
+    xpi = s.vcycle(1, torch.from_numpy(bpi).cuda()).cpu().numpy()
+    ru, rpi = precond.vcycle(pc.u_levels, bu), precond.vcycle(pc.pi_levels, bpi)
+    assert np.abs(xu - ru).max() <= 1e-10 * np.abs(ru).max()
+    assert np.abs(xpi - rpi).max() <= 1e-10 * np.abs(rpi).max()
+    v = rng.standard_normal(s.n)
+    z = s.apply_precond(torch.from_numpy(v).cuda()).cpu().numpy()
+    _blockwise_close(z, pc.apply(v), B.sizes, 1e-10)
+
+
+def _energy(B, pc, v):
+    nU, nP, _ = B.sizes
+    return np.sqrt(v[:nU] @ (B.Auu @ v[:nU]) + v[nU:nU + nP] @ (pc.Bt * v[nU:nU + nP])
+                   + v[nU + nP:] @ (pc.C @ v[nU + nP:]))
+
+
+def test_solve_matches_direct_solution(case):
+    prob, B, pc, s = case
+    rng = np.random.default_rng(4)
+    nU, nP, _ = B.sizes
+    u0 = rng.standard_normal(nU) * 1e-5
+    u0[B.u_fixed] = 0
+    xprev = np.concatenate([u0, rng.standard_normal(nP), np.zeros(B.sizes[2])])
+    b = s.build_rhs(torch.from_numpy(xprev).cuda())
+    x, st = s.solve(b, tol=1e-10)
+    x = x.cpu().numpy()
+    bref = system.rhs(B, u0, xprev[nU:nU + nP])
+    xd = oracle.solve_direct(B, bref)
+    assert st["converged"] and st["true_rel_residual"] <= 1.05e-10
+    assert _energy(B, pc, x - xd) <= 1e-8 * _energy(B, pc, xd)
+    # same algorithm in the oracle: same iteration count up to rounding
+    A = system.system_matrix(B)
+    sc = precond.equilibration(B, pc.Bt, pc.C)
+    _, info = fgmres.fgmres(lambda v: A @ v, pc.apply, bref, tol=1e-10, scale=sc)
+    assert abs(info["iters"] - st["iterations"]) <= 1, (info["iters"], st["iterations"])
+
+
+def test_time_steps_terzaghi_against_oracle():
+    """Three backward-Euler steps of the consolidation column: the CUDA
+    solver, chained through mhfp_build_rhs, tracks the oracle's direct
+    solves step by step."""
+    prob = mi.terzaghi_cube(6, dt=50.0)
+    B = oracle.assemble(prob)
+    pc = precond.build(B, "amg")
+    xs, _ = oracle.time_steps(prob, 3, kind="direct")
+    s = _prep(prob)
+    x = None
+    for k in range(3):
+        b = s.build_rhs(x)
+        x, st = s.solve(b, tol=1e-12)
+        e = x.cpu().numpy() - xs[k]
+        assert _energy(B, pc, e) <= 1e-8 * _energy(B, pc, xs[k]), k
+    s.close()
+
+
+def test_not_converged_and_nonfinite():
+    from paper_2002_09603_gb300 import MhfpError, default_options, Solver
+    prob = mi.random_small(5, 4, 4, seed=9)
+    opt = default_options()
+    opt.maxit = 2
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    b = s.build_rhs()
+    x, st = s.solve(b, tol=1e-12, raise_not_converged=False)
+    assert st["iterations"] == 2 and not st["converged"]
+    with pytest.raises(MhfpError) as ei:
+        s.solve(b, tol=1e-12)
+    assert ei.value.status == 5
+    bad = b.clone()
+    bad[3] = float("nan")
+    with pytest.raises(MhfpError) as ei:
+        s.solve(bad, tol=1e-8)
+    assert ei.value.status == 6
+    with pytest.raises(MhfpError) as ei:
+        s.solve(b, tol=0.0)
+    assert ei.value.status == 1
+    s.close()
+
+
+def test_inverted_element_is_rejected():
+    from paper_2002_09603_gb300 import MhfpError, Solver
+    prob = mi.random_small(2, 2, 2, seed=1)
+    c = prob.coords.copy()
+    c[13] = c[13] + np.array([0.9, 0.9, 0.9])   # the centre node through the far corner
+    prob.coords = c
+    s = Solver(prob)
+    with pytest.raises(MhfpError) as ei:
+        s.assemble_condense()
+    assert ei.value.status == 2
+    s.close()
+
+
+def test_call_order_is_enforced():
+    from paper_2002_09603_gb300 import MhfpError, Solver
+    s = Solver(mi.random_small(2, 2, 2, seed=1))
+    b = s.empty()
+    with pytest.raises(MhfpError) as ei:
+        s.solve(b)
+    assert ei.value.status == 8
+    s.close()
