@@ -168,6 +168,33 @@ mhfp_status mhfp_timing(mhfp_handle h, int enable);
 mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launches,
                              double* total_ms, double* bytes_per_launch);
 
+/* ||D_s (b - A_H x)|| and ||D_s b|| without allocating anything (the paper
+ * has no counterpart; this is a service of this library).
+ *
+ * Who needs it: callers that cannot call cudaMalloc at this point, such as
+ * hosts that hand all device memory to their own pool allocator up front, or
+ * loops that must not allocate once running.  mhfp_solve computes the same
+ * norm through the handle's Krylov workspace, which it allocates (about
+ * (2m+4) n doubles) on its first call; this entry point needs only an
+ * assembled and set-up handle.
+ *
+ * d_b, d_x: device vectors of length n (layout above).  d_out: device buffer
+ * of 2 doubles, receives { ||D_s (b - A_H x)||_2, ||D_s b||_2 }, with D_s the
+ * equilibration of mhfp_solve; their ratio is mhfp_solve's true relative
+ * residual.
+ *
+ * Scratch: a file-scope static __device__ array of 65536 x 2 doubles (1 MiB)
+ * that every GPU which loads the library holds until the process exits.
+ * Problems needing more than 65536 row blocks of 256 rows (about 128^3
+ * cells and up) are rejected with MHFP_ERR_ARG and a message saying so.
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's partial sums; every call overwrites each partial sum it reads, so
+ * nothing has to start at zero, but calls that overlap on the GPU (for
+ * example on two streams) race and must be serialised by the caller. */
+mhfp_status mhfp_residual_norm_noalloc(mhfp_handle h, const double* d_b, const double* d_x, double* d_out);
+
 /* Number of kernels this library has launched in the process so far (all
  * handles); a caller brackets a region with two reads to count its launches. */
 long long mhfp_launch_count(void);

@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "out of memory",
 EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhfp_setup_precond",
            "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
-           "mhfp_timing_read", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
+           "mhfp_timing_read", "mhfp_residual_norm_noalloc", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
 
 
 class MhfpError(RuntimeError):
@@ -89,6 +89,7 @@ def load(path: str | None = None):
         "mhfp_sizes": (i, [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]),
         "mhfp_timing": (i, [vp, i]),
         "mhfp_timing_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d), C.POINTER(d)]),
+        "mhfp_residual_norm_noalloc": (i, [vp, vp, vp, vp]),
         "mhfp_launch_count": (ll, []),
         "mhfp_last_error": (C.c_char_p, [vp]),
         "mhfp_status_string": (C.c_char_p, [i]),
@@ -225,6 +226,13 @@ class Solver:
         n, ms, b = C.c_longlong(), C.c_double(), C.c_double()
         self._check(self.lib.mhfp_timing_read(self.h, int(kernel_class), C.byref(n), C.byref(ms), C.byref(b)))
         return dict(launches=n.value, total_ms=ms.value, bytes_per_launch=b.value)
+
+    def residual_norm_noalloc(self, b, x, out=None):
+        """(||D_s (b - A x)||, ||D_s b||) into a 2-element device tensor; the
+        library allocates nothing for this call."""
+        out = self.empty(2) if out is None else out
+        self._check(self.lib.mhfp_residual_norm_noalloc(self.h, _ptr(b), _ptr(x), _ptr(out)))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -320,6 +320,14 @@ mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launche
   });
 }
 
+mhfp_status mhfp_residual_norm_noalloc(mhfp_handle h, const double* d_b, const double* d_x, double* d_out) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (!d_b || !d_x || !d_out) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::residual_norm_noalloc(c, d_b, d_x, d_out);
+  });
+}
+
 long long mhfp_launch_count(void) { return mhfp::g_launches; }
 
 void mhfp_destroy(mhfp_handle h) {

@@ -7,6 +7,7 @@
 #include "common.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace mhfp {
 
@@ -772,6 +773,211 @@ void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp) {
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu) {
   const Dims d = dims_of(c);
   k_prec_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aup, vu, zp, tu);
+  MHFP_LAUNCH_CHECK();
+}
+
+}  // namespace mhfp
+
+// ============================================================================
+// Residual norm without allocation.
+//
+// mhfp_solve checks its answer with ||D_s (b - A_H x)|| computed through the
+// handle's Krylov workspace (an n-vector and a partial-sum buffer, allocated
+// on the first solve).  Callers that must not trigger any device allocation
+// (hosts whose device memory is handed to their own pool allocator up front,
+// loops that must not allocate once running) use mhfp_residual_norm_noalloc
+// instead: each row kernel below folds the operator rows straight into
+// per-block partial sums that live in the file-scope array
+// g_noalloc_partials, so nothing is allocated per call.
+// ============================================================================
+namespace mhfp {
+namespace {
+
+constexpr int NOALLOC_BLOCK = 256;
+// 2 partial sums per thread block -> 65536 blocks = 1 MiB of device memory
+constexpr long long NOALLOC_MAX_BLOCKS = 65536;
+static __device__ __align__(256) double g_noalloc_partials[2 * NOALLOC_MAX_BLOCKS];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[128] = {};  // per device ordinal, filled on first use
+
+__device__ __forceinline__ void na_block_store(double r2, double b2, double* part, long long slot) {
+  __shared__ double sr[NOALLOC_BLOCK / 32], sb[NOALLOC_BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    b2 += __shfl_down_sync(0xffffffffu, b2, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sr[wid] = r2; sb[wid] = b2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < NOALLOC_BLOCK / 32; ++w) { a += sr[w]; c += sb[w]; }
+    part[2 * slot] = a;
+    part[2 * slot + 1] = c;
+  }
+}
+
+// u rows of D_s (b - A_H x): A_uu x_u + A_up x_p
+__global__ void __launch_bounds__(NOALLOC_BLOCK) k_na_u(Dims d, const double* __restrict__ Auu,
+                                                        const double* __restrict__ Aup, const double* __restrict__ x,
+                                                        const double* __restrict__ b, const double* __restrict__ ds,
+                                                        double* __restrict__ part, long long slot0) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0, b2 = 0.0;
+  if (n < d.nN) {
+    const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
+              nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+    const long long N = d.nN;
+    double y[3] = {0, 0, 0};
+    for (int o = 0; o < 27; ++o) {
+      const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+      const int mi = ni + dx, mj = nj + dy, mk = nk + dz;
+      if (mi < 0 || mi > d.nx || mj < 0 || mj > d.ny || mk < 0 || mk > d.nz) continue;
+      const long long m = node_id(d, mi, mj, mk);
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) y[r] += Auu[(long long)(o * 9 + 3 * r + s) * N + n] * x[3 * m + s];
+    }
+    const double* xp = x + 3 * N;
+    for (int cz = nk - 1; cz <= nk; ++cz)
+      for (int cy = nj - 1; cy <= nj; ++cy)
+        for (int cx = ni - 1; cx <= ni; ++cx) {
+          if (cx < 0 || cx >= d.nx || cy < 0 || cy >= d.ny || cz < 0 || cz >= d.nz) continue;
+          const long long T = cell_id(d, cx, cy, cz);
+          const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
+          for (int r = 0; r < 3; ++r) y[r] += Aup[(long long)(3 * a + r) * d.nT + T] * xp[T];
+        }
+    for (int r = 0; r < 3; ++r) {
+      const long long row = 3 * n + r;
+      const double sb = ds[row] * b[row];
+      const double rr = ds[row] * (b[row] - y[r]);
+      r2 += rr * rr;
+      b2 += sb * sb;
+    }
+  }
+  na_block_store(r2, b2, part, slot0 + blockIdx.x);
+}
+
+// p rows: A_pu x_u + (Abar_pp + A_stab) x_p + dt A_ppi x_pi
+__global__ void __launch_bounds__(NOALLOC_BLOCK) k_na_p(Dims d, const double* __restrict__ Aup,
+                                                        const double* __restrict__ Abar, const double* __restrict__ stabc,
+                                                        const double* __restrict__ ApPi, double dt,
+                                                        const double* __restrict__ x, const double* __restrict__ b,
+                                                        const double* __restrict__ ds, double* __restrict__ part,
+                                                        long long slot0) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0, b2 = 0.0;
+  if (T < d.nT) {
+    const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+    const long long nU = 3 * d.nN;
+    double s = 0.0;
+    for (int a = 0; a < 8; ++a) {
+      const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+      for (int c = 0; c < 3; ++c) s -= Aup[(long long)(3 * a + c) * d.nT + T] * x[3 * n + c];
+    }
+    const double* xp = x + nU;
+    const double cx = stabc[T], cy = stabc[d.nT + T], cz = stabc[2 * d.nT + T];
+    s += (Abar[T] + (cx + cy + cz)) * xp[T];
+    if (cx != 0.0) s -= cx * xp[cell_id(d, i ^ 1, j, k)];
+    if (cy != 0.0) s -= cy * xp[cell_id(d, i, j ^ 1, k)];
+    if (cz != 0.0) s -= cz * xp[cell_id(d, i, j, k ^ 1)];
+    const double* xpi = xp + d.nT;
+    double c = 0.0;
+    for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * xpi[cell_face(d, i, j, k, lf)];
+    s += dt * c;
+    const long long row = nU + T;
+    const double sb = ds[row] * b[row];
+    const double rr = ds[row] * (b[row] - s);
+    r2 = rr * rr;
+    b2 = sb * sb;
+  }
+  na_block_store(r2, b2, part, slot0 + blockIdx.x);
+}
+
+// pi rows: A_pip x_p + A_pipi x_pi
+__global__ void __launch_bounds__(NOALLOC_BLOCK) k_na_pi(Dims d, const double* __restrict__ ApPi,
+                                                         const int* __restrict__ col, const double* __restrict__ Apipi,
+                                                         const double* __restrict__ x, const double* __restrict__ b,
+                                                         const double* __restrict__ ds, double* __restrict__ part,
+                                                         long long slot0) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double r2 = 0.0, b2 = 0.0;
+  if (f < d.nF) {
+    long long cell[2];
+    int lf[2], ijk[2][3];
+    face_cells(d, f, cell, lf, ijk);
+    const long long nU = 3 * d.nN;
+    const double* xp = x + nU;
+    const double* xpi = xp + d.nT;
+    double s = 0.0;
+    for (int q = 0; q < 2; ++q)
+      if (cell[q] >= 0) s += ApPi[(long long)lf[q] * d.nT + cell[q]] * xp[cell[q]];
+    for (int q = 0; q < 11; ++q) s += Apipi[(long long)q * d.nF + f] * xpi[col[(long long)q * d.nF + f]];
+    const long long row = nU + d.nT + f;
+    const double sb = ds[row] * b[row];
+    const double rr = ds[row] * (b[row] - s);
+    r2 = rr * rr;
+    b2 = sb * sb;
+  }
+  na_block_store(r2, b2, part, slot0 + blockIdx.x);
+}
+
+// out[0] = sqrt(sum of the r^2 partials), out[1] = sqrt(sum of the (D_s b)^2 partials)
+__global__ void __launch_bounds__(NOALLOC_BLOCK) k_na_final(long long nblocks, const double* __restrict__ part,
+                                                            double* __restrict__ out) {
+  double r2 = 0.0, b2 = 0.0;
+  for (long long q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    r2 += part[2 * q];
+    b2 += part[2 * q + 1];
+  }
+  __shared__ double sr[NOALLOC_BLOCK / 32], sb[NOALLOC_BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_down_sync(0xffffffffu, r2, o);
+    b2 += __shfl_down_sync(0xffffffffu, b2, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sr[wid] = r2; sb[wid] = b2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < NOALLOC_BLOCK / 32; ++w) { a += sr[w]; c += sb[w]; }
+    out[0] = sqrt(a);
+    out[1] = sqrt(c);
+  }
+}
+
+// Device address of g_noalloc_partials for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress, once per device, with that device current.
+double* noalloc_scratch(int device) {
+  if (device < 0 || device >= 128) throw Error{MHFP_ERR_ARG, "device ordinal out of range"};
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    MHFP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partials));
+    g_noalloc_ptr[device] = (double*)p;
+  }
+  return g_noalloc_ptr[device];
+}
+
+}  // namespace
+
+void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out) {
+  const Dims d = dims_of(c);
+  const long long bu = (long long)grid_for(c.nN, NOALLOC_BLOCK);
+  const long long bp = (long long)grid_for(c.nT, NOALLOC_BLOCK);
+  const long long bf = (long long)grid_for(c.nF, NOALLOC_BLOCK);
+  if (bu + bp + bf > NOALLOC_MAX_BLOCKS)
+    throw Error{MHFP_ERR_ARG, "problem too large for the static scratch of mhfp_residual_norm_noalloc (" +
+                                  std::to_string(bu + bp + bf) + " row blocks > 65536)"};
+  double* part = noalloc_scratch(c.device);
+  k_na_u<<<(unsigned)bu, NOALLOC_BLOCK, 0, c.stream>>>(d, c.Auu.val, c.Aup, x, b, c.ds, part, 0);
+  MHFP_LAUNCH_CHECK();
+  k_na_p<<<(unsigned)bp, NOALLOC_BLOCK, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, c.dt, x, b, c.ds, part, bu);
+  MHFP_LAUNCH_CHECK();
+  k_na_pi<<<(unsigned)bf, NOALLOC_BLOCK, 0, c.stream>>>(d, c.ApPi, c.ell_col, c.Apipi, x, b, c.ds, part, bu + bp);
+  MHFP_LAUNCH_CHECK();
+  k_na_final<<<1, NOALLOC_BLOCK, 0, c.stream>>>(bu + bp + bf, part, out);
   MHFP_LAUNCH_CHECK();
 }
 

@@ -205,6 +205,7 @@ void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs);
 void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub);
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp);
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu);
+void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out);
 
 // amg.cu
 void build_hierarchies(Ctx& c);
