@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lognormal64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
+                    help="both: mixed headline with FP64-plain beside it (default)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-target", type=str, default="", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -213,20 +215,103 @@ def make_problem_sizes(name):
 
 
 def traffic_for(kernel):
-    """dram read+write bytes per launch of `kernel` at this workload, from the
-    committed ncu summary, or None if the kernel's source changed since."""
+    """dram read+write bytes per launch of `kernel` at the 64^3 workload, from
+    the committed ncu summary, or None if the kernel's source region changed
+    since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
     if not d:
         return None
-    src = os.path.join(ROOT, "paper_2002_09603_gb300", "csrc", d["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return d["bytes_per_launch"] if sha == d["source_sha"] else None
+    src = open(os.path.join(ROOT, "paper_2002_09603_gb300", "csrc", d["source"])).read()
+    tag = d["region"]
+    try:
+        a, b = src.index(f"// <{tag}>"), src.index(f"// </{tag}>")
+    except ValueError:
+        return None
+    sha = hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    return d["bytes_per_launch"] if sha == d["region_sha"] else None
+
+
+# FP64 peak of the part: ~2 FP64 FMA per clock per SM (from the pipe
+# utilisation ncu reports for k_cheb_u0), 152 SMs, 2 flop per FMA, at the
+# maximum SM clock -> 1.26 TFLOP/s (nominal GB300 FP64: 1.25 TFLOP/s).
+FP64_FMA_PER_CLK_SM = 2
+N_SM = 152
+
+
+def fp64_peak_tflops(sm_max_mhz):
+    return N_SM * FP64_FMA_PER_CLK_SM * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def cheb_u0_flops(n):
+    """Algorithmic FP64 flops of one k_cheb_u0 launch on an n^3 mesh:
+    2 per FMA of r = b - A x over the valid (node, neighbour) 3x3 blocks,
+    of D^-1 r, and 4 per dof for the two Chebyshev updates."""
+    L = n + 1
+    blocks = (3 * L - 2) ** 3
+    nodes = L ** 3
+    return 2 * 9 * blocks + 2 * 9 * nodes + 4 * 3 * nodes
 
 
 # ------------------------------------------------------------------ ours
+def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local):
+    """W warm-up steps, then K timed steps of a fresh simulation (CUDA events
+    on the library's stream), with kernel-class timing and clock sampling."""
+    x = None
+    for _ in range(args.warmup):
+        b = s.build_rhs(x)
+        x, _ = s.solve(b, tol=TOL)
+    x = None
+    iters = []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks_start(local) if sample_clocks else (None, None)
+    if sample_clocks:
+        time.sleep(0.3)
+    l0 = launch_count()
+    s.timing(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b = s.build_rhs(x)
+        x, st = s.solve(b, tol=TOL)
+        iters.append(st["iterations"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clocks_stop(*clk) if sample_clocks else None
+    kt = s.timing_read(0)
+    s.timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return dict(ms=ms, iters=iters, launches=launches, clocks=clocks, kt=kt)
+
+
+def _solver(prob, precision, torch):
+    from paper_2002_09603_gb300 import Solver, default_options
+    opt = default_options()
+    opt.precision = precision
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return s, e0.elapsed_time(e1)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -242,54 +327,27 @@ def run_ours(args):
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
-    from paper_2002_09603_gb300 import Solver, launch_count
+    from paper_2002_09603_gb300 import launch_count
 
     prob = make_problem(args.workload)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    s = Solver(prob)
-    s.assemble_condense()
-    s.setup_precond()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    setup_ms = e0.elapsed_time(e1)
+    n_mesh = WORKLOADS[args.workload]["n"]
+    peak, peak_kind = measured_peaks()
 
-    # warm-up: a full simulation prefix from the initial state
-    x = None
-    for _ in range(args.warmup):
-        b = s.build_rhs(x)
-        x, _ = s.solve(b, tol=TOL)
-
-    # timed: K steps of a fresh simulation, inputs resident in HBM
-    x = None
-    iters = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk, clk_path = clocks_start(local)
-    time.sleep(0.3)
-    l0 = launch_count()
-    s.timing(True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        b = s.build_rhs(x)
-        x, st = s.solve(b, tol=TOL)
-        iters.append(st["iterations"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = launch_count() - l0
-    ms = e0.elapsed_time(e1) / args.steps
-    clocks = clocks_stop(clk, clk_path)
-    kt = s.timing_read(0)
-    s.timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # FP64-plain form first (reported beside the headline), then the
+    # mixed form (FP32 V-cycles and Schur steps inside FP64 FGMRES)
+    r64, setup64 = None, None
+    if args.precision in ("both", "fp64"):
+        s64, setup64 = _solver(prob, 0, torch)
+        r64 = _timed_steps(s64, args, world, dist, torch, launch_count, args.precision == "fp64", local)
+        if args.precision == "fp64":
+            s, setup_ms, r32 = s64, setup64, r64
+        else:
+            s64.close()
+            del s64
+    if args.precision in ("both", "mixed"):
+        s, setup_ms = _solver(prob, 1, torch)
+        r32 = _timed_steps(s, args, world, dist, torch, launch_count, True, local)
+    ms = r32["ms"]
 
     # end to end through the C ABI with host buffers: the previous state comes
     # from pinned host memory and the solution goes back to it every step
@@ -315,33 +373,56 @@ def run_ours(args):
             e2e_ms = float(t.item())
         e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    peak, peak_kind = measured_peaks()
+    # roofline of the dominant kernel of the headline (mixed) form:
+    # k_cheb_u0<float>, HBM-bound
+    kt = r32["kt"]
     avg_ms = kt["total_ms"] / max(kt["launches"], 1)
-    achieved = kt["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9 if kt["launches"] else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None,
-                "traffic": traffic_for("k_cheb_u0"),
-                "kernel": "k_cheb_u0 (Chebyshev sweep, finest displacement level, 27-point 3x3-block stencil)",
-                "launches": kt["launches"], "avg_launch_us": avg_ms * 1e3,
-                "bytes_per_launch": kt["bytes_per_launch"], "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    gbs = kt["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9 if kt["launches"] else None
+    roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak if gbs else None,
+                "traffic": traffic_for("k_cheb_u0<float>") if args.workload == "lognormal64" else None,
+                "kernel": "k_cheb_u0<float> (Chebyshev sweep, finest displacement level, 27-point 3x3-block "
+                          "stencil, FP32)",
+                "launches": kt["launches"], "avg_launch_us": avg_ms * 1e3, "bytes_per_launch": kt["bytes_per_launch"],
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+    # the FP64-plain form's dominant kernel is bound by the FP64 pipe
+    k64 = (r64 or r32)["kt"]
+    avg64 = k64["total_ms"] / max(k64["launches"], 1)
+    sm_max = ((r32["clocks"] or {}).get("sm_max_mhz") or 2070.0)
+    fpk = fp64_peak_tflops(sm_max)
+    tf64 = cheb_u0_flops(n_mesh) / (avg64 * 1e-3) / 1e12 if k64["launches"] else None
+    roofline_fp64 = {"bound": "alu", "achieved": tf64, "peak": fpk, "unit": "TFLOP/s",
+                     "frac": tf64 / fpk if tf64 else None,
+                     "traffic": traffic_for("k_cheb_u0<double>") if args.workload == "lognormal64" else None,
+                     "kernel": "k_cheb_u0<double>", "avg_launch_us": avg64 * 1e3,
+                     "hbm_achieved_gbs": k64["bytes_per_launch"] / (avg64 * 1e-3) / 1e9 if k64["launches"] else None,
+                     "peak_source": "derived FP64 pipe peak: 152 SMs x 2 FMA/clk x 2 flop x max SM clock"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample_subprocess(s.n, statistics.mean(iters))
+        cpu = oracle_sample_subprocess(s.n, statistics.mean(r32["iters"]))
 
     nU, nP, nPi = s.sizes
     if rank == 0:
         line = {
             "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)",
+            "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
-                       "n_pi": nPi, "tol": TOL, "restart": 50, "iterations_per_step": iters,
-                       "setup_ms": setup_ms, "precision": "fp64 throughout",
-                       "l2": "inputs larger than L2 (A_uu alone is 534 MB)", "parallelism": "replicas",
+                       "n_pi": nPi, "tol": TOL, "restart": 50, "iterations_per_step": r32["iters"],
+                       "setup_ms": setup_ms, "precision": {"both": "FP32 V-cycles inside FP64 FGMRES",
+                                                           "mixed": "FP32 V-cycles inside FP64 FGMRES",
+                                                           "fp64": "FP64 throughout"}[args.precision],
+                       "fp64_plain": None if r64 is None else {
+                           "ms_per_step": r64["ms"], "iterations_per_step": r64["iters"], "setup_ms": setup64,
+                           "gpu_launches": r64["launches"]},
+                       "l2": "inputs larger than L2 (A_uu alone is 534 MB in FP64, 267 MB in FP32)",
+                       "parallelism": "replicas",
                        "hierarchy_u": s.hierarchy(0)["points"], "hierarchy_pi": s.hierarchy(1)["points"]},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "roofline": roofline, "roofline_fp64": roofline_fp64, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": r32["launches"], "clocks": r32["clocks"],
         }
         print(json.dumps(line), flush=True)
     s.close()

@@ -72,12 +72,16 @@ typedef struct {
 } mhfp_materials;
 
 typedef struct {
-  int restart;          /* FGMRES restart length m (default 50)                */
+  int restart;          /* FGMRES restart length m, 1..63 (default 50)         */
   int maxit;            /* maximum total FGMRES iterations (default 1000)      */
   int cheb_degree;      /* Chebyshev smoother degree (default 2)               */
   double cheb_ratio;    /* lmax / lmin of the smoother interval (default 10)   */
   int coarse_max;       /* coarsen while a level has more points (default 125) */
   int power_iters;      /* power iterations for rho(D^-1 A) (default 15)       */
+  int precision;        /* 0: FP64 preconditioner (default); 1: FP32 V-cycles  */
+                        /* and Schur steps inside the FP64 FGMRES (residuals,  */
+                        /* Gram-Schmidt, Hessenberg and the coarsest dense     */
+                        /* solve stay FP64)                                    */
 } mhfp_options;
 
 typedef struct {

@@ -110,6 +110,7 @@ __device__ __forceinline__ void spmv_body(const Lat& L, const T* __restrict__ va
   for (int r = 0; r < BS; ++r) y[BS * p + r] = b ? b[BS * p + r] - acc[r] : acc[r];
 }
 
+// <hot:k_cheb_u0> (bench.py hashes this region to tell whether profiles/traffic.json still applies)
 // Chebyshev step: r = b - A xin (r = b when xin is null), d = cd d + cr D^-1 r,
 // xout = xin + d.
 template <int BS, int KIND, typename T>
@@ -171,6 +172,116 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
                                                  T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
   cheb_body<3, ST_BOX1, T>(L, val, dinv, b, xin, xout, d, cd, cr);
 }
+// </hot:k_cheb_u0>
+
+// Coarse lattices have few points, so one thread per point leaves most of the
+// GPU idle behind long serial loops over 27-125 offsets.  These variants give
+// each point a group of TPP consecutive lanes that split the offsets and
+// combine their partial sums with a fixed-order xor shuffle (deterministic).
+template <int BS, int KIND, int TPP, typename T>
+__device__ __forceinline__ void group_residual(const Lat& L, long long p, bool valid, int sub,
+                                               const T* __restrict__ val, const T* __restrict__ x,
+                                               const T* __restrict__ b, T r[BS]) {
+#pragma unroll
+  for (int q = 0; q < BS; ++q) r[q] = T(0);
+  if (valid && x) {
+    int i, j, k;
+    L.ijk(p, i, j, k);
+    for (int o = sub; o < St<KIND>::N; o += TPP) {
+      int dx, dy, dz;
+      St<KIND>::off(o, dx, dy, dz);
+      if (!L.in(i + dx, j + dy, k + dz)) continue;
+      const long long q = p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
+      const T* v = val + (long long)o * BS * BS * L.N + p;
+#pragma unroll
+      for (int a = 0; a < BS; ++a)
+#pragma unroll
+        for (int s = 0; s < BS; ++s) r[a] -= v[(long long)(a * BS + s) * L.N] * x[BS * q + s];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+#pragma unroll
+    for (int m = TPP / 2; m > 0; m >>= 1) r[a] += __shfl_xor_sync(0xffffffffu, r[a], m);
+    if (valid && b) r[a] += b[BS * p + a];
+  }
+}
+
+// y = b - A x (b may be null: y = -A x is not used; callers pass b or want A x)
+template <int BS, int KIND, int TPP, typename T>
+__global__ void __launch_bounds__(256) k_spmv_g(Lat L, const T* __restrict__ val, const T* __restrict__ x,
+                                                const T* __restrict__ b, T* __restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long p = t / TPP;
+  const int sub = (int)(t % TPP);
+  const bool valid = p < L.N;
+  T r[BS];
+  group_residual<BS, KIND, TPP, T>(L, valid ? p : 0, valid, sub, val, x, b, r);
+  if (valid && sub == 0) {
+#pragma unroll
+    for (int a = 0; a < BS; ++a) y[BS * p + a] = b ? r[a] : -r[a];
+  }
+}
+
+template <int BS, int KIND, int TPP, typename T>
+__global__ void __launch_bounds__(256) k_cheb_g(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
+                                                const T* __restrict__ b, const T* __restrict__ xin,
+                                                T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long p = t / TPP;
+  const int sub = (int)(t % TPP);
+  const bool valid = p < L.N;
+  T r[BS];
+  group_residual<BS, KIND, TPP, T>(L, valid ? p : 0, valid, sub, val, xin, b, r);
+  if (valid && sub == 0) {
+#pragma unroll
+    for (int a = 0; a < BS; ++a) {
+      T z = T(0);
+#pragma unroll
+      for (int s = 0; s < BS; ++s) z += dinv[(long long)(a * BS + s) * L.N + p] * r[s];
+      const T dn = (cd != T(0)) ? cd * d[BS * p + a] + cr * z : cr * z;
+      d[BS * p + a] = dn;
+      xout[BS * p + a] = (xin ? xin[BS * p + a] : T(0)) + dn;
+    }
+  }
+}
+
+// restriction b_c = P^T r with one warp per coarse point; the lanes split
+// the (3 + 2R)^3 support box and reduce in a fixed order
+template <int BS, typename T>
+__global__ void __launch_bounds__(256) k_restrict_w(Lat F, Lat Cc, int R, const T* __restrict__ P,
+                                                    const T* __restrict__ r, T* __restrict__ bc) {
+  const long long J = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const bool valid = J < Cc.N;
+  int I = 0, Jj = 0, K = 0;
+  if (valid) Cc.ijk(J, I, Jj, K);
+  const int ns = p_slots(R);
+  const int w = 3 + 2 * R;
+  T acc[BS];
+#pragma unroll
+  for (int q = 0; q < BS; ++q) acc[q] = T(0);
+  if (valid) {
+    for (int e = lane; e < w * w * w; e += 32) {
+      const int a = 3 * I - R + e % w, b = 3 * Jj - R + (e / w) % w, c = 3 * K - R + e / (w * w);
+      if (!F.in(a, b, c)) continue;
+      const int sx = I - p_lo(a, R), sy = Jj - p_lo(b, R), sz = K - p_lo(c, R);
+      if (sx < 0 || sx >= ns || sy < 0 || sy >= ns || sz < 0 || sz >= ns) continue;
+      const long long p = F.id(a, b, c);
+      const T* pv = P + (long long)(sx + ns * (sy + ns * sz)) * BS * BS * F.N + p;
+#pragma unroll
+      for (int q = 0; q < BS; ++q)
+#pragma unroll
+        for (int t = 0; t < BS; ++t) acc[q] += pv[(long long)(t * BS + q) * F.N] * r[BS * p + t];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < BS; ++q) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], m);
+    if (valid && lane == 0) bc[BS * J + q] = acc[q];
+  }
+}
 
 // face level (ELL, 11 slots) versions
 template <typename T>
@@ -198,44 +309,6 @@ __global__ void k_cheb_ell(long long n, const int* __restrict__ col, const T* __
   const T dn = (cd != T(0)) ? cd * d[f] + cr * dinv[f] * r : cr * dinv[f] * r;
   d[f] = dn;
   xout[f] = (xin ? xin[f] : T(0)) + dn;
-}
-
-// restriction b_c = P^T r (gather over the support box of each coarse point)
-template <int BS, typename T>
-__global__ void k_restrict(Lat F, Lat Cc, int R, const T* __restrict__ P, const T* __restrict__ r,
-                           T* __restrict__ bc) {
-  const long long J = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (J >= Cc.N) return;
-  int I, Jj, K;
-  Cc.ijk(J, I, Jj, K);
-  const int ns = p_slots(R);
-  T acc[BS];
-#pragma unroll
-  for (int q = 0; q < BS; ++q) acc[q] = T(0);
-  for (int c = 3 * K - R; c <= 3 * K + 2 + R; ++c) {
-    if (c < 0 || c >= F.Lz) continue;
-    const int sz = K - p_lo(c, R);
-    if (sz < 0 || sz >= ns) continue;
-    for (int b = 3 * Jj - R; b <= 3 * Jj + 2 + R; ++b) {
-      if (b < 0 || b >= F.Ly) continue;
-      const int sy = Jj - p_lo(b, R);
-      if (sy < 0 || sy >= ns) continue;
-      for (int a = 3 * I - R; a <= 3 * I + 2 + R; ++a) {
-        if (a < 0 || a >= F.Lx) continue;
-        const int sx = I - p_lo(a, R);
-        if (sx < 0 || sx >= ns) continue;
-        const long long p = F.id(a, b, c);
-        const int s = sx + ns * (sy + ns * sz);
-        const T* pv = P + (long long)s * BS * BS * F.N + p;
-#pragma unroll
-        for (int q = 0; q < BS; ++q)
-#pragma unroll
-          for (int t = 0; t < BS; ++t) acc[q] += pv[(long long)(t * BS + q) * F.N] * r[BS * p + t];
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < BS; ++q) bc[BS * J + q] = acc[q];
 }
 
 // prolongation x += P x_c
@@ -331,16 +404,22 @@ __global__ void k_prolong_faces(FaceTopo d, const T* __restrict__ pw, const T* _
   x[f] += pw[f] * s;
 }
 
-// dense coarsest solve y = Ainv b (warp per row)
+// dense coarsest solve y = Ainv b (warp per row); the inverse and the sums
+// stay FP64 whatever the precision of the cycle's vectors
 template <typename T>
-__global__ void k_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ y) {
+__global__ void k_dense_mv(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ y) {
   const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  T s = T(0);
-  for (int c = lane; c < n; c += 32) s += Ainv[(long long)row * n + c] * b[c];
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += Ainv[(long long)row * n + c] * (double)b[c];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = s;
+  if (lane == 0) y[row] = (T)s;
+}
+
+__global__ void k_cast_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
 }
 
 // ------------------------------------------------------------------ setup
@@ -588,14 +667,41 @@ void dispatch_bs(int bs, F&& f) {
 
 FaceTopo face_topo(const Ctx& c) { return FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy}; }
 
+// lanes per lattice point: 1 on large levels, up to a warp on small ones
+int group_size(long long npts, int kind) {
+  if (npts >= 131072) return 1;
+  if (npts >= 32768) return 4;
+  return kind == ST_BOX2 ? 32 : 16;
+}
+
+template <class F>
+void dispatch_tpp(int tpp, F&& f) {
+  if (tpp == 1) f(std::integral_constant<int, 1>{});
+  else if (tpp == 4) f(std::integral_constant<int, 4>{});
+  else if (tpp == 16) f(std::integral_constant<int, 16>{});
+  else f(std::integral_constant<int, 32>{});
+}
+
 void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
   if (L.faces) {
     k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, x, b, y);
   } else {
     const Lat lat = lat_of(L.A);
+    const int tpp = group_size(lat.N, L.A.kind);
     dispatch_bs(L.bs, [&](auto BS) {
       dispatch_kind(L.A.kind, [&](auto K) {
-        k_spmv<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, y);
+        if (tpp == 1) {
+          k_spmv<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, y);
+        } else {
+          dispatch_tpp(tpp, [&](auto G) {
+            if (b) {
+              k_spmv_g<BS.value, K.value, G.value, double><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
+                  lat, L.A.val, x, b, y);
+            } else {
+              k_spmv<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, y);
+            }
+          });
+        }
       });
     });
   }
@@ -839,20 +945,56 @@ void build_pi(Ctx& c) {
 }
 
 // ------------------------------------------------------------------ V-cycle
-struct ChebCoef {
-  double theta, delta, sigma;
+// Pointers of one level in the precision T of the cycle: the FP64 arrays
+// built by the set-up, or their FP32 copies for the mixed-precision cycle.
+template <typename T>
+struct LV {
+  const T *val, *dinv, *P, *ell, *pw;
+  T *r, *d, *y;
 };
+LV<double> view(Ctx& c, Level& L, double) { return {L.A.val, L.dinv, L.P, c.Cpi, c.pw, L.r, L.d, L.y}; }
+LV<float> view(Ctx& c, Level& L, float) { return {L.valf, L.dinvf, L.Pf, c.Cpif, c.pwf, L.rf, L.df, L.yf}; }
+double* bvec(Level& L, double) { return L.b; }
+float* bvec(Level& L, float) { return L.bf; }
+double* xvec(Level& L, double) { return L.x; }
+float* xvec(Level& L, float) { return L.xf; }
 
-void smooth(Ctx& c, std::vector<Level>& H, int l, const double* b, double*& x, double* other, bool from_zero,
-            bool time_it) {
+template <typename T>
+void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
+  const LV<T> v = view(c, L, T());
+  if (L.faces) {
+    k_spmv_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, x, b, y);
+  } else {
+    const Lat lat = lat_of(L.A);
+    const int tpp = b ? group_size(lat.N, L.A.kind) : 1;
+    dispatch_bs(L.bs, [&](auto BS) {
+      dispatch_kind(L.A.kind, [&](auto K) {
+        if (tpp == 1) {
+          k_spmv<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, y);
+        } else {
+          dispatch_tpp(tpp, [&](auto G) {
+            k_spmv_g<BS.value, K.value, G.value, T><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
+                lat, v.val, x, b, y);
+          });
+        }
+      });
+    });
+  }
+  MHFP_LAUNCH_CHECK();
+}
+
+template <typename T>
+void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_zero, bool time_it) {
   Level& L = H[l];
+  const LV<T> v = view(c, L, T());
+  T* other = v.y;
   const double lmax = L.lmax, lmin = lmax / c.opt.cheb_ratio;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
   // ping-pong so that the last step writes x (each step reads neighbours of
   // its input, so it cannot update in place)
-  const double* xin = from_zero ? nullptr : x;
-  double* out = (from_zero && c.opt.cheb_degree % 2 == 1) ? x : other;
+  const T* xin = from_zero ? nullptr : x;
+  T* out = (from_zero && c.opt.cheb_degree % 2 == 1) ? x : other;
   for (int s = 0; s < c.opt.cheb_degree; ++s) {
     double cd = 0.0, cr = 1.0 / theta;
     if (s > 0) {
@@ -863,73 +1005,107 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const double* b, double*& x, d
     }
     if (time_it && xin) timing_begin(c, 0);
     if (L.faces) {
-      k_cheb_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, L.dinv, b, xin, out, L.d,
-                                                                  cd, cr);
+      k_cheb_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, v.dinv, b, xin, out, v.d, (T)cd,
+                                                             (T)cr);
     } else if (time_it) {
       const Lat lat = lat_of(L.A);
-      k_cheb_u0<double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, L.dinv, b, xin, out, L.d, cd, cr);
+      k_cheb_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
     } else {
       const Lat lat = lat_of(L.A);
+      const int tpp = group_size(lat.N, L.A.kind);
       dispatch_bs(L.bs, [&](auto BS) {
         dispatch_kind(L.A.kind, [&](auto K) {
-          k_cheb<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, L.dinv, b, xin,
-                                                                                         out, L.d, cd, cr);
+          if (tpp == 1) {
+            k_cheb<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out,
+                                                                                      v.d, (T)cd, (T)cr);
+          } else {
+            dispatch_tpp(tpp, [&](auto G) {
+              k_cheb_g<BS.value, K.value, G.value, T><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
+                  lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
+            });
+          }
         });
       });
     }
     MHFP_LAUNCH_CHECK();
     // algorithmic bytes of a Chebyshev sweep: 27 x 9 matrix values and the
     // 3x3 inverse diagonal per node, b, x_in, x_out and d read/written
-    if (time_it && xin) timing_end(c, 0, (27.0 * 9 + 9) * 8 * L.npts + 5.0 * 8 * L.n);
-    // next step reads what this one wrote
+    if (time_it && xin) timing_end(c, 0, (27.0 * 9 + 9) * sizeof(T) * L.npts + 5.0 * sizeof(T) * L.n);
     xin = out;
     out = (out == x) ? other : x;
   }
-  // result is in xin
-  if (xin != x) {
-    MHFP_CUDA(cudaMemcpyAsync(x, xin, L.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-  }
+  if (xin != x) MHFP_CUDA(cudaMemcpyAsync(x, xin, L.n * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
 }
 
-void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const double* b, double* x) {
+template <typename T>
+void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   Level& L = H[l];
+  const LV<T> v = view(c, L, T());
   if (L.dense_inv) {
     const int n = (int)L.n;
-    k_dense_mv<double><<<grid_for(n, 8), 256, 0, c.stream>>>(n, L.dense_inv, b, x);
+    k_dense_mv<T><<<grid_for(n, 8), 256, 0, c.stream>>>(n, L.dense_inv, b, x);
     MHFP_LAUNCH_CHECK();
     return;
   }
   const bool fine_u = (&H == &c.hu) && l == 0;
-  smooth(c, H, l, b, x, L.y, true, fine_u);
-  // residual
+  smooth<T>(c, H, l, b, x, true, fine_u);
   if (fine_u) {
     const Lat lat = lat_of(L.A);
-    k_resid_u0<double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, L.r);
+    k_resid_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, v.r);
     MHFP_LAUNCH_CHECK();
   } else {
-    level_spmv(c, L, x, b, L.r);
+    level_spmv_t<T>(c, L, x, b, v.r);
   }
   Level& C = H[l + 1];
+  T* cb = bvec(C, T());
+  T* cx = xvec(C, T());
   if (L.faces) {
-    k_restrict_faces<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(face_topo(c), c.pw, L.r, C.b);
+    k_restrict_faces<T><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb);
   } else {
     const Lat F = lat_of(L.A), Cc = lat_of(C.A);
     dispatch_bs(L.bs, [&](auto BS) {
-      k_restrict<BS.value, double><<<grid_for(Cc.N, 128), 128, 0, c.stream>>>(F, Cc, L.R, L.P, L.r, C.b);
+      k_restrict_w<BS.value, T><<<grid_for(Cc.N * 32, 256), 256, 0, c.stream>>>(F, Cc, L.R, v.P, v.r, cb);
     });
   }
   MHFP_LAUNCH_CHECK();
-  vcycle_level(c, H, l + 1, C.b, C.x);
+  vcycle_level<T>(c, H, l + 1, cb, cx);
   if (L.faces) {
-    k_prolong_faces<double><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(face_topo(c), c.pw, C.x, x);
+    k_prolong_faces<T><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, x);
   } else {
     const Lat F = lat_of(L.A), Cc = lat_of(C.A);
     dispatch_bs(L.bs, [&](auto BS) {
-      k_prolong<BS.value, double><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, L.R, L.P, C.x, x);
+      k_prolong<BS.value, T><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, L.R, v.P, cx, x);
     });
   }
   MHFP_LAUNCH_CHECK();
-  smooth(c, H, l, b, x, L.y, false, fine_u);
+  smooth<T>(c, H, l, b, x, false, fine_u);
+}
+
+float* cast_copy(Ctx& c, const double* src, size_t n) {
+  float* d = dalloc_n<float>(c, n);
+  k_cast_f32<<<grid_for((long long)n, 256), 256, 0, c.stream>>>((long long)n, src, d);
+  MHFP_LAUNCH_CHECK();
+  return d;
+}
+
+// FP32 copies of a hierarchy built in FP64 (the last level keeps its FP64
+// dense inverse)
+void make_fp32(Ctx& c, std::vector<Level>& H) {
+  for (size_t l = 0; l < H.size(); ++l) {
+    Level& L = H[l];
+    const size_t bs2 = (size_t)L.bs * L.bs;
+    if (!L.faces) L.valf = cast_copy(c, L.A.val, (size_t)L.A.noff() * bs2 * L.A.N);
+    if (L.dinv) L.dinvf = cast_copy(c, L.dinv, bs2 * L.npts);
+    if (L.P) {
+      const int ns = p_slots(L.R);
+      L.Pf = cast_copy(c, L.P, (size_t)ns * ns * ns * bs2 * L.npts);
+    }
+    L.xf = dalloc_n<float>(c, L.n);
+    L.bf = dalloc_n<float>(c, L.n);
+    L.rf = dalloc_n<float>(c, L.n);
+    L.df = dalloc_n<float>(c, L.n);
+    L.yf = dalloc_n<float>(c, L.n);
+  }
 }
 
 }  // namespace
@@ -937,18 +1113,19 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const double* b, double*
 void build_hierarchies(Ctx& c) {
   build_u(c);
   build_pi(c);
+  if (c.opt.precision == 1) {
+    make_fp32(c, c.hu);
+    make_fp32(c, c.hpi);
+    c.Cpif = cast_copy(c, c.Cpi, (size_t)11 * c.nF);
+    c.pwf = cast_copy(c, c.pw, c.nF);
+  }
 }
 
-void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x) { vcycle_level(c, H, 0, b, x); }
+void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x) { vcycle_level<double>(c, H, 0, b, x); }
+void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x) { vcycle_level<float>(c, H, 0, b, x); }
 
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y) {
-  Level& L = H[l];
-  if (L.faces) {
-    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, x, nullptr, y);
-    MHFP_LAUNCH_CHECK();
-  } else {
-    level_spmv(c, L, x, nullptr, y);
-  }
+  level_spmv_t<double>(c, H[l], x, nullptr, y);
 }
 
 }  // namespace mhfp

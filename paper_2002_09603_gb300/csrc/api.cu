@@ -105,6 +105,7 @@ void mhfp_default_options(mhfp_options* o) {
   o->cheb_ratio = 10.0;
   o->coarse_max = 125;
   o->power_iters = 15;
+  o->precision = 0;
 }
 
 const char* mhfp_status_string(mhfp_status s) {
@@ -197,13 +198,15 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
     if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
     if (c.prepared) throw Error{MHFP_ERR_STATE, "preconditioner already set up"};
     if (opt) {
-      if (opt->restart < 1 || opt->restart > 200 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
-          !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1)
+      if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
+          !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
+          (opt->precision != 0 && opt->precision != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }
     mhfp::build_preconditioner_blocks(c);
     mhfp::build_hierarchies(c);
+    if (c.opt.precision == 1) mhfp::make_fp32_blocks(c);
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
     c.prepared = true;
   });

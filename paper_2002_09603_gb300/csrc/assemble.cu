@@ -639,23 +639,26 @@ __global__ void k_apply_pi(Dims d, const double* __restrict__ ApPi, const int* _
 }
 
 // preconditioner pieces: z_p = B~^-1 (v_p - dt A_ppi z_pi), t_u = v_u - A_up z_p
-__global__ void k_prec_p(Dims d, const double* __restrict__ ApPi, const double* __restrict__ btilde, double dt,
-                         const double* __restrict__ vp, const double* __restrict__ zpi, double* __restrict__ zp) {
+// (FP64, or FP32 in the mixed-precision preconditioner)
+template <typename R>
+__global__ void k_prec_p(Dims d, const R* __restrict__ ApPi, const R* __restrict__ btilde, R dt,
+                         const R* __restrict__ vp, const R* __restrict__ zpi, R* __restrict__ zp) {
   const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= d.nT) return;
   const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
-  double c = 0.0;
+  R c = R(0);
   for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * zpi[cell_face(d, i, j, k, lf)];
   zp[T] = (vp[T] - dt * c) / btilde[T];
 }
 
-__global__ void k_prec_u(Dims d, const double* __restrict__ Aup, const double* __restrict__ vu,
-                         const double* __restrict__ zp, double* __restrict__ tu) {
+template <typename R>
+__global__ void k_prec_u(Dims d, const R* __restrict__ Aup, const R* __restrict__ vu,
+                         const R* __restrict__ zp, R* __restrict__ tu) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.nN) return;
   const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
             nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
-  double y0 = 0, y1 = 0, y2 = 0;
+  R y0 = R(0), y1 = R(0), y2 = R(0);
   for (int cz = nk - 1; cz <= nk; ++cz) {
     if (cz < 0 || cz >= d.nz) continue;
     for (int cy = nj - 1; cy <= nj; ++cy) {
@@ -664,7 +667,7 @@ __global__ void k_prec_u(Dims d, const double* __restrict__ Aup, const double* _
         if (cx < 0 || cx >= d.nx) continue;
         const long long T = cell_id(d, cx, cy, cz);
         const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
-        const double p = zp[T];
+        const R p = zp[T];
         y0 += Aup[(long long)(3 * a) * d.nT + T] * p;
         y1 += Aup[(long long)(3 * a + 1) * d.nT + T] * p;
         y2 += Aup[(long long)(3 * a + 2) * d.nT + T] * p;
@@ -766,14 +769,46 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
 
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp) {
   const Dims d = dims_of(c);
-  k_prec_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.ApPi, c.btilde, c.dt, vp, zpi, zp);
+  k_prec_p<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.ApPi, c.btilde, c.dt, vp, zpi, zp);
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu) {
   const Dims d = dims_of(c);
-  k_prec_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aup, vu, zp, tu);
+  k_prec_u<double><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aup, vu, zp, tu);
   MHFP_LAUNCH_CHECK();
+}
+
+void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp) {
+  const Dims d = dims_of(c);
+  k_prec_p<float><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.ApPif, c.btildef, (float)c.dt, vp, zpi, zp);
+  MHFP_LAUNCH_CHECK();
+}
+
+void precond_u_rhs(Ctx& c, const float* vu, const float* zp, float* tu) {
+  const Dims d = dims_of(c);
+  k_prec_u<float><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aupf, vu, zp, tu);
+  MHFP_LAUNCH_CHECK();
+}
+
+__global__ void k_cast_blocks(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+// FP32 copies of the blocks the mixed-precision preconditioner reads
+void make_fp32_blocks(Ctx& c) {
+  auto cast = [&](const double* src, long long n) {
+    float* d = dalloc_n<float>(c, n);
+    k_cast_blocks<<<grid_for(n, 256), 256, 0, c.stream>>>(n, src, d);
+    MHFP_LAUNCH_CHECK();
+    return d;
+  };
+  c.ApPif = cast(c.ApPi, 6 * c.nT);
+  c.btildef = cast(c.btilde, c.nT);
+  c.Aupf = cast(c.Aup, 24 * c.nT);
+  c.tf = dalloc_n<float>(c, c.n);
+  c.zf = dalloc_n<float>(c, c.n);
 }
 
 }  // namespace mhfp

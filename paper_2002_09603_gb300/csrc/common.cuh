@@ -127,6 +127,9 @@ struct Level {
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *y = nullptr;
   // last level: dense inverse (n x n, row-major)
   double* dense_inv = nullptr;
+  // FP32 copies for the mixed-precision cycle (precision == 1)
+  float *valf = nullptr, *dinvf = nullptr, *Pf = nullptr;
+  float *xf = nullptr, *bf = nullptr, *rf = nullptr, *df = nullptr, *yf = nullptr;
 };
 
 // ------------------------------------------------------------ handle
@@ -175,12 +178,16 @@ struct Ctx {
   double* ds = nullptr;     // [n] equilibration D_s
 
   std::vector<Level> hu, hpi;
+  // FP32 copies used by the mixed-precision preconditioner
+  float *Cpif = nullptr, *pwf = nullptr, *ApPif = nullptr, *btildef = nullptr, *Aupf = nullptr;
+  float *tf = nullptr, *zf = nullptr;
 
   // Krylov workspace
   int m_alloc = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *tmp = nullptr;
   double *h = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
          *partials = nullptr, *scal = nullptr;
+  int* dflag = nullptr;  // DGKS decision of the current Arnoldi step
   double* host_scal = nullptr;  // pinned
   int npart = 0;
 
@@ -205,11 +212,15 @@ void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs);
 void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub);
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp);
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu);
+void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp);
+void precond_u_rhs(Ctx& c, const float* vu, const float* zp, float* tu);
+void make_fp32_blocks(Ctx& c);
 void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out);
 
 // amg.cu
 void build_hierarchies(Ctx& c);
 void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x);
+void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x);
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y);
 
 // krylov.cu

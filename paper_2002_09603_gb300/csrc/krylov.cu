@@ -13,9 +13,8 @@ namespace mhfp {
 
 namespace {
 
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs
 constexpr int RED_THREADS = 256;
-constexpr int DOT_COLS = 8;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -29,27 +28,50 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;  // valid in thread 0
 }
 
-// partials[col * gridDim.x + block] = sum over this block's rows of V[:,col] . w
-__global__ void __launch_bounds__(RED_THREADS) k_dot_partials(long long n, const double* __restrict__ V, int ncols,
-                                                               const double* __restrict__ w,
-                                                               double* __restrict__ partials) {
+// Gram-Schmidt kernels.  On GB300 the FP64 pipe (about 2 FMA per clock per
+// SM) bounds these passes, so they are written for occupancy: few registers
+// per thread, many rows in flight, independent FMA chains.
+constexpr int GS_BLOCKS = 1216;   // 8 x 152 SMs
+constexpr int GS_COLS = 4;        // columns per block in the dot kernel
+
+// partials[c][block] = sum over this block's rows of V[:,c] . w for the
+// GS_COLS columns of blockIdx.y; block column 0 also sums w . w into slot
+// `ncols` when with_norm.  Skipped entirely when skip && *skip.
+__global__ void __launch_bounds__(RED_THREADS) k_gs_dots(long long n, const double* __restrict__ V, int ncols,
+                                                          const double* __restrict__ w, double* __restrict__ partials,
+                                                          const int* __restrict__ skip, int with_norm) {
+  if (skip && *skip) return;
   __shared__ double sh[RED_THREADS / 32];
-  const int c0 = blockIdx.y * DOT_COLS;
-  double acc[DOT_COLS];
+  const int c0 = blockIdx.y * GS_COLS;
+  const bool do_norm = with_norm && blockIdx.y == 0;
+  double acc[GS_COLS], nw = 0.0;
 #pragma unroll
-  for (int q = 0; q < DOT_COLS; ++q) acc[q] = 0.0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+  for (int q = 0; q < GS_COLS; ++q) acc[q] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+#pragma unroll 2
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     const double wr = w[r];
 #pragma unroll
-    for (int q = 0; q < DOT_COLS; ++q)
+    for (int q = 0; q < GS_COLS; ++q)
       if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * n + r] * wr;
+    if (do_norm) nw += wr * wr;
   }
 #pragma unroll
-  for (int q = 0; q < DOT_COLS; ++q) {
-    const double s = block_sum(acc[q], sh);
-    if (threadIdx.x == 0 && c0 + q < ncols) partials[(long long)(c0 + q) * gridDim.x + blockIdx.x] = s;
+  for (int q = 0; q < GS_COLS; ++q) {
+    const double t = block_sum(acc[q], sh);
+    if (threadIdx.x == 0 && c0 + q < ncols) partials[(long long)(c0 + q) * gridDim.x + blockIdx.x] = t;
+  }
+  if (do_norm) {
+    const double t = block_sum(nw, sh);
+    if (threadIdx.x == 0) partials[(long long)ncols * gridDim.x + blockIdx.x] = t;
   }
 }
+
+// same reduction, skipped when *skip != 0
+__global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partials, double* __restrict__ out,
+                                       const int* __restrict__ skip);
+
+__global__ void k_move(const double* __restrict__ src, double* __restrict__ dst) { dst[0] = src[0]; }
 
 // out[col] (+)= sum_b partials[col * nb + b] in a fixed order
 __global__ void k_reduce_partials(int nb, const double* __restrict__ partials, double* __restrict__ out, int accumulate) {
@@ -60,17 +82,38 @@ __global__ void k_reduce_partials(int nb, const double* __restrict__ partials, d
   if (threadIdx.x == 0) out[blockIdx.x] = accumulate ? out[blockIdx.x] + s : s;
 }
 
-// w -= V h; optionally partial sums of the updated w squared
+__global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partials, double* __restrict__ out,
+                                       const int* __restrict__ skip) {
+  if (*skip) return;
+  __shared__ double sh[RED_THREADS / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[(long long)blockIdx.x * nb + b];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// w -= V h (four independent FMA chains per row); partial sums of the
+// updated w . w into partials[block] when partials is given
 __global__ void __launch_bounds__(RED_THREADS) k_gemv_sub(long long n, const double* __restrict__ V, int ncols,
                                                            const double* __restrict__ h, double* __restrict__ w,
-                                                           double* __restrict__ partials) {
+                                                           double* __restrict__ partials,
+                                                           const int* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ double sh[RED_THREADS / 32];
   double acc = 0.0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    double s = w[r];
-    for (int c = 0; c < ncols; ++c) s -= V[(long long)c * n + r] * h[c];
-    w[r] = s;
-    acc += s * s;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int c = 0;
+    for (; c + 3 < ncols; c += 4) {
+      s0 += V[(long long)c * n + r] * h[c];
+      s1 += V[(long long)(c + 1) * n + r] * h[c + 1];
+      s2 += V[(long long)(c + 2) * n + r] * h[c + 2];
+      s3 += V[(long long)(c + 3) * n + r] * h[c + 3];
+    }
+    for (; c < ncols; ++c) s0 += V[(long long)c * n + r] * h[c];
+    const double v = w[r] - ((s0 + s1) + (s2 + s3));
+    w[r] = v;
+    acc += v * v;
   }
   if (partials) {
     const double t = block_sum(acc, sh);
@@ -113,6 +156,24 @@ __global__ void k_ewise(long long n, const double* __restrict__ x, const double*
                         double* __restrict__ y) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) y[r] = divide ? x[r] / s[r] : x[r] * s[r];
+}
+
+// DGKS test (Daniel, Gragg, Kaufman & Stewart, 1976): after one classical
+// Gram-Schmidt projection, reorthogonalise only if the norm fell below
+// 1/sqrt(2) of its value before the projection.  nrm[0] = ||w||^2 before,
+// nrm[1] = ||w||^2 after.  flag = 1 means "skip the second projection";
+// when it is skipped h2 is zeroed and the norm after the first pass is
+// carried into nrm[2], which the second pass overwrites otherwise.
+__global__ void k_dgks(int ncols, const double* __restrict__ nrm, int* __restrict__ flag, double* __restrict__ h2,
+                       double* __restrict__ nrm_final) {
+  const int i = threadIdx.x;
+  const bool skip = nrm[1] > 0.5 * nrm[0];
+  if (i == 0) {
+    *flag = skip ? 1 : 0;
+    if (skip) nrm_final[0] = nrm[1];
+  }
+  if (skip)
+    for (int c = i; c < ncols; c += blockDim.x) h2[c] = 0.0;
 }
 
 // One Arnoldi step's Hessenberg column: h = h1 + h2 (j+1 entries), the new
@@ -175,20 +236,32 @@ void ensure_workspace(Ctx& c) {
   c.sn = dalloc_n<double>(c, m);
   c.g = dalloc_n<double>(c, m + 1);
   c.yv = dalloc_n<double>(c, m);
-  c.npart = RED_BLOCKS;
-  c.partials = dalloc_n<double>(c, (size_t)(m + 1) * RED_BLOCKS);
+  c.npart = GS_BLOCKS;
+  c.partials = dalloc_n<double>(c, (size_t)(m + 2) * GS_BLOCKS);
   c.scal = dalloc_n<double>(c, 8);
+  c.dflag = dalloc_n<int>(c, 4);
   if (!c.host_scal) MHFP_CUDA(cudaMallocHost(&c.host_scal, 8 * sizeof(double)));
   c.m_alloc = m;
 }
 
-// h[0..ncols) = V[:, 0..ncols)^T w
-void multi_dot(Ctx& c, const double* V, int ncols, const double* w, double* h) {
-  dim3 grid(RED_BLOCKS, (ncols + DOT_COLS - 1) / DOT_COLS);
-  k_dot_partials<<<grid, RED_THREADS, 0, c.stream>>>(c.n, V, ncols, w, c.partials);
+// hout[0..ncols) = V^T w; with nrm2 non-null also ||w||^2 into nrm2[0];
+// with skip non-null nothing happens when *skip != 0
+void gs_dots(Ctx& c, int ncols, double* hout, double* nrm2, const int* skip) {
+  const int wn = nrm2 ? 1 : 0;
+  dim3 grid(GS_BLOCKS, (ncols + GS_COLS - 1) / GS_COLS);
+  k_gs_dots<<<grid, RED_THREADS, 0, c.stream>>>(c.n, c.V, ncols, c.w, c.partials, skip, wn);
   MHFP_LAUNCH_CHECK();
-  k_reduce_partials<<<ncols, RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials, h, 0);
+  if (skip) {
+    k_reduce_partials_flag<<<ncols, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials, hout, skip);
+  } else {
+    k_reduce_partials<<<ncols + wn, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials, hout, 0);
+  }
   MHFP_LAUNCH_CHECK();
+  if (nrm2) {
+    // the norm sits after the ncols dot products; move it to its slot
+    k_move<<<1, 1, 0, c.stream>>>(hout + ncols, nrm2);
+    MHFP_LAUNCH_CHECK();
+  }
 }
 
 // norm^2 into dst (device)
@@ -218,7 +291,42 @@ void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y,
   MHFP_LAUNCH_CHECK();
 }
 
+__global__ void k_to_f32(long long n, const double* __restrict__ x, const double* __restrict__ div,
+                         float* __restrict__ y) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) y[r] = (float)(div ? x[r] / div[r] : x[r]);
+}
+
+__global__ void k_to_f64(long long n, const float* __restrict__ x, double* __restrict__ y) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) y[r] = (double)x[r];
+}
+
+// z = M^-1 (v / div) with the FP32 V-cycles and Schur steps; v, z FP64
+void apply_precond_mixed(Ctx& c, const double* v, const double* div, double* z) {
+  const long long n = c.n;
+  k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, div, c.tf);
+  MHFP_LAUNCH_CHECK();
+  const float* tu = c.tf;
+  const float* tp = c.tf + c.nU;
+  const float* tpi = tp + c.nT;
+  float* zu = c.zf;
+  float* zp = c.zf + c.nU;
+  float* zpi = zp + c.nT;
+  vcycle(c, c.hpi, tpi, zpi);
+  precond_p_step(c, tp, zpi, zp);
+  float* ru = c.hu[0].bf;  // free at the fine level
+  precond_u_rhs(c, tu, zp, ru);
+  vcycle(c, c.hu, (const float*)ru, zu);
+  k_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.zf, z);
+  MHFP_LAUNCH_CHECK();
+}
+
 void apply_precond(Ctx& c, const double* v, double* z) {
+  if (c.opt.precision == 1) {
+    apply_precond_mixed(c, v, nullptr, z);
+    return;
+  }
   const double* vu = v;
   const double* vp = v + c.nU;
   const double* vpi = vp + c.nT;
@@ -265,19 +373,33 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
     for (int j = 0; j < m; ++j) {
       double* vj = c.V + (long long)j * n;
       double* zj = c.Z + (long long)j * n;
-      vec_scale(c, vj, c.ds, true, c.t, n);  // unscale into the preconditioner
-      apply_precond(c, c.t, zj);
+      if (c.opt.precision == 1) {
+        apply_precond_mixed(c, vj, c.ds, zj);  // unscale into the FP32 preconditioner
+      } else {
+        vec_scale(c, vj, c.ds, true, c.t, n);  // unscale into the preconditioner
+        apply_precond(c, c.t, zj);
+      }
       apply_operator(c, zj, c.w, c.ds, nullptr);  // w = D_s A z_j
       timing_begin(c, 2);
-      multi_dot(c, c.V, j + 1, c.w, c.h);
-      k_gemv_sub<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, nullptr);
+      // classical Gram-Schmidt with the DGKS reorthogonalisation test:
+      // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the
+      // norm dropped by more than 1/sqrt(2), h2 = V^T w and w -= V h2
+      gs_dots(c, j + 1, c.h, c.scal + 4, nullptr);
+      k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
+                                                         nullptr);
       MHFP_LAUNCH_CHECK();
-      multi_dot(c, c.V, j + 1, c.w, c.h + (m + 1));
-      k_gemv_sub<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w, c.partials + (size_t)m * RED_BLOCKS);
+      k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 5, 0);
       MHFP_LAUNCH_CHECK();
-      k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials + (size_t)m * RED_BLOCKS, c.scal + 2, 0);
+      k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2);
       MHFP_LAUNCH_CHECK();
-      timing_end(c, 2, 8.0 * n * (4.0 * (j + 1) + 6.0));
+      gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
+      k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
+                                                         c.partials + (size_t)m * GS_BLOCKS, c.dflag);
+      MHFP_LAUNCH_CHECK();
+      k_reduce_partials_flag<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
+                                                             c.scal + 2, c.dflag);
+      MHFP_LAUNCH_CHECK();
+      timing_end(c, 2, 8.0 * n * (2.0 * (j + 1) + 4.0));
       k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, c.h + (m + 1), c.scal + 2, c.H, c.cs, c.sn, c.g, c.scal);
       MHFP_LAUNCH_CHECK();
       k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
