@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lognormal64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--restart", type=int, default=12,
+                    help="FGMRES restart length (12: fastest measured on the 64^3 workload)")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="both: mixed headline with FP64-plain beside it (default)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -296,10 +298,11 @@ def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local
     return dict(ms=ms, iters=iters, launches=launches, clocks=clocks, kt=kt)
 
 
-def _solver(prob, precision, torch):
+def _solver(prob, precision, torch, restart=50):
     from paper_2002_09603_gb300 import Solver, default_options
     opt = default_options()
     opt.precision = precision
+    opt.restart = restart
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -337,7 +340,7 @@ def run_ours(args):
     # mixed form (FP32 V-cycles and Schur steps inside FP64 FGMRES)
     r64, setup64 = None, None
     if args.precision in ("both", "fp64"):
-        s64, setup64 = _solver(prob, 0, torch)
+        s64, setup64 = _solver(prob, 0, torch, args.restart)
         r64 = _timed_steps(s64, args, world, dist, torch, launch_count, args.precision == "fp64", local)
         if args.precision == "fp64":
             s, setup_ms, r32 = s64, setup64, r64
@@ -345,7 +348,7 @@ def run_ours(args):
             s64.close()
             del s64
     if args.precision in ("both", "mixed"):
-        s, setup_ms = _solver(prob, 1, torch)
+        s, setup_ms = _solver(prob, 1, torch, args.restart)
         r32 = _timed_steps(s, args, world, dist, torch, launch_count, True, local)
     ms = r32["ms"]
 
@@ -411,7 +414,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
-                       "n_pi": nPi, "tol": TOL, "restart": 50, "iterations_per_step": r32["iters"],
+                       "n_pi": nPi, "tol": TOL, "restart": args.restart, "iterations_per_step": r32["iters"],
                        "setup_ms": setup_ms, "precision": {"both": "FP32 V-cycles inside FP64 FGMRES",
                                                            "mixed": "FP32 V-cycles inside FP64 FGMRES",
                                                            "fp64": "FP64 throughout"}[args.precision],

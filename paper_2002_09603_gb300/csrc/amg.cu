@@ -94,7 +94,7 @@ __device__ __forceinline__ void spmv_body(const Lat& L, const T* __restrict__ va
   T acc[BS];
 #pragma unroll
   for (int r = 0; r < BS; ++r) acc[r] = T(0);
-#pragma unroll 1
+#pragma unroll
   for (int o = 0; o < St<KIND>::N; ++o) {
     int dx, dy, dz;
     St<KIND>::off(o, dx, dy, dz);
@@ -187,7 +187,9 @@ __device__ __forceinline__ void group_residual(const Lat& L, long long p, bool v
   if (valid && x) {
     int i, j, k;
     L.ijk(p, i, j, k);
-    for (int o = sub; o < St<KIND>::N; o += TPP) {
+    for (int oo = 0; oo < (St<KIND>::N + TPP - 1) / TPP; ++oo) {
+      const int o = oo * TPP + sub;
+      if (o >= St<KIND>::N) break;
       int dx, dy, dz;
       St<KIND>::off(o, dx, dy, dz);
       if (!L.in(i + dx, j + dy, k + dz)) continue;

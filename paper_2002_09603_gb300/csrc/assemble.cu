@@ -484,7 +484,7 @@ __global__ void k_face_ell(Dims d, const double* __restrict__ W, const double* _
 }
 
 __global__ void k_scalings(Dims d, const double* __restrict__ Auu, const double* __restrict__ btilde,
-                           const double* __restrict__ Cpi, double* __restrict__ ds) {
+                           const double* __restrict__ Cpi, double* __restrict__ ds, double* __restrict__ ds_inv) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nU = 3 * d.nN;
   if (r >= nU + d.nT + d.nF) return;
@@ -498,7 +498,9 @@ __global__ void k_scalings(Dims d, const double* __restrict__ Auu, const double*
   } else {
     v = Cpi[r - nU - d.nT];
   }
-  ds[r] = 1.0 / sqrt(v);
+  const double sq = sqrt(v);
+  ds[r] = 1.0 / sq;
+  ds_inv[r] = sq;
 }
 
 // ---------------------------------------------------------------- RHS
@@ -741,7 +743,8 @@ void build_preconditioner_blocks(Ctx& c) {
                                                         c.Cpi, c.pw);
   MHFP_LAUNCH_CHECK();
   c.ds = dalloc_n<double>(c, c.n);
-  k_scalings<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.btilde, c.Cpi, c.ds);
+  c.ds_inv = dalloc_n<double>(c, c.n);
+  k_scalings<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.btilde, c.Cpi, c.ds, c.ds_inv);
   MHFP_LAUNCH_CHECK();
 }
 

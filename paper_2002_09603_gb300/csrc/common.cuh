@@ -176,6 +176,7 @@ struct Ctx {
   double* fu = nullptr;     // [nU] traction load
   double* btilde = nullptr; // [nT]
   double* ds = nullptr;     // [n] equilibration D_s
+  double* ds_inv = nullptr; // [n] its inverse (multiplies instead of FP64 divisions)
 
   std::vector<Level> hu, hpi;
   // FP32 copies used by the mixed-precision preconditioner

@@ -291,10 +291,10 @@ void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y,
   MHFP_LAUNCH_CHECK();
 }
 
-__global__ void k_to_f32(long long n, const double* __restrict__ x, const double* __restrict__ div,
+__global__ void k_to_f32(long long n, const double* __restrict__ x, const double* __restrict__ mul,
                          float* __restrict__ y) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n) y[r] = (float)(div ? x[r] / div[r] : x[r]);
+  if (r < n) y[r] = (float)(mul ? x[r] * mul[r] : x[r]);
 }
 
 __global__ void k_to_f64(long long n, const float* __restrict__ x, double* __restrict__ y) {
@@ -302,10 +302,10 @@ __global__ void k_to_f64(long long n, const float* __restrict__ x, double* __res
   if (r < n) y[r] = (double)x[r];
 }
 
-// z = M^-1 (v / div) with the FP32 V-cycles and Schur steps; v, z FP64
-void apply_precond_mixed(Ctx& c, const double* v, const double* div, double* z) {
+// z = M^-1 (v .* mul) with the FP32 V-cycles and Schur steps; v, z FP64
+void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z) {
   const long long n = c.n;
-  k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, div, c.tf);
+  k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, mul, c.tf);
   MHFP_LAUNCH_CHECK();
   const float* tu = c.tf;
   const float* tp = c.tf + c.nU;
@@ -374,9 +374,9 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
       double* vj = c.V + (long long)j * n;
       double* zj = c.Z + (long long)j * n;
       if (c.opt.precision == 1) {
-        apply_precond_mixed(c, vj, c.ds, zj);  // unscale into the FP32 preconditioner
+        apply_precond_mixed(c, vj, c.ds_inv, zj);  // unscale into the FP32 preconditioner
       } else {
-        vec_scale(c, vj, c.ds, true, c.t, n);  // unscale into the preconditioner
+        vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
         apply_precond(c, c.t, zj);
       }
       apply_operator(c, zj, c.w, c.ds, nullptr);  // w = D_s A z_j
