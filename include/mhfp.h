@@ -139,6 +139,46 @@ mhfp_status mhfp_solve(mhfp_handle h, const double* d_rhs, double* d_x, double t
 /* y = A_H x (Eq. stab_A, hybrid form), unscaled. */
 mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y);
 
+/* y = A_H^T x.  The condensed operator satisfies A_H^T = D A_H D^-1 with
+ * D = diag(I, -I, -dt I) (A_pu = -A_up^T, A_pip = A_ppi^T; A_uu, A_pipi,
+ * Abar_pp + A_stab symmetric; Section 2 and the remark on symmetrisation
+ * after Eq. stab_A), so this applies the same blocks with the signs and dt
+ * factors of the off-diagonal blocks moved. */
+mhfp_status mhfp_apply_operator_t(mhfp_handle h, const double* d_x, double* d_y);
+
+/* Adjoint solve A_H^T lambda = g by FGMRES with the transposed
+ * preconditioner M^T (lower block-triangular, forward substitution u, p, pi,
+ * with the same symmetric V-cycles), on the equilibrated system
+ * D_s A_H^T D_s; same stopping rule, stats and synchronisation as
+ * mhfp_solve.  Not in the paper: the adjoint of its forward solve. */
+mhfp_status mhfp_adjoint_solve(mhfp_handle h, const double* d_g, double* d_lambda, double tol, mhfp_stats* stats);
+
+/* d_grad[T] -= lambda^T (d A_H / d ln kappa_T) x for every cell T (n_T
+ * values, accumulated).  kappa_T scales the cell's whole diagonal
+ * permeability, so W_T = A_ww,T^-1 is proportional to kappa_T and the
+ * derivative is cell T's condensed flow contribution (Eq. hmfeSys):
+ * p row dt (1^T W_T 1 p_T - (W_T 1)^T pi_T), pi rows W_T pi_T - W_T 1 p_T.
+ * With lambda_n the adjoint states of a time-stepped misfit J, summing this
+ * over the steps gives dJ / d ln kappa (the right-hand side does not depend
+ * on kappa). */
+mhfp_status mhfp_grad_logk(mhfp_handle h, const double* d_lambda, const double* d_x, double* d_grad);
+
+/* Misfit of one time step (not in the paper; the objective of the gradient
+ * growth): *d_J += 1/2 inv_su2 sum_top (u_z - u_z*)^2 + 1/2 inv_sp2
+ * sum_cells (p - p*)^2, and d_g (n values, overwritten) = dJ/dx.  The top
+ * u_z* are the (nx+1)(ny+1) nodes of the plane k = nz in lexicographic
+ * order; p* has n_T values.  d_J is a device scalar. */
+mhfp_status mhfp_misfit(mhfp_handle h, const double* d_x, const double* d_uz_target, const double* d_p_target,
+                        double inv_su2, double inv_sp2, double* d_J, double* d_g);
+
+/* Adjoint right-hand side of step n: d_rhs = d_g + C^T lambda_{n+1}, where
+ * C x = [0 ; A_pu u + S_eps|T| p ; 0] is how step n+1's right-hand side
+ * depends on step n (Section 2.1).  d_lambda_next may be NULL (last step). */
+mhfp_status mhfp_adjoint_rhs(mhfp_handle h, const double* d_g, const double* d_lambda_next, double* d_rhs);
+
+/* z = M^-T v (the adjoint's preconditioner), unscaled. */
+mhfp_status mhfp_apply_precond_t(mhfp_handle h, const double* d_v, double* d_z);
+
 /* z = M^-1 v with the multigrid inner solves (Eq. hybridPrec back
  * substitution: pi, then p, then u), unscaled. */
 mhfp_status mhfp_apply_precond(mhfp_handle h, const double* d_v, double* d_z);

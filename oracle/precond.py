@@ -280,6 +280,17 @@ class Preconditioner:
         zu = self.solve_uu(vu - self.B.Aup @ zp)
         return np.concatenate([zu, zp, zpi])
 
+    def apply_transpose(self, v):
+        """Forward substitution with M^T = [[A_uu, 0, 0], [A_up^T, B~_p, 0],
+        [0, dt A_ppi^T, C~_pi^T]] (u, then p, then pi); A_uu and C~_pi are
+        symmetric and so are the V-cycles that stand for their inverses."""
+        nU, nP, nPi = self.B.sizes
+        vu, vp, vpi = v[:nU], v[nU:nU + nP], v[nU + nP:]
+        zu = self.solve_uu(vu)
+        zp = (vp - self.B.Aup.T @ zu) / self.Bt
+        zpi = self.solve_pi(vpi - self.B.dt * (self.B.Appi.T @ zp))
+        return np.concatenate([zu, zp, zpi])
+
     def matrix(self):
         """M itself (for the spectral pins)."""
         B = self.B

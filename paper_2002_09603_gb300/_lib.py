@@ -21,7 +21,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "out of memory",
 
 # every symbol include/mhfp.h declares
 EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhfp_setup_precond",
-           "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_precond", "mhfp_vcycle",
+           "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_operator_t", "mhfp_adjoint_solve",
+           "mhfp_grad_logk", "mhfp_misfit", "mhfp_adjoint_rhs", "mhfp_apply_precond_t", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
            "mhfp_timing_read", "mhfp_residual_norm_noalloc", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
 
@@ -83,6 +84,12 @@ def load(path: str | None = None):
         "mhfp_solve": (i, [vp, vp, vp, d, C.POINTER(Stats)]),
         "mhfp_apply_operator": (i, [vp, vp, vp]),
         "mhfp_apply_precond": (i, [vp, vp, vp]),
+        "mhfp_apply_operator_t": (i, [vp, vp, vp]),
+        "mhfp_adjoint_solve": (i, [vp, vp, vp, d, C.POINTER(Stats)]),
+        "mhfp_grad_logk": (i, [vp, vp, vp, vp]),
+        "mhfp_apply_precond_t": (i, [vp, vp, vp]),
+        "mhfp_misfit": (i, [vp, vp, vp, vp, d, d, vp, vp]),
+        "mhfp_adjoint_rhs": (i, [vp, vp, vp, vp]),
         "mhfp_vcycle": (i, [vp, i, vp, vp]),
         "mhfp_level_apply": (i, [vp, i, i, vp, vp]),
         "mhfp_hierarchy": (i, [vp, i, C.POINTER(HierInfo)]),
@@ -191,6 +198,40 @@ class Solver:
     def apply_operator(self, x, out=None):
         out = self.empty() if out is None else out
         self._check(self.lib.mhfp_apply_operator(self.h, _ptr(x), _ptr(out)))
+        return out
+
+    def apply_operator_t(self, x, out=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_apply_operator_t(self.h, _ptr(x), _ptr(out)))
+        return out
+
+    def adjoint_solve(self, g, tol=1e-8, out=None, raise_not_converged=True):
+        out = self.empty() if out is None else out
+        st = Stats()
+        code = self.lib.mhfp_adjoint_solve(self.h, _ptr(g), _ptr(out), float(tol), C.byref(st))
+        if code != MHFP_OK and not (code == 5 and not raise_not_converged):
+            self._check(code)
+        return out, st.as_dict()
+
+    def grad_logk(self, lam, x, grad):
+        """grad -= lambda^T (dA/d ln kappa_T) x, per cell (accumulates)."""
+        self._check(self.lib.mhfp_grad_logk(self.h, _ptr(lam), _ptr(x), _ptr(grad)))
+        return grad
+
+    def misfit(self, x, uz_target, p_target, inv_su2, inv_sp2, J, g):
+        """J += step misfit (device scalar), g = its gradient."""
+        self._check(self.lib.mhfp_misfit(self.h, _ptr(x), _ptr(uz_target), _ptr(p_target), float(inv_su2),
+                                         float(inv_sp2), _ptr(J), _ptr(g)))
+        return J, g
+
+    def adjoint_rhs(self, g, lam_next, out=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_adjoint_rhs(self.h, _ptr(g), _ptr(lam_next), _ptr(out)))
+        return out
+
+    def apply_precond_t(self, v, out=None):
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_apply_precond_t(self.h, _ptr(v), _ptr(out)))
         return out
 
     def apply_precond(self, v, out=None):

@@ -236,6 +236,58 @@ mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y) {
   });
 }
 
+mhfp_status mhfp_apply_operator_t(mhfp_handle h, const double* d_x, double* d_y) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled || !c.prepared) throw Error{MHFP_ERR_STATE, "operator needs assemble + setup"};
+    if (!d_x || !d_y || d_x == d_y) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::apply_operator(c, d_x, d_y, nullptr, nullptr, true);
+  });
+}
+
+mhfp_status mhfp_adjoint_solve(mhfp_handle h, const double* d_g, double* d_lambda, double tol, mhfp_stats* stats) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (!d_g || !d_lambda || !(tol > 0.0) || !(tol < 1.0)) throw Error{MHFP_ERR_ARG, "bad adjoint argument"};
+    mhfp::fgmres_solve(c, d_g, d_lambda, tol, stats, true);
+  });
+}
+
+mhfp_status mhfp_grad_logk(mhfp_handle h, const double* d_lambda, const double* d_x, double* d_grad) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
+    if (!d_lambda || !d_x || !d_grad) throw Error{MHFP_ERR_ARG, "bad gradient argument"};
+    mhfp::grad_logk(c, d_lambda, d_x, d_grad);
+  });
+}
+
+mhfp_status mhfp_misfit(mhfp_handle h, const double* d_x, const double* d_uz_target, const double* d_p_target,
+                        double inv_su2, double inv_sp2, double* d_J, double* d_g) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
+    if (!d_x || !d_uz_target || !d_p_target || !d_J || !d_g || !std::isfinite(inv_su2) || !std::isfinite(inv_sp2))
+      throw Error{MHFP_ERR_ARG, "bad misfit argument"};
+    mhfp::ensure_workspace(c);
+    mhfp::misfit(c, d_x, d_uz_target, d_p_target, inv_su2, inv_sp2, d_J, d_g, c.partials,
+                 (long long)(c.opt.restart + 2) * c.npart);
+  });
+}
+
+mhfp_status mhfp_adjoint_rhs(mhfp_handle h, const double* d_g, const double* d_lambda_next, double* d_rhs) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
+    if (!d_g || !d_rhs) throw Error{MHFP_ERR_ARG, "bad adjoint rhs argument"};
+    mhfp::adjoint_rhs(c, d_g, d_lambda_next, d_rhs);
+  });
+}
+
+mhfp_status mhfp_apply_precond_t(mhfp_handle h, const double* d_v, double* d_z) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (!d_v || !d_z || d_v == d_z) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::apply_precond(c, d_v, d_z, true);
+  });
+}
+
 mhfp_status mhfp_apply_precond(mhfp_handle h, const double* d_v, double* d_z) {
   return guarded(h, [&](Ctx& c) {
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};

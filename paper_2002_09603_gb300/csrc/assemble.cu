@@ -537,9 +537,16 @@ __device__ __forceinline__ double finish(double y, long long r, const double* so
 }
 
 // u rows: A_uu x_u (27-point 3x3-block stencil) + A_up x_p (8 cells).
+//
+// The transposed operator uses the same kernels: A_H^T = D A_H D^-1 with
+// D = diag(I, -I, -dt I) (A_pu = -A_up^T, A_pip = A_ppi^T, A_uu, A_pipi and
+// Abar_pp + A_stab symmetric), so A_H^T x only changes the coefficients of
+// the off-diagonal blocks: cup (u rows, A_up x_p), cpu and cpi (p rows,
+// A_pu x_u and A_ppi x_pi), cpp (pi rows, A_pip x_p).
 __global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restrict__ Auu, const double* __restrict__ Aup,
                                                  const double* __restrict__ x, double* __restrict__ y,
-                                                 const double* __restrict__ so, const double* __restrict__ bsub) {
+                                                 const double* __restrict__ so, const double* __restrict__ bsub,
+                                                 double cup) {
   const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= d.nN) return;
   const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
@@ -577,7 +584,7 @@ __global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restric
         if (cx < 0 || cx >= d.nx) continue;
         const long long T = cell_id(d, cx, cy, cz);
         const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
-        const double p = xp[T];
+        const double p = cup * xp[T];
         y0 += Aup[(long long)(3 * a) * d.nT + T] * p;
         y1 += Aup[(long long)(3 * a + 1) * d.nT + T] * p;
         y2 += Aup[(long long)(3 * a + 2) * d.nT + T] * p;
@@ -591,18 +598,19 @@ __global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restric
 
 // p rows: A_pu x_u + (Abar_pp + A_stab) x_p + dt A_ppi x_pi.
 __global__ void k_apply_p(Dims d, const double* __restrict__ Aup, const double* __restrict__ Abar,
-                          const double* __restrict__ stabc, const double* __restrict__ ApPi, double dt,
+                          const double* __restrict__ stabc, const double* __restrict__ ApPi, double cpi,
                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ so,
-                          const double* __restrict__ bsub) {
+                          const double* __restrict__ bsub, double cpu) {
   const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= d.nT) return;
   const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
   const long long nU = 3 * d.nN;
-  double s = 0.0;
+  double su = 0.0;
   for (int a = 0; a < 8; ++a) {
     const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-    for (int c = 0; c < 3; ++c) s -= Aup[(long long)(3 * a + c) * d.nT + T] * x[3 * n + c];
+    for (int c = 0; c < 3; ++c) su -= Aup[(long long)(3 * a + c) * d.nT + T] * x[3 * n + c];
   }
+  double s = cpu * su;
   const double* xp = x + nU;
   const double cx = stabc[T], cy = stabc[d.nT + T], cz = stabc[2 * d.nT + T];
   double st = (Abar[T] + (cx + cy + cz)) * xp[T];
@@ -613,14 +621,14 @@ __global__ void k_apply_p(Dims d, const double* __restrict__ Aup, const double* 
   const double* xpi = xp + d.nT;
   double c = 0.0;
   for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * xpi[cell_face(d, i, j, k, lf)];
-  s += dt * c;
+  s += cpi * c;
   y[nU + T] = finish(s, nU + T, so, bsub);
 }
 
 // pi rows: A_pip x_p + A_pipi x_pi (ELL, 11 slots).
 __global__ void k_apply_pi(Dims d, const double* __restrict__ ApPi, const int* __restrict__ col,
                            const double* __restrict__ Apipi, const double* __restrict__ x, double* __restrict__ y,
-                           const double* __restrict__ so, const double* __restrict__ bsub) {
+                           const double* __restrict__ so, const double* __restrict__ bsub, double cpp) {
   const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= d.nF) return;
   long long cell[2];
@@ -632,6 +640,7 @@ __global__ void k_apply_pi(Dims d, const double* __restrict__ ApPi, const int* _
   double s = 0.0;
   for (int q = 0; q < 2; ++q)
     if (cell[q] >= 0) s += ApPi[(long long)lf[q] * d.nT + cell[q]] * xp[cell[q]];
+  s *= cpp;
   double a = 0.0;
 #pragma unroll
   for (int q = 0; q < 11; ++q) a += Apipi[(long long)q * d.nF + f] * xpi[col[(long long)q * d.nF + f]];
@@ -679,6 +688,145 @@ __global__ void k_prec_u(Dims d, const R* __restrict__ Aup, const R* __restrict_
   tu[3 * n] = vu[3 * n] - y0;
   tu[3 * n + 1] = vu[3 * n + 1] - y1;
   tu[3 * n + 2] = vu[3 * n + 2] - y2;
+}
+
+// transposed preconditioner M^T (forward substitution u, p, pi):
+// z_p = B~^-1 (v_p - A_up^T z_u),  t_pi = v_pi - dt A_ppi^T z_p
+template <typename R>
+__global__ void k_precT_p(Dims d, const R* __restrict__ Aup, const R* __restrict__ btilde, const R* __restrict__ vp,
+                          const R* __restrict__ zu, R* __restrict__ zp) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  R s = vp[T];
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    for (int c = 0; c < 3; ++c) s -= Aup[(long long)(3 * a + c) * d.nT + T] * zu[3 * n + c];
+  }
+  zp[T] = s / btilde[T];
+}
+
+template <typename R>
+__global__ void k_precT_pi(Dims d, const R* __restrict__ ApPi, R dt, const R* __restrict__ vpi,
+                           const R* __restrict__ zp, R* __restrict__ tpi) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nF) return;
+  long long cell[2];
+  int lf[2], ijk[2][3];
+  face_cells(d, f, cell, lf, ijk);
+  R s = R(0);
+  for (int q = 0; q < 2; ++q)
+    if (cell[q] >= 0) s += ApPi[(long long)lf[q] * d.nT + cell[q]] * zp[cell[q]];
+  tpi[f] = vpi[f] - dt * s;
+}
+
+// g_T -= lambda^T (dA_H / d ln kappa_T) x.  With kappa_T scaled as a whole,
+// W_T = A_ww,T^-1 is proportional to kappa_T, so the derivative of cell T's
+// condensed flow contribution is that contribution itself:
+// p row:  dt (1^T W 1 p_T - (W 1)^T pi_T);  pi rows: W pi_T - W 1 p_T
+// (drained faces, whose rows and columns are eliminated, take no part).
+__global__ void k_grad_logk(Dims d, const double* __restrict__ W, const double* __restrict__ W1,
+                            const double* __restrict__ sW, const unsigned char* __restrict__ face_bc, double dt,
+                            const double* __restrict__ lam, const double* __restrict__ x, double* __restrict__ grad) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  const long long nU = 3 * d.nN, oP = nU, oPi = nU + d.nT;
+  double pi[6], lpi[6];
+  for (int lf = 0; lf < 6; ++lf) {
+    const long long f = cell_face(d, i, j, k, lf);
+    const bool fixed = face_bc[f] & 2;
+    pi[lf] = fixed ? 0.0 : x[oPi + f];
+    lpi[lf] = fixed ? 0.0 : lam[oPi + f];
+  }
+  const double p = x[oP + T], lp = lam[oP + T];
+  double w1pi = 0.0;
+  for (int f = 0; f < 6; ++f) w1pi += W1[(long long)f * d.nT + T] * pi[f];
+  double acc = lp * dt * (sW[T] * p - w1pi);
+  for (int f = 0; f < 6; ++f) {
+    double r = -W1[(long long)f * d.nT + T] * p;
+    for (int g = 0; g < 6; ++g) r += W[(long long)(6 * f + g) * d.nT + T] * pi[g];
+    acc += lpi[f] * r;
+  }
+  grad[T] -= acc;
+}
+
+// Misfit of one step: J += 1/2 sum_top (u_z - u_z*)^2 / s_u^2
+//                          + 1/2 sum_cells (p - p*)^2 / s_p^2,
+// g = dJ/dx (zero outside the top u_z dofs and p).  Thread per term; block
+// partial sums of J, reduced in a fixed order afterwards.
+__global__ void k_misfit(Dims d, const double* __restrict__ x, const double* __restrict__ uzt,
+                         const double* __restrict__ pt, double wu, double wp, double* __restrict__ g,
+                         double* __restrict__ part) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long ntop = (long long)(d.nx + 1) * (d.ny + 1);
+  double j = 0.0;
+  if (t < ntop) {
+    const long long node = (long long)d.nz * ntop + t;
+    const double du = x[3 * node + 2] - uzt[t];
+    g[3 * node + 2] = wu * du;
+    j = 0.5 * wu * du * du;
+  } else if (t < ntop + d.nT) {
+    const long long T = t - ntop;
+    const double dp = x[3 * d.nN + T] - pt[T];
+    g[3 * d.nN + T] = wp * dp;
+    j = 0.5 * wp * dp * dp;
+  }
+  __shared__ double sh[8];
+  for (int o = 16; o > 0; o >>= 1) j += __shfl_down_sync(0xffffffffu, j, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = j;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_into(long long nb, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[8];
+  double v = 0.0;
+  for (long long b = threadIdx.x; b < nb; b += blockDim.x) v += part[b];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    out[0] += s;
+  }
+}
+
+// adjoint right-hand side g + C^T lambda_next, with C x = [0; A_pu u + S_eps|T| p; 0]
+// the dependence of step n's right-hand side on step n-1:
+// (C^T lambda)_u = A_pu^T lambda_p = -A_up lambda_p, (C^T lambda)_p = S_eps|T| lambda_p
+__global__ void k_adjoint_rhs(Dims d, const double* __restrict__ Aup, const double* __restrict__ Seps,
+                              const double* __restrict__ vol, const double* __restrict__ g,
+                              const double* __restrict__ lam, double* __restrict__ rhs) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nU = 3 * d.nN;
+  if (r >= nU + d.nT + d.nF) return;
+  double v = g[r];
+  if (lam) {
+    if (r < nU) {
+      const long long n = r / 3;
+      const int c = (int)(r % 3);
+      const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
+                nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
+      for (int cz = nk - 1; cz <= nk; ++cz)
+        for (int cy = nj - 1; cy <= nj; ++cy)
+          for (int cx = ni - 1; cx <= ni; ++cx) {
+            if (cx < 0 || cx >= d.nx || cy < 0 || cy >= d.ny || cz < 0 || cz >= d.nz) continue;
+            const long long T = cell_id(d, cx, cy, cz);
+            const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
+            v -= Aup[(long long)(3 * a + c) * d.nT + T] * lam[nU + T];
+          }
+    } else if (r < nU + d.nT) {
+      const long long T = r - nU;
+      v += Seps[T] * vol[T] * lam[r];
+    }
+  }
+  rhs[r] = v;
 }
 
 Dims dims_of(const Ctx& c) {
@@ -754,14 +902,17 @@ void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs) {
   MHFP_LAUNCH_CHECK();
 }
 
-void apply_operator(Ctx& c, const double* x, double* y, const double* so, const double* bsub) {
+void apply_operator(Ctx& c, const double* x, double* y, const double* so, const double* bsub, bool transpose) {
   const Dims d = dims_of(c);
   timing_begin(c, 1);
-  k_apply_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so, bsub);
+  const double sgn = transpose ? -1.0 : 1.0;
+  k_apply_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so, bsub, sgn);
   MHFP_LAUNCH_CHECK();
-  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, c.dt, x, y, so, bsub);
+  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, transpose ? 1.0 : c.dt, x, y,
+                                                       so, bsub, sgn);
   MHFP_LAUNCH_CHECK();
-  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(d, c.ApPi, c.ell_col, c.Apipi, x, y, so, bsub);
+  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(d, c.ApPi, c.ell_col, c.Apipi, x, y, so, bsub,
+                                                        transpose ? c.dt : 1.0);
   MHFP_LAUNCH_CHECK();
   // algorithmic bytes: A_uu values (27*9 doubles/node) + A_up read twice
   // (24 doubles/cell) + ELL (11 doubles + 11 ints/face) + p-block (~17
@@ -791,6 +942,51 @@ void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp) {
 void precond_u_rhs(Ctx& c, const float* vu, const float* zp, float* tu) {
   const Dims d = dims_of(c);
   k_prec_u<float><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aupf, vu, zp, tu);
+  MHFP_LAUNCH_CHECK();
+}
+
+void precondT_p_step(Ctx& c, const double* vp, const double* zu, double* zp) {
+  const Dims d = dims_of(c);
+  k_precT_p<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.btilde, vp, zu, zp);
+  MHFP_LAUNCH_CHECK();
+}
+void precondT_p_step(Ctx& c, const float* vp, const float* zu, float* zp) {
+  const Dims d = dims_of(c);
+  k_precT_p<float><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aupf, c.btildef, vp, zu, zp);
+  MHFP_LAUNCH_CHECK();
+}
+void precondT_pi_rhs(Ctx& c, const double* vpi, const double* zp, double* tpi) {
+  const Dims d = dims_of(c);
+  k_precT_pi<double><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(d, c.ApPi, c.dt, vpi, zp, tpi);
+  MHFP_LAUNCH_CHECK();
+}
+void precondT_pi_rhs(Ctx& c, const float* vpi, const float* zp, float* tpi) {
+  const Dims d = dims_of(c);
+  k_precT_pi<float><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(d, c.ApPif, (float)c.dt, vpi, zp, tpi);
+  MHFP_LAUNCH_CHECK();
+}
+void grad_logk(Ctx& c, const double* lam, const double* x, double* grad) {
+  const Dims d = dims_of(c);
+  k_grad_logk<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.W, c.W1, c.sW, c.face_bc, c.dt, lam, x, grad);
+  MHFP_LAUNCH_CHECK();
+}
+
+void misfit(Ctx& c, const double* x, const double* uzt, const double* pt, double wu, double wp, double* J,
+            double* g, double* part, long long npart) {
+  const Dims d = dims_of(c);
+  const long long nterm = (long long)(c.nx + 1) * (c.ny + 1) + c.nT;
+  const long long nb = grid_for(nterm, 256);
+  if (nb > npart) throw Error{MHFP_ERR_ARG, "misfit needs more partial sums than the workspace holds"};
+  MHFP_CUDA(cudaMemsetAsync(g, 0, c.n * sizeof(double), c.stream));
+  k_misfit<<<(unsigned)nb, 256, 0, c.stream>>>(d, x, uzt, pt, wu, wp, g, part);
+  MHFP_LAUNCH_CHECK();
+  k_sum_into<<<1, 256, 0, c.stream>>>(nb, part, J);
+  MHFP_LAUNCH_CHECK();
+}
+
+void adjoint_rhs(Ctx& c, const double* g, const double* lam_next, double* rhs) {
+  const Dims d = dims_of(c);
+  k_adjoint_rhs<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.Aup, c.Seps, c.vol, g, lam_next, rhs);
   MHFP_LAUNCH_CHECK();
 }
 

@@ -210,12 +210,22 @@ void timing_end(Ctx& c, int cls, double bytes);
 void assemble_all(Ctx& c);
 void build_preconditioner_blocks(Ctx& c);
 void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs);
-void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub);
+void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub,
+                    bool transpose = false);
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp);
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu);
 void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp);
 void precond_u_rhs(Ctx& c, const float* vu, const float* zp, float* tu);
 void make_fp32_blocks(Ctx& c);
+void precondT_p_step(Ctx& c, const double* vp, const double* zu, double* zp);
+void precondT_p_step(Ctx& c, const float* vp, const float* zu, float* zp);
+void precondT_pi_rhs(Ctx& c, const double* vpi, const double* zp, double* tpi);
+void precondT_pi_rhs(Ctx& c, const float* vpi, const float* zp, float* tpi);
+void grad_logk(Ctx& c, const double* lam, const double* x, double* grad);
+void misfit(Ctx& c, const double* x, const double* uzt, const double* pt, double wu, double wp, double* J,
+            double* g, double* part, long long npart);
+void adjoint_rhs(Ctx& c, const double* g, const double* lam_next, double* rhs);
+void ensure_workspace(Ctx& c);
 void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out);
 
 // amg.cu
@@ -225,8 +235,8 @@ void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x);
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y);
 
 // krylov.cu
-void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st);
-void apply_precond(Ctx& c, const double* v, double* z);
+void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st, bool transpose = false);
+void apply_precond(Ctx& c, const double* v, double* z, bool transpose = false);
 double device_norm2(Ctx& c, const double* x, long long n);
 void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y, long long n);
 

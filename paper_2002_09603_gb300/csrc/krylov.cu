@@ -221,28 +221,6 @@ __global__ void k_set_g(int m, double beta, double* __restrict__ g) {
   if (i <= m) g[i] = (i == 0) ? beta : 0.0;
 }
 
-void ensure_workspace(Ctx& c) {
-  const int m = c.opt.restart;
-  if (c.m_alloc == m) return;
-  if (c.m_alloc != 0) throw Error{MHFP_ERR_STATE, "restart length cannot change after the first solve"};
-  c.V = dalloc_n<double>(c, (size_t)(m + 1) * c.n);
-  c.Z = dalloc_n<double>(c, (size_t)m * c.n);
-  c.w = dalloc_n<double>(c, c.n);
-  c.t = dalloc_n<double>(c, c.n);
-  c.tmp = dalloc_n<double>(c, c.n);
-  c.h = dalloc_n<double>(c, 2 * (size_t)(m + 1));
-  c.H = dalloc_n<double>(c, (size_t)(m + 1) * m);
-  c.cs = dalloc_n<double>(c, m);
-  c.sn = dalloc_n<double>(c, m);
-  c.g = dalloc_n<double>(c, m + 1);
-  c.yv = dalloc_n<double>(c, m);
-  c.npart = GS_BLOCKS;
-  c.partials = dalloc_n<double>(c, (size_t)(m + 2) * GS_BLOCKS);
-  c.scal = dalloc_n<double>(c, 8);
-  c.dflag = dalloc_n<int>(c, 4);
-  if (!c.host_scal) MHFP_CUDA(cudaMallocHost(&c.host_scal, 8 * sizeof(double)));
-  c.m_alloc = m;
-}
 
 // hout[0..ncols) = V^T w; with nrm2 non-null also ||w||^2 into nrm2[0];
 // with skip non-null nothing happens when *skip != 0
@@ -280,6 +258,29 @@ double read_scalar(Ctx& c, const double* dsrc) {
 
 }  // namespace
 
+void ensure_workspace(Ctx& c) {
+  const int m = c.opt.restart;
+  if (c.m_alloc == m) return;
+  if (c.m_alloc != 0) throw Error{MHFP_ERR_STATE, "restart length cannot change after the first solve"};
+  c.V = dalloc_n<double>(c, (size_t)(m + 1) * c.n);
+  c.Z = dalloc_n<double>(c, (size_t)m * c.n);
+  c.w = dalloc_n<double>(c, c.n);
+  c.t = dalloc_n<double>(c, c.n);
+  c.tmp = dalloc_n<double>(c, c.n);
+  c.h = dalloc_n<double>(c, 2 * (size_t)(m + 1));
+  c.H = dalloc_n<double>(c, (size_t)(m + 1) * m);
+  c.cs = dalloc_n<double>(c, m);
+  c.sn = dalloc_n<double>(c, m);
+  c.g = dalloc_n<double>(c, m + 1);
+  c.yv = dalloc_n<double>(c, m);
+  c.npart = GS_BLOCKS;
+  c.partials = dalloc_n<double>(c, (size_t)(m + 2) * GS_BLOCKS);
+  c.scal = dalloc_n<double>(c, 8);
+  c.dflag = dalloc_n<int>(c, 4);
+  if (!c.host_scal) MHFP_CUDA(cudaMallocHost(&c.host_scal, 8 * sizeof(double)));
+  c.m_alloc = m;
+}
+
 double device_norm2(Ctx& c, const double* x, long long n) {
   ensure_workspace(c);
   norm2_dev(c, x, n, c.scal + 4);
@@ -302,45 +303,51 @@ __global__ void k_to_f64(long long n, const float* __restrict__ x, double* __res
   if (r < n) y[r] = (double)x[r];
 }
 
-// z = M^-1 (v .* mul) with the FP32 V-cycles and Schur steps; v, z FP64
-void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z) {
+// Back substitution with M (Eq. hybridPrec): pi, then p, then u; or, for the
+// adjoint, forward substitution with M^T: u, then p, then pi.  The V-cycles
+// are symmetric operators (Galerkin levels, R = P^T, the same Chebyshev
+// polynomial before and after), so M^T reuses them unchanged.
+template <typename T>
+void precond_blocks(Ctx& c, const T* t, T* z, T* work_u, T* work_pi, bool transpose) {
+  const T* tu = t;
+  const T* tp = t + c.nU;
+  const T* tpi = tp + c.nT;
+  T* zu = z;
+  T* zp = z + c.nU;
+  T* zpi = zp + c.nT;
+  if (!transpose) {
+    vcycle(c, c.hpi, tpi, zpi);
+    precond_p_step(c, tp, zpi, zp);
+    precond_u_rhs(c, tu, zp, work_u);
+    vcycle(c, c.hu, (const T*)work_u, zu);
+  } else {
+    vcycle(c, c.hu, tu, zu);
+    precondT_p_step(c, tp, zu, zp);
+    precondT_pi_rhs(c, tpi, zp, work_pi);
+    vcycle(c, c.hpi, (const T*)work_pi, zpi);
+  }
+}
+
+// z = M^-1 (v .* mul) (or M^-T) with the FP32 V-cycles and Schur steps; v, z FP64
+void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z, bool transpose) {
   const long long n = c.n;
   k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, mul, c.tf);
   MHFP_LAUNCH_CHECK();
-  const float* tu = c.tf;
-  const float* tp = c.tf + c.nU;
-  const float* tpi = tp + c.nT;
-  float* zu = c.zf;
-  float* zp = c.zf + c.nU;
-  float* zpi = zp + c.nT;
-  vcycle(c, c.hpi, tpi, zpi);
-  precond_p_step(c, tp, zpi, zp);
-  float* ru = c.hu[0].bf;  // free at the fine level
-  precond_u_rhs(c, tu, zp, ru);
-  vcycle(c, c.hu, (const float*)ru, zu);
+  // level-0 right-hand-side buffers are free at the finest levels
+  precond_blocks<float>(c, c.tf, c.zf, c.hu[0].bf, c.hpi[0].bf, transpose);
   k_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.zf, z);
   MHFP_LAUNCH_CHECK();
 }
 
-void apply_precond(Ctx& c, const double* v, double* z) {
+void apply_precond(Ctx& c, const double* v, double* z, bool transpose) {
   if (c.opt.precision == 1) {
-    apply_precond_mixed(c, v, nullptr, z);
+    apply_precond_mixed(c, v, nullptr, z, transpose);
     return;
   }
-  const double* vu = v;
-  const double* vp = v + c.nU;
-  const double* vpi = vp + c.nT;
-  double* zu = z;
-  double* zp = z + c.nU;
-  double* zpi = zp + c.nT;
-  vcycle(c, c.hpi, vpi, zpi);
-  precond_p_step(c, vp, zpi, zp);
-  double* tu = c.hu[0].b;  // level-0 right-hand side buffer is free at the fine level
-  precond_u_rhs(c, vu, zp, tu);
-  vcycle(c, c.hu, tu, zu);
+  precond_blocks<double>(c, v, z, c.hu[0].b, c.hpi[0].b, transpose);
 }
 
-void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st) {
+void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st, bool transpose) {
   const auto t0 = std::chrono::steady_clock::now();
   ensure_workspace(c);
   const int m = c.opt.restart;
@@ -360,7 +367,7 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
   bool converged = false;
   double est = 1.0;
   while (total < c.opt.maxit) {
-    apply_operator(c, x, c.tmp, c.ds, b);  // tmp = D_s (b - A x)
+    apply_operator(c, x, c.tmp, c.ds, b, transpose);  // tmp = D_s (b - A x)
     norm2_dev(c, c.tmp, n, c.scal + 4);
     const double beta = std::sqrt(read_scalar(c, c.scal + 4));
     if (!std::isfinite(beta)) throw Error{MHFP_ERR_NONFINITE, "non-finite residual"};
@@ -374,12 +381,12 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
       double* vj = c.V + (long long)j * n;
       double* zj = c.Z + (long long)j * n;
       if (c.opt.precision == 1) {
-        apply_precond_mixed(c, vj, c.ds_inv, zj);  // unscale into the FP32 preconditioner
+        apply_precond_mixed(c, vj, c.ds_inv, zj, transpose);  // unscale into the FP32 preconditioner
       } else {
         vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
-        apply_precond(c, c.t, zj);
+        apply_precond(c, c.t, zj, transpose);
       }
-      apply_operator(c, zj, c.w, c.ds, nullptr);  // w = D_s A z_j
+      apply_operator(c, zj, c.w, c.ds, nullptr, transpose);  // w = D_s A z_j
       timing_begin(c, 2);
       // classical Gram-Schmidt with the DGKS reorthogonalisation test:
       // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the
@@ -417,7 +424,7 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
     MHFP_LAUNCH_CHECK();
     ++cycles;
   }
-  apply_operator(c, x, c.tmp, c.ds, b);
+  apply_operator(c, x, c.tmp, c.ds, b, transpose);
   norm2_dev(c, c.tmp, n, c.scal + 4);
   const double true_rel = std::sqrt(read_scalar(c, c.scal + 4)) / bnorm;
   converged = converged || true_rel <= 1.05 * tol;

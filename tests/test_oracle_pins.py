@@ -431,3 +431,71 @@ def test_vcycles_are_symmetric_contractions():
         assert np.sqrt(e @ (A @ e)) < 0.9 * np.sqrt(x @ (A @ x))
         for lev in levels[1:]:
             assert abs(lev.A - lev.A.T).max() <= 1e-12 * abs(lev.A).max()
+
+
+# ------------------------------------------------------------------ adjoint
+def _adjoint_case(seed=3):
+    from oracle import adjoint
+    p = mi.random_small(3, 3, 4, seed=seed, S=1e-4, dt=0.05)
+    # isotropic permeability per cell (theta_T scales all three components)
+    p.kappa = np.repeat(p.kappa[:, :1], 3, axis=1)
+    B = oracle.assemble(p)
+    nsteps = 3
+    # targets: the same model with a perturbed permeability field
+    q = mi.Problem(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.__dict__.items()})
+    q.kappa *= np.exp(np.random.default_rng(seed).uniform(-0.5, 0.5, (p.n_cells, 1)))
+    Bq = oracle.assemble(q)
+    xq = adjoint.forward(Bq, nsteps)
+    nU, nP, _ = B.sizes
+    dofs = adjoint.top_uz_dofs(B)
+    targets = ([x[dofs] for x in xq], [x[nU:nU + nP] for x in xq])
+    return p, B, nsteps, targets
+
+
+def test_adjoint_transpose_identity():
+    """A_H^T = D A_H D^-1 with D = diag(I, -I, -dt I): the symmetrisation
+    the paper mentions after Eq. (stab_A), kept exact by the symmetric
+    Dirichlet treatment."""
+    p, B, _, _ = _adjoint_case()
+    A = system.system_matrix(B).toarray()
+    nU, nP, nPi = B.sizes
+    D = np.diag(np.concatenate([np.ones(nU), -np.ones(nP), -B.dt * np.ones(nPi)]))
+    assert np.allclose(A.T, D @ A @ np.linalg.inv(D), rtol=0, atol=1e-14 * np.abs(A).max())
+
+
+def test_cell_derivative_is_linearity_difference():
+    """The per-cell flow contribution used by the gradient equals the exact
+    derivative of the assembled operator: A is affine in kappa_T, so
+    dA/d ln kappa_T = A(2 kappa_T) - A(kappa_T) (assembly used as a black box)."""
+    from oracle import adjoint
+    p, B, _, _ = _adjoint_case()
+    rng = np.random.default_rng(7)
+    lam, x = rng.standard_normal((2, sum(B.sizes)))
+    nU, nP, nPi = B.sizes
+    x[nU + nP:][B.pi_fixed] = 0.0
+    g = adjoint.cell_derivative_apply(B, lam, x)
+    A0 = system.system_matrix(B)
+    for T in (0, 7, B.sizes[1] - 1):
+        q = mi.Problem(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.__dict__.items()})
+        q.kappa[T] *= 2.0
+        dA = system.system_matrix(oracle.assemble(q)) - A0
+        assert np.isclose(g[T], -(lam @ (dA @ x)), rtol=1e-9, atol=1e-12 * abs(g).max())
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """dJ/d ln kappa from the reverse sweep agrees with central finite
+    differences of J (direct solves) on several cells."""
+    from oracle import adjoint
+    p, B, nsteps, targets = _adjoint_case()
+    m = adjoint.Misfit(B, *targets)
+    J, g, _ = adjoint.gradient(B, nsteps, m)
+    # h = 1e-3 balances the O(h^2) truncation against the rounding of the
+    # (small) misfit differences; both stay below 4e-6 relative here
+    h = 1e-3
+    for T in np.argsort(-np.abs(g))[:4]:
+        qp = mi.Problem(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.__dict__.items()})
+        qm = mi.Problem(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.__dict__.items()})
+        qp.kappa[T] *= np.exp(h)
+        qm.kappa[T] *= np.exp(-h)
+        fd = (adjoint.objective(qp, nsteps, targets) - adjoint.objective(qm, nsteps, targets)) / (2 * h)
+        assert np.isclose(g[T], fd, rtol=1e-5, atol=0), (T, g[T], fd)
