@@ -82,6 +82,9 @@ typedef struct {
                         /* and Schur steps inside the FP64 FGMRES (residuals,  */
                         /* Gram-Schmidt, Hessenberg and the coarsest dense     */
                         /* solve stay FP64)                                    */
+  int graphs;           /* 1 (default): each Arnoldi step is captured once as  */
+                        /* a CUDA graph (on a private stream) and replayed;    */
+                        /* 0: kernels are launched one by one                  */
 } mhfp_options;
 
 typedef struct {

@@ -174,6 +174,70 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
 }
 // </hot:k_cheb_u0>
 
+// Scalar stencils (the interface-pressure cell levels) with their offset loop
+// unrolled: one lattice point per thread has only a handful of FMAs per
+// offset, so the independent loads of several offsets must be in flight at
+// once to cover the gather latency.
+template <int KIND, int UNR, typename T>
+__device__ __forceinline__ T scalar_residual(const Lat& L, long long p, const T* __restrict__ val,
+                                             const T* __restrict__ x, T r) {
+  int i, j, k;
+  L.ijk(p, i, j, k);
+#pragma unroll UNR
+  for (int o = 0; o < St<KIND>::N; ++o) {
+    int dx, dy, dz;
+    St<KIND>::off(o, dx, dy, dz);
+    const bool in = L.in(i + dx, j + dy, k + dz);
+    const long long q = in ? p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz) : p;
+    const T v = in ? val[(long long)o * L.N + p] : T(0);
+    r -= v * x[q];
+  }
+  return r;
+}
+
+template <int KIND, int UNR, typename T>
+__global__ void __launch_bounds__(256) k_spmv_s(Lat L, const T* __restrict__ val, const T* __restrict__ x,
+                                                const T* __restrict__ b, T* __restrict__ y) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const T r = scalar_residual<KIND, UNR, T>(L, p, val, x, T(0));
+  y[p] = b ? b[p] + r : -r;
+}
+
+template <int KIND, int UNR, typename T>
+__global__ void __launch_bounds__(256) k_cheb_s(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
+                                                const T* __restrict__ b, const T* __restrict__ xin,
+                                                T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  const T r = xin ? scalar_residual<KIND, UNR, T>(L, p, val, xin, b[p]) : b[p];
+  const T z = dinv[p] * r;
+  const T dn = (cd != T(0)) ? cd * d[p] + cr * z : cr * z;
+  d[p] = dn;
+  xout[p] = (xin ? xin[p] : T(0)) + dn;
+}
+
+// scalar prolongation x += P x_c with the slot loop unrolled
+template <int R, typename T>
+__global__ void __launch_bounds__(256) k_prolong_s(Lat F, Lat Cc, const T* __restrict__ P, const T* __restrict__ xc,
+                                                   T* __restrict__ x) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= F.N) return;
+  int a, b, c;
+  F.ijk(p, a, b, c);
+  constexpr int ns = (2 + 2 * R) / 3 + 1;
+  const int lx = p_lo(a, R), ly = p_lo(b, R), lz = p_lo(c, R);
+  T acc = T(0);
+#pragma unroll
+  for (int s = 0; s < ns * ns * ns; ++s) {
+    const int I = lx + s % ns, J = ly + (s / ns) % ns, K = lz + s / (ns * ns);
+    const bool in = Cc.in(I, J, K);
+    const T pv = in ? P[(long long)s * F.N + p] : T(0);
+    acc += pv * xc[in ? Cc.id(I, J, K) : 0];
+  }
+  x[p] += acc;
+}
+
 // Coarse lattices have few points, so one thread per point leaves most of the
 // GPU idle behind long serial loops over 27-125 offsets.  These variants give
 // each point a group of TPP consecutive lanes that split the offsets and
@@ -971,7 +1035,10 @@ void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
     const int tpp = b ? group_size(lat.N, L.A.kind) : 1;
     dispatch_bs(L.bs, [&](auto BS) {
       dispatch_kind(L.A.kind, [&](auto K) {
-        if (tpp == 1) {
+        if (tpp == 1 && BS.value == 1) {
+          k_spmv_s<K.value, (K.value == ST_BOX2 ? 5 : 25), T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(
+              lat, v.val, x, b, y);
+        } else if (tpp == 1) {
           k_spmv<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, y);
         } else {
           dispatch_tpp(tpp, [&](auto G) {
@@ -1017,7 +1084,10 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
       const int tpp = group_size(lat.N, L.A.kind);
       dispatch_bs(L.bs, [&](auto BS) {
         dispatch_kind(L.A.kind, [&](auto K) {
-          if (tpp == 1) {
+          if (tpp == 1 && BS.value == 1) {
+            k_cheb_s<K.value, (K.value == ST_BOX2 ? 5 : 25), T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(
+                lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
+          } else if (tpp == 1) {
             k_cheb<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out,
                                                                                       v.d, (T)cd, (T)cr);
           } else {
@@ -1075,9 +1145,13 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
     k_prolong_faces<T><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, x);
   } else {
     const Lat F = lat_of(L.A), Cc = lat_of(C.A);
-    dispatch_bs(L.bs, [&](auto BS) {
-      k_prolong<BS.value, T><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, L.R, v.P, cx, x);
-    });
+    if (L.bs == 1 && L.R == 2) {
+      k_prolong_s<2, T><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, v.P, cx, x);
+    } else {
+      dispatch_bs(L.bs, [&](auto BS) {
+        k_prolong<BS.value, T><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, L.R, v.P, cx, x);
+      });
+    }
   }
   MHFP_LAUNCH_CHECK();
   smooth<T>(c, H, l, b, x, false, fine_u);

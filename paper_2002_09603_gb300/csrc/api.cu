@@ -27,6 +27,16 @@ void dfree_all(Ctx& c) {
 }
 
 void timing_begin(Ctx& c, int cls) {
+  if (c.timing.capturing) {
+    // inside a graph capture: an external event-record node that records on
+    // every replay; the pair is read after each replay
+    TimedPair t{cls, nullptr, nullptr, 0.0};
+    MHFP_CUDA(cudaEventCreate(&t.start));
+    MHFP_CUDA(cudaEventCreate(&t.stop));
+    MHFP_CUDA(cudaEventRecordWithFlags(t.start, c.stream, cudaEventRecordExternal));
+    c.timing.capture_list->push_back(t);
+    return;
+  }
   if (!c.timing.enabled) return;
   auto& v = c.timing.ev_start[cls];
   if (c.timing.used[cls] >= v.size()) {
@@ -50,6 +60,12 @@ static void harvest(Ctx& c, int cls) {
 }
 
 void timing_end(Ctx& c, int cls, double bytes) {
+  if (c.timing.capturing) {
+    TimedPair& t = c.timing.capture_list->back();
+    t.bytes = bytes;
+    MHFP_CUDA(cudaEventRecordWithFlags(t.stop, c.stream, cudaEventRecordExternal));
+    return;
+  }
   if (!c.timing.enabled) return;
   MHFP_CUDA(cudaEventRecord(c.timing.ev_stop[cls][c.timing.used[cls]], c.stream));
   c.timing.used[cls]++;
@@ -106,6 +122,7 @@ void mhfp_default_options(mhfp_options* o) {
   o->coarse_max = 125;
   o->power_iters = 15;
   o->precision = 0;
+  o->graphs = 1;
 }
 
 const char* mhfp_status_string(mhfp_status s) {
@@ -200,7 +217,7 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
     if (opt) {
       if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
           !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
-          (opt->precision != 0 && opt->precision != 1))
+          (opt->precision != 0 && opt->precision != 1) || (opt->graphs != 0 && opt->graphs != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }
@@ -395,6 +412,15 @@ void mhfp_destroy(mhfp_handle h) {
     for (auto e : c.timing.ev_stop[k]) cudaEventDestroy(e);
   }
   if (c.host_scal) cudaFreeHost(c.host_scal);
+  for (int t = 0; t < 2; ++t)
+    for (auto& g : c.graphs[t]) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (auto& p : g.timed) {
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
+      }
+    }
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   mhfp::dfree_all(c);
   delete h;
 }

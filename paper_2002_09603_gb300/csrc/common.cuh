@@ -133,8 +133,23 @@ struct Level {
 };
 
 // ------------------------------------------------------------ handle
+struct TimedPair {
+  int cls;
+  cudaEvent_t start, stop;
+  double bytes;
+};
+
+// one captured FGMRES iteration (Arnoldi step j of a cycle)
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long nkernels = 0;
+  std::vector<TimedPair> timed;  // event-record nodes inside the graph
+};
+
 struct Timing {
   bool enabled = false;
+  bool capturing = false;                 // record events as graph nodes
+  std::vector<TimedPair>* capture_list = nullptr;
   std::vector<cudaEvent_t> ev_start[3], ev_stop[3];
   size_t used[3] = {0, 0, 0};
   long long launches[3] = {0, 0, 0};
@@ -194,6 +209,9 @@ struct Ctx {
 
   Timing timing;
   std::vector<void*> allocs;
+  // CUDA graphs of the Arnoldi steps: [transpose][j]
+  cudaStream_t cap_stream = nullptr;
+  std::vector<IterGraph> graphs[2];
 };
 
 // allocation helpers (tracked, freed at destroy)

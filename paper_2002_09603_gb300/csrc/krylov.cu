@@ -347,6 +347,103 @@ void apply_precond(Ctx& c, const double* v, double* z, bool transpose) {
   precond_blocks<double>(c, v, z, c.hu[0].b, c.hpi[0].b, transpose);
 }
 
+// Enqueue Arnoldi step j: z_j = M^-1 v_j, w = D_s A z_j, Gram-Schmidt, the
+// Givens update, v_{j+1}, and the copy of |g_{j+1}| to pinned host memory.
+void enqueue_arnoldi_step(Ctx& c, int j, bool transpose) {
+  const int m = c.opt.restart;
+  const long long n = c.n;
+  double* vj = c.V + (long long)j * n;
+  double* zj = c.Z + (long long)j * n;
+  if (c.opt.precision == 1) {
+    apply_precond_mixed(c, vj, c.ds_inv, zj, transpose);  // unscale into the FP32 preconditioner
+  } else {
+    vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
+    apply_precond(c, c.t, zj, transpose);
+  }
+  apply_operator(c, zj, c.w, c.ds, nullptr, transpose);  // w = D_s A z_j
+  timing_begin(c, 2);
+  // classical Gram-Schmidt with the DGKS reorthogonalisation test:
+  // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the
+  // norm dropped by more than 1/sqrt(2), h2 = V^T w and w -= V h2
+  gs_dots(c, j + 1, c.h, c.scal + 4, nullptr);
+  k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
+                                                     nullptr);
+  MHFP_LAUNCH_CHECK();
+  k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 5, 0);
+  MHFP_LAUNCH_CHECK();
+  k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2);
+  MHFP_LAUNCH_CHECK();
+  gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
+  k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
+                                                     c.partials + (size_t)m * GS_BLOCKS, c.dflag);
+  MHFP_LAUNCH_CHECK();
+  k_reduce_partials_flag<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 2,
+                                                         c.dflag);
+  MHFP_LAUNCH_CHECK();
+  timing_end(c, 2, 8.0 * n * (2.0 * (j + 1) + 4.0));
+  k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, c.h + (m + 1), c.scal + 2, c.H, c.cs, c.sn, c.g, c.scal);
+  MHFP_LAUNCH_CHECK();
+  k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
+  MHFP_LAUNCH_CHECK();
+  MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+}
+
+// Run Arnoldi step j and wait for it.  With graphs enabled the step is
+// captured once per (j, transpose) on a private stream and replayed into the
+// handle's stream afterwards: one launch instead of ~90.
+void arnoldi_step(Ctx& c, int j, bool transpose) {
+  if (!c.opt.graphs) {
+    enqueue_arnoldi_step(c, j, transpose);
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    return;
+  }
+  auto& G = c.graphs[transpose ? 1 : 0];
+  if ((int)G.size() < c.opt.restart) G.resize(c.opt.restart);
+  IterGraph& ig = G[j];
+  if (!ig.exec) {
+    if (!c.cap_stream) MHFP_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c.stream;
+    const long long l0 = g_launches;
+    c.stream = c.cap_stream;
+    c.timing.capturing = true;
+    c.timing.capture_list = &ig.timed;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        enqueue_arnoldi_step(c, j, transpose);
+      } catch (...) {
+        cudaStreamEndCapture(c.cap_stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        c.stream = user;
+        c.timing.capturing = false;
+        throw;
+      }
+      e = cudaStreamEndCapture(c.cap_stream, &graph);
+    }
+    c.stream = user;
+    c.timing.capturing = false;
+    c.timing.capture_list = nullptr;
+    MHFP_CUDA(e);
+    ig.nkernels = g_launches - l0;
+    g_launches = l0;  // nothing ran during the capture
+    e = cudaGraphInstantiate(&ig.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MHFP_CUDA(e);
+  }
+  MHFP_CUDA(cudaGraphLaunch(ig.exec, c.stream));
+  g_launches += ig.nkernels;
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  if (c.timing.enabled)
+    for (auto& t : ig.timed) {
+      float ms = 0.f;
+      MHFP_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+      c.timing.total_ms[t.cls] += ms;
+      c.timing.launches[t.cls] += 1;
+      c.timing.bytes[t.cls] += t.bytes;
+    }
+}
+
 void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st, bool transpose) {
   const auto t0 = std::chrono::steady_clock::now();
   ensure_workspace(c);
@@ -378,40 +475,8 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
     MHFP_LAUNCH_CHECK();
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      double* vj = c.V + (long long)j * n;
-      double* zj = c.Z + (long long)j * n;
-      if (c.opt.precision == 1) {
-        apply_precond_mixed(c, vj, c.ds_inv, zj, transpose);  // unscale into the FP32 preconditioner
-      } else {
-        vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
-        apply_precond(c, c.t, zj, transpose);
-      }
-      apply_operator(c, zj, c.w, c.ds, nullptr, transpose);  // w = D_s A z_j
-      timing_begin(c, 2);
-      // classical Gram-Schmidt with the DGKS reorthogonalisation test:
-      // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the
-      // norm dropped by more than 1/sqrt(2), h2 = V^T w and w -= V h2
-      gs_dots(c, j + 1, c.h, c.scal + 4, nullptr);
-      k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
-                                                         nullptr);
-      MHFP_LAUNCH_CHECK();
-      k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 5, 0);
-      MHFP_LAUNCH_CHECK();
-      k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2);
-      MHFP_LAUNCH_CHECK();
-      gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
-      k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
-                                                         c.partials + (size_t)m * GS_BLOCKS, c.dflag);
-      MHFP_LAUNCH_CHECK();
-      k_reduce_partials_flag<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
-                                                             c.scal + 2, c.dflag);
-      MHFP_LAUNCH_CHECK();
-      timing_end(c, 2, 8.0 * n * (2.0 * (j + 1) + 4.0));
-      k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, c.h + (m + 1), c.scal + 2, c.H, c.cs, c.sn, c.g, c.scal);
-      MHFP_LAUNCH_CHECK();
-      k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
-      MHFP_LAUNCH_CHECK();
-      const double resid = read_scalar(c, c.scal);
+      arnoldi_step(c, j, transpose);
+      const double resid = c.host_scal[0];
       ++total;
       k = j + 1;
       est = resid / bnorm;
