@@ -37,6 +37,8 @@ WORKLOADS = {
     "lognormal64": dict(n=64, desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
     "lognormal32": dict(n=32, desc="32^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
     "lognormal96": dict(n=96, desc="96^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "batch48": dict(n=0, desc="48 cubes n ~ U{16..64} (seed 4), own log-normal kappa (sigma 1.5), loads x0.5/1/2/4, "
+                              "FP32 V-cycles in FP64 FGMRES(12), one mhfp_solve_batch call per load"),
 }
 
 
@@ -433,8 +435,62 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Auxiliary workload: many uneven instances x 4 loads; reports the time
+    per solved system with all instances batched (concurrent streams and
+    graph replays) beside the same solves one after another."""
+    import torch
+    import mhfp_inputs as mi
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_09603_gb300 import launch_count
+    from paper_2002_09603_gb300.batch import prepare_batch, solve_loads
+
+    probs = mi.batch_instances()
+    t0 = time.perf_counter()
+    solvers = prepare_batch(probs, precision=1, restart=args.restart)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    for _ in range(max(1, args.warmup)):
+        solve_loads(solvers, (1.0,))
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    t0 = time.perf_counter()
+    res = solve_loads(solvers, mi.LOAD_SCALES)
+    torch.cuda.synchronize()
+    batched = time.perf_counter() - t0
+    launches = launch_count() - l0
+    nsys = len(solvers) * len(mi.LOAD_SCALES)
+    ok = all(c == 0 for _, _, codes in res for c in codes)
+    iters = [st["iterations"] for _, stats, _ in res for st in stats]
+    # the same solves one handle at a time
+    t0 = time.perf_counter()
+    for scale in mi.LOAD_SCALES:
+        for sv in solvers:
+            b = sv.build_rhs(None, load_scale=scale)
+            sv.solve(b, tol=TOL)
+            sv.stream.synchronize()
+    serial = time.perf_counter() - t0
+    unknowns = sum(sum(sv.sizes) for sv in solvers)
+    line = {"metric": "time per solved system, batched (" + METRIC + ")", "value": batched * 1e3 / nsys, "unit": "ms",
+            "n_gpus": 1, "steps": 1, "warmup": args.warmup, "ms_per_step": batched * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch48"]["desc"], "instances": len(solvers), "systems": nsys,
+                       "unknowns_per_load": unknowns, "sizes": [p.nx for p in probs], "all_converged": ok,
+                       "iterations_min_max": [min(iters), max(iters)], "setup_s": setup_s,
+                       "serial_ms_per_system": serial * 1e3 / nsys, "batched_speedup": serial / batched},
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    for sv in solvers:
+        sv.close()
+
+
 def main():
     args = parse()
+    if args.workload == "batch48":
+        run_batch(args)
+        return
     if args.oracle_sample:
         tgt, it = args.oracle_target.split(",")
         d, _ = oracle_sample(int(tgt), float(it), sample_n=args.oracle_sample)

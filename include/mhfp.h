@@ -85,6 +85,9 @@ typedef struct {
   int graphs;           /* 1 (default): each Arnoldi step is captured once as  */
                         /* a CUDA graph (on a private stream) and replayed;    */
                         /* 0: kernels are launched one by one                  */
+  int autotune;         /* 1 (default): time the lanes-per-point variants of   */
+                        /* each coarse level's smoother at set-up and keep the */
+                        /* fastest (launch schedule only, same arithmetic)     */
 } mhfp_options;
 
 typedef struct {
@@ -138,6 +141,17 @@ mhfp_status mhfp_build_rhs(mhfp_handle h, const double* d_x_prev, double load_sc
  * tol ||D_s b||.  d_rhs, d_x: device vectors (d_x is overwritten).
  * stats may be NULL.  Synchronises the stream. */
 mhfp_status mhfp_solve(mhfp_handle h, const double* d_rhs, double* d_x, double tol, mhfp_stats* stats);
+
+/* Solve `count` independent systems (different handles: meshes, materials,
+ * dt, right-hand sides) together.  Each handle's FGMRES (the same algorithm
+ * as mhfp_solve) is advanced step by step in round-robin order; the work of
+ * every Arnoldi step is one CUDA-graph replay on the handle's own stream, so
+ * handles created on distinct streams run concurrently on the device.
+ * stats and statuses (count entries each) may be NULL; returns the first
+ * non-OK status (in handle order), MHFP_OK if every solve converged.  Not in
+ * the paper: batching of its solve over parameter samples and loads. */
+mhfp_status mhfp_solve_batch(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
+                             double tol, mhfp_stats* stats, mhfp_status* statuses);
 
 /* y = A_H x (Eq. stab_A, hybrid form), unscaled. */
 mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y);

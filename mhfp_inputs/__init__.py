@@ -260,3 +260,18 @@ def state_vector(rng, prob: Problem) -> np.ndarray:
     """A seeded random vector in the solver's layout [u (node-major) | p | pi]."""
     nu_, np_, npi = prob.sizes
     return rng.standard_normal(nu_ + np_ + npi)
+
+
+def batch_instances(count=48, seed=4, nmin=16, nmax=64, sigma=1.5, ell=8.0, kappa_mean=1e-13, dt=1e-3):
+    """`count` independent cube problems of uneven size n ~ U{nmin..nmax}
+    (seeded), each with its own log-normal permeability field (sigma, ell
+    cells), S_eps = 0, consolidation-column boundaries.  The batched workload
+    solves each for the loads LOAD_SCALES."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(nmin, nmax + 1, size=count)
+    seeds = rng.integers(0, 2 ** 31 - 1, size=count)
+    return [lognormal_cube(int(n), seed=int(s), sigma=sigma, ell=ell, kappa_mean=kappa_mean, dt=dt)
+            for n, s in zip(sizes, seeds)]
+
+
+LOAD_SCALES = (0.5, 1.0, 2.0, 4.0)

@@ -6,4 +6,4 @@ The compute path is the CUDA library ``libmhfp.so`` (built in-tree by
 ``paper_2002_09603_gb300.build``); this package only marshals arguments.
 """
 from ._lib import (MhfpError, Options, Solver, default_options, load,  # noqa: F401
-                   prepare, launch_count, EXPORTS, LIB_PATH)
+                   prepare, launch_count, solve_batch, EXPORTS, LIB_PATH)

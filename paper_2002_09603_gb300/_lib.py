@@ -24,7 +24,7 @@ EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhf
            "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_operator_t", "mhfp_adjoint_solve",
            "mhfp_grad_logk", "mhfp_misfit", "mhfp_adjoint_rhs", "mhfp_apply_precond_t", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
-           "mhfp_timing_read", "mhfp_residual_norm_noalloc", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
+           "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
 
 
 class MhfpError(RuntimeError):
@@ -46,7 +46,7 @@ class Materials(C.Structure):
 class Options(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_ratio", C.c_double), ("coarse_max", C.c_int), ("power_iters", C.c_int),
-                ("precision", C.c_int), ("graphs", C.c_int)]
+                ("precision", C.c_int), ("graphs", C.c_int), ("autotune", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -98,6 +98,8 @@ def load(path: str | None = None):
         "mhfp_timing": (i, [vp, i]),
         "mhfp_timing_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d), C.POINTER(d)]),
         "mhfp_residual_norm_noalloc": (i, [vp, vp, vp, vp]),
+        "mhfp_solve_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, C.POINTER(Stats),
+                                 C.POINTER(i)]),
         "mhfp_launch_count": (ll, []),
         "mhfp_last_error": (C.c_char_p, [vp]),
         "mhfp_status_string": (C.c_char_p, [i]),
@@ -286,6 +288,21 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_batch(solvers, rhs, tol=1e-8, out=None):
+    """Solve every solvers[i] with rhs[i] together (mhfp_solve_batch).
+    Returns (xs, stats, statuses)."""
+    import torch
+    n = len(solvers)
+    xs = out if out is not None else [s.empty() for s in solvers]
+    H = (C.c_void_p * n)(*[s.h.value for s in solvers])
+    R = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
+    X = (C.c_void_p * n)(*[t.data_ptr() for t in xs])
+    st = (Stats * n)()
+    codes = (C.c_int * n)()
+    load().mhfp_solve_batch(n, H, R, X, float(tol), st, codes)
+    return xs, [s.as_dict() for s in st], list(codes)
 
 
 def prepare(prob, options: Options | None = None, stream=None) -> Solver:

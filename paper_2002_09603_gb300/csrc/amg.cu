@@ -734,6 +734,7 @@ void dispatch_bs(int bs, F&& f) {
 FaceTopo face_topo(const Ctx& c) { return FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy}; }
 
 // lanes per lattice point: 1 on large levels, up to a warp on small ones
+// (overridden per level by the set-up autotuner)
 int group_size(long long npts, int kind) {
   if (npts >= 131072) return 1;
   if (npts >= 32768) return 4;
@@ -1032,7 +1033,7 @@ void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
     k_spmv_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, x, b, y);
   } else {
     const Lat lat = lat_of(L.A);
-    const int tpp = b ? group_size(lat.N, L.A.kind) : 1;
+    const int tpp = b ? (L.tpp ? L.tpp : group_size(lat.N, L.A.kind)) : 1;
     dispatch_bs(L.bs, [&](auto BS) {
       dispatch_kind(L.A.kind, [&](auto K) {
         if (tpp == 1 && BS.value == 1) {
@@ -1050,6 +1051,68 @@ void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
     });
   }
   MHFP_LAUNCH_CHECK();
+}
+
+// one Chebyshev sweep on a lattice level with `tpp` lanes per point
+template <typename T>
+void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* out, T cd, T cr, int tpp) {
+  const Lat lat = lat_of(L.A);
+  dispatch_bs(L.bs, [&](auto BS) {
+    dispatch_kind(L.A.kind, [&](auto K) {
+      if (tpp == 1 && BS.value == 1) {
+        k_cheb_s<K.value, (K.value == ST_BOX2 ? 5 : 25), T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(
+            lat, v.val, v.dinv, b, xin, out, v.d, cd, cr);
+      } else if (tpp == 1) {
+        k_cheb<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d,
+                                                                                  cd, cr);
+      } else {
+        dispatch_tpp(tpp, [&](auto G) {
+          k_cheb_g<BS.value, K.value, G.value, T><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
+              lat, v.val, v.dinv, b, xin, out, v.d, cd, cr);
+        });
+      }
+    });
+  });
+}
+
+// Set-up autotuner: time the lanes-per-point variants of a coarse level's
+// Chebyshev sweep (same arithmetic, different launch schedule) and keep the
+// fastest for this level's sweeps and residuals.
+template <typename T>
+void autotune_level(Ctx& c, Level& L) {
+  const LV<T> v = view(c, L, T());
+  T* b = bvec(L, T());
+  T* x = xvec(L, T());
+  MHFP_CUDA(cudaMemsetAsync(b, 0, L.n * sizeof(T), c.stream));
+  MHFP_CUDA(cudaMemsetAsync(x, 0, L.n * sizeof(T), c.stream));
+  MHFP_CUDA(cudaMemsetAsync(v.d, 0, L.n * sizeof(T), c.stream));
+  cudaEvent_t e0, e1;
+  MHFP_CUDA(cudaEventCreate(&e0));
+  MHFP_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tpp = group_size(L.A.N, L.A.kind);
+  for (int tpp : {1, 4, 16, 32}) {
+    for (int rep = 0; rep < 3; ++rep) {
+      launch_cheb<T>(c, L, v, b, x, v.y, T(0.5), T(0.5), tpp);
+      MHFP_LAUNCH_CHECK();
+    }
+    MHFP_CUDA(cudaEventRecord(e0, c.stream));
+    for (int rep = 0; rep < 10; ++rep) {
+      launch_cheb<T>(c, L, v, b, x, v.y, T(0.5), T(0.5), tpp);
+      MHFP_LAUNCH_CHECK();
+    }
+    MHFP_CUDA(cudaEventRecord(e1, c.stream));
+    MHFP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MHFP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_tpp = tpp;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.tpp = best_tpp;
 }
 
 template <typename T>
@@ -1080,24 +1143,7 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
       const Lat lat = lat_of(L.A);
       k_cheb_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
     } else {
-      const Lat lat = lat_of(L.A);
-      const int tpp = group_size(lat.N, L.A.kind);
-      dispatch_bs(L.bs, [&](auto BS) {
-        dispatch_kind(L.A.kind, [&](auto K) {
-          if (tpp == 1 && BS.value == 1) {
-            k_cheb_s<K.value, (K.value == ST_BOX2 ? 5 : 25), T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(
-                lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
-          } else if (tpp == 1) {
-            k_cheb<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out,
-                                                                                      v.d, (T)cd, (T)cr);
-          } else {
-            dispatch_tpp(tpp, [&](auto G) {
-              k_cheb_g<BS.value, K.value, G.value, T><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
-                  lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
-            });
-          }
-        });
-      });
+      launch_cheb<T>(c, L, v, b, xin, out, (T)cd, (T)cr, L.tpp ? L.tpp : group_size(L.A.N, L.A.kind));
     }
     MHFP_LAUNCH_CHECK();
     // algorithmic bytes of a Chebyshev sweep: 27 x 9 matrix values and the
@@ -1194,6 +1240,16 @@ void build_hierarchies(Ctx& c) {
     make_fp32(c, c.hpi);
     c.Cpif = cast_copy(c, c.Cpi, (size_t)11 * c.nF);
     c.pwf = cast_copy(c, c.pw, c.nF);
+  }
+  if (c.opt.autotune) {
+    // the finest displacement level always runs k_cheb_u0; tune the others
+    for (auto* H : {&c.hu, &c.hpi})
+      for (size_t l = 0; l < H->size(); ++l) {
+        Level& L = (*H)[l];
+        if (L.faces || L.dense_inv || (H == &c.hu && l == 0)) continue;
+        if (c.opt.precision == 1) autotune_level<float>(c, L);
+        else autotune_level<double>(c, L);
+      }
   }
 }
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 namespace mhfp {
 
@@ -123,6 +124,7 @@ void mhfp_default_options(mhfp_options* o) {
   o->power_iters = 15;
   o->precision = 0;
   o->graphs = 1;
+  o->autotune = 1;
 }
 
 const char* mhfp_status_string(mhfp_status s) {
@@ -217,7 +219,8 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
     if (opt) {
       if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
           !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
-          (opt->precision != 0 && opt->precision != 1) || (opt->graphs != 0 && opt->graphs != 1))
+          (opt->precision != 0 && opt->precision != 1) || (opt->graphs != 0 && opt->graphs != 1) ||
+          (opt->autotune != 0 && opt->autotune != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }
@@ -398,6 +401,58 @@ mhfp_status mhfp_residual_norm_noalloc(mhfp_handle h, const double* d_b, const d
     if (!d_b || !d_x || !d_out) throw Error{MHFP_ERR_ARG, "bad vectors"};
     mhfp::residual_norm_noalloc(c, d_b, d_x, d_out);
   });
+}
+
+mhfp_status mhfp_solve_batch(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
+                             double tol, mhfp_stats* stats, mhfp_status* statuses) {
+  if (count < 0 || (count > 0 && (!hs || !d_rhs || !d_x))) return MHFP_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0)) return MHFP_ERR_ARG;
+  std::vector<mhfp::FgState> st(count);
+  std::vector<mhfp_status> code(count, MHFP_OK);
+  std::vector<char> active(count, 0);
+  auto fail = [&](int i, mhfp_status s, const std::string& msg) {
+    code[i] = s;
+    active[i] = 0;
+    if (hs[i]) hs[i]->c.err = msg;
+  };
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !d_rhs[i] || !d_x[i]) { code[i] = MHFP_ERR_ARG; continue; }
+    Ctx& c = hs[i]->c;
+    try {
+      MHFP_CUDA(cudaSetDevice(c.device));
+      if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+      mhfp::fgmres_begin(c, st[i], d_rhs[i], d_x[i], tol, false);
+      active[i] = 1;
+    } catch (const Error& e) {
+      fail(i, e.status, e.msg);
+    }
+  }
+  // every round: drain each handle's stream and queue its next piece of
+  // work; handles on distinct streams run concurrently on the device
+  bool any = true;
+  while (any) {
+    any = false;
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      Ctx& c = hs[i]->c;
+      try {
+        MHFP_CUDA(cudaSetDevice(c.device));
+        MHFP_CUDA(cudaStreamSynchronize(c.stream));
+        mhfp::fgmres_advance(c, st[i]);
+        if (st[i].phase == mhfp::FgState::DONE) active[i] = 0;
+      } catch (const Error& e) {
+        fail(i, e.status, e.msg);
+      }
+      any = any || active[i];
+    }
+  }
+  mhfp_status first = MHFP_OK;
+  for (int i = 0; i < count; ++i) {
+    if (stats) stats[i] = st[i].stats;
+    if (statuses) statuses[i] = code[i];
+    if (first == MHFP_OK && code[i] != MHFP_OK) first = code[i];
+  }
+  return first;
 }
 
 long long mhfp_launch_count(void) { return mhfp::g_launches; }

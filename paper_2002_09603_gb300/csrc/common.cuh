@@ -3,7 +3,7 @@
 
 #include <cuda_runtime.h>
 
-#include <atomic>
+#include <chrono>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -122,6 +122,7 @@ struct Level {
   // prolongator to the next level (lattice levels only): [p_slots^3][bs*bs][npts]
   double* P = nullptr;
   int R = 1;                  // stencil radius of A (L_inf)
+  int tpp = 0;                // lanes per point chosen by the autotuner (0: default rule)
   unsigned char* active = nullptr;  // [n] free dofs
   // work vectors of length n
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *y = nullptr;
@@ -214,6 +215,23 @@ struct Ctx {
   std::vector<IterGraph> graphs[2];
 };
 
+// resumable FGMRES: each advance consumes one scalar read back from the
+// device and queues the next piece of work (used to interleave many handles)
+struct FgState {
+  enum Phase { NEED_BNORM, NEED_BETA, NEED_RESID, DONE };
+  int phase = DONE;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double tol = 0.0;
+  bool transpose = false;
+  double bnorm = 0.0, est = 1.0;
+  int total = 0, cycles = 0, j = 0;
+  bool converged = false;
+  mhfp_stats stats{};
+  std::chrono::steady_clock::time_point t0;
+  IterGraph* graph = nullptr;
+};
+
 // allocation helpers (tracked, freed at destroy)
 void* dalloc(Ctx& c, size_t bytes);
 template <class T>
@@ -254,6 +272,8 @@ void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* 
 
 // krylov.cu
 void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st, bool transpose = false);
+void fgmres_begin(Ctx& c, FgState& f, const double* b, double* x, double tol, bool transpose);
+void fgmres_advance(Ctx& c, FgState& f);
 void apply_precond(Ctx& c, const double* v, double* z, bool transpose = false);
 double device_norm2(Ctx& c, const double* x, long long n);
 void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y, long long n);

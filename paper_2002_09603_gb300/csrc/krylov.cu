@@ -388,14 +388,15 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose) {
   MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
 }
 
-// Run Arnoldi step j and wait for it.  With graphs enabled the step is
-// captured once per (j, transpose) on a private stream and replayed into the
-// handle's stream afterwards: one launch instead of ~90.
-void arnoldi_step(Ctx& c, int j, bool transpose) {
+namespace {
+
+// Queue Arnoldi step j (no synchronisation).  With graphs enabled the step
+// is captured once per (j, transpose) on a private stream and replayed into
+// the handle's stream afterwards: one launch instead of ~90.
+IterGraph* launch_arnoldi_step(Ctx& c, int j, bool transpose) {
   if (!c.opt.graphs) {
     enqueue_arnoldi_step(c, j, transpose);
-    MHFP_CUDA(cudaStreamSynchronize(c.stream));
-    return;
+    return nullptr;
   }
   auto& G = c.graphs[transpose ? 1 : 0];
   if ((int)G.size() < c.opt.restart) G.resize(c.opt.restart);
@@ -433,74 +434,137 @@ void arnoldi_step(Ctx& c, int j, bool transpose) {
   }
   MHFP_CUDA(cudaGraphLaunch(ig.exec, c.stream));
   g_launches += ig.nkernels;
-  MHFP_CUDA(cudaStreamSynchronize(c.stream));
-  if (c.timing.enabled)
-    for (auto& t : ig.timed) {
-      float ms = 0.f;
-      MHFP_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
-      c.timing.total_ms[t.cls] += ms;
-      c.timing.launches[t.cls] += 1;
-      c.timing.bytes[t.cls] += t.bytes;
+  return &ig;
+}
+
+// queue D_s (b - A x) and its squared norm into host_scal[0]
+void enqueue_residual(Ctx& c, const FgState& f) {
+  apply_operator(c, f.x, c.tmp, c.ds, f.b, f.transpose);
+  norm2_dev(c, c.tmp, c.n, c.scal + 4);
+  MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+}
+
+void finish(Ctx& c, FgState& f, double true_rel) {
+  f.converged = f.converged || true_rel <= 1.05 * f.tol;
+  f.stats.iterations = f.total;
+  f.stats.restarts = f.cycles;
+  f.stats.converged = f.converged ? 1 : 0;
+  f.stats.rel_residual = f.est;
+  f.stats.true_rel_residual = true_rel;
+  f.stats.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - f.t0).count();
+  f.phase = FgState::DONE;
+  if (!f.converged) throw Error{MHFP_ERR_NOT_CONVERGED, "FGMRES reached maxit before the tolerance"};
+}
+
+}  // namespace
+
+// Start a solve: x = 0 and ||D_s b|| queued; the caller synchronises the
+// handle's stream and calls fgmres_advance until the state is DONE.
+void fgmres_begin(Ctx& c, FgState& f, const double* b, double* x, double tol, bool transpose) {
+  f = FgState{};
+  f.b = b;
+  f.x = x;
+  f.tol = tol;
+  f.transpose = transpose;
+  f.t0 = std::chrono::steady_clock::now();
+  ensure_workspace(c);
+  MHFP_CUDA(cudaMemsetAsync(x, 0, c.n * sizeof(double), c.stream));
+  vec_scale(c, b, c.ds, false, c.tmp, c.n);
+  norm2_dev(c, c.tmp, c.n, c.scal + 4);
+  MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  f.phase = FgState::NEED_BNORM;
+}
+
+// One state transition, after the handle's stream has drained: read the
+// scalar the last queued work produced and queue the next piece of work.
+// Right-preconditioned FGMRES(m), zero initial guess (Section 5), on the
+// equilibrated system; a cycle restarts from the true residual, and the
+// solve ends when that true residual meets 1.05 tol (or maxit is reached).
+void fgmres_advance(Ctx& c, FgState& f) {
+  const int m = c.opt.restart;
+  const long long n = c.n;
+  switch (f.phase) {
+    case FgState::NEED_BNORM: {
+      f.bnorm = std::sqrt(c.host_scal[0]);
+      if (!std::isfinite(f.bnorm)) throw Error{MHFP_ERR_NONFINITE, "non-finite right-hand side"};
+      if (f.bnorm == 0.0) {
+        f.converged = true;
+        f.est = 0.0;
+        finish(c, f, 0.0);
+        return;
+      }
+      enqueue_residual(c, f);
+      f.phase = FgState::NEED_BETA;
+      return;
     }
+    case FgState::NEED_BETA: {
+      const double beta = std::sqrt(c.host_scal[0]);
+      if (!std::isfinite(beta)) throw Error{MHFP_ERR_NONFINITE, "non-finite residual"};
+      if (beta <= 1.05 * f.tol * f.bnorm) {
+        f.converged = true;
+        f.est = beta / f.bnorm;
+        finish(c, f, beta / f.bnorm);
+        return;
+      }
+      if (f.total >= c.opt.maxit) {
+        finish(c, f, beta / f.bnorm);
+        return;
+      }
+      k_scale_host<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.tmp, 1.0 / beta, c.V);
+      MHFP_LAUNCH_CHECK();
+      k_set_g<<<1, 64, 0, c.stream>>>(m, beta, c.g);
+      MHFP_LAUNCH_CHECK();
+      f.j = 0;
+      f.graph = launch_arnoldi_step(c, 0, f.transpose);
+      f.phase = FgState::NEED_RESID;
+      return;
+    }
+    case FgState::NEED_RESID: {
+      if (f.graph && c.timing.enabled)
+        for (auto& t : f.graph->timed) {
+          float ms = 0.f;
+          MHFP_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+          c.timing.total_ms[t.cls] += ms;
+          c.timing.launches[t.cls] += 1;
+          c.timing.bytes[t.cls] += t.bytes;
+        }
+      const double resid = c.host_scal[0];
+      ++f.total;
+      const int k = f.j + 1;
+      f.est = resid / f.bnorm;
+      if (!std::isfinite(resid)) throw Error{MHFP_ERR_NONFINITE, "non-finite Arnoldi residual"};
+      if (resid <= f.tol * f.bnorm || f.total >= c.opt.maxit || k == m) {
+        k_lsq<<<1, 32, 0, c.stream>>>(k, m, c.H, c.g, c.yv);
+        MHFP_LAUNCH_CHECK();
+        k_gemv_add<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, k, c.yv, f.x);
+        MHFP_LAUNCH_CHECK();
+        ++f.cycles;
+        enqueue_residual(c, f);
+        f.phase = FgState::NEED_BETA;
+        return;
+      }
+      f.j = k;
+      f.graph = launch_arnoldi_step(c, f.j, f.transpose);
+      return;
+    }
+    default:
+      return;
+  }
 }
 
 void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st, bool transpose) {
-  const auto t0 = std::chrono::steady_clock::now();
-  ensure_workspace(c);
-  const int m = c.opt.restart;
-  const long long n = c.n;
-  MHFP_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), c.stream));
-  vec_scale(c, b, c.ds, false, c.tmp, n);
-  norm2_dev(c, c.tmp, n, c.scal + 4);
-  const double bnorm = std::sqrt(read_scalar(c, c.scal + 4));
-  mhfp_stats s{};
-  if (!std::isfinite(bnorm)) throw Error{MHFP_ERR_NONFINITE, "non-finite right-hand side"};
-  if (bnorm == 0.0) {
-    s.converged = 1;
-    if (st) *st = s;
-    return;
-  }
-  int total = 0, cycles = 0;
-  bool converged = false;
-  double est = 1.0;
-  while (total < c.opt.maxit) {
-    apply_operator(c, x, c.tmp, c.ds, b, transpose);  // tmp = D_s (b - A x)
-    norm2_dev(c, c.tmp, n, c.scal + 4);
-    const double beta = std::sqrt(read_scalar(c, c.scal + 4));
-    if (!std::isfinite(beta)) throw Error{MHFP_ERR_NONFINITE, "non-finite residual"};
-    if (beta <= 1.05 * tol * bnorm) { converged = true; est = beta / bnorm; break; }
-    k_scale_host<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.tmp, 1.0 / beta, c.V);
-    MHFP_LAUNCH_CHECK();
-    k_set_g<<<1, 64, 0, c.stream>>>(m, beta, c.g);
-    MHFP_LAUNCH_CHECK();
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      arnoldi_step(c, j, transpose);
-      const double resid = c.host_scal[0];
-      ++total;
-      k = j + 1;
-      est = resid / bnorm;
-      if (!std::isfinite(resid)) throw Error{MHFP_ERR_NONFINITE, "non-finite Arnoldi residual"};
-      if (resid <= tol * bnorm || total >= c.opt.maxit) break;
+  FgState f;
+  fgmres_begin(c, f, b, x, tol, transpose);
+  try {
+    while (f.phase != FgState::DONE) {
+      MHFP_CUDA(cudaStreamSynchronize(c.stream));
+      fgmres_advance(c, f);
     }
-    k_lsq<<<1, 32, 0, c.stream>>>(k, m, c.H, c.g, c.yv);
-    MHFP_LAUNCH_CHECK();
-    k_gemv_add<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, k, c.yv, x);
-    MHFP_LAUNCH_CHECK();
-    ++cycles;
+  } catch (const Error& e) {
+    if (st) *st = f.stats;
+    throw;
   }
-  apply_operator(c, x, c.tmp, c.ds, b, transpose);
-  norm2_dev(c, c.tmp, n, c.scal + 4);
-  const double true_rel = std::sqrt(read_scalar(c, c.scal + 4)) / bnorm;
-  converged = converged || true_rel <= 1.05 * tol;
-  s.iterations = total;
-  s.restarts = cycles;
-  s.converged = converged ? 1 : 0;
-  s.rel_residual = est;
-  s.true_rel_residual = true_rel;
-  s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (st) *st = s;
-  if (!converged) throw Error{MHFP_ERR_NOT_CONVERGED, "FGMRES reached maxit before the tolerance"};
+  if (st) *st = f.stats;
 }
 
 }  // namespace mhfp

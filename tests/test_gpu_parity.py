@@ -295,6 +295,7 @@ def test_graph_replay_matches_direct_launches(precision):
         opt = default_options()
         opt.precision = precision
         opt.graphs = graphs
+        opt.autotune = 0  # same launch schedule in both runs
         opt.restart = 8
         s = Solver(prob)
         s.assemble_condense()
@@ -306,3 +307,29 @@ def test_graph_replay_matches_direct_launches(precision):
         s.close()
     assert xs[0][2:] == xs[1][2:]
     assert np.array_equal(xs[0][0], xs[1][0]) and np.array_equal(xs[0][1], xs[1][1])
+
+
+def test_batch_solve_matches_individual_solves():
+    """mhfp_solve_batch over handles of uneven size, each on its own stream,
+    gives the same iterates as solving each handle alone (same kernels, same
+    order per handle), for every load of the batched workload."""
+    from paper_2002_09603_gb300 import solve_batch
+    from paper_2002_09603_gb300.batch import prepare_batch
+    probs = [mi.lognormal_cube(n, seed=s, sigma=1.5) for n, s in ((6, 1), (11, 2), (9, 3), (14, 4))]
+    solvers = prepare_batch(probs, precision=1, restart=12)
+    for scale in (0.5, 2.0):
+        rhs = [s.build_rhs(None, load_scale=scale) for s in solvers]
+        torch.cuda.synchronize()
+        alone = []
+        for s, b in zip(solvers, rhs):
+            x, st = s.solve(b, tol=1e-9)
+            s.stream.synchronize()
+            alone.append((x.cpu().numpy(), st["iterations"]))
+        xs, stats, codes = solve_batch(solvers, rhs, tol=1e-9)
+        torch.cuda.synchronize()
+        assert codes == [0] * len(solvers)
+        for (xa, ia), xb, st in zip(alone, xs, stats):
+            assert st["iterations"] == ia and st["converged"]
+            assert np.array_equal(xa, xb.cpu().numpy())
+    for s in solvers:
+        s.close()
