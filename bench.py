@@ -259,6 +259,24 @@ def cheb_u0_flops(n):
     return 2 * 9 * blocks + 2 * 9 * nodes + 4 * 3 * nodes
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_max(value, dist, device):
+    """Max of a per-rank float over all ranks (the job's time is its slowest
+    rank's); identity on one process."""
+    import torch
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_time(ms_max, world):
+    """Whole-job time per step for a time-like metric with independent
+    replicas: world systems advance one step in the slowest rank's time."""
+    return ms_max / world
+
+
 # ------------------------------------------------------------------ ours
 def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local):
     """W warm-up steps, then K timed steps of a fresh simulation (CUDA events
@@ -294,9 +312,7 @@ def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local
     kt = s.timing_read(0)
     s.timing(False)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_max(ms, dist, "cuda")
     return dict(ms=ms, iters=iters, launches=launches, clocks=clocks, kt=kt)
 
 
@@ -373,10 +389,9 @@ def run_ours(args):
             torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
         if world > 1:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            e2e_ms = reduce_max(e2e_ms, dist, "cuda")
+        e2e = {"value": aggregate_time(e2e_ms, world), "unit": "ms", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel of the headline (mixed) form:
     # k_cheb_u0<float>, HBM-bound
@@ -411,7 +426,7 @@ def run_ours(args):
     nU, nP, nPi = s.sizes
     if rank == 0:
         line = {
-            "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": aggregate_time(ms, world), "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)",
             "data": "synthetic",

@@ -22,10 +22,24 @@ from . import elements, fgmres, mesh, precond, system  # noqa: F401
 from .system import assemble, rhs, system_matrix  # noqa: F401
 
 
-def solve_direct(B, b):
-    """The plain definition of the per-step result: x = A_H^-1 b."""
+def solve_direct(B, b, refine=2):
+    """The plain definition of the per-step result: x = A_H^-1 b.
+
+    The blocks of A_H differ by many orders of magnitude (stiffness vs.
+    kappa h / mu), so the LU is taken of the symmetrically scaled matrix
+    D A_H D with D = |diag(A_H)|^(-1/2), followed by `refine` steps of
+    iterative refinement on the unscaled residual."""
+    import numpy as np
+    import scipy.sparse as sp
     import scipy.sparse.linalg as spla
-    return spla.spsolve(system_matrix(B).tocsc(), b)
+    A = system_matrix(B).tocsc()
+    d = 1.0 / np.sqrt(np.abs(A.diagonal()))
+    D = sp.diags(d)
+    lu = spla.splu((D @ A @ D).tocsc())
+    x = d * lu.solve(d * b)
+    for _ in range(refine):
+        x = x + d * lu.solve(d * (b - A @ x))
+    return x
 
 
 def time_steps(prob, nsteps, kind="direct", tol=1e-10, restart=50, load_scale=1.0):

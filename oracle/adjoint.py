@@ -60,9 +60,26 @@ def coupling_matrix(B):
                     [None, None, sp.csr_matrix((nPi, nPi))]], format="csr")
 
 
+class _ScaledLU:
+    """x = M^-1 b from an LU of D M D, D = |diag(M)|^(-1/2), plus two steps of
+    iterative refinement (the blocks differ by many orders of magnitude)."""
+
+    def __init__(self, M):
+        self.M = M.tocsc()
+        self.d = 1.0 / np.sqrt(np.abs(self.M.diagonal()))
+        D = sp.diags(self.d)
+        self.lu = spla.splu((D @ self.M @ D).tocsc())
+
+    def solve(self, b):
+        x = self.d * self.lu.solve(self.d * b)
+        for _ in range(2):
+            x = x + self.d * self.lu.solve(self.d * (b - self.M @ x))
+        return x
+
+
 def forward(B, nsteps, load_scale=1.0):
     A = system.system_matrix(B).tocsc()
-    lu = spla.splu(A)
+    lu = _ScaledLU(A)
     nU, nP, _ = B.sizes
     xs, x = [], None
     for _ in range(nsteps):
@@ -94,7 +111,7 @@ def gradient(B, nsteps, misfit, load_scale=1.0):
     """(J, dJ/d ln kappa) by the discrete adjoint with direct solves."""
     xs = forward(B, nsteps, load_scale)
     A = system.system_matrix(B)
-    luT = spla.splu(A.T.tocsc())
+    luT = _ScaledLU(A.T)
     C = coupling_matrix(B)
     J = 0.0
     grad = np.zeros(B.sizes[1])

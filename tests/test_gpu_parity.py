@@ -46,6 +46,9 @@ CASES = [
     ("one", lambda: mi.random_small(1, 1, 1, seed=4)),
     ("terzaghi8", lambda: mi.terzaghi_cube(8)),
     ("ragged", lambda: mi.random_small(10, 4, 7, seed=5, jitter=0.1)),
+    # the 128^3 workload's physics at 16^3: jitter 0.2h, 8 layers with kappa over
+    # six decades and E over two, S_eps = 0, dt = 0.1 s
+    ("layered16", lambda: mi.layered_jitter_cube(16)),
 ]
 
 
@@ -237,7 +240,7 @@ def test_call_order_is_enforced():
 
 
 # ------------------------------------------------------------ FP32 V-cycles
-FP32_CASES = [c for c in CASES if c[0] in ("odd", "jitter7", "terzaghi8", "ragged")]
+FP32_CASES = [c for c in CASES if c[0] in ("odd", "jitter7", "terzaghi8", "ragged", "layered16")]
 
 
 @pytest.fixture(scope="module", params=FP32_CASES, ids=[c[0] for c in FP32_CASES])
