@@ -82,8 +82,11 @@ typedef struct {
                         /* and Schur steps inside the FP64 FGMRES (residuals,  */
                         /* Gram-Schmidt, Hessenberg and the coarsest dense     */
                         /* solve stay FP64)                                    */
-  int graphs;           /* 1 (default): each Arnoldi step is captured once as  */
-                        /* a CUDA graph (on a private stream) and replayed;    */
+  int graphs;           /* 2 (default): the whole solve is one CUDA graph      */
+                        /* (restart cycles in a WHILE node, Arnoldi steps in   */
+                        /* IF nodes, decisions taken on the device); 1: each   */
+                        /* Arnoldi step is one graph replay driven by the      */
+                        /* host (used whenever kernel timing is enabled);      */
                         /* 0: kernels are launched one by one                  */
   int autotune;         /* 1 (default): time the lanes-per-point variants of   */
                         /* each coarse level's smoother at set-up and keep the */

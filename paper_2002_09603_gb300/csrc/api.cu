@@ -28,6 +28,7 @@ void dfree_all(Ctx& c) {
 }
 
 void timing_begin(Ctx& c, int cls) {
+  if (c.suppress_events) return;
   if (c.timing.capturing) {
     // inside a graph capture: an external event-record node that records on
     // every replay; the pair is read after each replay
@@ -61,6 +62,7 @@ static void harvest(Ctx& c, int cls) {
 }
 
 void timing_end(Ctx& c, int cls, double bytes) {
+  if (c.suppress_events) return;
   if (c.timing.capturing) {
     TimedPair& t = c.timing.capture_list->back();
     t.bytes = bytes;
@@ -123,7 +125,7 @@ void mhfp_default_options(mhfp_options* o) {
   o->coarse_max = 125;
   o->power_iters = 15;
   o->precision = 0;
-  o->graphs = 1;
+  o->graphs = 2;
   o->autotune = 1;
 }
 
@@ -219,7 +221,7 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
     if (opt) {
       if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
           !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
-          (opt->precision != 0 && opt->precision != 1) || (opt->graphs != 0 && opt->graphs != 1) ||
+          (opt->precision != 0 && opt->precision != 1) || (opt->graphs < 0 || opt->graphs > 2) ||
           (opt->autotune != 0 && opt->autotune != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
@@ -421,8 +423,35 @@ mhfp_status mhfp_solve_batch(int count, const mhfp_handle* hs, const double* con
     try {
       MHFP_CUDA(cudaSetDevice(c.device));
       if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
-      mhfp::fgmres_begin(c, st[i], d_rhs[i], d_x[i], tol, false);
+      if (!(c.opt.graphs == 2 && !c.timing.enabled)) mhfp::fgmres_begin(c, st[i], d_rhs[i], d_x[i], tol, false);
       active[i] = 1;
+    } catch (const Error& e) {
+      fail(i, e.status, e.msg);
+    }
+  }
+  // device-driven solves: one graph launch per handle, all queued before any
+  // is waited for
+  std::vector<char> dev(count, 0);
+  for (int i = 0; i < count; ++i) {
+    if (!active[i]) continue;
+    Ctx& c = hs[i]->c;
+    if (c.opt.graphs != 2 || c.timing.enabled) continue;
+    try {
+      MHFP_CUDA(cudaSetDevice(c.device));
+      st[i] = mhfp::FgState{};
+      mhfp::solve_device_graph_launch(c, d_rhs[i], tol, false);
+      dev[i] = 1;
+    } catch (const Error& e) {
+      fail(i, e.status, e.msg);
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    if (!dev[i]) continue;
+    Ctx& c = hs[i]->c;
+    try {
+      MHFP_CUDA(cudaSetDevice(c.device));
+      mhfp::solve_device_graph_finish(c, d_x[i], &st[i].stats);
+      active[i] = 0;
     } catch (const Error& e) {
       fail(i, e.status, e.msg);
     }
@@ -476,6 +505,9 @@ void mhfp_destroy(mhfp_handle h) {
       }
     }
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  for (int t = 0; t < 2; ++t)
+    if (c.solve_exec[t]) cudaGraphExecDestroy(c.solve_exec[t]);
+  if (c.host_ctl) cudaFreeHost(c.host_ctl);
   mhfp::dfree_all(c);
   delete h;
 }

@@ -140,6 +140,12 @@ struct TimedPair {
   double bytes;
 };
 
+// FGMRES control block kept in device memory by the device-driven solve
+struct DevCtl {
+  double tol, bnorm, tolb, est, true_rel, pad0, pad1, pad2;
+  int maxit, m, total, cycles, k, converged, status, pad3;
+};
+
 // one captured FGMRES iteration (Arnoldi step j of a cycle)
 struct IterGraph {
   cudaGraphExec_t exec = nullptr;
@@ -209,10 +215,21 @@ struct Ctx {
   int npart = 0;
 
   Timing timing;
+  bool suppress_events = false;  // capture without timing events (conditional bodies)
   std::vector<void*> allocs;
   // CUDA graphs of the Arnoldi steps: [transpose][j]
   cudaStream_t cap_stream = nullptr;
   std::vector<IterGraph> graphs[2];
+  // device-driven whole solves (one graph launch per solve): [transpose]
+  cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
+  long long solve_nkernels[2] = {0, 0};        // kernels before the cycles
+  long long solve_cycle_kernels[2] = {0, 0};  // kernels of one cycle's fixed part
+  long long solve_step_kernels[2] = {0, 0};   // kernels of one Arnoldi step
+  int solve_pending = 0;
+  std::chrono::steady_clock::time_point solve_t0;
+  DevCtl* ctl = nullptr;                 // device control block
+  DevCtl* host_ctl = nullptr;            // pinned copy
+  double *bcur = nullptr, *xcur = nullptr;
 };
 
 // resumable FGMRES: each advance consumes one scalar read back from the
@@ -274,6 +291,8 @@ void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* 
 void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st, bool transpose = false);
 void fgmres_begin(Ctx& c, FgState& f, const double* b, double* x, double tol, bool transpose);
 void fgmres_advance(Ctx& c, FgState& f);
+void solve_device_graph_launch(Ctx& c, const double* b, double tol, bool transpose);
+void solve_device_graph_finish(Ctx& c, double* x, mhfp_stats* st);
 void apply_precond(Ctx& c, const double* v, double* z, bool transpose = false);
 double device_norm2(Ctx& c, const double* x, long long n);
 void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y, long long n);

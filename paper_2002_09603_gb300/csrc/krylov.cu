@@ -349,7 +349,7 @@ void apply_precond(Ctx& c, const double* v, double* z, bool transpose) {
 
 // Enqueue Arnoldi step j: z_j = M^-1 v_j, w = D_s A z_j, Gram-Schmidt, the
 // Givens update, v_{j+1}, and the copy of |g_{j+1}| to pinned host memory.
-void enqueue_arnoldi_step(Ctx& c, int j, bool transpose) {
+void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) {
   const int m = c.opt.restart;
   const long long n = c.n;
   double* vj = c.V + (long long)j * n;
@@ -385,7 +385,7 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose) {
   MHFP_LAUNCH_CHECK();
   k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
   MHFP_LAUNCH_CHECK();
-  MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  if (host_copy) MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
 }
 
 namespace {
@@ -552,7 +552,309 @@ void fgmres_advance(Ctx& c, FgState& f) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven solve: the whole FGMRES(m) -- restart cycles in a WHILE
+// conditional node, Arnoldi step j in IF node j -- is one CUDA graph,
+// launched once per solve.  The decisions the host loop makes (stop, restart,
+// next step) are taken by single-thread kernels that read the residual
+// estimates on the device and set the conditional handles.  Every loop is
+// bounded: a cycle runs at most m steps and the WHILE ends once maxit steps
+// have run.
+
+__global__ void k_ctl_init(DevCtl* __restrict__ ctl, const double* __restrict__ nrm2, cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double bn = sqrt(nrm2[0]);
+  ctl->bnorm = bn;
+  ctl->tolb = ctl->tol * bn;
+  ctl->est = 1.0;
+  ctl->true_rel = 0.0;
+  ctl->total = 0;
+  ctl->cycles = 0;
+  ctl->k = 0;
+  ctl->converged = 0;
+  ctl->status = 0;
+  ctl->pad3 = 0;  // cycle starts, a second bound on the WHILE loop
+  if (!isfinite(bn)) {
+    ctl->status = (int)MHFP_ERR_NONFINITE;
+    cudaGraphSetConditional(hw, 0);
+  } else if (bn == 0.0) {
+    ctl->converged = 1;
+    ctl->est = 0.0;
+    cudaGraphSetConditional(hw, 0);
+  } else {
+    cudaGraphSetConditional(hw, 1);
+  }
+}
+
+// start of a cycle: beta = ||D_s (b - A x)||; stop, or open step 0
+__global__ void k_cycle_decide(DevCtl* __restrict__ ctl, const double* __restrict__ nrm2, double* __restrict__ scal,
+                               double* __restrict__ g, cudaGraphConditionalHandle hw,
+                               const cudaGraphConditionalHandle* __restrict__ hif) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = ctl->m;
+  const double beta = sqrt(nrm2[0]);
+  ctl->k = 0;
+  ctl->pad3 += 1;
+  // every cycle either runs at least one step (total grows by one) or
+  // stops; the count of cycle starts bounds the loop even if a step did not
+  // run, so the WHILE node always terminates
+  bool stop = ctl->pad3 > ctl->maxit + 1;
+  if (stop) {
+    ctl->true_rel = beta / ctl->bnorm;
+  } else if (!isfinite(beta)) {
+    ctl->status = (int)MHFP_ERR_NONFINITE;
+    stop = true;
+  } else if (beta <= 1.05 * ctl->tolb) {
+    ctl->converged = 1;
+    ctl->est = beta / ctl->bnorm;
+    ctl->true_rel = beta / ctl->bnorm;
+    stop = true;
+  } else if (ctl->total >= ctl->maxit) {
+    ctl->true_rel = beta / ctl->bnorm;
+    stop = true;
+  }
+  if (stop) {
+    scal[6] = 0.0;
+    cudaGraphSetConditional(hw, 0);
+    for (int j = 0; j < m; ++j) cudaGraphSetConditional(hif[j], 0);
+    return;
+  }
+  scal[6] = 1.0 / beta;
+  g[0] = beta;
+  for (int i = 1; i <= m; ++i) g[i] = 0.0;
+  cudaGraphSetConditional(hif[0], 1);
+  for (int j = 1; j < m; ++j) cudaGraphSetConditional(hif[j], 0);
+}
+
+// after Arnoldi step j: count it and open step j+1 unless converged / done
+__global__ void k_step_done(DevCtl* __restrict__ ctl, const double* __restrict__ scal, int j,
+                            cudaGraphConditionalHandle hnext, int has_next, cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double resid = scal[0];
+  ctl->total += 1;
+  ctl->k = j + 1;
+  ctl->est = resid / ctl->bnorm;
+  bool next = has_next && resid > ctl->tolb && ctl->total < ctl->maxit;
+  if (!isfinite(resid)) {
+    ctl->status = (int)MHFP_ERR_NONFINITE;
+    next = false;
+    cudaGraphSetConditional(hw, 0);
+  }
+  if (has_next) cudaGraphSetConditional(hnext, next ? 1 : 0);
+}
+
+__global__ void k_lsq_dev(const DevCtl* __restrict__ ctl, const double* __restrict__ H, const double* __restrict__ g,
+                          double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = ctl->k, m = ctl->m;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int c = i + 1; c < k; ++c) s -= H[(long long)c * (m + 1) + i] * y[c];
+    const double d = H[(long long)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+__global__ void k_gemv_add_dev(long long n, const double* __restrict__ Z, const DevCtl* __restrict__ ctl,
+                               const double* __restrict__ y, double* __restrict__ x) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int k = ctl->k;
+  double s = x[r];
+  for (int c = 0; c < k; ++c) s += Z[(long long)c * n + r] * y[c];
+  x[r] = s;
+}
+
+__global__ void k_cycle_end(DevCtl* __restrict__ ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && ctl->k > 0) ctl->cycles += 1;
+}
+
+namespace {
+
+template <typename... P, typename... A>
+cudaGraphNode_t add_kernel(cudaGraph_t g, cudaGraphNode_t dep, void (*f)(P...), dim3 grid, dim3 block, A... args) {
+  void* params[] = {(void*)&args...};
+  cudaKernelNodeParams kp{};
+  kp.func = (void*)f;
+  kp.gridDim = grid;
+  kp.blockDim = block;
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = params;
+  kp.extra = nullptr;
+  cudaGraphNode_t node;
+  MHFP_CUDA(cudaGraphAddKernelNode(&node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp));
+  ++g_launches;  // counted like a launch; removed again after the build
+  return node;
+}
+
+template <class F>
+cudaGraph_t capture_piece(Ctx& c, F&& enqueue) {
+  if (!c.cap_stream) MHFP_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c.stream;
+  c.stream = c.cap_stream;
+  c.suppress_events = true;
+  cudaGraph_t graph = nullptr;
+  MHFP_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    enqueue();
+  } catch (...) {
+    cudaStreamEndCapture(c.cap_stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    c.stream = user;
+    c.suppress_events = false;
+    throw;
+  }
+  cudaError_t e = cudaStreamEndCapture(c.cap_stream, &graph);
+  c.stream = user;
+  c.suppress_events = false;
+  MHFP_CUDA(e);
+  return graph;
+}
+
+cudaGraphNode_t add_child(cudaGraph_t parent, cudaGraphNode_t dep, cudaGraph_t child) {
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, dep ? &dep : nullptr, dep ? 1 : 0, child);
+  cudaGraphDestroy(child);
+  MHFP_CUDA(e);
+  return node;
+}
+
+cudaGraphNode_t add_conditional(cudaGraph_t parent, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+                                cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  MHFP_CUDA(cudaGraphAddNode(&node, parent, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &np));
+  *body = np.conditional.phGraph_out[0];
+  return node;
+}
+
+void build_solve_graph(Ctx& c, bool transpose) {
+  ensure_workspace(c);
+  const int m = c.opt.restart;
+  const long long n = c.n;
+  if (!c.ctl) {
+    c.ctl = dalloc_n<DevCtl>(c, 1);
+    MHFP_CUDA(cudaMallocHost(&c.host_ctl, sizeof(DevCtl)));
+    c.bcur = dalloc_n<double>(c, n);
+    c.xcur = dalloc_n<double>(c, n);
+  }
+  const long long l0 = g_launches;
+  cudaGraph_t G;
+  MHFP_CUDA(cudaGraphCreate(&G, 0));
+  // the WHILE node sits in G, the IF nodes in the WHILE body: each handle is
+  // created on the graph that contains its node
+  cudaGraphConditionalHandle hw;
+  MHFP_CUDA(cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault));
+  DevCtl* ctl = c.ctl;
+  // x = 0, ||D_s b|| and the control block
+  cudaGraphNode_t last = add_child(G, nullptr, capture_piece(c, [&] {
+    MHFP_CUDA(cudaMemsetAsync(c.xcur, 0, n * sizeof(double), c.stream));
+    vec_scale(c, c.bcur, c.ds, false, c.tmp, n);
+    norm2_dev(c, c.tmp, n, c.scal + 4);
+  }));
+  const long long nk_start = g_launches - l0;
+  last = add_kernel(G, last, k_ctl_init, dim3(1), dim3(32), ctl, (const double*)(c.scal + 4), hw);
+  cudaGraph_t W;
+  cudaGraphNode_t wnode = add_conditional(G, last, hw, cudaGraphCondTypeWhile, &W);
+  std::vector<cudaGraphConditionalHandle> hif(m);
+  for (int j = 0; j < m; ++j) MHFP_CUDA(cudaGraphConditionalHandleCreate(&hif[j], W, 0, 0));
+  cudaGraphConditionalHandle* d_hif = dalloc_n<cudaGraphConditionalHandle>(c, m);
+  MHFP_CUDA(cudaMemcpy(d_hif, hif.data(), m * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice));
+  // while body: the cycle
+  const long long l1 = g_launches;
+  cudaGraphNode_t b = add_child(W, nullptr, capture_piece(c, [&] {
+    apply_operator(c, c.xcur, c.tmp, c.ds, c.bcur, transpose);
+    norm2_dev(c, c.tmp, n, c.scal + 4);
+  }));
+  b = add_kernel(W, b, k_cycle_decide, dim3(1), dim3(32), ctl, (const double*)(c.scal + 4), c.scal, c.g, hw,
+                 (const cudaGraphConditionalHandle*)d_hif);
+  b = add_child(W, b, capture_piece(c, [&] {
+    k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.tmp, c.scal + 6, c.V);
+    MHFP_LAUNCH_CHECK();
+  }));
+  const long long nk_cycle = g_launches - l1;
+  long long nk_step = 0;
+  for (int j = 0; j < m; ++j) {
+    cudaGraph_t body;
+    b = add_conditional(W, b, hif[j], cudaGraphCondTypeIf, &body);
+    const long long l2 = g_launches;
+    cudaGraphNode_t s = add_child(body, nullptr, capture_piece(c, [&] { enqueue_arnoldi_step(c, j, transpose, false); }));
+    add_kernel(body, s, k_step_done, dim3(1), dim3(32), ctl, (const double*)c.scal, j,
+               j + 1 < m ? hif[j + 1] : hif[j], j + 1 < m ? 1 : 0, hw);
+    nk_step = g_launches - l2;
+  }
+  const long long l3 = g_launches;
+  b = add_child(W, b, capture_piece(c, [&] {
+    k_lsq_dev<<<1, 32, 0, c.stream>>>(ctl, c.H, c.g, c.yv);
+    MHFP_LAUNCH_CHECK();
+    k_gemv_add_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, ctl, c.yv, c.xcur);
+    MHFP_LAUNCH_CHECK();
+    k_cycle_end<<<1, 32, 0, c.stream>>>(ctl);
+    MHFP_LAUNCH_CHECK();
+  }));
+  const long long nk_end = g_launches - l3;
+  // after the loop: the control block back to pinned host memory
+  cudaGraphNode_t fin;
+  MHFP_CUDA(cudaGraphAddMemcpyNode1D(&fin, G, &wnode, 1, c.host_ctl, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost));
+  g_launches = l0;  // nothing ran during the build
+  cudaGraphExec_t exec;
+  cudaError_t e = cudaGraphInstantiate(&exec, G, 0);
+  cudaGraphDestroy(G);
+  MHFP_CUDA(e);
+  const int t = transpose ? 1 : 0;
+  c.solve_exec[t] = exec;
+  // launches of one solve = start + per cycle (cycle + end) + per step
+  c.solve_nkernels[t] = nk_start + 1;
+  c.solve_cycle_kernels[t] = nk_cycle + nk_end;
+  c.solve_step_kernels[t] = nk_step;
+}
+
+}  // namespace
+
+void solve_device_graph_launch(Ctx& c, const double* b, double tol, bool transpose) {
+  const int t = transpose ? 1 : 0;
+  if (!c.solve_exec[t]) build_solve_graph(c, transpose);
+  c.solve_t0 = std::chrono::steady_clock::now();
+  MHFP_CUDA(cudaMemcpyAsync(c.bcur, b, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  DevCtl h{};
+  h.tol = tol;
+  h.maxit = c.opt.maxit;
+  h.m = c.opt.restart;
+  *c.host_ctl = h;
+  MHFP_CUDA(cudaMemcpyAsync(c.ctl, c.host_ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, c.stream));
+  MHFP_CUDA(cudaGraphLaunch(c.solve_exec[t], c.stream));
+  c.solve_pending = t;
+}
+
+void solve_device_graph_finish(Ctx& c, double* x, mhfp_stats* st) {
+  const int t = c.solve_pending;
+  MHFP_CUDA(cudaMemcpyAsync(x, c.xcur, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  const DevCtl& h = *c.host_ctl;
+  g_launches += c.solve_nkernels[t] + (long long)(h.cycles + 1) * c.solve_cycle_kernels[t] +
+                (long long)h.total * c.solve_step_kernels[t];
+  mhfp_stats s{};
+  s.iterations = h.total;
+  s.restarts = h.cycles;
+  s.converged = h.converged;
+  s.rel_residual = h.est;
+  s.true_rel_residual = h.true_rel;
+  s.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c.solve_t0).count();
+  if (st) *st = s;
+  if (h.status == (int)MHFP_ERR_NONFINITE) throw Error{MHFP_ERR_NONFINITE, "non-finite value in the solve"};
+  if (!h.converged) throw Error{MHFP_ERR_NOT_CONVERGED, "FGMRES reached maxit before the tolerance"};
+}
+
 void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st, bool transpose) {
+  if (c.opt.graphs == 2 && !c.timing.enabled) {
+    solve_device_graph_launch(c, b, tol, transpose);
+    solve_device_graph_finish(c, x, st);
+    return;
+  }
   FgState f;
   fgmres_begin(c, f, b, x, tol, transpose);
   try {

@@ -288,13 +288,14 @@ def test_fp32_solve_reaches_fp64_accuracy(case32):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_graph_replay_matches_direct_launches(precision):
-    """The captured-and-replayed Arnoldi steps run the same kernels in the
-    same order as direct launches: identical iterates, bit for bit, over a
-    restart and across two solves (graphs reused)."""
+    """Direct launches (0), per-step graph replays (1) and the device-driven
+    whole-solve graph (2, WHILE/IF conditional nodes) run the same kernels in
+    the same order: identical iterates, bit for bit, over several restarts
+    and across two solves (graphs reused)."""
     from paper_2002_09603_gb300 import Solver, default_options
     prob = mi.random_small(7, 6, 5, seed=3, jitter=0.25)
     xs = {}
-    for graphs in (0, 1):
+    for graphs in (0, 1, 2):
         opt = default_options()
         opt.precision = precision
         opt.graphs = graphs
@@ -308,8 +309,33 @@ def test_graph_replay_matches_direct_launches(precision):
         x2, st2 = s.solve(s.build_rhs(x1), tol=1e-10)
         xs[graphs] = (x1.cpu().numpy(), x2.cpu().numpy(), st1["iterations"], st2["iterations"])
         s.close()
-    assert xs[0][2:] == xs[1][2:]
-    assert np.array_equal(xs[0][0], xs[1][0]) and np.array_equal(xs[0][1], xs[1][1])
+    for g in (1, 2):
+        assert xs[0][2:] == xs[g][2:]
+        assert np.array_equal(xs[0][0], xs[g][0]) and np.array_equal(xs[0][1], xs[g][1])
+
+
+def test_device_driven_solve_stops_on_maxit_and_nonfinite():
+    """The whole-solve graph ends its WHILE loop on maxit (reporting
+    not-converged with the last iterate) and on a NaN right-hand side."""
+    from paper_2002_09603_gb300 import MhfpError, Solver, default_options
+    prob = mi.random_small(5, 4, 4, seed=9)
+    opt = default_options()
+    opt.graphs = 2
+    opt.maxit = 5
+    opt.restart = 3
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    b = s.build_rhs()
+    x, st = s.solve(b, tol=1e-12, raise_not_converged=False)
+    assert st["iterations"] == 5 and not st["converged"] and st["restarts"] == 2
+    assert torch.isfinite(x).all()
+    bad = b.clone()
+    bad[7] = float("nan")
+    with pytest.raises(MhfpError) as ei:
+        s.solve(bad, tol=1e-8)
+    assert ei.value.status == 6
+    s.close()
 
 
 def test_batch_solve_matches_individual_solves():
