@@ -34,17 +34,24 @@ TOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
 
 WORKLOADS = {
-    "lognormal64": dict(n=64, desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "lognormal64": dict(n=64, restart=12, desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
     "lognormal32": dict(n=32, desc="32^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
     "lognormal96": dict(n=96, desc="96^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "layered128": dict(n=128, gen="layered", restart=20,
+                       desc="128^3 hex, interior node jitter U(+-0.2h), 8 z-layers: kappa log-U[1e-18,1e-12] m^2, "
+                            "E log-U[1e8,1e10] Pa, nu U[0.2,0.35]; S_eps=0, dt=0.1 s (seed 3)"),
     "batch48": dict(n=0, desc="48 cubes n ~ U{16..64} (seed 4), own log-normal kappa (sigma 1.5), loads x0.5/1/2/4, "
                               "FP32 V-cycles in FP64 FGMRES(12), one mhfp_solve_batch call per load"),
 }
 
 
-def make_problem(name):
+def make_problem(name, n=None):
+    """The workload's problem, or the same generator at n^3 (oracle samples)."""
     import mhfp_inputs as mi
-    return mi.lognormal_cube(WORKLOADS[name]["n"])
+    n = WORKLOADS[name]["n"] if n is None else n
+    if WORKLOADS[name].get("gen") == "layered":
+        return mi.layered_jitter_cube(n)
+    return mi.lognormal_cube(n)
 
 
 def parse():
@@ -56,25 +63,33 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lognormal64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--restart", type=int, default=12,
-                    help="FGMRES restart length (12: fastest measured on the 64^3 workload)")
+    ap.add_argument("--restart", type=int, default=None,
+                    help="FGMRES restart length (default: the fastest measured for the workload, 12 at 64^3, "
+                         "20 at 128^3)")
+    ap.add_argument("--reorth", type=int, choices=[0, 1], default=0,
+                    help="Gram-Schmidt: 0 one classical pass (PETSc's GMRES default; same iterations and "
+                         "residuals on the workloads), 1 DGKS reorthogonalisation when needed")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="both: mixed headline with FP64-plain beside it (default)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-target", type=str, default="", help=argparse.SUPPRESS)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.restart is None:
+        args.restart = WORKLOADS[args.workload].get("restart", 12)
+    return args
 
 
 SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
                      "NUMEXPR_NUM_THREADS": "1"}
 
 
-def oracle_sample_subprocess(n_target_dofs, gpu_iters, sample_n=32):
+def oracle_sample_subprocess(workload, n_target_dofs, gpu_iters, sample_n=32):
     """Run the oracle sample in a fresh interpreter pinned to one BLAS/OpenMP
     thread (so the reported core count is exact), not forked from this
     CUDA process."""
     env = dict(os.environ, **SINGLE_THREAD_ENV)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(sample_n),
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", workload,
+                        "--oracle-sample", str(sample_n),
                         "--oracle-target", f"{n_target_dofs},{gpu_iters}"], env=env, capture_output=True,
                        text=True, timeout=600)
     if r.returncode != 0:
@@ -135,15 +150,13 @@ def clocks_stop(proc, path):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(n_target_dofs, gpu_iters, sample_n=32, nsteps=1):
+def oracle_sample(workload, n_target_dofs, gpu_iters, sample_n=32, nsteps=1):
     """The FP64 oracle (as it stands) on a bounded sample of the workload:
     `nsteps` time steps of the same generator at sample_n^3 (setup not
     timed), scaled to the full workload by unknowns x FGMRES iterations."""
-    import numpy as np
-    import mhfp_inputs as mi
     import oracle
     from oracle import fgmres, precond, system
-    prob = mi.lognormal_cube(sample_n)
+    prob = make_problem(workload, sample_n)
     B = oracle.assemble(prob)
     pc = precond.build(B, "amg")
     A = system.system_matrix(B)
@@ -175,12 +188,11 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import mhfp_inputs as mi
     n_full = sum(make_problem_sizes(args.workload))
     import oracle
     from oracle import fgmres, precond, system
     sample_n = 24
-    prob = mi.lognormal_cube(sample_n)
+    prob = make_problem(args.workload, sample_n)
     B = oracle.assemble(prob)
     pc = precond.build(B, "amg")
     A = system.system_matrix(B)
@@ -321,11 +333,12 @@ def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local
     return dict(ms=ms, iters=iters, launches=launches, clocks=clocks, kt=kt)
 
 
-def _solver(prob, precision, torch, restart=50):
+def _solver(prob, precision, torch, restart=50, reorth=1):
     from paper_2002_09603_gb300 import Solver, default_options
     opt = default_options()
     opt.precision = precision
     opt.restart = restart
+    opt.reorth = reorth
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -363,7 +376,7 @@ def run_ours(args):
     # mixed form (FP32 V-cycles and Schur steps inside FP64 FGMRES)
     r64, setup64 = None, None
     if args.precision in ("both", "fp64"):
-        s64, setup64 = _solver(prob, 0, torch, args.restart)
+        s64, setup64 = _solver(prob, 0, torch, args.restart, args.reorth)
         r64 = _timed_steps(s64, args, world, dist, torch, launch_count, args.precision == "fp64", local)
         r64["kt"] = _timed_steps(s64, args, world, dist, torch, launch_count, False, local, True)["kt"]
         if args.precision == "fp64":
@@ -372,7 +385,7 @@ def run_ours(args):
             s64.close()
             del s64
     if args.precision in ("both", "mixed"):
-        s, setup_ms = _solver(prob, 1, torch, args.restart)
+        s, setup_ms = _solver(prob, 1, torch, args.restart, args.reorth)
         r32 = _timed_steps(s, args, world, dist, torch, launch_count, True, local)
         # second pass over the same steps with the kernel events on (roofline)
         rk = _timed_steps(s, args, world, dist, torch, launch_count, False, local, True)
@@ -434,9 +447,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample_subprocess(s.n, statistics.mean(r32["iters"]))
+        cpu = oracle_sample_subprocess(args.workload, s.n, statistics.mean(r32["iters"]))
 
     nU, nP, nPi = s.sizes
+    auu_mb = 27 * 9 * 8 * (n_mesh + 1) ** 3 / 1e6  # 27 3x3 FP64 blocks per node
     if rank == 0:
         line = {
             "metric": METRIC, "value": aggregate_time(ms, world), "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -444,14 +458,16 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
-                       "n_pi": nPi, "tol": TOL, "restart": args.restart, "iterations_per_step": r32["iters"],
+                       "n_pi": nPi, "tol": TOL, "restart": args.restart, "reorth": args.reorth,
+                       "iterations_per_step": r32["iters"],
                        "setup_ms": setup_ms, "precision": {"both": "FP32 V-cycles inside FP64 FGMRES",
                                                            "mixed": "FP32 V-cycles inside FP64 FGMRES",
                                                            "fp64": "FP64 throughout"}[args.precision],
                        "fp64_plain": None if r64 is None else {
                            "ms_per_step": r64["ms"], "iterations_per_step": r64["iters"], "setup_ms": setup64,
                            "gpu_launches": r64["launches"]},
-                       "l2": "inputs larger than L2 (A_uu alone is 534 MB in FP64, 267 MB in FP32)",
+                       "l2": (f"inputs larger than L2 (A_uu alone is {auu_mb:.0f} MB in FP64, "
+                              f"{auu_mb / 2:.0f} MB in FP32)"),
                        "parallelism": "replicas",
                        "hierarchy_u": s.hierarchy(0)["points"], "hierarchy_pi": s.hierarchy(1)["points"]},
             "roofline": roofline, "roofline_fp64": roofline_fp64, "cpu_baseline": cpu, "e2e": e2e,
@@ -476,7 +492,7 @@ def run_batch(args):
 
     probs = mi.batch_instances()
     t0 = time.perf_counter()
-    solvers = prepare_batch(probs, precision=1, restart=args.restart)
+    solvers = prepare_batch(probs, precision=1, restart=args.restart, reorth=args.reorth)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     for _ in range(max(1, args.warmup)):
@@ -505,6 +521,7 @@ def run_batch(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)", "data": "synthetic",
             "config": {"workload": WORKLOADS["batch48"]["desc"], "instances": len(solvers), "systems": nsys,
+                       "restart": args.restart, "reorth": args.reorth,
                        "unknowns_per_load": unknowns, "sizes": [p.nx for p in probs], "all_converged": ok,
                        "iterations_min_max": [min(iters), max(iters)], "setup_s": setup_s,
                        "serial_ms_per_system": serial * 1e3 / nsys, "batched_speedup": serial / batched},
@@ -521,7 +538,7 @@ def main():
         return
     if args.oracle_sample:
         tgt, it = args.oracle_target.split(",")
-        d, _ = oracle_sample(int(tgt), float(it), sample_n=args.oracle_sample)
+        d, _ = oracle_sample(args.workload, int(tgt), float(it), sample_n=args.oracle_sample)
         print(json.dumps(d), flush=True)
         return
     if args.impl == "reference":

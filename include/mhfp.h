@@ -91,6 +91,12 @@ typedef struct {
   int autotune;         /* 1 (default): time the lanes-per-point variants of   */
                         /* each coarse level's smoother at set-up and keep the */
                         /* fastest (launch schedule only, same arithmetic)     */
+  int reorth;           /* Gram-Schmidt of each Arnoldi step (the paper names  */
+                        /* GMRES in PETSc, Section 5, and no orthogonalisation)*/
+                        /* 1 (default): classical Gram-Schmidt, repeated once  */
+                        /* when the norm falls below 1/sqrt(2) of its value    */
+                        /* (DGKS test); 0: one classical pass, never repeated  */
+                        /* (PETSc's GMRES default)                             */
 } mhfp_options;
 
 typedef struct {

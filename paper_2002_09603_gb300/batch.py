@@ -9,7 +9,7 @@ from __future__ import annotations
 from ._lib import Solver, default_options, solve_batch
 
 
-def prepare_batch(problems, precision=1, restart=12, autotune=1):
+def prepare_batch(problems, precision=1, restart=12, autotune=1, reorth=1):
     import torch
     solvers = []
     for prob in problems:
@@ -17,6 +17,7 @@ def prepare_batch(problems, precision=1, restart=12, autotune=1):
         opt.precision = precision
         opt.restart = restart
         opt.autotune = autotune
+        opt.reorth = reorth
         st = torch.cuda.Stream()
         s = Solver(prob, stream=st)
         s.assemble_condense()

@@ -127,6 +127,7 @@ void mhfp_default_options(mhfp_options* o) {
   o->precision = 0;
   o->graphs = 2;
   o->autotune = 1;
+  o->reorth = 1;
 }
 
 const char* mhfp_status_string(mhfp_status s) {
@@ -222,7 +223,7 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
       if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
           !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
           (opt->precision != 0 && opt->precision != 1) || (opt->graphs < 0 || opt->graphs > 2) ||
-          (opt->autotune != 0 && opt->autotune != 1))
+          (opt->autotune != 0 && opt->autotune != 1) || (opt->reorth != 0 && opt->reorth != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }

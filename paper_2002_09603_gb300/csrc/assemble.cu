@@ -543,17 +543,27 @@ __device__ __forceinline__ double finish(double y, long long r, const double* so
 // Abar_pp + A_stab symmetric), so A_H^T x only changes the coefficients of
 // the off-diagonal blocks: cup (u rows, A_up x_p), cpu and cpi (p rows,
 // A_pu x_u and A_ppi x_pi), cpp (pi rows, A_pip x_p).
-__global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restrict__ Auu, const double* __restrict__ Aup,
-                                                 const double* __restrict__ x, double* __restrict__ y,
-                                                 const double* __restrict__ so, const double* __restrict__ bsub,
-                                                 double cup) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+//
+// One thread per (node, component) row: blockDim = (APPLY_U_NODES, 3) with
+// threadIdx.y the component, so each warp streams 32 consecutive nodes of one
+// coefficient array, every thread carries a single FMA chain (81 + 8 FP64
+// FMA), and the 3 x nN threads fill the SMs in one wave of small blocks.
+constexpr int APPLY_U_NODES = 64;
+
+__global__ void __launch_bounds__(APPLY_U_NODES * 3) k_apply_u(Dims d, const double* __restrict__ Auu,
+                                                              const double* __restrict__ Aup,
+                                                              const double* __restrict__ x, double* __restrict__ y,
+                                                              const double* __restrict__ so,
+                                                              const double* __restrict__ bsub, double cup) {
+  const long long n = (long long)blockIdx.x * APPLY_U_NODES + threadIdx.x;
   if (n >= d.nN) return;
+  const int comp = threadIdx.y;
   const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
             nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
-  const long long sx = 1, sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
-  double y0 = 0, y1 = 0, y2 = 0;
+  const long long sy = d.nx + 1, sz = (long long)(d.nx + 1) * (d.ny + 1);
   const long long N = d.nN;
+  const double* row = Auu + (long long)(3 * comp) * N + n;  // block entries (comp, 0..2) of offset 0
+  double acc = 0.0;
 #pragma unroll 3
   for (int dz = -1; dz <= 1; ++dz) {
     const int mk = nk + dz;
@@ -565,17 +575,16 @@ __global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restric
         const int mi = ni + dx;
         if (mi < 0 || mi > d.nx) continue;
         const int o = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        const long long m = n + dx * sx + dy * sy + dz * sz;
-        const double x0 = x[3 * m], x1 = x[3 * m + 1], x2 = x[3 * m + 2];
-        const double* v = Auu + (long long)o * 9 * N + n;
-        y0 += v[0] * x0 + v[N] * x1 + v[2 * N] * x2;
-        y1 += v[3 * N] * x0 + v[4 * N] * x1 + v[5 * N] * x2;
-        y2 += v[6 * N] * x0 + v[7 * N] * x1 + v[8 * N] * x2;
+        const double* xm = x + 3 * (n + dx + dy * sy + dz * sz);
+        const double* v = row + (long long)o * 9 * N;
+        acc = fma(v[0], xm[0], acc);
+        acc = fma(v[N], xm[1], acc);
+        acc = fma(v[2 * N], xm[2], acc);
       }
     }
   }
-  const long long nU = 3 * N;
-  const double* xp = x + nU;
+  const double* xp = x + 3 * N;
+  double sp = 0.0;
   for (int cz = nk - 1; cz <= nk; ++cz) {
     if (cz < 0 || cz >= d.nz) continue;
     for (int cy = nj - 1; cy <= nj; ++cy) {
@@ -584,16 +593,12 @@ __global__ void __launch_bounds__(256) k_apply_u(Dims d, const double* __restric
         if (cx < 0 || cx >= d.nx) continue;
         const long long T = cell_id(d, cx, cy, cz);
         const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
-        const double p = cup * xp[T];
-        y0 += Aup[(long long)(3 * a) * d.nT + T] * p;
-        y1 += Aup[(long long)(3 * a + 1) * d.nT + T] * p;
-        y2 += Aup[(long long)(3 * a + 2) * d.nT + T] * p;
+        sp = fma(Aup[(long long)(3 * a + comp) * d.nT + T], xp[T], sp);
       }
     }
   }
-  y[3 * n] = finish(y0, 3 * n, so, bsub);
-  y[3 * n + 1] = finish(y1, 3 * n + 1, so, bsub);
-  y[3 * n + 2] = finish(y2, 3 * n + 2, so, bsub);
+  const long long r = 3 * n + comp;
+  y[r] = finish(fma(cup, sp, acc), r, so, bsub);
 }
 
 // p rows: A_pu x_u + (Abar_pp + A_stab) x_p + dt A_ppi x_pi.
@@ -906,7 +911,8 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
   const Dims d = dims_of(c);
   timing_begin(c, 1);
   const double sgn = transpose ? -1.0 : 1.0;
-  k_apply_u<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so, bsub, sgn);
+  k_apply_u<<<grid_for(c.nN, APPLY_U_NODES), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
+                                                                                    bsub, sgn);
   MHFP_LAUNCH_CHECK();
   k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, transpose ? 1.0 : c.dt, x, y,
                                                        so, bsub, sgn);

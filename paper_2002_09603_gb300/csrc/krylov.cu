@@ -37,33 +37,82 @@ constexpr int GS_COLS = 4;        // columns per block in the dot kernel
 // partials[c][block] = sum over this block's rows of V[:,c] . w for the
 // GS_COLS columns of blockIdx.y; block column 0 also sums w . w into slot
 // `ncols` when with_norm.  Skipped entirely when skip && *skip.
-__global__ void __launch_bounds__(RED_THREADS) k_gs_dots(long long n, const double* __restrict__ V, int ncols,
-                                                          const double* __restrict__ w, double* __restrict__ partials,
-                                                          const int* __restrict__ skip, int with_norm) {
-  if (skip && *skip) return;
-  __shared__ double sh[RED_THREADS / 32];
-  const int c0 = blockIdx.y * GS_COLS;
-  const bool do_norm = with_norm && blockIdx.y == 0;
-  double acc[GS_COLS], nw = 0.0;
-#pragma unroll
-  for (int q = 0; q < GS_COLS; ++q) acc[q] = 0.0;
+// Sum of (a0, a1, a2, a3) over the warp by a transposed butterfly: each
+// exchange halves the number of live columns per lane, so the four sums
+// cost 6 FP64 adds and 6 shuffles per lane instead of 20 and 20.  Lane
+// 8q + r (r = 0..7) returns the warp's sum for column q.
+__device__ __forceinline__ double warp_sum4(double a0, double a1, double a2, double a3) {
+  const unsigned lane = threadIdx.x & 31u;
+  const bool h16 = lane & 16u;
+  double k0 = h16 ? a2 : a0, k1 = h16 ? a3 : a1;
+  const double s0 = h16 ? a0 : a2, s1 = h16 ? a1 : a3;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);  // columns 2*h16, 2*h16 + 1
+  const bool h8 = lane & 8u;
+  double k = h8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);  // column lane >> 3
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// acc[q] += V[:, c0 + q] . w over this thread's rows for q < NC (the
+// valid columns of the block's group, so no predicated-off FMA is issued),
+// and nw += w . w when NORM
+template <int NC, bool NORM>
+__device__ __forceinline__ void gs_rows(long long n, const double* __restrict__ V, int c0,
+                                        const double* __restrict__ w, double (&acc)[GS_COLS], double& nw) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-#pragma unroll 2
+#pragma unroll 1
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     const double wr = w[r];
 #pragma unroll
-    for (int q = 0; q < GS_COLS; ++q)
-      if (c0 + q < ncols) acc[q] += V[(long long)(c0 + q) * n + r] * wr;
-    if (do_norm) nw += wr * wr;
+    for (int q = 0; q < NC; ++q) acc[q] = fma(V[(long long)(c0 + q) * n + r], wr, acc[q]);
+    if (NORM) nw = fma(wr, wr, nw);
   }
-#pragma unroll
-  for (int q = 0; q < GS_COLS; ++q) {
-    const double t = block_sum(acc[q], sh);
-    if (threadIdx.x == 0 && c0 + q < ncols) partials[(long long)(c0 + q) * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(RED_THREADS, 8) k_gs_dots(long long n, const double* __restrict__ V, int ncols,
+                                                             const double* __restrict__ w,
+                                                             double* __restrict__ partials,
+                                                             const int* __restrict__ skip, int with_norm) {
+  static_assert(GS_COLS == 4, "warp_sum4 reduces four columns");
+  if (skip && *skip) return;
+  __shared__ double sh[RED_THREADS / 32][GS_COLS];
+  __shared__ double shn[RED_THREADS / 32];
+  const int c0 = blockIdx.y * GS_COLS;
+  const bool do_norm = with_norm && blockIdx.y == 0;
+  double acc[GS_COLS] = {0.0, 0.0, 0.0, 0.0}, nw = 0.0;
+  // block-uniform branch on the number of valid columns in this group
+  switch ((ncols - c0 < GS_COLS ? ncols - c0 : GS_COLS) + (do_norm ? 8 : 0)) {
+    case 1: gs_rows<1, false>(n, V, c0, w, acc, nw); break;
+    case 2: gs_rows<2, false>(n, V, c0, w, acc, nw); break;
+    case 3: gs_rows<3, false>(n, V, c0, w, acc, nw); break;
+    case 4: gs_rows<4, false>(n, V, c0, w, acc, nw); break;
+    case 9: gs_rows<1, true>(n, V, c0, w, acc, nw); break;
+    case 10: gs_rows<2, true>(n, V, c0, w, acc, nw); break;
+    case 11: gs_rows<3, true>(n, V, c0, w, acc, nw); break;
+    case 12: gs_rows<4, true>(n, V, c0, w, acc, nw); break;
+    default: break;
   }
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  const double t = warp_sum4(acc[0], acc[1], acc[2], acc[3]);
+  if ((lane & 7u) == 0) sh[wid][lane >> 3] = t;
   if (do_norm) {
-    const double t = block_sum(nw, sh);
-    if (threadIdx.x == 0) partials[(long long)ncols * gridDim.x + blockIdx.x] = t;
+    for (int o = 16; o > 0; o >>= 1) nw += __shfl_xor_sync(0xffffffffu, nw, o);
+    if (lane == 0) shn[wid] = nw;
+  }
+  __syncthreads();
+  if (threadIdx.x < GS_COLS && c0 + (int)threadIdx.x < ncols) {
+    double s = 0.0;
+    for (int k = 0; k < RED_THREADS / 32; ++k) s += sh[k][threadIdx.x];
+    partials[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+  }
+  if (do_norm && threadIdx.x == 32) {
+    double s = 0.0;
+    for (int k = 0; k < RED_THREADS / 32; ++k) s += shn[k];
+    partials[(long long)ncols * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -92,28 +141,36 @@ __global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partia
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// w -= V h (four independent FMA chains per row); partial sums of the
-// updated w . w into partials[block] when partials is given
-__global__ void __launch_bounds__(RED_THREADS) k_gemv_sub(long long n, const double* __restrict__ V, int ncols,
-                                                           const double* __restrict__ h, double* __restrict__ w,
-                                                           double* __restrict__ partials,
-                                                           const int* __restrict__ skip) {
+// w -= V h as one FMA chain per row, two rows per thread for independent
+// chains (ncols + 1 FP64 operations per row, the norm included); partial
+// sums of the updated w . w into partials[block] when partials is given
+__global__ void __launch_bounds__(RED_THREADS, 8) k_gemv_sub(long long n, const double* __restrict__ V, int ncols,
+                                                              const double* __restrict__ h, double* __restrict__ w,
+                                                              double* __restrict__ partials,
+                                                              const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double sh[RED_THREADS / 32];
+  __shared__ double nh[64];
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) nh[c] = -h[c];
+  __syncthreads();
   double acc = 0.0;
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int c = 0;
-    for (; c + 3 < ncols; c += 4) {
-      s0 += V[(long long)c * n + r] * h[c];
-      s1 += V[(long long)(c + 1) * n + r] * h[c + 1];
-      s2 += V[(long long)(c + 2) * n + r] * h[c + 2];
-      s3 += V[(long long)(c + 3) * n + r] * h[c + 3];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += 2 * stride) {
+    const long long r1 = r + stride;
+    const bool two = r1 < n;
+    double v0 = w[r], v1 = two ? w[r1] : 0.0;
+#pragma unroll 2
+    for (int c = 0; c < ncols; ++c) {
+      const double* col = V + (long long)c * n;
+      v0 = fma(col[r], nh[c], v0);
+      if (two) v1 = fma(col[r1], nh[c], v1);
     }
-    for (; c < ncols; ++c) s0 += V[(long long)c * n + r] * h[c];
-    const double v = w[r] - ((s0 + s1) + (s2 + s3));
-    w[r] = v;
-    acc += v * v;
+    w[r] = v0;
+    acc = fma(v0, v0, acc);
+    if (two) {
+      w[r1] = v1;
+      acc = fma(v1, v1, acc);
+    }
   }
   if (partials) {
     const double t = block_sum(acc, sh);
@@ -163,11 +220,12 @@ __global__ void k_ewise(long long n, const double* __restrict__ x, const double*
 // 1/sqrt(2) of its value before the projection.  nrm[0] = ||w||^2 before,
 // nrm[1] = ||w||^2 after.  flag = 1 means "skip the second projection";
 // when it is skipped h2 is zeroed and the norm after the first pass is
-// carried into nrm[2], which the second pass overwrites otherwise.
+// carried into nrm[2], which the second pass overwrites otherwise.  With
+// never != 0 the second projection is always skipped (one classical pass).
 __global__ void k_dgks(int ncols, const double* __restrict__ nrm, int* __restrict__ flag, double* __restrict__ h2,
-                       double* __restrict__ nrm_final) {
+                       double* __restrict__ nrm_final, int never) {
   const int i = threadIdx.x;
-  const bool skip = nrm[1] > 0.5 * nrm[0];
+  const bool skip = never || nrm[1] > 0.5 * nrm[0];
   if (i == 0) {
     *flag = skip ? 1 : 0;
     if (skip) nrm_final[0] = nrm[1];
@@ -365,21 +423,25 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
   // classical Gram-Schmidt with the DGKS reorthogonalisation test:
   // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the
   // norm dropped by more than 1/sqrt(2), h2 = V^T w and w -= V h2
+  // (reorth = 0: the first pass alone, the second is not even queued)
+  const bool reorth = c.opt.reorth != 0;
   gs_dots(c, j + 1, c.h, c.scal + 4, nullptr);
   k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
                                                      nullptr);
   MHFP_LAUNCH_CHECK();
   k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 5, 0);
   MHFP_LAUNCH_CHECK();
-  k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2);
+  k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2, reorth ? 0 : 1);
   MHFP_LAUNCH_CHECK();
-  gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
-  k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
-                                                     c.partials + (size_t)m * GS_BLOCKS, c.dflag);
-  MHFP_LAUNCH_CHECK();
-  k_reduce_partials_flag<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 2,
-                                                         c.dflag);
-  MHFP_LAUNCH_CHECK();
+  if (reorth) {
+    gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
+    k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
+                                                       c.partials + (size_t)m * GS_BLOCKS, c.dflag);
+    MHFP_LAUNCH_CHECK();
+    k_reduce_partials_flag<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
+                                                           c.scal + 2, c.dflag);
+    MHFP_LAUNCH_CHECK();
+  }
   timing_end(c, 2, 8.0 * n * (2.0 * (j + 1) + 4.0));
   k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, c.h + (m + 1), c.scal + 2, c.H, c.cs, c.sn, c.g, c.scal);
   MHFP_LAUNCH_CHECK();

@@ -45,3 +45,40 @@ def test_argument_validation_without_gpu():
     assert lib.mhfp_status_string(5) == b"not converged"
     o = L.default_options()
     assert (o.restart, o.maxit, o.cheb_degree, o.coarse_max) == (50, 1000, 2, 125)
+
+
+def _structs(prob):
+    import numpy as np
+    import paper_2002_09603_gb300._lib as L
+    keep = {k: np.ascontiguousarray(getattr(prob, k)) for k in
+            ("coords", "node_fix", "face_bc", "E", "nu", "biot", "Seps", "mu", "kappa")}
+    mesh = L.Mesh(prob.nx, prob.ny, prob.nz, keep["coords"].ctypes.data, keep["node_fix"].ctypes.data,
+                  keep["face_bc"].ctypes.data)
+    mats = L.Materials(*(keep[k].ctypes.data for k in ("E", "nu", "biot", "Seps", "mu", "kappa")))
+    return mesh, mats, keep
+
+
+@pytest.mark.parametrize("field,value", [("nu", 0.5), ("E", -1.0), ("kappa", 0.0), ("mu", 0.0),
+                                         ("Seps", -1e-9), ("nx", 0)])
+def test_create_rejects_invalid_inputs_on_the_host(field, value):
+    """Empty meshes and non-physical materials are rejected by mhfp_create
+    before any device call (so this runs without a GPU)."""
+    import mhfp_inputs as mi
+    import paper_2002_09603_gb300._lib as L
+    from paper_2002_09603_gb300 import build
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    prob = mi.random_small(2, 2, 2, seed=1)
+    if field == "nx":
+        prob.nx = value
+    else:
+        arr = getattr(prob, field).copy()
+        arr.flat[3] = value
+        setattr(prob, field, arr)
+    mesh, mats, keep = _structs(prob)
+    h = ctypes.c_void_p()
+    trac = (ctypes.c_double * 3)(0.0, 0.0, -1.0)
+    assert L.load().mhfp_create(ctypes.byref(mesh), ctypes.byref(mats), 0.1, trac, None, ctypes.byref(h)) == 1
+    assert not h.value

@@ -67,3 +67,38 @@ def test_bench_solve_full_size(full):
     p = x[nU:nU + nP].reshape(64, 64 * 64)
     assert np.allclose(p[:60], 1.0, rtol=0, atol=1e-4)
     assert 25 <= st["iterations"] <= 40
+
+
+def test_layered_jittered_128_cubed():
+    """The 128^3 jittered, layered workload (14,877,827 unknowns; kappa over
+    six decades, E over two, S_eps = 0, dt = 0.1 s) at full size: the mixed
+    and the FP64 solves both reach 1e-8, agree with each other, and the
+    solution is linear in the load (properties that hold at any size)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_09603_gb300 import Solver, default_options
+    prob = mi.layered_jitter_cube(128)
+    xs = {}
+    for precision in (1, 0):
+        opt = default_options()
+        opt.precision = precision
+        opt.restart = 12
+        s = Solver(prob)
+        s.assemble_condense()
+        s.setup_precond(opt)
+        assert s.sizes == (3 * 129 ** 3, 128 ** 3, 3 * 128 * 128 * 129)
+        b = s.build_rhs()
+        x, st = s.solve(b, tol=1e-8)
+        assert st["converged"] and st["true_rel_residual"] <= 1.05e-8
+        rn, bn = s.residual_norm_noalloc(b, x).cpu().numpy()
+        assert rn / bn <= 1.1e-8
+        if precision == 1:
+            x2, st2 = s.solve(s.build_rhs(None, load_scale=2.0), tol=1e-8)
+            d = (x2 - 2 * x).norm() / (2 * x).norm()
+            assert d.item() <= 1e-5
+        xs[precision] = x.cpu().numpy()
+        s.close()
+    diff = np.linalg.norm(xs[1] - xs[0]) / np.linalg.norm(xs[0])
+    assert diff <= 1e-5, diff

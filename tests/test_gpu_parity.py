@@ -362,3 +362,43 @@ def test_batch_solve_matches_individual_solves():
             assert np.array_equal(xa, xb.cpu().numpy())
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["jitter7", "ragged", "layered16"])
+def test_single_pass_gram_schmidt_reaches_the_same_solution(name, precision):
+    """reorth = 0 (one classical Gram-Schmidt pass per Arnoldi step, no
+    reorthogonalisation) reaches the same 1e-10 true residual and 1e-8
+    energy-norm error against the oracle's direct solution as the DGKS form,
+    in at most two more iterations."""
+    from paper_2002_09603_gb300 import Solver, default_options
+    prob = dict(CASES)[name]()
+    B = oracle.assemble(prob)
+    pc = precond.build(B, "amg")
+    xd = oracle.solve_direct(B, system.rhs(B))
+    its = {}
+    for reorth in (1, 0):
+        opt = default_options()
+        opt.precision = precision
+        opt.restart = 12
+        opt.reorth = reorth
+        s = Solver(prob)
+        s.assemble_condense()
+        s.setup_precond(opt)
+        x, st = s.solve(s.build_rhs(), tol=1e-10)
+        assert st["converged"] and st["true_rel_residual"] <= 1.05e-10
+        assert _energy(B, pc, x.cpu().numpy() - xd) <= 1e-8 * _energy(B, pc, xd)
+        its[reorth] = st["iterations"]
+        s.close()
+    assert its[0] <= its[1] + 2, its
+
+
+def test_invalid_reorth_is_rejected():
+    from paper_2002_09603_gb300 import MhfpError, Solver, default_options
+    opt = default_options()
+    opt.reorth = 2
+    s = Solver(mi.random_small(2, 2, 2, seed=1))
+    s.assemble_condense()
+    with pytest.raises(MhfpError):
+        s.setup_precond(opt)
+    s.close()
