@@ -19,6 +19,8 @@
 // sparse-matrix hashing.
 #include "common.cuh"
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 
@@ -173,6 +175,84 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
   cheb_body<3, ST_BOX1, T>(L, val, dinv, b, xin, xout, d, cd, cr);
 }
 // </hot:k_cheb_u0>
+
+// <hot:k_cheb_u0_sym> (hashed like the region above)
+// The finest displacement level in FP32 with symmetric storage (A_uu is
+// symmetric): per node the diagonal 3x3 block (slot 0) and the blocks
+// A(n, n + e_o) of the 13 neighbours with stencil index o = 13 + u > 13
+// (slots u = 1..13), i.e. the last 14 offsets of the full layout.  The
+// lower blocks are read transposed from the neighbour that owns them:
+// A(n, n - e_o) = A(n - e_o, n)^T, slot u of node n - e_o.  Each stored
+// block is read by its owner and by one neighbour at most a lattice plane
+// apart, so the second read hits L2 and HBM carries each value once.
+template <typename T>
+__device__ __forceinline__ void sym_residual(const Lat& L, long long p, const T* __restrict__ up,
+                                             const T* __restrict__ x, T r[3]) {
+  const long long N = L.N;
+  int i, j, k;
+  L.ijk(p, i, j, k);
+  {
+    const T* v = up + p;
+    const T x0 = x[3 * p], x1 = x[3 * p + 1], x2 = x[3 * p + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) r[a] -= v[(3 * a) * N] * x0 + v[(3 * a + 1) * N] * x1 + v[(3 * a + 2) * N] * x2;
+  }
+#pragma unroll 1
+  for (int u = 1; u <= 13; ++u) {
+    int dx, dy, dz;
+    St<ST_BOX1>::off(13 + u, dx, dy, dz);
+    const long long s = dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
+    const T* vu = up + (long long)u * 9 * N;
+    if (L.in(i + dx, j + dy, k + dz)) {
+      const long long q = p + s;
+      const T* v = vu + p;
+      const T x0 = x[3 * q], x1 = x[3 * q + 1], x2 = x[3 * q + 2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[a] -= v[(3 * a) * N] * x0 + v[(3 * a + 1) * N] * x1 + v[(3 * a + 2) * N] * x2;
+    }
+    if (L.in(i - dx, j - dy, k - dz)) {
+      const long long q = p - s;
+      const T* v = vu + q;
+      const T x0 = x[3 * q], x1 = x[3 * q + 1], x2 = x[3 * q + 2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[a] -= v[a * N] * x0 + v[(3 + a) * N] * x1 + v[(6 + a) * N] * x2;
+    }
+  }
+}
+
+// MINB resident blocks per SM: 8 (32 registers) fills the SMs in one wave
+// when the level has at most 152 x 2048 nodes; 6 (40 registers) keeps more
+// loads in flight per thread on larger levels.  The set-up autotuner picks.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, const T* __restrict__ up,
+                                                            const T* __restrict__ x, const T* __restrict__ b,
+                                                            T* __restrict__ y) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
+  sym_residual<T>(L, p, up, x, r);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) y[3 * p + a] = r[a];
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, const T* __restrict__ up,
+                                                           const T* __restrict__ dinv, const T* __restrict__ b,
+                                                           const T* __restrict__ xin, T* __restrict__ xout,
+                                                           T* __restrict__ d, T cd, T cr) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= L.N) return;
+  T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
+  if (xin) sym_residual<T>(L, p, up, xin, r);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T z = dinv[(3 * a) * L.N + p] * r[0] + dinv[(3 * a + 1) * L.N + p] * r[1] + dinv[(3 * a + 2) * L.N + p] * r[2];
+    const T dn = (cd != T(0)) ? cd * d[3 * p + a] + cr * z : cr * z;
+    d[3 * p + a] = dn;
+    xout[3 * p + a] = (xin ? xin[3 * p + a] : T(0)) + dn;
+  }
+}
+// </hot:k_cheb_u0_sym>
 
 // Scalar stencils (the interface-pressure cell levels) with their offset loop
 // unrolled: one lattice point per thread has only a handful of FMAs per
@@ -1075,6 +1155,63 @@ void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* 
   });
 }
 
+// The symmetric FP32 sweep and residual of the finest displacement level
+// with L.tpp resident blocks per SM (6 or 8; 0: 8 when one wave of 8 blocks
+// of 256 per SM covers the level, else 6).
+int sym_minb(const Level& L) {
+  if (L.tpp == 6 || L.tpp == 8) return L.tpp;
+  return L.A.N <= 152LL * 8 * 256 ? 8 : 6;
+}
+void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, float* xout, float* d, float cd,
+                     float cr) {
+  const Lat lat = lat_of(L.A);
+  if (sym_minb(L) == 8)
+    k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout, d, cd,
+                                                                        cr);
+  else
+    k_cheb_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout, d, cd,
+                                                                        cr);
+  MHFP_LAUNCH_CHECK();
+}
+void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, float* y) {
+  const Lat lat = lat_of(L.A);
+  if (sym_minb(L) == 8)
+    k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+  else
+    k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+  MHFP_LAUNCH_CHECK();
+}
+
+// Set-up autotuner for the finest displacement level in FP32: time the two
+// occupancy variants of the symmetric sweep and keep the faster in L.tpp.
+void autotune_fine_sym(Ctx& c, Level& L) {
+  MHFP_CUDA(cudaMemsetAsync(L.bf, 0, L.n * sizeof(float), c.stream));
+  MHFP_CUDA(cudaMemsetAsync(L.xf, 0, L.n * sizeof(float), c.stream));
+  MHFP_CUDA(cudaMemsetAsync(L.df, 0, L.n * sizeof(float), c.stream));
+  cudaEvent_t e0, e1;
+  MHFP_CUDA(cudaEventCreate(&e0));
+  MHFP_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_minb = 0;
+  for (int minb : {8, 6}) {
+    L.tpp = minb;
+    for (int rep = 0; rep < 2; ++rep) launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f);
+    MHFP_CUDA(cudaEventRecord(e0, c.stream));
+    for (int rep = 0; rep < 5; ++rep) launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f);
+    MHFP_CUDA(cudaEventRecord(e1, c.stream));
+    MHFP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MHFP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_minb = minb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.tpp = best_minb;
+}
+
 // Set-up autotuner: time the lanes-per-point variants of a coarse level's
 // Chebyshev sweep (same arithmetic, different launch schedule) and keep the
 // fastest for this level's sweeps and residuals.
@@ -1140,15 +1277,21 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
       k_cheb_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, v.dinv, b, xin, out, v.d, (T)cd,
                                                              (T)cr);
     } else if (time_it) {
-      const Lat lat = lat_of(L.A);
-      k_cheb_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
+      if constexpr (std::is_same<T, float>::value) {
+        launch_cheb_sym(c, L, b, xin, out, v.d, (T)cd, (T)cr);
+      } else {
+        const Lat lat = lat_of(L.A);
+        k_cheb_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
+      }
     } else {
       launch_cheb<T>(c, L, v, b, xin, out, (T)cd, (T)cr, L.tpp ? L.tpp : group_size(L.A.N, L.A.kind));
     }
     MHFP_LAUNCH_CHECK();
-    // algorithmic bytes of a Chebyshev sweep: 27 x 9 matrix values and the
-    // 3x3 inverse diagonal per node, b, x_in, x_out and d read/written
-    if (time_it && xin) timing_end(c, 0, (27.0 * 9 + 9) * sizeof(T) * L.npts + 5.0 * sizeof(T) * L.n);
+    // algorithmic bytes of a Chebyshev sweep: the matrix values (27 blocks
+    // per node in FP64, the 14 stored blocks of the symmetric FP32 copy) and
+    // the 3x3 inverse diagonal per node, b, x_in, x_out and d read/written
+    const double blocks = std::is_same<T, float>::value ? 14.0 : 27.0;
+    if (time_it && xin) timing_end(c, 0, (blocks * 9 + 9) * sizeof(T) * L.npts + 5.0 * sizeof(T) * L.n);
     xin = out;
     out = (out == x) ? other : x;
   }
@@ -1168,9 +1311,13 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   const bool fine_u = (&H == &c.hu) && l == 0;
   smooth<T>(c, H, l, b, x, true, fine_u);
   if (fine_u) {
-    const Lat lat = lat_of(L.A);
-    k_resid_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, v.r);
-    MHFP_LAUNCH_CHECK();
+    if constexpr (std::is_same<T, float>::value) {
+      launch_resid_sym(c, L, x, b, v.r);
+    } else {
+      const Lat lat = lat_of(L.A);
+      k_resid_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, v.r);
+      MHFP_LAUNCH_CHECK();
+    }
   } else {
     level_spmv_t<T>(c, L, x, b, v.r);
   }
@@ -1211,12 +1358,20 @@ float* cast_copy(Ctx& c, const double* src, size_t n) {
 }
 
 // FP32 copies of a hierarchy built in FP64 (the last level keeps its FP64
-// dense inverse)
-void make_fp32(Ctx& c, std::vector<Level>& H) {
+// dense inverse).  With fine_sym, level 0 (the finest displacement level,
+// 27-point 3x3-block stencil) keeps only its symmetric half: the diagonal
+// block and the 13 offsets after it, the last 14 x 9 x N values of the
+// offset-major FP64 array.
+void make_fp32(Ctx& c, std::vector<Level>& H, bool fine_sym) {
   for (size_t l = 0; l < H.size(); ++l) {
     Level& L = H[l];
     const size_t bs2 = (size_t)L.bs * L.bs;
-    if (!L.faces) L.valf = cast_copy(c, L.A.val, (size_t)L.A.noff() * bs2 * L.A.N);
+    if (fine_sym && l == 0 && !L.dense_inv) {
+      const size_t N = (size_t)L.A.N;
+      L.symf = cast_copy(c, L.A.val + 13 * 9 * N, 14 * 9 * N);
+    } else if (!L.faces) {
+      L.valf = cast_copy(c, L.A.val, (size_t)L.A.noff() * bs2 * L.A.N);
+    }
     if (L.dinv) L.dinvf = cast_copy(c, L.dinv, bs2 * L.npts);
     if (L.P) {
       const int ns = p_slots(L.R);
@@ -1236,13 +1391,15 @@ void build_hierarchies(Ctx& c) {
   build_u(c);
   build_pi(c);
   if (c.opt.precision == 1) {
-    make_fp32(c, c.hu);
-    make_fp32(c, c.hpi);
+    make_fp32(c, c.hu, true);
+    make_fp32(c, c.hpi, false);
     c.Cpif = cast_copy(c, c.Cpi, (size_t)11 * c.nF);
     c.pwf = cast_copy(c, c.pw, c.nF);
   }
   if (c.opt.autotune) {
-    // the finest displacement level always runs k_cheb_u0; tune the others
+    // the finest displacement level runs k_cheb_u0 (FP64) or the symmetric
+    // FP32 sweep, whose two occupancy variants are timed; tune the others
+    if (c.opt.precision == 1 && !c.hu[0].dense_inv) autotune_fine_sym(c, c.hu[0]);
     for (auto* H : {&c.hu, &c.hpi})
       for (size_t l = 0; l < H->size(); ++l) {
         Level& L = (*H)[l];
@@ -1253,8 +1410,19 @@ void build_hierarchies(Ctx& c) {
   }
 }
 
-void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x) { vcycle_level<double>(c, H, 0, b, x); }
-void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x) { vcycle_level<float>(c, H, 0, b, x); }
+// timed as class 4 (displacement) or 5 (interface pressure)
+void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x) {
+  const int cls = (&H == &c.hu) ? 4 : 5;
+  timing_begin(c, cls);
+  vcycle_level<double>(c, H, 0, b, x);
+  timing_end(c, cls, 0.0);
+}
+void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x) {
+  const int cls = (&H == &c.hu) ? 4 : 5;
+  timing_begin(c, cls);
+  vcycle_level<float>(c, H, 0, b, x);
+  timing_end(c, cls, 0.0);
+}
 
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y) {
   level_spmv_t<double>(c, H[l], x, nullptr, y);

@@ -32,7 +32,7 @@ void timing_begin(Ctx& c, int cls) {
   if (c.timing.capturing) {
     // inside a graph capture: an external event-record node that records on
     // every replay; the pair is read after each replay
-    TimedPair t{cls, nullptr, nullptr, 0.0};
+    TimedPair t{cls, nullptr, nullptr, 0.0, false};
     MHFP_CUDA(cudaEventCreate(&t.start));
     MHFP_CUDA(cudaEventCreate(&t.stop));
     MHFP_CUDA(cudaEventRecordWithFlags(t.start, c.stream, cudaEventRecordExternal));
@@ -64,10 +64,17 @@ static void harvest(Ctx& c, int cls) {
 void timing_end(Ctx& c, int cls, double bytes) {
   if (c.suppress_events) return;
   if (c.timing.capturing) {
-    TimedPair& t = c.timing.capture_list->back();
-    t.bytes = bytes;
-    MHFP_CUDA(cudaEventRecordWithFlags(t.stop, c.stream, cudaEventRecordExternal));
-    return;
+    // the innermost open pair of this class (classes nest)
+    auto& list = *c.timing.capture_list;
+    for (size_t i = list.size(); i-- > 0;) {
+      TimedPair& t = list[i];
+      if (t.cls != cls || t.closed) continue;
+      t.bytes = bytes;
+      t.closed = true;
+      MHFP_CUDA(cudaEventRecordWithFlags(t.stop, c.stream, cudaEventRecordExternal));
+      return;
+    }
+    throw Error{MHFP_ERR_STATE, "timing_end without timing_begin"};
   }
   if (!c.timing.enabled) return;
   MHFP_CUDA(cudaEventRecord(c.timing.ev_stop[cls][c.timing.used[cls]], c.stream));
@@ -374,7 +381,7 @@ mhfp_status mhfp_sizes(mhfp_handle h, long long* n_u, long long* n_p, long long*
 mhfp_status mhfp_timing(mhfp_handle h, int enable) {
   return guarded(h, [&](Ctx& c) {
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < mhfp::TIMING_CLASSES; ++k) {
       c.timing.used[k] = 0;
       if (enable) {
         c.timing.launches[k] = 0;
@@ -389,7 +396,8 @@ mhfp_status mhfp_timing(mhfp_handle h, int enable) {
 mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launches, double* total_ms,
                              double* bytes_per_launch) {
   return guarded(h, [&](Ctx& c) {
-    if (kernel_class < 0 || kernel_class > 2) throw Error{MHFP_ERR_ARG, "kernel class out of range"};
+    if (kernel_class < 0 || kernel_class >= mhfp::TIMING_CLASSES)
+      throw Error{MHFP_ERR_ARG, "kernel class out of range"};
     mhfp::harvest(c, kernel_class);
     if (launches) *launches = c.timing.launches[kernel_class];
     if (total_ms) *total_ms = c.timing.total_ms[kernel_class];
@@ -492,7 +500,7 @@ void mhfp_destroy(mhfp_handle h) {
   Ctx& c = h->c;
   cudaSetDevice(c.device);
   cudaStreamSynchronize(c.stream);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < mhfp::TIMING_CLASSES; ++k) {
     for (auto e : c.timing.ev_start[k]) cudaEventDestroy(e);
     for (auto e : c.timing.ev_stop[k]) cudaEventDestroy(e);
   }

@@ -122,7 +122,8 @@ struct Level {
   // prolongator to the next level (lattice levels only): [p_slots^3][bs*bs][npts]
   double* P = nullptr;
   int R = 1;                  // stencil radius of A (L_inf)
-  int tpp = 0;                // lanes per point chosen by the autotuner (0: default rule)
+  int tpp = 0;                // lanes per point chosen by the autotuner (0: default rule);
+                              // on the finest FP32 displacement level: blocks per SM (6 or 8)
   unsigned char* active = nullptr;  // [n] free dofs
   // work vectors of length n
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *y = nullptr;
@@ -130,6 +131,7 @@ struct Level {
   double* dense_inv = nullptr;
   // FP32 copies for the mixed-precision cycle (precision == 1)
   float *valf = nullptr, *dinvf = nullptr, *Pf = nullptr;
+  float* symf = nullptr;      // finest displacement level, FP32: symmetric half [14][9][N]
   float *xf = nullptr, *bf = nullptr, *rf = nullptr, *df = nullptr, *yf = nullptr;
 };
 
@@ -138,7 +140,13 @@ struct TimedPair {
   int cls;
   cudaEvent_t start, stop;
   double bytes;
+  bool closed;  // stop recorded (classes nest: M^-1 > V-cycle > sweep)
 };
+
+// Timed classes: 0 finest displacement Chebyshev sweeps, 1 operator apply,
+// 2 Gram-Schmidt, 3 preconditioner apply M^-1, 4 displacement V-cycle,
+// 5 interface-pressure V-cycle
+constexpr int TIMING_CLASSES = 6;
 
 // FGMRES control block kept in device memory by the device-driven solve
 struct DevCtl {
@@ -157,11 +165,11 @@ struct Timing {
   bool enabled = false;
   bool capturing = false;                 // record events as graph nodes
   std::vector<TimedPair>* capture_list = nullptr;
-  std::vector<cudaEvent_t> ev_start[3], ev_stop[3];
-  size_t used[3] = {0, 0, 0};
-  long long launches[3] = {0, 0, 0};
-  double total_ms[3] = {0, 0, 0};
-  double bytes[3] = {0, 0, 0};
+  std::vector<cudaEvent_t> ev_start[TIMING_CLASSES], ev_stop[TIMING_CLASSES];
+  size_t used[TIMING_CLASSES] = {};
+  long long launches[TIMING_CLASSES] = {};
+  double total_ms[TIMING_CLASSES] = {};
+  double bytes[TIMING_CLASSES] = {};
 };
 
 struct Ctx {

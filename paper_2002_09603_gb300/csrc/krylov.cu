@@ -389,12 +389,14 @@ void precond_blocks(Ctx& c, const T* t, T* z, T* work_u, T* work_pi, bool transp
 // z = M^-1 (v .* mul) (or M^-T) with the FP32 V-cycles and Schur steps; v, z FP64
 void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z, bool transpose) {
   const long long n = c.n;
+  timing_begin(c, 3);
   k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, mul, c.tf);
   MHFP_LAUNCH_CHECK();
   // level-0 right-hand-side buffers are free at the finest levels
   precond_blocks<float>(c, c.tf, c.zf, c.hu[0].bf, c.hpi[0].bf, transpose);
   k_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.zf, z);
   MHFP_LAUNCH_CHECK();
+  timing_end(c, 3, 0.0);
 }
 
 void apply_precond(Ctx& c, const double* v, double* z, bool transpose) {
@@ -402,7 +404,9 @@ void apply_precond(Ctx& c, const double* v, double* z, bool transpose) {
     apply_precond_mixed(c, v, nullptr, z, transpose);
     return;
   }
+  timing_begin(c, 3);
   precond_blocks<double>(c, v, z, c.hu[0].b, c.hpi[0].b, transpose);
+  timing_end(c, 3, 0.0);
 }
 
 // Enqueue Arnoldi step j: z_j = M^-1 v_j, w = D_s A z_j, Gram-Schmidt, the

@@ -402,3 +402,33 @@ def test_invalid_reorth_is_rejected():
     with pytest.raises(MhfpError):
         s.setup_precond(opt)
     s.close()
+
+
+def test_timing_classes_nest():
+    """With timing on, every class records one interval per event: the
+    preconditioner apply (3) holds both V-cycles (4, 5), and the displacement
+    V-cycle holds the timed finest-level sweeps (0); class 6 does not exist."""
+    from paper_2002_09603_gb300 import MhfpError, Solver, default_options
+    opt = default_options()
+    opt.precision = 1
+    opt.restart = 6
+    s = Solver(mi.random_small(7, 6, 5, seed=3, jitter=0.25))
+    s.assemble_condense()
+    s.setup_precond(opt)
+    b = s.build_rhs()
+    s.timing(True)
+    x, st = s.solve(b, tol=1e-8)
+    r = [s.timing_read(k) for k in range(6)]
+    s.timing(False)
+    its = st["iterations"]
+    assert r[3]["launches"] == its and r[4]["launches"] == its and r[5]["launches"] == its
+    assert r[1]["launches"] >= its and r[2]["launches"] == its
+    # Chebyshev(2): the first pre-smoothing sweep starts from zero and is not
+    # a stencil sweep; the second and both post-smoothing sweeps are timed
+    assert r[0]["launches"] == 3 * its
+    assert all(t["total_ms"] > 0 for t in r)
+    assert r[3]["total_ms"] >= r[4]["total_ms"] + r[5]["total_ms"]
+    assert r[4]["total_ms"] >= r[0]["total_ms"]
+    with pytest.raises(MhfpError):
+        s.timing_read(6)
+    s.close()
