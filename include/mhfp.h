@@ -88,9 +88,13 @@ typedef struct {
                         /* Arnoldi step is one graph replay driven by the      */
                         /* host (used whenever kernel timing is enabled);      */
                         /* 0: kernels are launched one by one                  */
-  int autotune;         /* 1 (default): time the lanes-per-point variants of   */
-                        /* each coarse level's smoother at set-up and keep the */
-                        /* fastest (launch schedule only, same arithmetic)     */
+  int autotune;         /* 1 (default): time the launch schedules of each      */
+                        /* coarse level's smoother at set-up (one point per    */
+                        /* thread, or the stencil offsets split over 4, 8 or   */
+                        /* 16 warps) and the two occupancy variants of the     */
+                        /* finest FP32 displacement sweep, and keep the        */
+                        /* fastest (schedule only: the same products, summed   */
+                        /* in a schedule-dependent fixed order)                */
   int reorth;           /* Gram-Schmidt of each Arnoldi step (the paper names  */
                         /* GMRES in PETSc, Section 5, and no orthogonalisation)*/
                         /* 1 (default): classical Gram-Schmidt, repeated once  */
@@ -113,6 +117,12 @@ typedef struct {
   long long points[8];  /* lattice points (or faces) per level                 */
   int block[8];         /* unknowns per point (3 for u, 1 for pi)              */
   double lmax[8];       /* 1.1 * rho(D^-1 A) per level (0 on the last level)   */
+  int schedule[8];      /* launch schedule of the level's sweeps: 1 = one point */
+                        /* per thread, 4/8/16 = offsets split over that many    */
+                        /* warps; finest FP32 displacement level: resident     */
+                        /* blocks per SM (6 or 8); 0 = not a lattice sweep     */
+  double sweep_us[8];   /* set-up autotuner's time of one sweep under that     */
+                        /* schedule, microseconds (0 when not timed)           */
 } mhfp_hierarchy_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -60,7 +60,7 @@ class Stats(C.Structure):
 
 class HierInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("points", C.c_longlong * 8), ("block", C.c_int * 8),
-                ("lmax", C.c_double * 8)]
+                ("lmax", C.c_double * 8), ("schedule", C.c_int * 8), ("sweep_us", C.c_double * 8)]
 
 
 _lib = None
@@ -256,7 +256,8 @@ class Solver:
         info = HierInfo()
         self._check(self.lib.mhfp_hierarchy(self.h, int(which), C.byref(info)))
         L = info.levels
-        return dict(levels=L, points=list(info.points[:L]), block=list(info.block[:L]), lmax=list(info.lmax[:L]))
+        return dict(levels=L, points=list(info.points[:L]), block=list(info.block[:L]), lmax=list(info.lmax[:L]),
+                    schedule=list(info.schedule[:L]), sweep_us=list(info.sweep_us[:L]))
 
     def scalings(self):
         bt = self.empty(self.sizes[1])

@@ -112,6 +112,79 @@ __device__ __forceinline__ void spmv_body(const Lat& L, const T* __restrict__ va
   for (int r = 0; r < BS; ++r) y[BS * p + r] = b ? b[BS * p + r] - acc[r] : acc[r];
 }
 
+// ------------------------------------------------------- lattice helpers
+// 32-bit lattice indexing for the coarse levels (see the coarse-level sweeps
+// below).
+// q = n / d for every 32-bit n, from a magic multiplier fixed at set-up
+struct Div32 {
+  unsigned m = 1, d = 1;
+  int s1 = 0, s2 = 0;
+  static Div32 make(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;  // l = ceil(log2 d)
+    Div32 r;
+    r.d = d;
+    r.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    r.s1 = l < 1 ? l : 1;
+    r.s2 = l < 1 ? 0 : l - 1;
+    return r;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    const unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+struct Lat32 {
+  int Lx, Ly, Lz, N, LxLy;
+  Div32 dx, dy;
+  __device__ __forceinline__ void ijk(unsigned p, int& i, int& j, int& k) const {
+    const unsigned r = dx.div(p);
+    i = (int)(p - r * (unsigned)Lx);
+    k = (int)dy.div(r);
+    j = (int)(r - (unsigned)k * (unsigned)Ly);
+  }
+};
+
+// box index (x+2) + 5 (y+2) + 25 (z+2) of the o-th offset with |d|_1 <= 2,
+// in box order (the order of stencil_offset for ST_DIAMOND2)
+__host__ __device__ constexpr int dia_box(int o) { return o == 0 ? 12 : o == 1 ? 32 : o == 2 ? 36 : o == 3 ? 37 : o == 4 ? 38 : o == 5 ? 42 : o == 6 ? 52 : o == 7 ? 56 : o == 8 ? 57 : o == 9 ? 58 : o == 10 ? 60 : o == 11 ? 61 : o == 12 ? 62 : o == 13 ? 63 : o == 14 ? 64 : o == 15 ? 66 : o == 16 ? 67 : o == 17 ? 68 : o == 18 ? 72 : o == 19 ? 82 : o == 20 ? 86 : o == 21 ? 87 : o == 22 ? 88 : o == 23 ? 92 : 112; }
+constexpr bool dia_table_matches_box_order() {
+  int n = 0;
+  for (int b = 0; b < 125; ++b) {
+    const int x = b % 5 - 2, y = (b / 5) % 5 - 2, z = b / 25 - 2;
+    if ((x < 0 ? -x : x) + (y < 0 ? -y : y) + (z < 0 ? -z : z) > 2) continue;
+    if (dia_box(n++) != b) return false;
+  }
+  return n == 25;
+}
+static_assert(dia_table_matches_box_order(), "diamond offset table out of box order");
+
+// compile-time offsets of each stencil kind
+template <int KIND>
+struct Sf;
+template <>
+struct Sf<ST_BOX1> {
+  static constexpr int N = 27, R = 1;
+  __device__ static constexpr int x(int o) { return o % 3 - 1; }
+  __device__ static constexpr int y(int o) { return (o / 3) % 3 - 1; }
+  __device__ static constexpr int z(int o) { return o / 9 - 1; }
+};
+template <>
+struct Sf<ST_BOX2> {
+  static constexpr int N = 125, R = 2;
+  __device__ static constexpr int x(int o) { return o % 5 - 2; }
+  __device__ static constexpr int y(int o) { return (o / 5) % 5 - 2; }
+  __device__ static constexpr int z(int o) { return o / 25 - 2; }
+};
+template <>
+struct Sf<ST_DIAMOND2> {
+  static constexpr int N = 25, R = 2;
+  __device__ static constexpr int x(int o) { return dia_box(o) % 5 - 2; }
+  __device__ static constexpr int y(int o) { return (dia_box(o) / 5) % 5 - 2; }
+  __device__ static constexpr int z(int o) { return dia_box(o) / 25 - 2; }
+};
+
 // <hot:k_cheb_u0> (bench.py hashes this region to tell whether profiles/traffic.json still applies)
 // Chebyshev step: r = b - A xin (r = b when xin is null), d = cd d + cr D^-1 r,
 // xout = xin + d.
@@ -186,9 +259,9 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
 // block is read by its owner and by one neighbour at most a lattice plane
 // apart, so the second read hits L2 and HBM carries each value once.
 template <typename T>
-__device__ __forceinline__ void sym_residual(const Lat& L, long long p, const T* __restrict__ up,
+__device__ __forceinline__ void sym_residual(const Lat& L, long long ld, long long p, const T* __restrict__ up,
                                              const T* __restrict__ x, T r[3]) {
-  const long long N = L.N;
+  const long long N = ld;  // row stride of the stored values (>= number of nodes)
   int i, j, k;
   L.ijk(p, i, j, k);
   {
@@ -224,26 +297,26 @@ __device__ __forceinline__ void sym_residual(const Lat& L, long long p, const T*
 // when the level has at most 152 x 2048 nodes; 6 (40 registers) keeps more
 // loads in flight per thread on larger levels.  The set-up autotuner picks.
 template <typename T, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, const T* __restrict__ up,
+__global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, long long ld, const T* __restrict__ up,
                                                             const T* __restrict__ x, const T* __restrict__ b,
                                                             T* __restrict__ y) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
-  sym_residual<T>(L, p, up, x, r);
+  sym_residual<T>(L, ld, p, up, x, r);
 #pragma unroll
   for (int a = 0; a < 3; ++a) y[3 * p + a] = r[a];
 }
 
 template <typename T, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, const T* __restrict__ up,
+__global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, const T* __restrict__ up,
                                                            const T* __restrict__ dinv, const T* __restrict__ b,
                                                            const T* __restrict__ xin, T* __restrict__ xout,
                                                            T* __restrict__ d, T cd, T cr) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
-  if (xin) sym_residual<T>(L, p, up, xin, r);
+  if (xin) sym_residual<T>(L, ld, p, up, xin, r);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const T z = dinv[(3 * a) * L.N + p] * r[0] + dinv[(3 * a + 1) * L.N + p] * r[1] + dinv[(3 * a + 2) * L.N + p] * r[2];
@@ -252,50 +325,8 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, const T* __res
     xout[3 * p + a] = (xin ? xin[3 * p + a] : T(0)) + dn;
   }
 }
+
 // </hot:k_cheb_u0_sym>
-
-// Scalar stencils (the interface-pressure cell levels) with their offset loop
-// unrolled: one lattice point per thread has only a handful of FMAs per
-// offset, so the independent loads of several offsets must be in flight at
-// once to cover the gather latency.
-template <int KIND, int UNR, typename T>
-__device__ __forceinline__ T scalar_residual(const Lat& L, long long p, const T* __restrict__ val,
-                                             const T* __restrict__ x, T r) {
-  int i, j, k;
-  L.ijk(p, i, j, k);
-#pragma unroll UNR
-  for (int o = 0; o < St<KIND>::N; ++o) {
-    int dx, dy, dz;
-    St<KIND>::off(o, dx, dy, dz);
-    const bool in = L.in(i + dx, j + dy, k + dz);
-    const long long q = in ? p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz) : p;
-    const T v = in ? val[(long long)o * L.N + p] : T(0);
-    r -= v * x[q];
-  }
-  return r;
-}
-
-template <int KIND, int UNR, typename T>
-__global__ void __launch_bounds__(256) k_spmv_s(Lat L, const T* __restrict__ val, const T* __restrict__ x,
-                                                const T* __restrict__ b, T* __restrict__ y) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.N) return;
-  const T r = scalar_residual<KIND, UNR, T>(L, p, val, x, T(0));
-  y[p] = b ? b[p] + r : -r;
-}
-
-template <int KIND, int UNR, typename T>
-__global__ void __launch_bounds__(256) k_cheb_s(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
-                                                const T* __restrict__ b, const T* __restrict__ xin,
-                                                T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.N) return;
-  const T r = xin ? scalar_residual<KIND, UNR, T>(L, p, val, xin, b[p]) : b[p];
-  const T z = dinv[p] * r;
-  const T dn = (cd != T(0)) ? cd * d[p] + cr * z : cr * z;
-  d[p] = dn;
-  xout[p] = (xin ? xin[p] : T(0)) + dn;
-}
 
 // scalar prolongation x += P x_c with the slot loop unrolled
 template <int R, typename T>
@@ -318,78 +349,180 @@ __global__ void __launch_bounds__(256) k_prolong_s(Lat F, Lat Cc, const T* __res
   x[p] += acc;
 }
 
-// Coarse lattices have few points, so one thread per point leaves most of the
-// GPU idle behind long serial loops over 27-125 offsets.  These variants give
-// each point a group of TPP consecutive lanes that split the offsets and
-// combine their partial sums with a fixed-order xor shuffle (deterministic).
-template <int BS, int KIND, int TPP, typename T>
-__device__ __forceinline__ void group_residual(const Lat& L, long long p, bool valid, int sub,
-                                               const T* __restrict__ val, const T* __restrict__ x,
-                                               const T* __restrict__ b, T r[BS]) {
+// ------------------------------------------------------- coarse-level sweeps
+// Sweeps and residuals of the coarse lattice levels and of the interface-
+// pressure cell levels.  Their data is a few to a few tens of MB, so the cost
+// is latency and issue, not bytes: index arithmetic is 32-bit (the lattice
+// point is split with multiply-high division by invariant integers,
+// Granlund & Montgomery 1994, no 64-bit division), stencil offsets are
+// compile-time constants, bounds are three small per-axis masks, and every
+// offset of a chunk issues its loads before any is used (an out-of-lattice
+// neighbour reads the point itself and is then replaced by 0).
+
+// r -= sum over the offsets o with o % step == first of A(p, p + e_o) x(p + e_o)
+template <int BS, int KIND, int CHUNK, typename T>
+__device__ __forceinline__ void coarse_residual(const Lat32& L, unsigned p, const T* __restrict__ val,
+                                                const T* __restrict__ x, T r[BS], int first, int step) {
+  constexpr int R = Sf<KIND>::R, NO = Sf<KIND>::N;
+  int i, j, k;
+  L.ijk(p, i, j, k);
+  bool mx[2 * R + 1], my[2 * R + 1], mz[2 * R + 1];
 #pragma unroll
-  for (int q = 0; q < BS; ++q) r[q] = T(0);
-  if (valid && x) {
-    int i, j, k;
-    L.ijk(p, i, j, k);
-    for (int oo = 0; oo < (St<KIND>::N + TPP - 1) / TPP; ++oo) {
-      const int o = oo * TPP + sub;
-      if (o >= St<KIND>::N) break;
-      int dx, dy, dz;
-      St<KIND>::off(o, dx, dy, dz);
-      if (!L.in(i + dx, j + dy, k + dz)) continue;
-      const long long q = p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
-      const T* v = val + (long long)o * BS * BS * L.N + p;
-#pragma unroll
-      for (int a = 0; a < BS; ++a)
-#pragma unroll
-        for (int s = 0; s < BS; ++s) r[a] -= v[(long long)(a * BS + s) * L.N] * x[BS * q + s];
-    }
+  for (int t = -R; t <= R; ++t) {
+    mx[t + R] = (unsigned)(i + t) < (unsigned)L.Lx;
+    my[t + R] = (unsigned)(j + t) < (unsigned)L.Ly;
+    mz[t + R] = (unsigned)(k + t) < (unsigned)L.Lz;
   }
+  const unsigned N = (unsigned)L.N;
+#pragma unroll
+  for (int o0 = 0; o0 < NO; o0 += CHUNK) {
+    T vv[CHUNK][BS * BS], xx[CHUNK][BS];
+#pragma unroll
+    for (int c = 0; c < CHUNK; ++c) {
+      const int o = o0 + c;
+      if (o < NO && o % step == first) {
+        const int dx = Sf<KIND>::x(o), dy = Sf<KIND>::y(o), dz = Sf<KIND>::z(o);
+        const bool in = mx[dx + R] && my[dy + R] && mz[dz + R];
+        const unsigned q = in ? p + (unsigned)(dx + L.Lx * dy + L.LxLy * dz) : p;
+        const T* row = val + (size_t)o * BS * BS * N;
+#pragma unroll
+        for (int e = 0; e < BS * BS; ++e) vv[c][e] = row[e * N + p];
+#pragma unroll
+        for (int s = 0; s < BS; ++s) {
+          const T xs = x[BS * q + s];
+          xx[c][s] = in ? xs : T(0);  // a select, not a multiply (no FP64 pipe work)
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CHUNK; ++c)
+      if (o0 + c < NO && (o0 + c) % step == first)
+#pragma unroll
+        for (int a = 0; a < BS; ++a)
+#pragma unroll
+          for (int s = 0; s < BS; ++s) r[a] -= vv[c][a * BS + s] * xx[c][s];
+  }
+}
+
+// one point per thread: loads of CHUNK offsets in flight at once
+template <int BS, typename T>
+constexpr int f_chunk() { return sizeof(T) == 4 ? (BS == 1 ? 25 : 3) : (BS == 1 ? 8 : 1); }
+
+// y = b - A x, or y = A x when b is null
+template <int BS, int KIND, typename T>
+__global__ void __launch_bounds__(256) k_spmv_f(Lat32 L, const T* __restrict__ val, const T* __restrict__ x,
+                                                const T* __restrict__ b, T* __restrict__ y) {
+  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (unsigned)L.N) return;
+  T r[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) r[a] = T(0);
+  coarse_residual<BS, KIND, f_chunk<BS, T>(), T>(L, p, val, x, r, 0, 1);
+#pragma unroll
+  for (int a = 0; a < BS; ++a) y[BS * p + a] = b ? b[BS * p + a] + r[a] : -r[a];
+}
+
+// Chebyshev step: r = b - A xin (r = b when xin is null), d = cd d + cr D^-1 r, xout = xin + d
+template <typename T, int BS>
+__device__ __forceinline__ void cheb_update(unsigned p, unsigned N, const T r[BS], const T* __restrict__ dinv,
+                                            const T* __restrict__ xin, T* __restrict__ xout, T* __restrict__ d, T cd,
+                                            T cr) {
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
+    T z = T(0);
 #pragma unroll
-    for (int m = TPP / 2; m > 0; m >>= 1) r[a] += __shfl_xor_sync(0xffffffffu, r[a], m);
-    if (valid && b) r[a] += b[BS * p + a];
+    for (int s = 0; s < BS; ++s) z += dinv[(a * BS + s) * N + p] * r[s];
+    const T dn = (cd != T(0)) ? cd * d[BS * p + a] + cr * z : cr * z;
+    d[BS * p + a] = dn;
+    xout[BS * p + a] = (xin ? xin[BS * p + a] : T(0)) + dn;
   }
 }
 
-// y = b - A x (b may be null: y = -A x is not used; callers pass b or want A x)
-template <int BS, int KIND, int TPP, typename T>
-__global__ void __launch_bounds__(256) k_spmv_g(Lat L, const T* __restrict__ val, const T* __restrict__ x,
-                                                const T* __restrict__ b, T* __restrict__ y) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long p = t / TPP;
-  const int sub = (int)(t % TPP);
-  const bool valid = p < L.N;
-  T r[BS];
-  group_residual<BS, KIND, TPP, T>(L, valid ? p : 0, valid, sub, val, x, b, r);
-  if (valid && sub == 0) {
-#pragma unroll
-    for (int a = 0; a < BS; ++a) y[BS * p + a] = b ? r[a] : -r[a];
-  }
-}
-
-template <int BS, int KIND, int TPP, typename T>
-__global__ void __launch_bounds__(256) k_cheb_g(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
+template <int BS, int KIND, typename T>
+__global__ void __launch_bounds__(256) k_cheb_f(Lat32 L, const T* __restrict__ val, const T* __restrict__ dinv,
                                                 const T* __restrict__ b, const T* __restrict__ xin,
                                                 T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long p = t / TPP;
-  const int sub = (int)(t % TPP);
-  const bool valid = p < L.N;
+  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (unsigned)L.N) return;
   T r[BS];
-  group_residual<BS, KIND, TPP, T>(L, valid ? p : 0, valid, sub, val, xin, b, r);
-  if (valid && sub == 0) {
 #pragma unroll
-    for (int a = 0; a < BS; ++a) {
-      T z = T(0);
+  for (int a = 0; a < BS; ++a) r[a] = b[BS * p + a];
+  coarse_residual<BS, KIND, f_chunk<BS, T>(), T>(L, p, val, xin, r, 0, 1);
+  cheb_update<T, BS>(p, (unsigned)L.N, r, dinv, xin, xout, d, cd, cr);
+}
+
+// the first Chebyshev step from x = 0: d = cr D^-1 b, xout = d (no stencil)
+template <int BS, typename T>
+__global__ void __launch_bounds__(256) k_cheb_zero(long long npts, const T* __restrict__ dinv,
+                                                   const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ d,
+                                                   T cr) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  T r[BS];
 #pragma unroll
-      for (int s = 0; s < BS; ++s) z += dinv[(long long)(a * BS + s) * L.N + p] * r[s];
-      const T dn = (cd != T(0)) ? cd * d[BS * p + a] + cr * z : cr * z;
-      d[BS * p + a] = dn;
-      xout[BS * p + a] = (xin ? xin[BS * p + a] : T(0)) + dn;
-    }
+  for (int a = 0; a < BS; ++a) r[a] = b[BS * p + a];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    T z = T(0);
+#pragma unroll
+    for (int s = 0; s < BS; ++s) z += dinv[(a * BS + s) * npts + p] * r[s];
+    d[BS * p + a] = cr * z;
+    xout[BS * p + a] = cr * z;
   }
+}
+
+// Warp-split offsets: blockDim = (32, W); warp y takes the offsets o with
+// o % W == y for 32 consecutive points, so every load instruction reads one
+// stored row for 32 consecutive points; the W partial sums meet in shared
+// memory and are added in a fixed order.
+template <int BS, typename T>
+constexpr int w_chunk() { return sizeof(T) == 4 ? (BS == 1 ? 8 : 2) : (BS == 1 ? 4 : 1); }
+
+template <int BS, int KIND, int W, typename T>
+__device__ __forceinline__ bool wsplit_residual(const Lat32& L, const T* __restrict__ val, const T* __restrict__ x,
+                                                T (&part)[W][BS][32], unsigned& p, T r[BS]) {
+  p = blockIdx.x * 32 + threadIdx.x;
+  const bool valid = p < (unsigned)L.N;
+  T acc[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) acc[a] = T(0);
+  if (valid && x) coarse_residual<BS, KIND, w_chunk<BS, T>(), T>(L, p, val, x, acc, threadIdx.y, W);
+#pragma unroll
+  for (int a = 0; a < BS; ++a) part[threadIdx.y][a][threadIdx.x] = acc[a];
+  __syncthreads();
+  if (threadIdx.y != 0 || !valid) return false;
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int u = 0; u < W; ++u) s += part[u][a][threadIdx.x];
+    r[a] = s;  // = -(A x)_a
+  }
+  return true;
+}
+
+template <int BS, int KIND, int W, typename T>
+__global__ void __launch_bounds__(32 * W) k_spmv_w(Lat32 L, const T* __restrict__ val, const T* __restrict__ x,
+                                                   const T* __restrict__ b, T* __restrict__ y) {
+  __shared__ T part[W][BS][32];
+  unsigned p;
+  T r[BS];
+  if (!wsplit_residual<BS, KIND, W, T>(L, val, x, part, p, r)) return;
+#pragma unroll
+  for (int a = 0; a < BS; ++a) y[BS * p + a] = b ? b[BS * p + a] + r[a] : -r[a];
+}
+
+template <int BS, int KIND, int W, typename T>
+__global__ void __launch_bounds__(32 * W) k_cheb_w(Lat32 L, const T* __restrict__ val, const T* __restrict__ dinv,
+                                                   const T* __restrict__ b, const T* __restrict__ xin,
+                                                   T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+  __shared__ T part[W][BS][32];
+  unsigned p;
+  T r[BS];
+  if (!wsplit_residual<BS, KIND, W, T>(L, val, xin, part, p, r)) return;
+#pragma unroll
+  for (int a = 0; a < BS; ++a) r[a] += b[BS * p + a];
+  cheb_update<T, BS>(p, (unsigned)L.N, r, dinv, xin, xout, d, cd, cr);
 }
 
 // restriction b_c = P^T r with one warp per coarse point; the lanes split
@@ -566,6 +699,14 @@ __global__ void k_dense_mv(int n, const double* __restrict__ Ainv, const T* __re
 __global__ void k_cast_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = (float)x[i];
+}
+
+// rows x n FP64 values (row stride n) to FP32 with row stride ld >= n
+__global__ void k_cast_f32_rows(int rows, long long n, const double* __restrict__ x, float* __restrict__ y,
+                                long long ld) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * n) return;
+  y[(i / n) * ld + i % n] = (float)x[i];
 }
 
 // ------------------------------------------------------------------ setup
@@ -813,44 +954,58 @@ void dispatch_bs(int bs, F&& f) {
 
 FaceTopo face_topo(const Ctx& c) { return FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy}; }
 
-// lanes per lattice point: 1 on large levels, up to a warp on small ones
-// (overridden per level by the set-up autotuner)
-int group_size(long long npts, int kind) {
-  if (npts >= 131072) return 1;
-  if (npts >= 32768) return 4;
-  return kind == ST_BOX2 ? 32 : 16;
+// 32-bit lattice view for the coarse-level kernels (their indices e N + p
+// and bs q + s stay below 2^31)
+Lat32 lat32_of(const StructOp& A) {
+  if ((long long)A.bs * A.bs * A.N >= (1LL << 31))
+    throw Error{MHFP_ERR_ARG, "lattice level too large for 32-bit indexing"};
+  Lat32 L;
+  L.Lx = A.Lx;
+  L.Ly = A.Ly;
+  L.Lz = A.Lz;
+  L.N = (int)A.N;
+  L.LxLy = A.Lx * A.Ly;
+  L.dx = Div32::make((unsigned)A.Lx);
+  L.dy = Div32::make((unsigned)A.Ly);
+  return L;
 }
 
+// Launch schedule of a level's sweeps and residuals: 1 = one point per
+// thread, W = 4, 8, 16 = warp-split offsets over W warps.  The set-up
+// autotuner times all four; without it, scalar levels of 64K points and up
+// take one point per thread and the others eight warps.
+int default_schedule(long long npts, int bs) { return (bs == 1 && npts >= 65536) ? 1 : 8; }
+
 template <class F>
-void dispatch_tpp(int tpp, F&& f) {
-  if (tpp == 1) f(std::integral_constant<int, 1>{});
-  else if (tpp == 4) f(std::integral_constant<int, 4>{});
-  else if (tpp == 16) f(std::integral_constant<int, 16>{});
-  else f(std::integral_constant<int, 32>{});
+void dispatch_sched(int sched, F&& f) {
+  if (sched == 1) f(std::integral_constant<int, 1>{});
+  else if (sched == 4) f(std::integral_constant<int, 4>{});
+  else if (sched == 16) f(std::integral_constant<int, 16>{});
+  else f(std::integral_constant<int, 8>{});
+}
+
+// y = b - A x (y = A x when b is null) on a lattice level with schedule sched
+template <typename T>
+void launch_spmv(Ctx& c, const StructOp& A, int bs, const T* val, const T* x, const T* b, T* y, int sched) {
+  const Lat32 L = lat32_of(A);
+  dispatch_bs(bs, [&](auto BS) {
+    dispatch_kind(A.kind, [&](auto K) {
+      dispatch_sched(sched, [&](auto S) {
+        if constexpr (S.value == 1)
+          k_spmv_f<BS.value, K.value, T><<<grid_for(A.N, 256), 256, 0, c.stream>>>(L, val, x, b, y);
+        else
+          k_spmv_w<BS.value, K.value, S.value, T><<<grid_for(A.N, 32), dim3(32, S.value), 0, c.stream>>>(L, val, x,
+                                                                                                          b, y);
+      });
+    });
+  });
 }
 
 void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
   if (L.faces) {
     k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, x, b, y);
   } else {
-    const Lat lat = lat_of(L.A);
-    const int tpp = group_size(lat.N, L.A.kind);
-    dispatch_bs(L.bs, [&](auto BS) {
-      dispatch_kind(L.A.kind, [&](auto K) {
-        if (tpp == 1) {
-          k_spmv<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, y);
-        } else {
-          dispatch_tpp(tpp, [&](auto G) {
-            if (b) {
-              k_spmv_g<BS.value, K.value, G.value, double><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
-                  lat, L.A.val, x, b, y);
-            } else {
-              k_spmv<BS.value, K.value, double><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, x, b, y);
-            }
-          });
-        }
-      });
-    });
+    launch_spmv<double>(c, L.A, L.bs, L.A.val, x, b, y, default_schedule(L.A.N, L.bs));
   }
   MHFP_LAUNCH_CHECK();
 }
@@ -1112,45 +1267,32 @@ void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
   if (L.faces) {
     k_spmv_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, x, b, y);
   } else {
-    const Lat lat = lat_of(L.A);
-    const int tpp = b ? (L.tpp ? L.tpp : group_size(lat.N, L.A.kind)) : 1;
-    dispatch_bs(L.bs, [&](auto BS) {
-      dispatch_kind(L.A.kind, [&](auto K) {
-        if (tpp == 1 && BS.value == 1) {
-          k_spmv_s<K.value, (K.value == ST_BOX2 ? 5 : 25), T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(
-              lat, v.val, x, b, y);
-        } else if (tpp == 1) {
-          k_spmv<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, y);
-        } else {
-          dispatch_tpp(tpp, [&](auto G) {
-            k_spmv_g<BS.value, K.value, G.value, T><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
-                lat, v.val, x, b, y);
-          });
-        }
-      });
-    });
+    launch_spmv<T>(c, L.A, L.bs, v.val, x, b, y, L.tpp ? L.tpp : default_schedule(L.A.N, L.bs));
   }
   MHFP_LAUNCH_CHECK();
 }
 
-// one Chebyshev sweep on a lattice level with `tpp` lanes per point
+// one Chebyshev sweep on a lattice level with schedule sched (the first
+// sweep from zero has no stencil work and always runs one point per thread)
 template <typename T>
-void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* out, T cd, T cr, int tpp) {
-  const Lat lat = lat_of(L.A);
+void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* out, T cd, T cr, int sched) {
+  if (!xin) {
+    dispatch_bs(L.bs, [&](auto BS) {
+      k_cheb_zero<BS.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(L.A.N, v.dinv, b, out, v.d, cr);
+    });
+    return;
+  }
+  const Lat32 lat = lat32_of(L.A);
   dispatch_bs(L.bs, [&](auto BS) {
     dispatch_kind(L.A.kind, [&](auto K) {
-      if (tpp == 1 && BS.value == 1) {
-        k_cheb_s<K.value, (K.value == ST_BOX2 ? 5 : 25), T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(
-            lat, v.val, v.dinv, b, xin, out, v.d, cd, cr);
-      } else if (tpp == 1) {
-        k_cheb<BS.value, K.value, T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d,
-                                                                                  cd, cr);
-      } else {
-        dispatch_tpp(tpp, [&](auto G) {
-          k_cheb_g<BS.value, K.value, G.value, T><<<grid_for(lat.N * G.value, 256), 256, 0, c.stream>>>(
+      dispatch_sched(sched, [&](auto S) {
+        if constexpr (S.value == 1)
+          k_cheb_f<BS.value, K.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out,
+                                                                                     v.d, cd, cr);
+        else
+          k_cheb_w<BS.value, K.value, S.value, T><<<grid_for(L.A.N, 32), dim3(32, S.value), 0, c.stream>>>(
               lat, v.val, v.dinv, b, xin, out, v.d, cd, cr);
-        });
-      }
+      });
     });
   });
 }
@@ -1158,6 +1300,9 @@ void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* 
 // The symmetric FP32 sweep and residual of the finest displacement level
 // with L.tpp resident blocks per SM (6 or 8; 0: 8 when one wave of 8 blocks
 // of 256 per SM covers the level, else 6).
+// schedule of the finest FP32 displacement level: 6 or 8 resident blocks of
+// 256 threads per SM (0: 8 when one wave of 8 blocks per SM covers the
+// level, else 6)
 int sym_minb(const Level& L) {
   if (L.tpp == 6 || L.tpp == 8) return L.tpp;
   return L.A.N <= 152LL * 8 * 256 ? 8 : 6;
@@ -1165,20 +1310,25 @@ int sym_minb(const Level& L) {
 void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, float* xout, float* d, float cd,
                      float cr) {
   const Lat lat = lat_of(L.A);
+  if (!xin) {  // the first step from zero has no stencil work
+    k_cheb_zero<3, float><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat.N, L.dinvf, b, xout, d, cr);
+    MHFP_LAUNCH_CHECK();
+    return;
+  }
   if (sym_minb(L) == 8)
-    k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout, d, cd,
-                                                                        cr);
+    k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+                                                                        d, cd, cr);
   else
-    k_cheb_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout, d, cd,
-                                                                        cr);
+    k_cheb_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+                                                                        d, cd, cr);
   MHFP_LAUNCH_CHECK();
 }
 void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, float* y) {
   const Lat lat = lat_of(L.A);
   if (sym_minb(L) == 8)
-    k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+    k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
   else
-    k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+    k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
   MHFP_LAUNCH_CHECK();
 }
 
@@ -1210,11 +1360,13 @@ void autotune_fine_sym(Ctx& c, Level& L) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   L.tpp = best_minb;
+  L.sweep_us = best * 1e3 / 5;
 }
 
-// Set-up autotuner: time the lanes-per-point variants of a coarse level's
-// Chebyshev sweep (same arithmetic, different launch schedule) and keep the
-// fastest for this level's sweeps and residuals.
+// Set-up autotuner: time the launch schedules of a coarse level's Chebyshev
+// sweep (one point per thread; offsets split over 4, 8 or 16 warps: same
+// arithmetic up to the order of the partial sums) and keep the fastest for
+// this level's sweeps and residuals.
 template <typename T>
 void autotune_level(Ctx& c, Level& L) {
   const LV<T> v = view(c, L, T());
@@ -1227,8 +1379,8 @@ void autotune_level(Ctx& c, Level& L) {
   MHFP_CUDA(cudaEventCreate(&e0));
   MHFP_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_tpp = group_size(L.A.N, L.A.kind);
-  for (int tpp : {1, 4, 16, 32}) {
+  int best_tpp = default_schedule(L.A.N, L.bs);
+  for (int tpp : {1, 4, 8, 16}) {
     for (int rep = 0; rep < 3; ++rep) {
       launch_cheb<T>(c, L, v, b, x, v.y, T(0.5), T(0.5), tpp);
       MHFP_LAUNCH_CHECK();
@@ -1250,6 +1402,7 @@ void autotune_level(Ctx& c, Level& L) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   L.tpp = best_tpp;
+  L.sweep_us = best * 1e3 / 10;
 }
 
 template <typename T>
@@ -1284,7 +1437,7 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
         k_cheb_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
       }
     } else {
-      launch_cheb<T>(c, L, v, b, xin, out, (T)cd, (T)cr, L.tpp ? L.tpp : group_size(L.A.N, L.A.kind));
+      launch_cheb<T>(c, L, v, b, xin, out, (T)cd, (T)cr, L.tpp ? L.tpp : default_schedule(L.A.N, L.bs));
     }
     MHFP_LAUNCH_CHECK();
     // algorithmic bytes of a Chebyshev sweep: the matrix values (27 blocks
@@ -1367,8 +1520,12 @@ void make_fp32(Ctx& c, std::vector<Level>& H, bool fine_sym) {
     Level& L = H[l];
     const size_t bs2 = (size_t)L.bs * L.bs;
     if (fine_sym && l == 0 && !L.dense_inv) {
-      const size_t N = (size_t)L.A.N;
-      L.symf = cast_copy(c, L.A.val + 13 * 9 * N, 14 * 9 * N);
+      const long long N = L.A.N;
+      L.sym_ld = (N + 63) / 64 * 64;  // rows start on 256-byte boundaries
+      L.symf = dalloc_n<float>(c, (size_t)126 * L.sym_ld);
+      MHFP_CUDA(cudaMemsetAsync(L.symf, 0, (size_t)126 * L.sym_ld * sizeof(float), c.stream));
+      k_cast_f32_rows<<<grid_for(126 * N, 256), 256, 0, c.stream>>>(126, N, L.A.val + 13 * 9 * N, L.symf, L.sym_ld);
+      MHFP_LAUNCH_CHECK();
     } else if (!L.faces) {
       L.valf = cast_copy(c, L.A.val, (size_t)L.A.noff() * bs2 * L.A.N);
     }
@@ -1408,6 +1565,12 @@ void build_hierarchies(Ctx& c) {
         else autotune_level<double>(c, L);
       }
   }
+}
+
+int level_schedule(Ctx& c, std::vector<Level>& H, int l) {
+  const Level& L = H[l];
+  if (&H == &c.hu && l == 0) return L.symf ? sym_minb(L) : 0;  // FP64: the full-storage k_cheb_u0
+  return L.tpp ? L.tpp : default_schedule(L.A.N, L.bs);
 }
 
 // timed as class 4 (displacement) or 5 (interface pressure)

@@ -357,6 +357,9 @@ mhfp_status mhfp_hierarchy(mhfp_handle h, int which, mhfp_hierarchy_info* info) 
       info->points[l] = H[l].npts;
       info->block[l] = H[l].bs;
       info->lmax[l] = H[l].dense_inv ? 0.0 : H[l].lmax;
+      const bool lattice = !H[l].dense_inv && !H[l].faces;
+      info->schedule[l] = !lattice ? 0 : (H[l].tpp ? H[l].tpp : mhfp::level_schedule(c, H, (int)l));
+      info->sweep_us[l] = H[l].sweep_us;
     }
   });
 }

@@ -122,8 +122,9 @@ struct Level {
   // prolongator to the next level (lattice levels only): [p_slots^3][bs*bs][npts]
   double* P = nullptr;
   int R = 1;                  // stencil radius of A (L_inf)
-  int tpp = 0;                // lanes per point chosen by the autotuner (0: default rule);
-                              // on the finest FP32 displacement level: blocks per SM (6 or 8)
+  int tpp = 0;                // launch schedule chosen by the autotuner (0: default rule):
+                              // 1 = one point per thread, 4/8/16 = warps splitting the
+                              // offsets; finest FP32 displacement level: blocks per SM (6, 8)
   unsigned char* active = nullptr;  // [n] free dofs
   // work vectors of length n
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *y = nullptr;
@@ -131,7 +132,9 @@ struct Level {
   double* dense_inv = nullptr;
   // FP32 copies for the mixed-precision cycle (precision == 1)
   float *valf = nullptr, *dinvf = nullptr, *Pf = nullptr;
-  float* symf = nullptr;      // finest displacement level, FP32: symmetric half [14][9][N]
+  float* symf = nullptr;      // finest displacement level, FP32: symmetric half [14][9][sym_ld]
+  long long sym_ld = 0;       // row stride of symf: the node count rounded up to 64
+  double sweep_us = 0.0;      // autotuner's time of one sweep under the chosen schedule
   float *xf = nullptr, *bf = nullptr, *rf = nullptr, *df = nullptr, *yf = nullptr;
 };
 
@@ -264,6 +267,7 @@ T* dalloc_n(Ctx& c, size_t n) { return (T*)dalloc(c, n * sizeof(T)); }
 void dfree_all(Ctx& c);
 
 // timing helpers
+int level_schedule(Ctx& c, std::vector<Level>& H, int l);  // effective schedule of a lattice level
 void timing_begin(Ctx& c, int cls);
 void timing_end(Ctx& c, int cls, double bytes);
 
