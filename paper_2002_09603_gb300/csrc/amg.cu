@@ -115,26 +115,6 @@ __device__ __forceinline__ void spmv_body(const Lat& L, const T* __restrict__ va
 // ------------------------------------------------------- lattice helpers
 // 32-bit lattice indexing for the coarse levels (see the coarse-level sweeps
 // below).
-// q = n / d for every 32-bit n, from a magic multiplier fixed at set-up
-struct Div32 {
-  unsigned m = 1, d = 1;
-  int s1 = 0, s2 = 0;
-  static Div32 make(unsigned d) {
-    int l = 0;
-    while ((1ull << l) < d) ++l;  // l = ceil(log2 d)
-    Div32 r;
-    r.d = d;
-    r.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
-    r.s1 = l < 1 ? l : 1;
-    r.s2 = l < 1 ? 0 : l - 1;
-    return r;
-  }
-  __device__ __forceinline__ unsigned div(unsigned n) const {
-    const unsigned t = __umulhi(m, n);
-    return (t + ((n - t) >> s1)) >> s2;
-  }
-};
-
 struct Lat32 {
   int Lx, Ly, Lz, N, LxLy;
   Div32 dx, dy;
@@ -563,27 +543,35 @@ __global__ void __launch_bounds__(256) k_restrict_w(Lat F, Lat Cc, int R, const 
 }
 
 // face level (ELL, 11 slots) versions
+// y = b - C x (y = C x when b is null) on the face level; the 11 columns of
+// each row follow from the face topology (FaceTopo32::ell_cols), so only
+// the values stream from memory
 template <typename T>
-__global__ void k_spmv_ell(long long n, const int* __restrict__ col, const T* __restrict__ val,
-                           const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ y) {
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n) return;
+__global__ void __launch_bounds__(256) k_spmv_ell(FaceTopo32 t, const T* __restrict__ val, const T* __restrict__ x,
+                                                  const T* __restrict__ b, T* __restrict__ y) {
+  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nF) return;
+  unsigned col[11];
+  t.ell_cols(f, col);
   T a = T(0);
 #pragma unroll
-  for (int q = 0; q < 11; ++q) a += val[q * n + f] * x[col[q * n + f]];
+  for (int q = 0; q < 11; ++q) a += val[q * t.nF + f] * x[col[q]];
   y[f] = b ? b[f] - a : a;
 }
 
 template <typename T>
-__global__ void k_cheb_ell(long long n, const int* __restrict__ col, const T* __restrict__ val,
-                           const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ xin,
-                           T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n) return;
+__global__ void __launch_bounds__(256) k_cheb_ell(FaceTopo32 t, const T* __restrict__ val,
+                                                  const T* __restrict__ dinv, const T* __restrict__ b,
+                                                  const T* __restrict__ xin, T* __restrict__ xout, T* __restrict__ d,
+                                                  T cd, T cr) {
+  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nF) return;
   T r = b[f];
   if (xin) {
+    unsigned col[11];
+    t.ell_cols(f, col);
 #pragma unroll
-    for (int q = 0; q < 11; ++q) r -= val[q * n + f] * xin[col[q * n + f]];
+    for (int q = 0; q < 11; ++q) r -= val[q * t.nF + f] * xin[col[q]];
   }
   const T dn = (cd != T(0)) ? cd * d[f] + cr * dinv[f] * r : cr * dinv[f] * r;
   d[f] = dn;
@@ -620,7 +608,7 @@ __global__ void k_prolong(Lat F, Lat Cc, int R, const T* __restrict__ P, const T
   for (int q = 0; q < BS; ++q) x[BS * p + q] += acc[q];
 }
 
-// faces -> cells transfer of the interface-pressure hierarchy
+// faces -> cells Galerkin product of the interface-pressure hierarchy (set-up)
 struct FaceTopo {
   int nx, ny, nz;
   long long nT, nF, nFx, nFy;
@@ -660,26 +648,34 @@ __device__ __forceinline__ int ft_face_cells(const FaceTopo& d, long long f, int
 }
 
 template <typename T>
-__global__ void k_restrict_faces(FaceTopo d, const T* __restrict__ pw, const T* __restrict__ r, T* __restrict__ bc) {
-  const long long Tc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (Tc >= d.nT) return;
-  const int i = (int)(Tc % d.nx), j = (int)((Tc / d.nx) % d.ny), k = (int)(Tc / ((long long)d.nx * d.ny));
+__global__ void __launch_bounds__(256) k_restrict_faces(FaceTopo32 t, const T* __restrict__ pw,
+                                                        const T* __restrict__ r, T* __restrict__ bc) {
+  const unsigned Tc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Tc >= t.nT) return;
+  const unsigned q = t.d_nx.div(Tc);
+  const int i = (int)(Tc - q * (unsigned)t.nx);
+  const int k = (int)t.d_ny.div(q), j = (int)(q - (unsigned)k * (unsigned)t.ny);
   T s = T(0);
+#pragma unroll
   for (int lf = 0; lf < 6; ++lf) {
-    const long long f = ft_cell_face(d, i, j, k, lf);
+    const unsigned f = t.face(i, j, k, lf);
     s += pw[f] * r[f];
   }
   bc[Tc] = s;
 }
 
 template <typename T>
-__global__ void k_prolong_faces(FaceTopo d, const T* __restrict__ pw, const T* __restrict__ xc, T* __restrict__ x) {
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= d.nF) return;
-  int c[2][3];
-  const int cnt = ft_face_cells(d, f, c);
+__global__ void __launch_bounds__(256) k_prolong_faces(FaceTopo32 t, const T* __restrict__ pw,
+                                                       const T* __restrict__ xc, T* __restrict__ x) {
+  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nF) return;
+  int c[2][3], lf[2];
+  bool ok[2];
+  t.cells(f, c, ok, lf);
   T s = T(0);
-  for (int q = 0; q < cnt; ++q) s += xc[c[q][0] + (long long)d.nx * (c[q][1] + (long long)d.ny * c[q][2])];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (ok[q]) s += xc[t.cell(c[q][0], c[q][1], c[q][2])];
   x[f] += pw[f] * s;
 }
 
@@ -952,7 +948,11 @@ void dispatch_bs(int bs, F&& f) {
   else f(std::integral_constant<int, 1>{});
 }
 
-FaceTopo face_topo(const Ctx& c) { return FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy}; }
+// the face level's topology for the sweeps and transfers (32-bit: nF < 2^31)
+FaceTopo32 face_topo(const Ctx& c) {
+  if (c.nF >= (1LL << 31) / 11) throw Error{MHFP_ERR_ARG, "too many faces for 32-bit face indexing"};
+  return FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy);
+}
 
 // 32-bit lattice view for the coarse-level kernels (their indices e N + p
 // and bs q + s stay below 2^31)
@@ -1003,7 +1003,7 @@ void launch_spmv(Ctx& c, const StructOp& A, int bs, const T* val, const T* x, co
 
 void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
   if (L.faces) {
-    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, c.Cpi, x, b, y);
+    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), c.Cpi, x, b, y);
   } else {
     launch_spmv<double>(c, L.A, L.bs, L.A.val, x, b, y, default_schedule(L.A.N, L.bs));
   }
@@ -1230,7 +1230,8 @@ void build_pi(Ctx& c) {
     L1.npts = c.nT; L1.n = c.nT; L1.R = 2;
     L1.A.val = dalloc_n<double>(c, (size_t)25 * c.nT);
     L1.active = dalloc_n<unsigned char>(c, c.nT);
-    k_rap_faces<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(face_topo(c), c.ell_col, c.Cpi, c.pw, L1.A.val, L1.active);
+    k_rap_faces<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy},
+                                                           c.ell_col, c.Cpi, c.pw, L1.A.val, L1.active);
     MHFP_LAUNCH_CHECK();
     c.hpi.push_back(L1);
   }
@@ -1265,7 +1266,7 @@ template <typename T>
 void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
   const LV<T> v = view(c, L, T());
   if (L.faces) {
-    k_spmv_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, x, b, y);
+    k_spmv_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), v.ell, x, b, y);
   } else {
     launch_spmv<T>(c, L.A, L.bs, v.val, x, b, y, L.tpp ? L.tpp : default_schedule(L.A.N, L.bs));
   }
@@ -1332,35 +1333,76 @@ void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, fl
   MHFP_LAUNCH_CHECK();
 }
 
+// Device time of one call of `body` (which enqueues kernels on c.stream):
+// `reps` calls captured once into a CUDA graph on a private stream, the
+// graph replayed once to warm up and three times under events, the fastest
+// replay kept.  Timing graph replays leaves out host launch overhead, as in
+// the solve, which runs as graphs.
+template <class F>
+float graph_time_us(Ctx& c, int reps, F&& body) {
+  cudaStream_t user = c.stream, st = nullptr;
+  MHFP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  MHFP_CUDA(cudaStreamSynchronize(user));
+  const long long l0 = g_launches;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  c.stream = st;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    try {
+      for (int r = 0; r < reps; ++r) body();
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      c.stream = user;
+      cudaStreamDestroy(st);
+      throw;
+    }
+    e = cudaStreamEndCapture(st, &g);
+  }
+  c.stream = user;
+  g_launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  float best = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int it = 0; it < 4 && e == cudaSuccess; ++it) {
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && it > 0 && ms < best) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaStreamDestroy(st);
+  MHFP_CUDA(e);
+  return best * 1e3f / reps;
+}
+
 // Set-up autotuner for the finest displacement level in FP32: time the two
 // occupancy variants of the symmetric sweep and keep the faster in L.tpp.
 void autotune_fine_sym(Ctx& c, Level& L) {
   MHFP_CUDA(cudaMemsetAsync(L.bf, 0, L.n * sizeof(float), c.stream));
   MHFP_CUDA(cudaMemsetAsync(L.xf, 0, L.n * sizeof(float), c.stream));
   MHFP_CUDA(cudaMemsetAsync(L.df, 0, L.n * sizeof(float), c.stream));
-  cudaEvent_t e0, e1;
-  MHFP_CUDA(cudaEventCreate(&e0));
-  MHFP_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_minb = 0;
   for (int minb : {8, 6}) {
     L.tpp = minb;
-    for (int rep = 0; rep < 2; ++rep) launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f);
-    MHFP_CUDA(cudaEventRecord(e0, c.stream));
-    for (int rep = 0; rep < 5; ++rep) launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f);
-    MHFP_CUDA(cudaEventRecord(e1, c.stream));
-    MHFP_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    MHFP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
+    const float us = graph_time_us(c, 5, [&] { launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f); });
+    if (us < best) {
+      best = us;
       best_minb = minb;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   L.tpp = best_minb;
-  L.sweep_us = best * 1e3 / 5;
+  L.sweep_us = best;
 }
 
 // Set-up autotuner: time the launch schedules of a coarse level's Chebyshev
@@ -1375,34 +1417,20 @@ void autotune_level(Ctx& c, Level& L) {
   MHFP_CUDA(cudaMemsetAsync(b, 0, L.n * sizeof(T), c.stream));
   MHFP_CUDA(cudaMemsetAsync(x, 0, L.n * sizeof(T), c.stream));
   MHFP_CUDA(cudaMemsetAsync(v.d, 0, L.n * sizeof(T), c.stream));
-  cudaEvent_t e0, e1;
-  MHFP_CUDA(cudaEventCreate(&e0));
-  MHFP_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tpp = default_schedule(L.A.N, L.bs);
   for (int tpp : {1, 4, 8, 16}) {
-    for (int rep = 0; rep < 3; ++rep) {
+    const float us = graph_time_us(c, 10, [&] {
       launch_cheb<T>(c, L, v, b, x, v.y, T(0.5), T(0.5), tpp);
       MHFP_LAUNCH_CHECK();
-    }
-    MHFP_CUDA(cudaEventRecord(e0, c.stream));
-    for (int rep = 0; rep < 10; ++rep) {
-      launch_cheb<T>(c, L, v, b, x, v.y, T(0.5), T(0.5), tpp);
-      MHFP_LAUNCH_CHECK();
-    }
-    MHFP_CUDA(cudaEventRecord(e1, c.stream));
-    MHFP_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    MHFP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
+    });
+    if (us < best) {
+      best = us;
       best_tpp = tpp;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   L.tpp = best_tpp;
-  L.sweep_us = best * 1e3 / 10;
+  L.sweep_us = best;
 }
 
 template <typename T>
@@ -1427,7 +1455,7 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
     }
     if (time_it && xin) timing_begin(c, 0);
     if (L.faces) {
-      k_cheb_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.ell_col, v.ell, v.dinv, b, xin, out, v.d, (T)cd,
+      k_cheb_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), v.ell, v.dinv, b, xin, out, v.d, (T)cd,
                                                              (T)cr);
     } else if (time_it) {
       if constexpr (std::is_same<T, float>::value) {

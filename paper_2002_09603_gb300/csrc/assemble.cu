@@ -630,27 +630,33 @@ __global__ void k_apply_p(Dims d, const double* __restrict__ Aup, const double* 
   y[nU + T] = finish(s, nU + T, so, bsub);
 }
 
-// pi rows: A_pip x_p + A_pipi x_pi (ELL, 11 slots).
-__global__ void k_apply_pi(Dims d, const double* __restrict__ ApPi, const int* __restrict__ col,
-                           const double* __restrict__ Apipi, const double* __restrict__ x, double* __restrict__ y,
-                           const double* __restrict__ so, const double* __restrict__ bsub, double cpp) {
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= d.nF) return;
-  long long cell[2];
-  int lf[2], ijk[2][3];
-  face_cells(d, f, cell, lf, ijk);
-  const long long nU = 3 * d.nN;
+// pi rows: A_pip x_p + A_pipi x_pi (ELL, 11 slots; the columns follow from
+// the face topology, FaceTopo32::ell_cols, in the stored slot order).
+__global__ void __launch_bounds__(256) k_apply_pi(FaceTopo32 t, long long nU, const double* __restrict__ ApPi,
+                                                  const double* __restrict__ Apipi, const double* __restrict__ x,
+                                                  double* __restrict__ y, const double* __restrict__ so,
+                                                  const double* __restrict__ bsub, double cpp) {
+  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nF) return;
+  int c[2][3], lf[2];
+  bool ok[2];
+  t.cells(f, c, ok, lf);
   const double* xp = x + nU;
-  const double* xpi = xp + d.nT;
+  const double* xpi = xp + t.nT;
   double s = 0.0;
   for (int q = 0; q < 2; ++q)
-    if (cell[q] >= 0) s += ApPi[(long long)lf[q] * d.nT + cell[q]] * xp[cell[q]];
+    if (ok[q]) {
+      const unsigned T = t.cell(c[q][0], c[q][1], c[q][2]);
+      s += ApPi[(long long)lf[q] * t.nT + T] * xp[T];
+    }
   s *= cpp;
+  unsigned col[11];
+  t.ell_cols(f, col);
   double a = 0.0;
 #pragma unroll
-  for (int q = 0; q < 11; ++q) a += Apipi[(long long)q * d.nF + f] * xpi[col[(long long)q * d.nF + f]];
+  for (int q = 0; q < 11; ++q) a += Apipi[(long long)q * t.nF + f] * xpi[col[q]];
   s += a;
-  const long long r = nU + d.nT + f;
+  const long long r = nU + t.nT + f;
   y[r] = finish(s, r, so, bsub);
 }
 
@@ -917,13 +923,15 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
   k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, transpose ? 1.0 : c.dt, x, y,
                                                        so, bsub, sgn);
   MHFP_LAUNCH_CHECK();
-  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(d, c.ApPi, c.ell_col, c.Apipi, x, y, so, bsub,
+  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy),
+                                                        3 * c.nN, c.ApPi, c.Apipi, x, y, so, bsub,
                                                         transpose ? c.dt : 1.0);
   MHFP_LAUNCH_CHECK();
   // algorithmic bytes: A_uu values (27*9 doubles/node) + A_up read twice
-  // (24 doubles/cell) + ELL (11 doubles + 11 ints/face) + p-block (~17
-  // doubles/cell) + vectors (read x, write y: 2 * 8 B per dof).
-  const double bytes = 27.0 * 9 * 8 * c.nN + 2.0 * 24 * 8 * c.nT + 11.0 * 12 * c.nF + 17.0 * 8 * c.nT + 16.0 * c.n;
+  // (24 doubles/cell) + ELL values (11 doubles/face; the columns are
+  // computed) + p-block (~17 doubles/cell) + vectors (read x, write y: 2 * 8
+  // B per dof).
+  const double bytes = 27.0 * 9 * 8 * c.nN + 2.0 * 24 * 8 * c.nT + 11.0 * 8 * c.nF + 17.0 * 8 * c.nT + 16.0 * c.n;
   timing_end(c, 1, bytes);
 }
 

@@ -110,6 +110,98 @@ __host__ __device__ inline int p_slots(int R) { return (2 + 2 * R) / 3 + 1; }
 __host__ __device__ inline int q_lo(int a, int R) { return (a - 2 * R + 6) / 3 - 2; } // = ceil((a-2-2R)/3), a >= 0
 __host__ __device__ inline int q_slots(int R) { return (2 + 4 * R) / 3 + 1; }
 
+// q = n / d for every 32-bit n, from a magic multiplier fixed at set-up
+struct Div32 {
+  unsigned m = 1, d = 1;
+  int s1 = 0, s2 = 0;
+  static Div32 make(unsigned d) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;  // l = ceil(log2 d)
+    Div32 r;
+    r.d = d;
+    r.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    r.s1 = l < 1 ? l : 1;
+    r.s2 = l < 1 ? 0 : l - 1;
+    return r;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    const unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+// 32-bit face topology with invariant-divisor decoding.  Faces are numbered
+// by family: x-faces i + (nx+1)(j + ny k), then y-faces i + nx (j + (ny+1) k),
+// then z-faces i + nx (j + ny k); local face 2a (2a+1) of a cell is its face
+// on the - (+) side of axis a.
+struct FaceTopo32 {
+  int nx = 0, ny = 0, nz = 0;
+  unsigned nT = 0, nF = 0, nFx = 0, nFy = 0;
+  Div32 d_nx1, d_ny, d_nx, d_ny1;
+  static FaceTopo32 make(int nx, int ny, int nz, long long nT, long long nF, long long nFx, long long nFy) {
+    FaceTopo32 t;
+    t.nx = nx; t.ny = ny; t.nz = nz;
+    t.nT = (unsigned)nT; t.nF = (unsigned)nF; t.nFx = (unsigned)nFx; t.nFy = (unsigned)nFy;
+    t.d_nx1 = Div32::make((unsigned)nx + 1);
+    t.d_ny = Div32::make((unsigned)ny);
+    t.d_nx = Div32::make((unsigned)nx);
+    t.d_ny1 = Div32::make((unsigned)ny + 1);
+    return t;
+  }
+  __device__ __forceinline__ unsigned cell(int i, int j, int k) const {
+    return (unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)k);
+  }
+  // face lf (0..5) of cell (i, j, k)
+  __device__ __forceinline__ unsigned face(int i, int j, int k, int lf) const {
+    const int ax = lf >> 1, up = lf & 1;
+    if (ax == 0) return (unsigned)(i + up) + (unsigned)(nx + 1) * ((unsigned)j + (unsigned)ny * (unsigned)k);
+    if (ax == 1) return nFx + (unsigned)i + (unsigned)nx * ((unsigned)(j + up) + (unsigned)(ny + 1) * (unsigned)k);
+    return nFx + nFy + (unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)(k + up));
+  }
+  // axis of face f and the lattice index (i, j, k) of the cell on its + side
+  __device__ __forceinline__ int decode(unsigned f, int& i, int& j, int& k) const {
+    if (f < nFx) {
+      const unsigned r = d_nx1.div(f);
+      i = (int)(f - r * (unsigned)(nx + 1)); k = (int)d_ny.div(r); j = (int)(r - (unsigned)k * (unsigned)ny);
+      return 0;
+    }
+    if (f < nFx + nFy) {
+      const unsigned g = f - nFx, r = d_nx.div(g);
+      i = (int)(g - r * (unsigned)nx); k = (int)d_ny1.div(r); j = (int)(r - (unsigned)k * (unsigned)(ny + 1));
+      return 1;
+    }
+    const unsigned g = f - nFx - nFy, r = d_nx.div(g);
+    i = (int)(g - r * (unsigned)nx); k = (int)d_ny.div(r); j = (int)(r - (unsigned)k * (unsigned)ny);
+    return 2;
+  }
+  // The up to two cells of face f: slot 0 on the - side (f is its local face
+  // 2a+1), slot 1 on the + side (local face 2a); absent cells give ok = false.
+  __device__ __forceinline__ void cells(unsigned f, int c[2][3], bool ok[2], int lf[2]) const {
+    int i, j, k;
+    const int ax = decode(f, i, j, k);
+    c[0][0] = i - (ax == 0); c[0][1] = j - (ax == 1); c[0][2] = k - (ax == 2);
+    c[1][0] = i; c[1][1] = j; c[1][2] = k;
+    ok[0] = ax == 0 ? i > 0 : (ax == 1 ? j > 0 : k > 0);
+    ok[1] = ax == 0 ? i < nx : (ax == 1 ? j < ny : k < nz);
+    lf[0] = 2 * ax + 1;
+    lf[1] = 2 * ax;
+  }
+  // The 11 columns of face f's row of the face operators, in the slot order
+  // of the stored ELL: 0 = f; 1 + 5 s + q = the q-th local face other than
+  // f of cell s (in local-face order); f itself where cell s is absent.
+  __device__ __forceinline__ void ell_cols(unsigned f, unsigned col[11]) const {
+    int c[2][3], lf[2];
+    bool ok[2];
+    cells(f, c, ok, lf);
+    col[0] = f;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        col[1 + 5 * s + q] = ok[s] ? face(c[s][0], c[s][1], c[s][2], q + (q >= lf[s])) : f;
+  }
+};
+
 // ------------------------------------------------------------ multigrid level
 struct Level {
   bool faces = false;         // level 0 of the interface-pressure hierarchy
