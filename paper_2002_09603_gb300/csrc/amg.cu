@@ -308,27 +308,6 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
 
 // </hot:k_cheb_u0_sym>
 
-// scalar prolongation x += P x_c with the slot loop unrolled
-template <int R, typename T>
-__global__ void __launch_bounds__(256) k_prolong_s(Lat F, Lat Cc, const T* __restrict__ P, const T* __restrict__ xc,
-                                                   T* __restrict__ x) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= F.N) return;
-  int a, b, c;
-  F.ijk(p, a, b, c);
-  constexpr int ns = (2 + 2 * R) / 3 + 1;
-  const int lx = p_lo(a, R), ly = p_lo(b, R), lz = p_lo(c, R);
-  T acc = T(0);
-#pragma unroll
-  for (int s = 0; s < ns * ns * ns; ++s) {
-    const int I = lx + s % ns, J = ly + (s / ns) % ns, K = lz + s / (ns * ns);
-    const bool in = Cc.in(I, J, K);
-    const T pv = in ? P[(long long)s * F.N + p] : T(0);
-    acc += pv * xc[in ? Cc.id(I, J, K) : 0];
-  }
-  x[p] += acc;
-}
-
 // ------------------------------------------------------- coarse-level sweeps
 // Sweeps and residuals of the coarse lattice levels and of the interface-
 // pressure cell levels.  Their data is a few to a few tens of MB, so the cost
@@ -505,34 +484,147 @@ __global__ void __launch_bounds__(32 * W) k_cheb_w(Lat32 L, const T* __restrict_
   cheb_update<T, BS>(p, (unsigned)L.N, r, dinv, xin, xout, d, cd, cr);
 }
 
-// restriction b_c = P^T r with one warp per coarse point; the lanes split
-// the (3 + 2R)^3 support box and reduce in a fixed order
-template <int BS, typename T>
-__global__ void __launch_bounds__(256) k_restrict_w(Lat F, Lat Cc, int R, const T* __restrict__ P,
+// ---------------------------------------------------------------- transfers
+// Prolongation x += P x_c and restriction b_c = P^T r between lattice levels,
+// with the same 32-bit indexing and batched loads as the sweeps.  P is
+// stored [ns^3 slots][bs^2][fine points]; slot (sx, sy, sz) of fine point
+// (a, b, c) is coarse point (p_lo(a) + sx, p_lo(b) + sy, p_lo(c) + sz).  An
+// absent coarse point contributes 0 (a select, not a multiply).
+template <int BS, int R, int CH, typename T>
+__device__ __forceinline__ void prolong_sum(const Lat32& F, const Lat32& C, unsigned p, const T* __restrict__ P,
+                                            const T* __restrict__ xc, T acc[BS], int first, int step) {
+  constexpr int ns = (2 + 2 * R) / 3 + 1, NS = ns * ns * ns;
+  int a, b, c;
+  F.ijk(p, a, b, c);
+  const int lx = p_lo(a, R), ly = p_lo(b, R), lz = p_lo(c, R);
+  bool vx[ns], vy[ns], vz[ns];
+#pragma unroll
+  for (int t = 0; t < ns; ++t) {
+    vx[t] = (unsigned)(lx + t) < (unsigned)C.Lx;
+    vy[t] = (unsigned)(ly + t) < (unsigned)C.Ly;
+    vz[t] = (unsigned)(lz + t) < (unsigned)C.Lz;
+  }
+  const unsigned N = (unsigned)F.N;
+#pragma unroll
+  for (int s0 = 0; s0 < NS; s0 += CH) {
+    T pv[CH][BS * BS], xv[CH][BS];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int sl = s0 + q;
+      if (sl < NS && sl % step == first) {
+        const int sx = sl % ns, sy = (sl / ns) % ns, sz = sl / (ns * ns);
+        const bool in = vx[sx] && vy[sy] && vz[sz];
+        const unsigned J = in ? (unsigned)(lx + sx) + (unsigned)C.Lx * ((unsigned)(ly + sy) + (unsigned)C.Ly * (unsigned)(lz + sz)) : 0u;
+#pragma unroll
+        for (int e = 0; e < BS * BS; ++e) {
+          const T v = P[(unsigned)(sl * BS * BS + e) * N + p];
+          pv[q][e] = in ? v : T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < BS; ++t) {
+          const T v = xc[BS * J + t];
+          xv[q][t] = in ? v : T(0);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q)
+      if (s0 + q < NS && (s0 + q) % step == first)
+#pragma unroll
+        for (int r = 0; r < BS; ++r)
+#pragma unroll
+          for (int t = 0; t < BS; ++t) acc[r] += pv[q][r * BS + t] * xv[q][t];
+  }
+}
+
+template <int BS>
+constexpr int prolong_chunk() { return BS == 1 ? 9 : 4; }
+
+// one fine point per thread
+template <int BS, int R, typename T>
+__global__ void __launch_bounds__(256) k_prolong_f(Lat32 F, Lat32 C, const T* __restrict__ P,
+                                                   const T* __restrict__ xc, T* __restrict__ x) {
+  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (unsigned)F.N) return;
+  T acc[BS];
+#pragma unroll
+  for (int r = 0; r < BS; ++r) acc[r] = T(0);
+  prolong_sum<BS, R, prolong_chunk<BS>(), T>(F, C, p, P, xc, acc, 0, 1);
+#pragma unroll
+  for (int r = 0; r < BS; ++r) x[BS * p + r] += acc[r];
+}
+
+// small fine levels: the slots split over W warps for 32 consecutive fine
+// points, partial sums added in a fixed order through shared memory
+template <int BS, int R, int W, typename T>
+__global__ void __launch_bounds__(32 * W) k_prolong_w(Lat32 F, Lat32 C, const T* __restrict__ P,
+                                                      const T* __restrict__ xc, T* __restrict__ x) {
+  __shared__ T part[W][BS][32];
+  const unsigned p = blockIdx.x * 32 + threadIdx.x;
+  const bool valid = p < (unsigned)F.N;
+  T acc[BS];
+#pragma unroll
+  for (int r = 0; r < BS; ++r) acc[r] = T(0);
+  if (valid) prolong_sum<BS, R, 2, T>(F, C, p, P, xc, acc, threadIdx.y, W);
+#pragma unroll
+  for (int r = 0; r < BS; ++r) part[threadIdx.y][r][threadIdx.x] = acc[r];
+  __syncthreads();
+  if (threadIdx.y != 0 || !valid) return;
+#pragma unroll
+  for (int r = 0; r < BS; ++r) {
+    T sum = T(0);
+#pragma unroll
+    for (int u = 0; u < W; ++u) sum += part[u][r][threadIdx.x];
+    x[BS * p + r] += sum;
+  }
+}
+
+// restriction b_c = P^T r, one warp per coarse point: the lanes split the
+// (3 + 2R)^3 fine box around it, each lane issuing the loads of all its box
+// points before the sums, then a fixed-order xor reduction over the warp
+template <int BS, int R, typename T>
+__global__ void __launch_bounds__(256) k_restrict_f(Lat32 F, Lat32 C, const T* __restrict__ P,
                                                     const T* __restrict__ r, T* __restrict__ bc) {
-  const long long J = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  constexpr int ns = (2 + 2 * R) / 3 + 1, w = 3 + 2 * R, NB = w * w * w, PER = (NB + 31) / 32;
+  const unsigned J = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const bool valid = J < Cc.N;
-  int I = 0, Jj = 0, K = 0;
-  if (valid) Cc.ijk(J, I, Jj, K);
-  const int ns = p_slots(R);
-  const int w = 3 + 2 * R;
+  const bool valid = J < (unsigned)C.N;
   T acc[BS];
 #pragma unroll
   for (int q = 0; q < BS; ++q) acc[q] = T(0);
   if (valid) {
-    for (int e = lane; e < w * w * w; e += 32) {
-      const int a = 3 * I - R + e % w, b = 3 * Jj - R + (e / w) % w, c = 3 * K - R + e / (w * w);
-      if (!F.in(a, b, c)) continue;
+    int I, Jj, K;
+    C.ijk(J, I, Jj, K);
+    const unsigned N = (unsigned)F.N;
+    T pv[PER][BS * BS], rv[PER][BS];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = lane + 32 * k;
+      const int ex = e % w, ey = (e / w) % w, ez = e / (w * w);
+      const int a = 3 * I - R + ex, b = 3 * Jj - R + ey, c = 3 * K - R + ez;
+      const bool in = e < NB && (unsigned)a < (unsigned)F.Lx && (unsigned)b < (unsigned)F.Ly &&
+                      (unsigned)c < (unsigned)F.Lz;
       const int sx = I - p_lo(a, R), sy = Jj - p_lo(b, R), sz = K - p_lo(c, R);
-      if (sx < 0 || sx >= ns || sy < 0 || sy >= ns || sz < 0 || sz >= ns) continue;
-      const long long p = F.id(a, b, c);
-      const T* pv = P + (long long)(sx + ns * (sy + ns * sz)) * BS * BS * F.N + p;
+      const bool ok = in && (unsigned)sx < (unsigned)ns && (unsigned)sy < (unsigned)ns && (unsigned)sz < (unsigned)ns;
+      const unsigned fp = ok ? (unsigned)a + (unsigned)F.Lx * ((unsigned)b + (unsigned)F.Ly * (unsigned)c) : 0u;
+      const int sl = ok ? sx + ns * (sy + ns * sz) : 0;
+#pragma unroll
+      for (int t = 0; t < BS * BS; ++t) {
+        const T v = P[(unsigned)(sl * BS * BS + t) * N + fp];
+        pv[k][t] = ok ? v : T(0);
+      }
+#pragma unroll
+      for (int t = 0; t < BS; ++t) {
+        const T v = r[BS * fp + t];
+        rv[k][t] = ok ? v : T(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
 #pragma unroll
       for (int q = 0; q < BS; ++q)
 #pragma unroll
-        for (int t = 0; t < BS; ++t) acc[q] += pv[(long long)(t * BS + q) * F.N] * r[BS * p + t];
-    }
+        for (int t = 0; t < BS; ++t) acc[q] += pv[k][t * BS + q] * rv[k][t];
   }
 #pragma unroll
   for (int q = 0; q < BS; ++q) {
@@ -576,36 +668,6 @@ __global__ void __launch_bounds__(256) k_cheb_ell(FaceTopo32 t, const T* __restr
   const T dn = (cd != T(0)) ? cd * d[f] + cr * dinv[f] * r : cr * dinv[f] * r;
   d[f] = dn;
   xout[f] = (xin ? xin[f] : T(0)) + dn;
-}
-
-// prolongation x += P x_c
-template <int BS, typename T>
-__global__ void k_prolong(Lat F, Lat Cc, int R, const T* __restrict__ P, const T* __restrict__ xc,
-                          T* __restrict__ x) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= F.N) return;
-  int a, b, c;
-  F.ijk(p, a, b, c);
-  const int ns = p_slots(R);
-  const int lx = p_lo(a, R), ly = p_lo(b, R), lz = p_lo(c, R);
-  T acc[BS];
-#pragma unroll
-  for (int q = 0; q < BS; ++q) acc[q] = T(0);
-  for (int sz = 0; sz < ns; ++sz)
-    for (int sy = 0; sy < ns; ++sy)
-      for (int sx = 0; sx < ns; ++sx) {
-        const int I = lx + sx, J = ly + sy, K = lz + sz;
-        if (!Cc.in(I, J, K)) continue;
-        const long long Jc = Cc.id(I, J, K);
-        const int s = sx + ns * (sy + ns * sz);
-        const T* pv = P + (long long)s * BS * BS * F.N + p;
-#pragma unroll
-        for (int q = 0; q < BS; ++q)
-#pragma unroll
-          for (int t = 0; t < BS; ++t) acc[q] += pv[(long long)(q * BS + t) * F.N] * xc[BS * Jc + t];
-      }
-#pragma unroll
-  for (int q = 0; q < BS; ++q) x[BS * p + q] += acc[q];
 }
 
 // faces -> cells Galerkin product of the interface-pressure hierarchy (set-up)
@@ -945,6 +1007,12 @@ void dispatch_kind(int kind, F&& f) {
 template <class F>
 void dispatch_bs(int bs, F&& f) {
   if (bs == 3) f(std::integral_constant<int, 3>{});
+  else f(std::integral_constant<int, 1>{});
+}
+
+template <class F>
+void dispatch_r(int R, F&& f) {
+  if (R == 2) f(std::integral_constant<int, 2>{});
   else f(std::integral_constant<int, 1>{});
 }
 
@@ -1508,9 +1576,11 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   if (L.faces) {
     k_restrict_faces<T><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb);
   } else {
-    const Lat F = lat_of(L.A), Cc = lat_of(C.A);
+    const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
     dispatch_bs(L.bs, [&](auto BS) {
-      k_restrict_w<BS.value, T><<<grid_for(Cc.N * 32, 256), 256, 0, c.stream>>>(F, Cc, L.R, v.P, v.r, cb);
+      dispatch_r(L.R, [&](auto RR) {
+        k_restrict_f<BS.value, RR.value, T><<<grid_for(C.A.N * 32, 256), 256, 0, c.stream>>>(F, Cc, v.P, v.r, cb);
+      });
     });
   }
   MHFP_LAUNCH_CHECK();
@@ -1518,14 +1588,16 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   if (L.faces) {
     k_prolong_faces<T><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, x);
   } else {
-    const Lat F = lat_of(L.A), Cc = lat_of(C.A);
-    if (L.bs == 1 && L.R == 2) {
-      k_prolong_s<2, T><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, v.P, cx, x);
-    } else {
-      dispatch_bs(L.bs, [&](auto BS) {
-        k_prolong<BS.value, T><<<grid_for(F.N, 256), 256, 0, c.stream>>>(F, Cc, L.R, v.P, cx, x);
+    // one fine point per thread on large levels, slots split over 8 warps on small ones
+    const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
+    dispatch_bs(L.bs, [&](auto BS) {
+      dispatch_r(L.R, [&](auto RR) {
+        if (L.A.N >= 65536)
+          k_prolong_f<BS.value, RR.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(F, Cc, v.P, cx, x);
+        else
+          k_prolong_w<BS.value, RR.value, 8, T><<<grid_for(L.A.N, 32), dim3(32, 8), 0, c.stream>>>(F, Cc, v.P, cx, x);
       });
-    }
+    });
   }
   MHFP_LAUNCH_CHECK();
   smooth<T>(c, H, l, b, x, false, fine_u);
