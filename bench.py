@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the fastest measured for the workload, 12 at 64^3, "
                          "20 at 128^3)")
+    ap.add_argument("--coarse-max", type=int, default=512,
+                    help="coarsen while a multigrid level has more lattice points (512: the 64^3 workload's "
+                         "hierarchies end at 8^3 points, inverted densely on the GPU)")
     ap.add_argument("--reorth", type=int, choices=[0, 1], default=0,
                     help="Gram-Schmidt: 0 one classical pass (PETSc's GMRES default; same iterations and "
                          "residuals on the workloads), 1 DGKS reorthogonalisation when needed")
@@ -333,12 +336,13 @@ def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local
     return dict(ms=ms, iters=iters, launches=launches, clocks=clocks, kt=kt)
 
 
-def _solver(prob, precision, torch, restart=50, reorth=1):
+def _solver(prob, precision, torch, restart=50, reorth=1, coarse_max=125):
     from paper_2002_09603_gb300 import Solver, default_options
     opt = default_options()
     opt.precision = precision
     opt.restart = restart
     opt.reorth = reorth
+    opt.coarse_max = coarse_max
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -376,7 +380,7 @@ def run_ours(args):
     # mixed form (FP32 V-cycles and Schur steps inside FP64 FGMRES)
     r64, setup64 = None, None
     if args.precision in ("both", "fp64"):
-        s64, setup64 = _solver(prob, 0, torch, args.restart, args.reorth)
+        s64, setup64 = _solver(prob, 0, torch, args.restart, args.reorth, args.coarse_max)
         r64 = _timed_steps(s64, args, world, dist, torch, launch_count, args.precision == "fp64", local)
         r64["kt"] = _timed_steps(s64, args, world, dist, torch, launch_count, False, local, True)["kt"]
         if args.precision == "fp64":
@@ -385,7 +389,7 @@ def run_ours(args):
             s64.close()
             del s64
     if args.precision in ("both", "mixed"):
-        s, setup_ms = _solver(prob, 1, torch, args.restart, args.reorth)
+        s, setup_ms = _solver(prob, 1, torch, args.restart, args.reorth, args.coarse_max)
         r32 = _timed_steps(s, args, world, dist, torch, launch_count, True, local)
         # second pass over the same steps with the kernel events on (roofline)
         rk = _timed_steps(s, args, world, dist, torch, launch_count, False, local, True)
@@ -459,7 +463,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
                        "n_pi": nPi, "tol": TOL, "restart": args.restart, "reorth": args.reorth,
-                       "iterations_per_step": r32["iters"],
+                       "coarse_max": args.coarse_max, "iterations_per_step": r32["iters"],
                        "setup_ms": setup_ms, "precision": {"both": "FP32 V-cycles inside FP64 FGMRES",
                                                            "mixed": "FP32 V-cycles inside FP64 FGMRES",
                                                            "fp64": "FP64 throughout"}[args.precision],

@@ -25,7 +25,8 @@ restated independently of the CUDA code:
   D^-1 A from v0[d] = 1 + ((7919 d) mod 97) / 97;
 * Galerkin coarse operators P^T A P; a coarse dof with no free fine dof gets
   a unit diagonal;
-* coarsen while a level has more than 125 lattice points; exact dense solve
+* coarsen while a level has more than coarse_max lattice points (default
+  125); exact dense solve
   on the last level;
 * V(1,1) cycle, smoother = Chebyshev of degree 2 preconditioned by D on
   [lmax/10, lmax].
@@ -163,12 +164,12 @@ def _dense_coarse(lev: Level):
     lev.dense_inv = np.linalg.inv(lev.A.toarray())
 
 
-def build_u_hierarchy(B: Blocks):
+def build_u_hierarchy(B: Blocks, coarse_max=COARSE_MAX):
     m = B.mesh
     dims = (m.nx + 1, m.ny + 1, m.nz + 1)
     lev = Level(B.Auu.tocsr(), 3, dims, active=~B.u_fixed)
     levels = [lev]
-    while lev.dims[0] * lev.dims[1] * lev.dims[2] > COARSE_MAX:
+    while lev.dims[0] * lev.dims[1] * lev.dims[2] > coarse_max:
         _finish_level(lev)
         P, cdims, act = _sa_prolongator(lev)
         lev.P = P
@@ -195,11 +196,11 @@ def face_to_cell_prolongator(B: Blocks) -> sp.csr_matrix:
     return P
 
 
-def build_pi_hierarchy(B: Blocks, C: sp.csr_matrix):
+def build_pi_hierarchy(B: Blocks, C: sp.csr_matrix, coarse_max=COARSE_MAX):
     m = B.mesh
     lev = Level(C.tocsr(), 1, None, active=~B.pi_fixed)
     levels = [lev]
-    if m.n_faces <= COARSE_MAX:
+    if m.n_faces <= coarse_max:
         _dense_coarse(lev)
         return levels
     _finish_level(lev)
@@ -208,7 +209,7 @@ def build_pi_hierarchy(B: Blocks, C: sp.csr_matrix):
     act = np.asarray(abs(P0).sum(axis=0)).ravel() > 0
     lev = Level(_galerkin(P0, lev.A, act), 1, (m.nx, m.ny, m.nz), active=act)
     levels.append(lev)
-    while lev.dims[0] * lev.dims[1] * lev.dims[2] > COARSE_MAX:
+    while lev.dims[0] * lev.dims[1] * lev.dims[2] > coarse_max:
         _finish_level(lev)
         P, cdims, act = _sa_prolongator(lev)
         lev.P = P
@@ -299,7 +300,7 @@ class Preconditioner:
                         [None, None, self.C]], format="csr")
 
 
-def build(B: Blocks, kind="amg") -> Preconditioner:
+def build(B: Blocks, kind="amg", coarse_max=COARSE_MAX) -> Preconditioner:
     Bt = btilde(B)
     C = ctilde(B, Bt)
     pc = Preconditioner(B, Bt, C, kind)
@@ -307,6 +308,6 @@ def build(B: Blocks, kind="amg") -> Preconditioner:
         pc._luu = spla.splu(B.Auu.tocsc())
         pc._lpi = spla.splu(C.tocsc())
     else:
-        pc.u_levels = build_u_hierarchy(B)
-        pc.pi_levels = build_pi_hierarchy(B, C)
+        pc.u_levels = build_u_hierarchy(B, coarse_max)
+        pc.pi_levels = build_pi_hierarchy(B, C, coarse_max)
     return pc

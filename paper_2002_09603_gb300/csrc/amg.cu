@@ -1113,32 +1113,90 @@ double spectral_radius(Ctx& c, Level& L) {
 }
 
 // Gauss-Jordan inverse with partial pivoting (host, FP64), row-major
-void invert_dense(std::vector<double>& A, int n) {
-  std::vector<double> I(n * (size_t)n, 0.0);
-  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
-  for (int col = 0; col < n; ++col) {
-    int piv = col;
-    for (int r = col + 1; r < n; ++r)
-      if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
-    if (A[(size_t)piv * n + col] == 0.0) throw Error{MHFP_ERR_ARG, "singular coarsest multigrid level"};
-    if (piv != col)
-      for (int k = 0; k < n; ++k) {
-        std::swap(A[(size_t)piv * n + k], A[(size_t)col * n + k]);
-        std::swap(I[(size_t)piv * n + k], I[(size_t)col * n + k]);
-      }
-    const double inv = 1.0 / A[(size_t)col * n + col];
-    for (int k = 0; k < n; ++k) { A[(size_t)col * n + k] *= inv; I[(size_t)col * n + k] *= inv; }
-    for (int r = 0; r < n; ++r) {
-      if (r == col) continue;
-      const double f = A[(size_t)r * n + col];
-      if (f == 0.0) continue;
-      for (int k = 0; k < n; ++k) {
-        A[(size_t)r * n + k] -= f * A[(size_t)col * n + k];
-        I[(size_t)r * n + k] -= f * I[(size_t)col * n + k];
-      }
-    }
+// Dense inverse of the coarsest level by Gauss-Jordan elimination on the GPU
+// (FP64, augmented [A | I] of n x 2n, row-major).  The coarse operators are
+// Galerkin products of SPD operators (Dirichlet rows carry a unit diagonal),
+// so elimination needs no pivoting; a pivot that is not positive and finite
+// sets *err and the host reports a singular level.  Column col takes two
+// kernels: the first copies the scaled pivot row and the multipliers, the
+// second updates every row from those copies (no read/write hazard).
+__global__ void k_gj_pivot(int n, int col, const double* __restrict__ M, double* __restrict__ prow,
+                           double* __restrict__ fcol, int* __restrict__ err) {
+  const int w = 2 * n;
+  const double piv = M[(long long)col * w + col];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0 && !(piv > 0.0 && piv < 1e300)) *err = 1;
+  if (t < w) prow[t] = t < col ? 0.0 : M[(long long)col * w + t] / piv;
+  if (t < n) fcol[t] = M[(long long)t * w + col];
+}
+
+__global__ void k_gj_update(int n, int col, double* __restrict__ M, const double* __restrict__ prow,
+                            const double* __restrict__ fcol) {
+  const int w = 2 * n;
+  const int k = col + blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (k >= w) return;
+  double* m = M + (long long)r * w + k;
+  *m = (r == col) ? prow[k] : *m - fcol[r] * prow[k];
+}
+
+__global__ void k_gj_extract(int n, const double* __restrict__ M, double* __restrict__ inv) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  const long long r = t / n, cidx = t % n;
+  inv[t] = M[r * 2 * n + n + cidx];
+}
+
+__global__ void k_gj_init(int n, const double* __restrict__ A, double* __restrict__ M) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * 2 * n) return;
+  const long long r = t / (2 * n), cidx = t % (2 * n);
+  M[t] = cidx < n ? A[r * n + cidx] : (cidx - n == r ? 1.0 : 0.0);
+}
+
+// A (host, n x n row-major) -> its inverse in device memory `inv`
+void invert_dense_gpu(Ctx& c, const std::vector<double>& A, int n, double* inv) {
+  double *dA = nullptr, *M = nullptr, *prow = nullptr, *fcol = nullptr;
+  int* err = nullptr;
+  auto release = [&] {
+    cudaFree(dA);
+    cudaFree(M);
+    cudaFree(prow);
+    cudaFree(fcol);
+    cudaFree(err);
+  };
+  cudaError_t e = cudaMalloc(&dA, (size_t)n * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&M, (size_t)n * 2 * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&prow, (size_t)2 * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&fcol, (size_t)n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e != cudaSuccess) {
+    release();
+    throw Error{MHFP_ERR_OOM, "device allocation failed (dense coarsest level)"};
   }
-  A.swap(I);
+  try {
+    MHFP_CUDA(cudaMemcpyAsync(dA, A.data(), (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    MHFP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), c.stream));
+    k_gj_init<<<grid_for((long long)n * 2 * n, 256), 256, 0, c.stream>>>(n, dA, M);
+    MHFP_LAUNCH_CHECK();
+    for (int col = 0; col < n; ++col) {
+      k_gj_pivot<<<grid_for(2 * n, 256), 256, 0, c.stream>>>(n, col, M, prow, fcol, err);
+      MHFP_LAUNCH_CHECK();
+      k_gj_update<<<dim3(grid_for(2 * n - col, 256), n), 256, 0, c.stream>>>(n, col, M, prow, fcol);
+      MHFP_LAUNCH_CHECK();
+    }
+    k_gj_extract<<<grid_for((long long)n * n, 256), 256, 0, c.stream>>>(n, M, inv);
+    MHFP_LAUNCH_CHECK();
+    int h_err = 0;
+    MHFP_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    if (h_err) throw Error{MHFP_ERR_ARG, "singular or indefinite coarsest multigrid level"};
+  } catch (...) {
+    cudaStreamSynchronize(c.stream);
+    release();
+    throw;
+  }
+  release();
 }
 
 void make_dense_coarse(Ctx& c, Level& L) {
@@ -1172,10 +1230,8 @@ void make_dense_coarse(Ctx& c, Level& L) {
       }
     }
   }
-  invert_dense(A, n);
   L.dense_inv = dalloc_n<double>(c, (size_t)n * n);
-  MHFP_CUDA(cudaMemcpyAsync(L.dense_inv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  invert_dense_gpu(c, A, n, L.dense_inv);
 }
 
 void finish_level(Ctx& c, Level& L) {

@@ -1,6 +1,6 @@
 """Parity on the benchmark workload at its full size (64^3, 1,884,739
 unknowns), in the launch configuration bench.py times (FP32 V-cycles inside
-FP64 FGMRES(12), graphs, autotuned schedules).
+FP64 FGMRES(12), coarsening limit 512, graphs, autotuned schedules).
 
 The oracle assembles the whole 64^3 system (about 1.5 min on the host) and
 checks, element by element, A_H x for a seeded x, then the GPU solution's
@@ -35,6 +35,8 @@ def full():
     opt = default_options()
     opt.precision = 1
     opt.restart = 12
+    opt.coarse_max = 512
+    opt.reorth = 0
     s = Solver(prob)
     s.assemble_condense()
     s.setup_precond(opt)
@@ -84,7 +86,9 @@ def test_layered_jittered_128_cubed():
     for precision in (1, 0):
         opt = default_options()
         opt.precision = precision
-        opt.restart = 12
+        opt.restart = 20
+        opt.coarse_max = 512
+        opt.reorth = 0
         s = Solver(prob)
         s.assemble_condense()
         s.setup_precond(opt)
