@@ -33,6 +33,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // per thread, many rows in flight, independent FMA chains.
 constexpr int GS_BLOCKS = 1216;   // 8 x 152 SMs
 constexpr int GS_COLS = 4;        // columns per block in the dot kernel
+constexpr int GS_DOT_BLOCKS = 608;  // 4 x 152 SMs: about 12 rows per thread, so the
+                                    // block reductions' FP64 adds stay small
 
 // partials[c][block] = sum over this block's rows of V[:,c] . w for the
 // GS_COLS columns of blockIdx.y; block column 0 also sums w . w into slot
@@ -120,9 +122,22 @@ __global__ void __launch_bounds__(RED_THREADS, 8) k_gs_dots(long long n, const d
 __global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partials, double* __restrict__ out,
                                        const int* __restrict__ skip);
 
-__global__ void k_move(const double* __restrict__ src, double* __restrict__ dst) { dst[0] = src[0]; }
 
 // out[col] (+)= sum_b partials[col * nb + b] in a fixed order
+// the ncols dot products into hout[0..ncols) and, when nrm2 is given, the
+// norm partials (row ncols) into *nrm2; same fixed-order sums as below
+__global__ void k_reduce_dots(int nb, const double* __restrict__ partials, double* __restrict__ hout, int ncols,
+                              double* __restrict__ nrm2) {
+  __shared__ double sh[RED_THREADS / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[(long long)blockIdx.x * nb + b];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    if ((int)blockIdx.x < ncols) hout[blockIdx.x] = s;
+    else *nrm2 = s;
+  }
+}
+
 __global__ void k_reduce_partials(int nb, const double* __restrict__ partials, double* __restrict__ out, int accumulate) {
   __shared__ double sh[RED_THREADS / 32];
   double v = 0.0;
@@ -220,12 +235,11 @@ __global__ void k_ewise(long long n, const double* __restrict__ x, const double*
 // 1/sqrt(2) of its value before the projection.  nrm[0] = ||w||^2 before,
 // nrm[1] = ||w||^2 after.  flag = 1 means "skip the second projection";
 // when it is skipped h2 is zeroed and the norm after the first pass is
-// carried into nrm[2], which the second pass overwrites otherwise.  With
-// never != 0 the second projection is always skipped (one classical pass).
+// carried into nrm[2], which the second pass overwrites otherwise.
 __global__ void k_dgks(int ncols, const double* __restrict__ nrm, int* __restrict__ flag, double* __restrict__ h2,
-                       double* __restrict__ nrm_final, int never) {
+                       double* __restrict__ nrm_final) {
   const int i = threadIdx.x;
-  const bool skip = never || nrm[1] > 0.5 * nrm[0];
+  const bool skip = nrm[1] > 0.5 * nrm[0];
   if (i == 0) {
     *flag = skip ? 1 : 0;
     if (skip) nrm_final[0] = nrm[1];
@@ -234,7 +248,8 @@ __global__ void k_dgks(int ncols, const double* __restrict__ nrm, int* __restric
     for (int c = i; c < ncols; c += blockDim.x) h2[c] = 0.0;
 }
 
-// One Arnoldi step's Hessenberg column: h = h1 + h2 (j+1 entries), the new
+// One Arnoldi step's Hessenberg column: h = h1 + h2 (j+1 entries; h2 null
+// after a single Gram-Schmidt pass), the new
 // subdiagonal ||w|| = sqrt(nrm2); apply the previous rotations, make the new
 // one, update g.  scal[0] = |g_{j+1}|, scal[1] = 1/||w|| (0 on breakdown).
 __global__ void k_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
@@ -242,7 +257,7 @@ __global__ void k_givens(int j, int m, const double* __restrict__ h1, const doub
                          double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = H + (long long)j * (m + 1);
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  for (int i = 0; i <= j; ++i) col[i] = h2 ? h1[i] + h2[i] : h1[i];
   const double hn = sqrt(nrm2[0]);
   col[j + 1] = hn;
   for (int i = 0; i < j; ++i) {
@@ -284,20 +299,15 @@ __global__ void k_set_g(int m, double beta, double* __restrict__ g) {
 // with skip non-null nothing happens when *skip != 0
 void gs_dots(Ctx& c, int ncols, double* hout, double* nrm2, const int* skip) {
   const int wn = nrm2 ? 1 : 0;
-  dim3 grid(GS_BLOCKS, (ncols + GS_COLS - 1) / GS_COLS);
+  dim3 grid(GS_DOT_BLOCKS, (ncols + GS_COLS - 1) / GS_COLS);
   k_gs_dots<<<grid, RED_THREADS, 0, c.stream>>>(c.n, c.V, ncols, c.w, c.partials, skip, wn);
   MHFP_LAUNCH_CHECK();
   if (skip) {
-    k_reduce_partials_flag<<<ncols, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials, hout, skip);
+    k_reduce_partials_flag<<<ncols, RED_THREADS, 0, c.stream>>>(GS_DOT_BLOCKS, c.partials, hout, skip);
   } else {
-    k_reduce_partials<<<ncols + wn, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials, hout, 0);
+    k_reduce_dots<<<ncols + wn, RED_THREADS, 0, c.stream>>>(GS_DOT_BLOCKS, c.partials, hout, ncols, nrm2);
   }
   MHFP_LAUNCH_CHECK();
-  if (nrm2) {
-    // the norm sits after the ncols dot products; move it to its slot
-    k_move<<<1, 1, 0, c.stream>>>(hout + ncols, nrm2);
-    MHFP_LAUNCH_CHECK();
-  }
 }
 
 // norm^2 into dst (device)
@@ -433,11 +443,13 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
   k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
                                                      nullptr);
   MHFP_LAUNCH_CHECK();
-  k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS, c.scal + 5, 0);
-  MHFP_LAUNCH_CHECK();
-  k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2, reorth ? 0 : 1);
+  // one pass: the new norm goes straight to the slot the Givens step reads
+  k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
+                                                     reorth ? c.scal + 5 : c.scal + 2, 0);
   MHFP_LAUNCH_CHECK();
   if (reorth) {
+    k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2);
+    MHFP_LAUNCH_CHECK();
     gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
     k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
                                                        c.partials + (size_t)m * GS_BLOCKS, c.dflag);
@@ -447,7 +459,8 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
     MHFP_LAUNCH_CHECK();
   }
   timing_end(c, 2, 8.0 * n * (2.0 * (j + 1) + 4.0));
-  k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, c.h + (m + 1), c.scal + 2, c.H, c.cs, c.sn, c.g, c.scal);
+  k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, reorth ? c.h + (m + 1) : nullptr, c.scal + 2, c.H, c.cs, c.sn, c.g,
+                                   c.scal);
   MHFP_LAUNCH_CHECK();
   k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
   MHFP_LAUNCH_CHECK();
