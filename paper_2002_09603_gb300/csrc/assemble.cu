@@ -663,38 +663,57 @@ __global__ void __launch_bounds__(256) k_apply_pi(FaceTopo32 t, long long nU, co
 // preconditioner pieces: z_p = B~^-1 (v_p - dt A_ppi z_pi), t_u = v_u - A_up z_p
 // (FP64, or FP32 in the mixed-precision preconditioner)
 template <typename R>
-__global__ void k_prec_p(Dims d, const R* __restrict__ ApPi, const R* __restrict__ btilde, R dt,
-                         const R* __restrict__ vp, const R* __restrict__ zpi, R* __restrict__ zp) {
-  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= d.nT) return;
-  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+__global__ void __launch_bounds__(256) k_prec_p(FaceTopo32 t, const R* __restrict__ ApPi,
+                                                const R* __restrict__ btilde, R dt, const R* __restrict__ vp,
+                                                const R* __restrict__ zpi, R* __restrict__ zp) {
+  const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= t.nT) return;
+  const unsigned q = t.d_nx.div(T);
+  const int i = (int)(T - q * (unsigned)t.nx), k = (int)t.d_ny.div(q), j = (int)(q - (unsigned)k * (unsigned)t.ny);
+  R a[6], z[6];
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) {
+    a[lf] = ApPi[lf * t.nT + T];
+    z[lf] = zpi[t.face(i, j, k, lf)];
+  }
   R c = R(0);
-  for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * zpi[cell_face(d, i, j, k, lf)];
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) c += a[lf] * z[lf];
   zp[T] = (vp[T] - dt * c) / btilde[T];
 }
 
+// t_u = v_u - A_up z_p: each node gathers its (up to) eight cells; 32-bit
+// node decoding, every cell's loads issued before the sums
 template <typename R>
-__global__ void k_prec_u(Dims d, const R* __restrict__ Aup, const R* __restrict__ vu,
-                         const R* __restrict__ zp, R* __restrict__ tu) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= d.nN) return;
-  const int ni = (int)(n % (d.nx + 1)), nj = (int)((n / (d.nx + 1)) % (d.ny + 1)),
-            nk = (int)(n / ((long long)(d.nx + 1) * (d.ny + 1)));
-  R y0 = R(0), y1 = R(0), y2 = R(0);
-  for (int cz = nk - 1; cz <= nk; ++cz) {
-    if (cz < 0 || cz >= d.nz) continue;
-    for (int cy = nj - 1; cy <= nj; ++cy) {
-      if (cy < 0 || cy >= d.ny) continue;
-      for (int cx = ni - 1; cx <= ni; ++cx) {
-        if (cx < 0 || cx >= d.nx) continue;
-        const long long T = cell_id(d, cx, cy, cz);
-        const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);
-        const R p = zp[T];
-        y0 += Aup[(long long)(3 * a) * d.nT + T] * p;
-        y1 += Aup[(long long)(3 * a + 1) * d.nT + T] * p;
-        y2 += Aup[(long long)(3 * a + 2) * d.nT + T] * p;
-      }
+__global__ void __launch_bounds__(256) k_prec_u(FaceTopo32 t, const R* __restrict__ Aup, const R* __restrict__ vu,
+                                                const R* __restrict__ zp, R* __restrict__ tu) {
+  const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nN = (unsigned)(t.nx + 1) * (unsigned)(t.ny + 1) * (unsigned)(t.nz + 1);
+  if (n >= nN) return;
+  const unsigned r = t.d_nx1.div(n);
+  const int ni = (int)(n - r * (unsigned)(t.nx + 1)), nk = (int)t.d_ny1.div(r),
+            nj = (int)(r - (unsigned)nk * (unsigned)(t.ny + 1));
+  R av[8][3], pv[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {  // c = dx + 2 dy + 4 dz: cell (ni - 1 + dx, nj - 1 + dy, nk - 1 + dz)
+    const int cx = ni - 1 + (c & 1), cy = nj - 1 + ((c >> 1) & 1), cz = nk - 1 + (c >> 2);
+    const bool in = cx >= 0 && cx < t.nx && cy >= 0 && cy < t.ny && cz >= 0 && cz < t.nz;
+    const unsigned T = in ? t.cell(cx, cy, cz) : 0u;
+    const int a = (ni - cx) + 2 * (nj - cy) + 4 * (nk - cz);  // local node of n in cell T
+    const R p = zp[T];
+    pv[c] = in ? p : R(0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const R v = Aup[(unsigned)(3 * a + q) * t.nT + T];
+      av[c][q] = in ? v : R(0);
     }
+  }
+  R y0 = R(0), y1 = R(0), y2 = R(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    y0 += av[c][0] * pv[c];
+    y1 += av[c][1] * pv[c];
+    y2 += av[c][2] * pv[c];
   }
   tu[3 * n] = vu[3 * n] - y0;
   tu[3 * n + 1] = vu[3 * n + 1] - y1;
@@ -844,6 +863,9 @@ Dims dims_of(const Ctx& c) {
   return Dims{c.nx, c.ny, c.nz, c.nN, c.nT, c.nF, c.nFx, c.nFy};
 }
 
+// 32-bit topology (invariant-divisor decoding of nodes, cells and faces)
+FaceTopo32 topo32(const Ctx& c) { return FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy); }
+
 }  // namespace
 
 void assemble_all(Ctx& c) {
@@ -937,25 +959,26 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
 
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp) {
   const Dims d = dims_of(c);
-  k_prec_p<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.ApPi, c.btilde, c.dt, vp, zpi, zp);
+  k_prec_p<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.ApPi, c.btilde, c.dt, vp, zpi, zp);
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu) {
   const Dims d = dims_of(c);
-  k_prec_u<double><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aup, vu, zp, tu);
+  k_prec_u<double><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, vu, zp, tu);
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp) {
   const Dims d = dims_of(c);
-  k_prec_p<float><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.ApPif, c.btildef, (float)c.dt, vp, zpi, zp);
+  k_prec_p<float><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.ApPif, c.btildef, (float)c.dt, vp, zpi,
+                                                             zp);
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_u_rhs(Ctx& c, const float* vu, const float* zp, float* tu) {
   const Dims d = dims_of(c);
-  k_prec_u<float><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.Aupf, vu, zp, tu);
+  k_prec_u<float><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(topo32(c), c.Aupf, vu, zp, tu);
   MHFP_LAUNCH_CHECK();
 }
 
