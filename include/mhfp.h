@@ -76,7 +76,11 @@ typedef struct {
   int maxit;            /* maximum total FGMRES iterations (default 1000)      */
   int cheb_degree;      /* Chebyshev smoother degree (default 2)               */
   double cheb_ratio;    /* lmax / lmin of the smoother interval (default 10)   */
-  int coarse_max;       /* coarsen while a level has more points (default 125) */
+  int coarse_max;       /* coarsen while a level has more lattice points       */
+                        /* (default 125, at most 4096); the last level is      */
+                        /* solved with a dense FP64 inverse built on the GPU   */
+                        /* by Gauss-Jordan elimination (2 n^3 FMA for its n    */
+                        /* unknowns; MHFP_ERR_ARG if a pivot is not positive)  */
   int power_iters;      /* power iterations for rho(D^-1 A) (default 15)       */
   int precision;        /* 0: FP64 preconditioner (default); 1: FP32 V-cycles  */
                         /* and Schur steps inside the FP64 FGMRES (residuals,  */
