@@ -741,17 +741,26 @@ __global__ void __launch_bounds__(256) k_prolong_faces(FaceTopo32 t, const T* __
   x[f] += pw[f] * s;
 }
 
-// dense coarsest solve y = Ainv b (warp per row); the inverse and the sums
-// stay FP64 whatever the precision of the cycle's vectors
+// dense coarsest solve y = Ainv b, one block of 256 threads per row (each
+// thread a strided slice of the row, then a fixed-order block sum); the
+// inverse and the sums stay FP64 whatever the precision of the cycle's vectors
 template <typename T>
-__global__ void k_dense_mv(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ y) {
-  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
+__global__ void __launch_bounds__(256) k_dense_mv(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
+                                                  T* __restrict__ y) {
+  __shared__ double sh[8];
+  const int row = blockIdx.x;
+  const double* a = Ainv + (long long)row * n;
   double s = 0.0;
-  for (int c = lane; c < n; c += 32) s += Ainv[(long long)row * n + c] * (double)b[c];
+#pragma unroll 4
+  for (int c = threadIdx.x; c < n; c += 256) s += a[c] * (double)b[c];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = (T)s;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    y[row] = (T)t;
+  }
 }
 
 __global__ void k_cast_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
@@ -1609,7 +1618,7 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   const LV<T> v = view(c, L, T());
   if (L.dense_inv) {
     const int n = (int)L.n;
-    k_dense_mv<T><<<grid_for(n, 8), 256, 0, c.stream>>>(n, L.dense_inv, b, x);
+    k_dense_mv<T><<<n, 256, 0, c.stream>>>(n, L.dense_inv, b, x);
     MHFP_LAUNCH_CHECK();
     return;
   }
