@@ -124,8 +124,12 @@ struct Div32 {
     r.s2 = l < 1 ? 0 : l - 1;
     return r;
   }
-  __device__ __forceinline__ unsigned div(unsigned n) const {
+  __host__ __device__ __forceinline__ unsigned div(unsigned n) const {
+#ifdef __CUDA_ARCH__
     const unsigned t = __umulhi(m, n);
+#else
+    const unsigned t = (unsigned)(((unsigned long long)m * n) >> 32);
+#endif
     return (t + ((n - t) >> s1)) >> s2;
   }
 };
@@ -148,18 +152,18 @@ struct FaceTopo32 {
     t.d_ny1 = Div32::make((unsigned)ny + 1);
     return t;
   }
-  __device__ __forceinline__ unsigned cell(int i, int j, int k) const {
+  __host__ __device__ __forceinline__ unsigned cell(int i, int j, int k) const {
     return (unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)k);
   }
   // face lf (0..5) of cell (i, j, k)
-  __device__ __forceinline__ unsigned face(int i, int j, int k, int lf) const {
+  __host__ __device__ __forceinline__ unsigned face(int i, int j, int k, int lf) const {
     const int ax = lf >> 1, up = lf & 1;
     if (ax == 0) return (unsigned)(i + up) + (unsigned)(nx + 1) * ((unsigned)j + (unsigned)ny * (unsigned)k);
     if (ax == 1) return nFx + (unsigned)i + (unsigned)nx * ((unsigned)(j + up) + (unsigned)(ny + 1) * (unsigned)k);
     return nFx + nFy + (unsigned)i + (unsigned)nx * ((unsigned)j + (unsigned)ny * (unsigned)(k + up));
   }
   // axis of face f and the lattice index (i, j, k) of the cell on its + side
-  __device__ __forceinline__ int decode(unsigned f, int& i, int& j, int& k) const {
+  __host__ __device__ __forceinline__ int decode(unsigned f, int& i, int& j, int& k) const {
     if (f < nFx) {
       const unsigned r = d_nx1.div(f);
       i = (int)(f - r * (unsigned)(nx + 1)); k = (int)d_ny.div(r); j = (int)(r - (unsigned)k * (unsigned)ny);
@@ -176,7 +180,7 @@ struct FaceTopo32 {
   }
   // The up to two cells of face f: slot 0 on the - side (f is its local face
   // 2a+1), slot 1 on the + side (local face 2a); absent cells give ok = false.
-  __device__ __forceinline__ void cells(unsigned f, int c[2][3], bool ok[2], int lf[2]) const {
+  __host__ __device__ __forceinline__ void cells(unsigned f, int c[2][3], bool ok[2], int lf[2]) const {
     int i, j, k;
     const int ax = decode(f, i, j, k);
     c[0][0] = i - (ax == 0); c[0][1] = j - (ax == 1); c[0][2] = k - (ax == 2);
@@ -189,7 +193,7 @@ struct FaceTopo32 {
   // The 11 columns of face f's row of the face operators, in the slot order
   // of the stored ELL: 0 = f; 1 + 5 s + q = the q-th local face other than
   // f of cell s (in local-face order); f itself where cell s is absent.
-  __device__ __forceinline__ void ell_cols(unsigned f, unsigned col[11]) const {
+  __host__ __device__ __forceinline__ void ell_cols(unsigned f, unsigned col[11]) const {
     int c[2][3], lf[2];
     bool ok[2];
     cells(f, c, ok, lf);
