@@ -471,7 +471,7 @@ namespace {
 
 // Queue Arnoldi step j (no synchronisation).  With graphs enabled the step
 // is captured once per (j, transpose) on a private stream and replayed into
-// the handle's stream afterwards: one launch instead of ~90.
+// the handle's stream afterwards: one launch instead of about 50.
 IterGraph* launch_arnoldi_step(Ctx& c, int j, bool transpose) {
   if (!c.opt.graphs) {
     enqueue_arnoldi_step(c, j, transpose);
