@@ -433,6 +433,27 @@ def test_vcycles_are_symmetric_contractions():
             assert abs(lev.A - lev.A.T).max() <= 1e-12 * abs(lev.A).max()
 
 
+def test_multigrid_without_coarsening_is_the_exact_preconditioner():
+    """With a coarsening limit above every level's size each hierarchy is a
+    single level solved by its dense inverse, so the multigrid form of M must
+    be M_I^(h) of Section 5 (exact inner solves with A_uu and C~_pi), which
+    the oracle builds independently from sparse LU factors.  Pins the dense
+    coarsest-level path and the coarsening-limit parameter."""
+    p = mi.random_small(5, 4, 6, seed=21, jitter=0.15)
+    B = oracle.assemble(p)
+    pa = precond.build(B, "amg", coarse_max=10 ** 9)
+    pe = precond.build(B, "exact")
+    assert len(pa.u_levels) == 1 and len(pa.pi_levels) == 1
+    assert len(precond.build(B, "amg").u_levels) > 1  # the default limit does coarsen this mesh
+    rng = np.random.default_rng(5)
+    nU, nP, _ = B.sizes
+    for _ in range(3):
+        v = rng.standard_normal(sum(B.sizes))
+        za, ze = pa.apply(v), pe.apply(v)
+        for a, b in ((0, nU), (nU, nU + nP), (nU + nP, len(v))):
+            assert np.abs(za[a:b] - ze[a:b]).max() <= 1e-9 * np.abs(ze[a:b]).max()
+
+
 # ------------------------------------------------------------------ adjoint
 def _adjoint_case(seed=3):
     from oracle import adjoint
