@@ -602,32 +602,42 @@ __global__ void __launch_bounds__(APPLY_U_NODES * 3) k_apply_u(Dims d, const dou
 }
 
 // p rows: A_pu x_u + (Abar_pp + A_stab) x_p + dt A_ppi x_pi.
-__global__ void k_apply_p(Dims d, const double* __restrict__ Aup, const double* __restrict__ Abar,
-                          const double* __restrict__ stabc, const double* __restrict__ ApPi, double cpi,
-                          const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ so,
-                          const double* __restrict__ bsub, double cpu) {
-  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= d.nT) return;
-  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
-  const long long nU = 3 * d.nN;
+__global__ void __launch_bounds__(256) k_apply_p(FaceTopo32 t, const double* __restrict__ Aup,
+                                                 const double* __restrict__ Abar, const double* __restrict__ stabc,
+                                                 const double* __restrict__ ApPi, double cpi,
+                                                 const double* __restrict__ x, double* __restrict__ y,
+                                                 const double* __restrict__ so, const double* __restrict__ bsub,
+                                                 double cpu) {
+  // 32-bit cell and node decoding; the same sums in the same order as the
+  // definition: A_pu x_u, then the p block, then A_ppi x_pi
+  const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= t.nT) return;
+  const unsigned q = t.d_nx.div(T);
+  const int i = (int)(T - q * (unsigned)t.nx), k = (int)t.d_ny.div(q), j = (int)(q - (unsigned)k * (unsigned)t.ny);
+  const unsigned Lx = (unsigned)t.nx + 1, Ly = (unsigned)t.ny + 1;
+  const unsigned nU = 3 * Lx * Ly * ((unsigned)t.nz + 1);
   double su = 0.0;
+#pragma unroll
   for (int a = 0; a < 8; ++a) {
-    const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-    for (int c = 0; c < 3; ++c) su -= Aup[(long long)(3 * a + c) * d.nT + T] * x[3 * n + c];
+    const unsigned n = (unsigned)(i + (a & 1)) + Lx * ((unsigned)(j + ((a >> 1) & 1)) + Ly * (unsigned)(k + (a >> 2)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) su -= Aup[(unsigned)(3 * a + c) * t.nT + T] * x[3 * n + c];
   }
   double s = cpu * su;
   const double* xp = x + nU;
-  const double cx = stabc[T], cy = stabc[d.nT + T], cz = stabc[2 * d.nT + T];
+  const double cx = stabc[T], cy = stabc[t.nT + T], cz = stabc[2 * t.nT + T];
   double st = (Abar[T] + (cx + cy + cz)) * xp[T];
-  if (cx != 0.0) st -= cx * xp[cell_id(d, i ^ 1, j, k)];
-  if (cy != 0.0) st -= cy * xp[cell_id(d, i, j ^ 1, k)];
-  if (cz != 0.0) st -= cz * xp[cell_id(d, i, j, k ^ 1)];
+  if (cx != 0.0) st -= cx * xp[t.cell(i ^ 1, j, k)];
+  if (cy != 0.0) st -= cy * xp[t.cell(i, j ^ 1, k)];
+  if (cz != 0.0) st -= cz * xp[t.cell(i, j, k ^ 1)];
   s += st;
-  const double* xpi = xp + d.nT;
+  const double* xpi = xp + t.nT;
   double c = 0.0;
-  for (int lf = 0; lf < 6; ++lf) c += ApPi[(long long)lf * d.nT + T] * xpi[cell_face(d, i, j, k, lf)];
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) c += ApPi[(unsigned)lf * t.nT + T] * xpi[t.face(i, j, k, lf)];
   s += cpi * c;
-  y[nU + T] = finish(s, nU + T, so, bsub);
+  const long long r = (long long)nU + T;
+  y[r] = finish(s, r, so, bsub);
 }
 
 // pi rows: A_pip x_p + A_pipi x_pi (ELL, 11 slots; the columns follow from
@@ -942,8 +952,8 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
   k_apply_u<<<grid_for(c.nN, APPLY_U_NODES), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
                                                                                     bsub, sgn);
   MHFP_LAUNCH_CHECK();
-  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.Aup, c.Abar, c.stabc, c.ApPi, transpose ? 1.0 : c.dt, x, y,
-                                                       so, bsub, sgn);
+  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Abar, c.stabc, c.ApPi,
+                                                       transpose ? 1.0 : c.dt, x, y, so, bsub, sgn);
   MHFP_LAUNCH_CHECK();
   k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy),
                                                         3 * c.nN, c.ApPi, c.Apipi, x, y, so, bsub,
