@@ -16,6 +16,9 @@ Plain numpy / scipy in FP64, written from the paper:
 * ``precond``  B~_p, C~_pi, the block-triangular preconditioner (Eq.
                hybridPrec) with exact inner solves (M_I^(h)) or with this
                library's multigrid spec (parity unpinned by the paper)
+* ``rbm``      the M_III^(h) displacement multigrid: smoothed aggregation
+               with the six rigid-body modes as near-kernel (Section 5;
+               parity unpinned by the paper)
 * ``fgmres``   right-preconditioned flexible GMRES (Section 5)
 """
 from . import elements, fgmres, mesh, precond, system  # noqa: F401

@@ -256,7 +256,7 @@ class Preconditioner:
     B: Blocks
     Bt: np.ndarray
     C: sp.csr_matrix
-    kind: str                      # "exact" (M_I) or "amg" (M_II)
+    kind: str                      # "exact" (M_I), "amg" (M_II) or "amg_rbm" (M_III)
     u_levels: list = field(default_factory=list)
     pi_levels: list = field(default_factory=list)
     _luu: object = None
@@ -265,6 +265,9 @@ class Preconditioner:
     def solve_uu(self, r):
         if self.kind == "exact":
             return self._luu.solve(r)
+        if self.kind == "amg_rbm":
+            from . import rbm
+            return rbm.vcycle(self.u_levels, r)
         return vcycle(self.u_levels, r)
 
     def solve_pi(self, r):
@@ -307,6 +310,10 @@ def build(B: Blocks, kind="amg", coarse_max=COARSE_MAX) -> Preconditioner:
     if kind == "exact":
         pc._luu = spla.splu(B.Auu.tocsc())
         pc._lpi = spla.splu(C.tocsc())
+    elif kind == "amg_rbm":
+        from . import rbm
+        pc.u_levels = rbm.build_u_hierarchy(B, coarse_max)
+        pc.pi_levels = build_pi_hierarchy(B, C, coarse_max)
     else:
         pc.u_levels = build_u_hierarchy(B, coarse_max)
         pc.pi_levels = build_pi_hierarchy(B, C, coarse_max)
