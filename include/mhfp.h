@@ -272,11 +272,15 @@ mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launche
  *
  * Scratch: a file-scope static __device__ array of 65536 x 2 doubles (1 MiB)
  * that every GPU which loads the library holds until the process exits.
- * Problems needing more than 65536 row blocks of 256 rows (about 128^3
- * cells and up) are rejected with MHFP_ERR_ARG and a message saying so.
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
+ * The call needs ceil(n_nodes/256) + ceil(n_T/256) + ceil(n_faces/256) row
+ * blocks (one partial-sum pair each); meshes needing more than 65536 are
+ * rejected with MHFP_ERR_ARG and a message saying so (a cube of 149^3 cells
+ * needs 65,132 and is accepted, 150^3 needs 66,449 and is not; 128^3 needs
+ * 41,346).  The first call on each device looks up the array's device
+ * address with cudaGetSymbolAddress (with that device current) and caches
+ * it for the life of the process, so the device's primary context must not
+ * be reset (cudaDeviceReset) between calls; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last
  * call's partial sums; every call overwrites each partial sum it reads, so
  * nothing has to start at zero, but calls that overlap on the GPU (for
  * example on two streams) race and must be serialised by the caller. */

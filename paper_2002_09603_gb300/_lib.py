@@ -129,6 +129,24 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def check_vec(t, n, device, name, at_least=False):
+    """Reject a tensor the C ABI would read or write out of bounds: it must be
+    a float64, contiguous torch tensor on ``device`` with exactly ``n``
+    elements (at least ``n`` when ``at_least``).  Raises ValueError."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: expected float64, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name}: expected a tensor on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor is not contiguous")
+    if (t.numel() < n) if at_least else (t.numel() != n):
+        raise ValueError(f"{name}: expected {'at least ' if at_least else ''}{n} elements, got {t.numel()}")
+    return t
+
+
 class Solver:
     """One stabilized hybridized poromechanics system on one GPU.
 
@@ -168,6 +186,7 @@ class Solver:
         nu_, np_, npi = C.c_longlong(), C.c_longlong(), C.c_longlong()
         self.lib.mhfp_sizes(h, C.byref(nu_), C.byref(np_), C.byref(npi))
         self.sizes = (nu_.value, np_.value, npi.value)
+        self.dims = (int(prob.nx), int(prob.ny), int(prob.nz))
         self.n = sum(self.sizes)
 
     # ------------------------------------------------------------ helpers
@@ -178,6 +197,19 @@ class Solver:
     def empty(self, n=None):
         return self.torch.empty(self.n if n is None else n, dtype=self.torch.float64, device=self.device)
 
+    def _v(self, t, name, n=None, optional=False, at_least=False):
+        """Device pointer of a checked vector (length n, default the system size)."""
+        if t is None and optional:
+            return None
+        check_vec(t, self.n if n is None else n, self.device, name, at_least)
+        return _ptr(t)
+
+    def level_size(self, which, level):
+        h = self.hierarchy(which)
+        if not 0 <= level < h["levels"]:
+            raise ValueError(f"level {level} out of range (hierarchy has {h['levels']})")
+        return h["points"][level] * h["block"][level]
+
     # ------------------------------------------------------------ C ABI
     def assemble_condense(self):
         self._check(self.lib.mhfp_assemble_condense(self.h))
@@ -187,69 +219,77 @@ class Solver:
 
     def build_rhs(self, x_prev=None, load_scale=1.0, out=None):
         out = self.empty() if out is None else out
-        self._check(self.lib.mhfp_build_rhs(self.h, _ptr(x_prev), float(load_scale), _ptr(out)))
+        self._check(self.lib.mhfp_build_rhs(self.h, self._v(x_prev, "x_prev", optional=True), float(load_scale),
+                                            self._v(out, "out")))
         return out
 
     def solve(self, rhs, tol=1e-8, out=None, raise_not_converged=True):
         out = self.empty() if out is None else out
         st = Stats()
-        code = self.lib.mhfp_solve(self.h, _ptr(rhs), _ptr(out), float(tol), C.byref(st))
+        code = self.lib.mhfp_solve(self.h, self._v(rhs, "rhs"), self._v(out, "out"), float(tol), C.byref(st))
         if code != MHFP_OK and not (code == 5 and not raise_not_converged):
             self._check(code)
         return out, st.as_dict()
 
     def apply_operator(self, x, out=None):
         out = self.empty() if out is None else out
-        self._check(self.lib.mhfp_apply_operator(self.h, _ptr(x), _ptr(out)))
+        self._check(self.lib.mhfp_apply_operator(self.h, self._v(x, "x"), self._v(out, "out")))
         return out
 
     def apply_operator_t(self, x, out=None):
         out = self.empty() if out is None else out
-        self._check(self.lib.mhfp_apply_operator_t(self.h, _ptr(x), _ptr(out)))
+        self._check(self.lib.mhfp_apply_operator_t(self.h, self._v(x, "x"), self._v(out, "out")))
         return out
 
     def adjoint_solve(self, g, tol=1e-8, out=None, raise_not_converged=True):
         out = self.empty() if out is None else out
         st = Stats()
-        code = self.lib.mhfp_adjoint_solve(self.h, _ptr(g), _ptr(out), float(tol), C.byref(st))
+        code = self.lib.mhfp_adjoint_solve(self.h, self._v(g, "g"), self._v(out, "out"), float(tol), C.byref(st))
         if code != MHFP_OK and not (code == 5 and not raise_not_converged):
             self._check(code)
         return out, st.as_dict()
 
     def grad_logk(self, lam, x, grad):
         """grad -= lambda^T (dA/d ln kappa_T) x, per cell (accumulates)."""
-        self._check(self.lib.mhfp_grad_logk(self.h, _ptr(lam), _ptr(x), _ptr(grad)))
+        self._check(self.lib.mhfp_grad_logk(self.h, self._v(lam, "lam"), self._v(x, "x"),
+                                            self._v(grad, "grad", n=self.sizes[1])))
         return grad
 
     def misfit(self, x, uz_target, p_target, inv_su2, inv_sp2, J, g):
         """J += step misfit (device scalar), g = its gradient."""
-        self._check(self.lib.mhfp_misfit(self.h, _ptr(x), _ptr(uz_target), _ptr(p_target), float(inv_su2),
-                                         float(inv_sp2), _ptr(J), _ptr(g)))
+        ntop = self.uz_target_size()
+        self._check(self.lib.mhfp_misfit(self.h, self._v(x, "x"), self._v(uz_target, "uz_target", n=ntop),
+                                         self._v(p_target, "p_target", n=self.sizes[1]), float(inv_su2),
+                                         float(inv_sp2), self._v(J, "J", n=1), self._v(g, "g")))
         return J, g
 
     def adjoint_rhs(self, g, lam_next, out=None):
         out = self.empty() if out is None else out
-        self._check(self.lib.mhfp_adjoint_rhs(self.h, _ptr(g), _ptr(lam_next), _ptr(out)))
+        self._check(self.lib.mhfp_adjoint_rhs(self.h, self._v(g, "g"), self._v(lam_next, "lam_next", optional=True),
+                                              self._v(out, "out")))
         return out
 
     def apply_precond_t(self, v, out=None):
         out = self.empty() if out is None else out
-        self._check(self.lib.mhfp_apply_precond_t(self.h, _ptr(v), _ptr(out)))
+        self._check(self.lib.mhfp_apply_precond_t(self.h, self._v(v, "v"), self._v(out, "out")))
         return out
 
     def apply_precond(self, v, out=None):
         out = self.empty() if out is None else out
-        self._check(self.lib.mhfp_apply_precond(self.h, _ptr(v), _ptr(out)))
+        self._check(self.lib.mhfp_apply_precond(self.h, self._v(v, "v"), self._v(out, "out")))
         return out
 
     def vcycle(self, which, b, out=None):
-        out = self.torch.empty_like(b) if out is None else out
-        self._check(self.lib.mhfp_vcycle(self.h, int(which), _ptr(b), _ptr(out)))
+        n = self.sizes[0] if int(which) == 0 else self.sizes[2]
+        out = self.empty(n) if out is None else out
+        self._check(self.lib.mhfp_vcycle(self.h, int(which), self._v(b, "b", n=n), self._v(out, "out", n=n)))
         return out
 
     def level_apply(self, which, level, x, out=None):
-        out = self.torch.empty_like(x) if out is None else out
-        self._check(self.lib.mhfp_level_apply(self.h, int(which), int(level), _ptr(x), _ptr(out)))
+        n = self.level_size(int(which), int(level))
+        out = self.empty(n) if out is None else out
+        self._check(self.lib.mhfp_level_apply(self.h, int(which), int(level), self._v(x, "x", n=n),
+                                              self._v(out, "out", n=n)))
         return out
 
     def hierarchy(self, which):
@@ -259,10 +299,14 @@ class Solver:
         return dict(levels=L, points=list(info.points[:L]), block=list(info.block[:L]), lmax=list(info.lmax[:L]),
                     schedule=list(info.schedule[:L]), sweep_us=list(info.sweep_us[:L]))
 
+    def uz_target_size(self):
+        """Top-plane node count (nx+1)(ny+1), the length of a u_z target."""
+        return (self.dims[0] + 1) * (self.dims[1] + 1)
+
     def scalings(self):
         bt = self.empty(self.sizes[1])
         ds = self.empty()
-        self._check(self.lib.mhfp_get_scalings(self.h, _ptr(bt), _ptr(ds)))
+        self._check(self.lib.mhfp_get_scalings(self.h, self._v(bt, "btilde", n=self.sizes[1]), self._v(ds, "ds")))
         return bt, ds
 
     def timing(self, enable: bool):
@@ -277,7 +321,8 @@ class Solver:
         """(||D_s (b - A x)||, ||D_s b||) into a 2-element device tensor; the
         library allocates nothing for this call."""
         out = self.empty(2) if out is None else out
-        self._check(self.lib.mhfp_residual_norm_noalloc(self.h, _ptr(b), _ptr(x), _ptr(out)))
+        self._check(self.lib.mhfp_residual_norm_noalloc(self.h, self._v(b, "b"), self._v(x, "x"),
+                                                        self._v(out, "out", n=2, at_least=True)))
         return out
 
     def close(self):
@@ -297,7 +342,12 @@ def solve_batch(solvers, rhs, tol=1e-8, out=None):
     Returns (xs, stats, statuses)."""
     import torch
     n = len(solvers)
+    if len(rhs) != n or (out is not None and len(out) != n):
+        raise ValueError("solve_batch: one right-hand side (and output) per solver")
     xs = out if out is not None else [s.empty() for s in solvers]
+    for i, s in enumerate(solvers):
+        check_vec(rhs[i], s.n, s.device, f"rhs[{i}]")
+        check_vec(xs[i], s.n, s.device, f"out[{i}]")
     H = (C.c_void_p * n)(*[s.h.value for s in solvers])
     R = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
     X = (C.c_void_p * n)(*[t.data_ptr() for t in xs])

@@ -1074,13 +1074,16 @@ void make_fp32_blocks(Ctx& c) {
 namespace mhfp {
 namespace {
 
-constexpr int NOALLOC_BLOCK = 256;
-// 2 partial sums per thread block -> 65536 blocks = 1 MiB of device memory
-constexpr long long NOALLOC_MAX_BLOCKS = 65536;
+constexpr int NOALLOC_BLOCK = (int)NOALLOC_ROWS_PER_BLOCK;
+// 2 partial sums per thread block -> NOALLOC_MAX_BLOCKS (65536) blocks = 1 MiB
+// of device memory
 static __device__ __align__(256) double g_noalloc_partials[2 * NOALLOC_MAX_BLOCKS];
 
 std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[128] = {};  // per device ordinal, filled on first use
+// Per device ordinal, filled on first use.  The cached address stays valid
+// for as long as the device's primary context lives; the library assumes it
+// lives for the whole process (no cudaDeviceReset between calls).
+double* g_noalloc_ptr[128] = {};
 
 __device__ __forceinline__ void na_block_store(double r2, double b2, double* part, long long slot) {
   __shared__ double sr[NOALLOC_BLOCK / 32], sb[NOALLOC_BLOCK / 32];
@@ -1248,9 +1251,11 @@ void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out
   const long long bu = (long long)grid_for(c.nN, NOALLOC_BLOCK);
   const long long bp = (long long)grid_for(c.nT, NOALLOC_BLOCK);
   const long long bf = (long long)grid_for(c.nF, NOALLOC_BLOCK);
-  if (bu + bp + bf > NOALLOC_MAX_BLOCKS)
+  const long long need = noalloc_row_blocks(c.nx, c.ny, c.nz);
+  if (need != bu + bp + bf) throw Error{MHFP_ERR_ARG, "row block count mismatch"};
+  if (need > NOALLOC_MAX_BLOCKS)
     throw Error{MHFP_ERR_ARG, "problem too large for the static scratch of mhfp_residual_norm_noalloc (" +
-                                  std::to_string(bu + bp + bf) + " row blocks > 65536)"};
+                                  std::to_string(need) + " row blocks > 65536)"};
   double* part = noalloc_scratch(c.device);
   k_na_u<<<(unsigned)bu, NOALLOC_BLOCK, 0, c.stream>>>(d, c.Auu.val, c.Aup, x, b, c.ds, part, 0);
   MHFP_LAUNCH_CHECK();

@@ -39,6 +39,22 @@ inline unsigned grid_for(long long n, int block) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Row blocks that mhfp_residual_norm_noalloc needs for a mesh of nx*ny*nz
+// cells: one partial-sum slot per block of 256 rows in each of its three row
+// kernels (displacement nodes, cells, faces).  The call accepts a mesh when
+// this count is at most the static scratch's 65536 slots (a cube of up to
+// about 149^3 cells).  Host-callable so the limit can be checked without a
+// GPU.
+constexpr long long NOALLOC_ROWS_PER_BLOCK = 256;
+constexpr long long NOALLOC_MAX_BLOCKS = 65536;
+__host__ __device__ inline long long noalloc_row_blocks(long long nx, long long ny, long long nz) {
+  const long long nN = (nx + 1) * (ny + 1) * (nz + 1);
+  const long long nT = nx * ny * nz;
+  const long long nF = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1);
+  const long long B = NOALLOC_ROWS_PER_BLOCK;
+  return (nN + B - 1) / B + (nT + B - 1) / B + (nF + B - 1) / B;
+}
+
 // ------------------------------------------------------------ stencils
 // Offsets of a structured lattice operator.  BOX1: the 27 neighbours with
 // |d|_inf <= 1 (Q1 node coupling), DIAMOND2: the 25 with |d|_1 <= 2 (cell

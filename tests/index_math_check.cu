@@ -107,10 +107,42 @@ int check_faces(int nx, int ny, int nz) {
   return 0;
 }
 
+// Row blocks of the no-allocation residual norm against a count written out
+// here (ceil of rows / 256 for nodes, cells and faces), and the acceptance
+// rule at its edge: 149^3 fits in the 65536 static slots, 150^3 does not, and
+// a mesh needing exactly 65536 blocks is accepted while 65537 is not.
+int check_noalloc_blocks() {
+  auto ceil256 = [](long long v) { return (v + 255) / 256; };
+  auto ref = [&](long long nx, long long ny, long long nz) {
+    const long long nodes = (nx + 1) * (ny + 1) * (nz + 1), cells = nx * ny * nz;
+    const long long faces = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1);
+    return ceil256(nodes) + ceil256(cells) + ceil256(faces);
+  };
+  const long long cases[][3] = {{1, 1, 1}, {6, 5, 4}, {64, 64, 64}, {128, 128, 128}, {149, 149, 149},
+                                {150, 150, 150}, {1000, 3, 2}, {255, 1, 1}, {256, 1, 1}};
+  for (const auto& c : cases)
+    if (mhfp::noalloc_row_blocks(c[0], c[1], c[2]) != ref(c[0], c[1], c[2]))
+      return fail("noalloc row blocks", c[0], c[1], c[2]);
+  if (mhfp::noalloc_row_blocks(128, 128, 128) != 41346) return fail("noalloc 128^3", 41346, 0, 0);
+  if (mhfp::noalloc_row_blocks(149, 149, 149) > mhfp::NOALLOC_MAX_BLOCKS) return fail("noalloc 149^3 rejected", 0, 0, 0);
+  if (mhfp::noalloc_row_blocks(150, 150, 150) <= mhfp::NOALLOC_MAX_BLOCKS) return fail("noalloc 150^3 accepted", 0, 0, 0);
+  // find meshes (nx, 1, 1) whose count lands exactly on the limit and one past it
+  bool at = false, past = false;
+  for (long long nx = 1; nx < 10000000 && !(at && past); ++nx) {
+    const long long b = mhfp::noalloc_row_blocks(nx, 1, 1);
+    if (b == mhfp::NOALLOC_MAX_BLOCKS) at = true;
+    if (b == mhfp::NOALLOC_MAX_BLOCKS + 1) past = true;
+  }
+  if (!at || !past) return fail("noalloc edge cases not reached", at, past, 0);
+  if (mhfp::NOALLOC_MAX_BLOCKS != 65536) return fail("noalloc slots", mhfp::NOALLOC_MAX_BLOCKS, 0, 0);
+  return 0;
+}
+
 }  // namespace
 
 int main() {
   if (check_div()) return 1;
+  if (check_noalloc_blocks()) return 1;
   const int dims[][3] = {{1, 1, 1}, {2, 3, 4}, {5, 4, 3}, {7, 1, 2}, {1, 6, 1}, {10, 4, 7}, {16, 16, 16}, {9, 13, 5}};
   for (const auto& d : dims)
     if (check_faces(d[0], d[1], d[2])) return 1;
