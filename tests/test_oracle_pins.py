@@ -267,7 +267,8 @@ def _spectral_case(seed, dims, dt):
     return p, B, pc
 
 
-@pytest.mark.parametrize("seed,dims,dt", [(1, (2, 2, 2), 0.1), (2, (3, 2, 2), 1e-4)])
+@pytest.mark.parametrize("seed,dims,dt", [(1, (2, 2, 2), 0.1), (2, (3, 2, 2), 1e-4), (3, (3, 3, 3), 1e-3),
+                                           (4, (3, 3, 3), 10.0)])
 def test_theorem_eigenvalues_of_preconditioned_matrix(seed, dims, dt):
     """Theorem 1: A_H M^-1 has eigenvalue 1 with multiplicity
     n_u + n_pi - n_p; Lemma 1 bounds the others, |mu| <= eps +
@@ -411,6 +412,37 @@ def test_table_can1_iteration_counts_exact_inner_solves():
             paper = rows[(rows[:, 0] == n) & np.isclose(rows[:, 1], dt), 2][0]
             assert info["converged"] and its[n] <= paper, (n, dt, its[n], paper)
         assert its[20] <= 1.25 * its[10], (dt, its)
+
+
+def test_table_can1_stabilization_removes_the_undrained_degradation():
+    """Table tab:can_1 (Section 5.2): near the undrained limit the
+    unstabilized hybrid formulation more than doubles M_I^(h)'s iteration
+    count (39 -> 88 at 10^3, dt = 1e-5), while the stabilized one stays at the
+    stabilized level.  At the printed permeability this oracle's B_p is
+    dominated by dt 1^T W 1 even at dt = 1e-5 (E_p small, no near-singular
+    modes to remove), so the pin runs at kappa = 1e-13 m^2, where kappa dt is
+    small enough to expose the unstable Q1-P0 pressure modes: the stabilized
+    count must stay within the paper's and the unstabilized one must be at
+    least 1.5 times it (the paper's ratio is 2.3)."""
+    import copy
+    rows = np.loadtxt(os.path.join(GOLDEN, "tab_can1.txt"))
+    paper = rows[(rows[:, 0] == 10) & np.isclose(rows[:, 1], 1e-5), 2][0]
+    its = {}
+    for stab in (True, False):
+        p = mi.cantilever_cube(10, dt=1e-5, kappa=1e-13)
+        B = oracle.assemble(p)
+        if not stab:
+            B = copy.copy(B)
+            B.Astab = sp.csr_matrix(B.Astab.shape)
+        pc = precond.build(B, "exact")
+        A = system.system_matrix(B)
+        s = precond.equilibration(B, pc.Bt, pc.C)
+        _, info = fgmres.fgmres(lambda v: A @ v, pc.apply, system.rhs(B), tol=1e-6, restart=300, maxit=300,
+                                scale=s)
+        assert info["converged"]
+        its[stab] = info["iters"]
+    assert its[True] <= paper, its
+    assert its[False] >= 1.5 * its[True], its
 
 
 def test_vcycles_are_symmetric_contractions():
@@ -591,3 +623,226 @@ def test_m3_takes_fewer_iterations_than_m2_on_the_cantilever(n):
         assert info["converged"]
         its[kind] = info["iters"]
     assert its["amg_rbm"] <= 0.75 * its["amg"], its
+
+
+# ------------------------------------------- B~_p in closed form (Eq. app_Bp)
+def _btilde_closed_form(hx, hy, hz, E, nu, b, S, mu, kap, dt):
+    """B~_p of a cell whose 8 nodes are free and whose macro-element is a full
+    2x2x2 patch of identical hx*hy*hz boxes, written out by hand:
+
+    * S_eps |T|;
+    * diag(A_stab) = 3 beta_M |M| (each cell of the Q3 cube graph has three
+      neighbours inside its macro), beta_M = (3b)^2 / [32 (lambda + 4G)],
+      |M| = 8 |T|;
+    * dt 1^T W_T 1 = dt * 12 sum_d kappa_d A_d / (mu h_d), with A_d the area
+      of the faces normal to d (the RT0 box mass closed form);
+    * the fixed-stress term sum_{a,d} (A_up)_{(a,d),T}^2 / K_(a,d) over the 8
+      nodes and 3 directions, with (A_up)_{(a,d),T} = -b int_T dN_a/dx_d =
+      -+ b A_d / 4 and K_(a,d) the assembled Q1 diagonal of an interior node,
+      8 [(lambda + 2G) A_d/(9 h_d) + G sum_{e != d} A_e/(9 h_e)]
+      (int_T (dN_a/dx_e)^2 = A_e / (9 h_e) for a trilinear hat).
+    Returns the four terms."""
+    lam, G = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    h = (hx, hy, hz)
+    vol = hx * hy * hz
+    A = (hy * hz, hx * hz, hx * hy)
+    storage = S * vol
+    stab = 3.0 * (9.0 * b * b / (32.0 * (lam + 4 * G))) * 8.0 * vol
+    flow = dt * 12.0 * sum(kap[d] * A[d] / (mu * h[d]) for d in range(3))
+    K = [8.0 * ((lam + 2 * G) * A[d] / (9 * h[d]) + G * sum(A[e] / (9 * h[e]) for e in range(3) if e != d))
+         for d in range(3)]
+    fixed_stress = 8.0 * sum((b * A[d] / 4.0) ** 2 / K[d] for d in range(3))
+    return storage, stab, flow, fixed_stress
+
+
+def _interior_cells(nx, ny, nz):
+    out = []
+    for k in range(1, nz - 1):
+        for j in range(1, ny - 1):
+            for i in range(1, nx - 1):
+                # nodes i..i+1 are off every roller plane, the macro is complete
+                if (i // 2) * 2 + 1 < nx and (j // 2) * 2 + 1 < ny and (k // 2) * 2 + 1 < nz:
+                    out.append(i + nx * (j + ny * k))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("box", [(1.0, 1.0, 1.0), (1.0, 0.5, 2.0)])
+def test_btilde_closed_form_at_interior_cells(box):
+    """Eq. (app_Bp) with H~ of the M_I^(h) definition (Section 5): B~_p =
+    S_eps|T| + diag(A_stab) + diag(A_up^T diag(A_uu)^-1 A_up) + dt 1^T W 1,
+    each term derived by hand for identical box cells with homogeneous,
+    anisotropic materials.  dt is chosen so the four terms are of comparable
+    size; dropping any one of them fails this check."""
+    n = 6
+    lx, ly, lz = box
+    E, nu, b, S, mu = 1e4, 0.25, 1.0, 1e-4, 1e-3
+    kap = (1e-12, 3e-12, 0.5e-12)
+    p = mi.terzaghi_cube(n, E=E, nu=nu, b=b, S=S, mu=mu, dt=100.0)
+    p.coords = mi.box_coords(n, n, n, lx, ly, lz)
+    p.kappa[:] = kap
+    B = oracle.assemble(p)
+    terms = _btilde_closed_form(lx / n, ly / n, lz / n, E, nu, b, S, mu, kap, p.dt)
+    ref = sum(terms)
+    assert min(terms) > 0.05 * max(terms), terms      # every term matters at this dt
+    cells = _interior_cells(n, n, n)
+    assert len(cells) >= 27
+    bt = precond.btilde(B)
+    assert np.allclose(bt[cells], ref, rtol=1e-12, atol=0)
+    # the individual terms the oracle stores
+    assert np.allclose(B.App.diagonal()[cells], terms[0], rtol=1e-12)
+    assert np.allclose(B.Astab.diagonal()[cells], terms[1], rtol=1e-12)
+    assert np.allclose(p.dt * B.Dw[cells], terms[2], rtol=1e-12)
+    # planted mistakes in the oracle's inputs: each dropped term is caught
+    import copy
+    for drop in ("App", "Astab", "Dw", "Aup"):
+        Bm = copy.copy(B)
+        if drop == "Dw":
+            Bm.Dw = 0.0 * B.Dw
+        else:
+            setattr(Bm, drop, 0.0 * getattr(B, drop))
+        assert not np.allclose(precond.btilde(Bm)[cells], ref, rtol=1e-6, atol=0), drop
+
+
+# ----------------------------------------------- Chebyshev and power iteration
+def _rand_spd(n, bs, seed):
+    rng = np.random.default_rng(seed)
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T / n + np.diag(rng.uniform(0.2, 3.0, n))
+    return sp.csr_matrix(A)
+
+
+def _matfun_of_DinvA(A, Dinv, bs, f):
+    """f(D^-1 A) for D^-1 A similar to the SPD D^-1/2 A D^-1/2 (eigen-
+    decomposition, no iteration)."""
+    n = A.shape[0]
+    Dm = np.zeros((n, n))
+    for i in range(n // bs):
+        Dm[bs * i:bs * i + bs, bs * i:bs * i + bs] = Dinv[i]
+    lam, V = np.linalg.eig(Dm @ A.toarray())
+    assert np.abs(lam.imag).max() < 1e-10 * np.abs(lam).max()
+    lam, V = lam.real, V.real
+    return V @ np.diag(f(lam)) @ np.linalg.inv(V), lam
+
+
+@pytest.mark.parametrize("bs", [1, 3])
+@pytest.mark.parametrize("degree", [1, 2, 3, 4])
+def test_chebyshev_error_is_the_scaled_chebyshev_polynomial(bs, degree):
+    """Chebyshev smoothing of degree k from x = 0 on [lmax/ratio, lmax],
+    preconditioned by the (block) diagonal D, leaves the error
+    e_k = p_k(D^-1 A) e_0 with p_k(t) = T_k((theta - t)/delta) / T_k(theta/delta)
+    (theta, delta the interval's centre and half-width).  Checked against that
+    polynomial evaluated on the eigenvalues of D^-1 A; a wrong recurrence
+    coefficient or interval fails it."""
+    n = 30
+    A = _rand_spd(n, bs, 40 + bs)
+    Dinv = precond.block_diag_inv(A, bs)
+    _, lam = _matfun_of_DinvA(A, Dinv, bs, lambda t: t)
+    lev = precond.Level(A, bs, None, Dinv=Dinv, lmax=1.05 * lam.max())
+    lmin = lev.lmax / precond.CHEB_RATIO
+    theta, delta = 0.5 * (lev.lmax + lmin), 0.5 * (lev.lmax - lmin)
+    Tk = np.polynomial.chebyshev.Chebyshev.basis(degree)
+    pk = lambda t: Tk((theta - t) / delta) / Tk(theta / delta)
+    P, _ = _matfun_of_DinvA(A, Dinv, bs, pk)
+    b = np.random.default_rng(5).standard_normal(n)
+    xs = np.linalg.solve(A.toarray(), b)
+    x = precond.chebyshev(lev, b, np.zeros(n), degree=degree)
+    assert np.allclose(xs - x, P @ xs, rtol=0, atol=1e-12 * np.abs(xs).max())
+    # the residual polynomial is bounded by 1/T_k(theta/delta) on the interval
+    inside = (lam >= lmin) & (lam <= lev.lmax)
+    assert np.all(np.abs(pk(lam[inside])) <= 1.0 / abs(Tk(theta / delta)) * (1 + 1e-12))
+
+
+@pytest.mark.parametrize("bs", [1, 3])
+def test_power_iteration_matches_its_closed_form(bs):
+    """spectral_radius takes POWER_ITERS steps v <- D^-1 A v / ||.|| from the
+    fixed start vector and returns the last norm, i.e. ||M^k v0|| /
+    ||M^(k-1) v0|| with M = D^-1 A; here that ratio comes from the eigen-
+    decomposition of M.  For D = c I (M symmetric) the estimate is below
+    lambda_max and converges to it from below."""
+    n = 45
+    A = _rand_spd(n, bs, 7 + bs)
+    Dinv = precond.block_diag_inv(A, bs)
+    k = precond.POWER_ITERS
+    v0 = precond.power_start(n)
+    Mk, lam = _matfun_of_DinvA(A, Dinv, bs, lambda t: t ** k)
+    Mk1, _ = _matfun_of_DinvA(A, Dinv, bs, lambda t: t ** (k - 1))
+    ref = np.linalg.norm(Mk @ v0) / np.linalg.norm(Mk1 @ v0)
+    rho = precond.spectral_radius(A, Dinv, bs)
+    assert np.isclose(rho, ref, rtol=1e-10)
+    # symmetric case: lower bound of lambda_max, increasing in k
+    c = 2.5
+    Dc = np.repeat((np.eye(bs) / c)[None], n // bs, axis=0)
+    rho_c = precond.spectral_radius(A, Dc, bs)
+    lmax = np.linalg.eigvalsh(A.toarray()).max() / c
+    assert rho_c <= lmax * (1 + 1e-12) and rho_c >= 0.5 * lmax
+
+
+def test_smoother_interval_covers_the_spectrum_on_every_level():
+    """The Chebyshev interval's top, lmax = 1.1 rho, lies above every
+    eigenvalue of D^-1 A on each multigrid level of a small heterogeneous
+    problem, so the smoother damps instead of amplifying."""
+    p = mi.random_small(7, 5, 6, seed=17, jitter=0.2)
+    B = oracle.assemble(p)
+    pc = precond.build(B, "amg", coarse_max=27)
+    for levels in (pc.u_levels, pc.pi_levels):
+        for lev in levels[:-1]:
+            _, lam = _matfun_of_DinvA(lev.A, lev.Dinv, lev.bs, lambda t: t)
+            assert lam.max() <= lev.lmax, (lam.max(), lev.lmax)
+
+
+# ------------------------------------ Terzaghi's consolidation over many steps
+def _terzaghi_series(zp, t, p0, cv, H=1.0, terms=400):
+    """p(z', t) = sum_m (2 p0 / M) sin(M z'/H) exp(-M^2 c_v t / H^2),
+    M = (2m+1) pi / 2, z' measured down from the drained top."""
+    out = np.zeros_like(zp)
+    for m in range(terms):
+        M = (2 * m + 1) * np.pi / 2
+        out += 2 * p0 / M * np.sin(M * zp / H) * np.exp(-M * M * cv * t / (H * H))
+    return out
+
+
+def _terzaghi_column_error(N, steps, S, rhs=None):
+    """Relative RMS error of the cell pressures of a 1 x 1 x N consolidation
+    column after `steps` backward-Euler steps that reach c_v t / H^2 = 0.1."""
+    E, nu, mu, kap = 1e4, 0.25, 1e-3, 1e-12
+    lam, G = el.lame(E, nu)
+    Kv = lam + 2 * G
+    cv = kap / mu * Kv / (1.0 + S * Kv)
+    p0 = 1.0 / (1.0 + S * Kv)
+    tfin = 0.1 / cv
+    p = mi.terzaghi_cube(nx=1, ny=1, nz=N, E=E, nu=nu, S=S, mu=mu, kappa=kap, dt=tfin / steps)
+    B = oracle.assemble(p)
+    lu = spla.splu(system.system_matrix(B).tocsc())
+    nU, nP, _ = B.sizes
+    u, pp = np.zeros(nU), np.zeros(nP)
+    for _ in range(steps):
+        x = lu.solve((rhs or system.rhs)(B, u, pp))
+        u, pp = x[:nU], x[nU:nU + nP]
+    zp = 1.0 - (np.arange(N) + 0.5) / N
+    ex = _terzaghi_series(zp, tfin, p0, cv)
+    return np.sqrt(np.mean((pp - ex) ** 2)) / p0
+
+
+@pytest.mark.parametrize("S", [0.0, 1e-4])
+def test_terzaghi_series_first_order_in_h_and_dt(S):
+    """Terzaghi's series solution of 1D consolidation pins the time coupling
+    f_p = A_pu u_{n-1} + S_eps |T| p_{n-1} (Section 2.1, Appendix A) over many
+    steps: refining h and dt together (dt ~ h, so the stabilization, which is
+    O(h^2/dt) relative, shrinks at the same rate) halves the error each time,
+    the first order of backward Euler.  Planting a mistake in the oracle's
+    time coupling (dropping either term) stalls the error at O(1)."""
+    errs = [_terzaghi_column_error(N, st, S) for N, st in ((16, 8), (32, 16), (64, 32), (128, 64))]
+    rates = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.8 <= r <= 2.2 for r in rates), (errs, rates)
+    assert errs[-1] < 2e-3, errs
+    base = system.rhs
+
+    def no_u(B, u_prev=None, p_prev=None, load_scale=1.0):
+        return base(B, None if u_prev is None else 0 * u_prev, p_prev, load_scale)
+
+    def no_p(B, u_prev=None, p_prev=None, load_scale=1.0):
+        return base(B, u_prev, None if p_prev is None else 0 * p_prev, load_scale)
+
+    planted = [no_u] + ([no_p] if S > 0 else [])
+    for f in planted:
+        assert _terzaghi_column_error(64, 32, S, rhs=f) > 50 * errs[2]
