@@ -105,6 +105,14 @@ typedef struct {
                         /* when the norm falls below 1/sqrt(2) of its value    */
                         /* (DGKS test); 0: one classical pass, never repeated  */
                         /* (PETSc's GMRES default)                             */
+  int schedule;         /* 0 (default): each coarse lattice level's sweeps and */
+                        /* residuals take the autotuner's schedule (the size   */
+                        /* rule when autotune = 0); 1, 4, 8 or 16: every       */
+                        /* coarse lattice level uses that schedule (1 = one    */
+                        /* point per thread, W = offsets over W warps)         */
+  int fine_blocks;      /* 0 (default): autotuned (size rule without it); 6 or */
+                        /* 8: resident blocks per SM of the finest FP32        */
+                        /* displacement sweep and residual (precision = 1)     */
 } mhfp_options;
 
 typedef struct {
@@ -203,6 +211,24 @@ mhfp_status mhfp_adjoint_solve(mhfp_handle h, const double* d_g, double* d_lambd
  * on kappa). */
 mhfp_status mhfp_grad_logk(mhfp_handle h, const double* d_lambda, const double* d_x, double* d_grad);
 
+/* New per-cell log-permeability for an existing, set-up handle (the
+ * adjoint loop's parameter update; not in the paper, which solves for fixed
+ * materials).  d_logk: device array of n_T values theta_T; every cell gets
+ * kappa_T = exp(theta_T) times its create-time anisotropy ratios
+ * (kappa_T,q / kappa_T,x), so theta_T = ln kappa_T,x.  Recomputes in place
+ * what depends on kappa: the RT0 condensation W_T = A_ww,T^-1, W_T 1,
+ * 1^T W_T 1 and Abar_pp (Eq. hmfeSys), B~_p and C~_pi (Eq. app_Bp, Section
+ * 4), the equilibration D_s, the interface-pressure multigrid hierarchy
+ * (same levels and launch schedules, no autotuning) and the FP32 copies.
+ * A_uu, A_up, the stabilization and the displacement hierarchy do not
+ * depend on kappa and are kept.  No device buffer of the handle is
+ * reallocated (the first update allocates its scratch once: the anisotropy
+ * ratios, the Galerkin product workspace and the dense-inverse workspace).
+ * The captured solve graphs are dropped and captured again by the next
+ * solve.  MHFP_ERR_ARG if some exp(theta_T) is not a positive finite
+ * permeability (nothing is changed then).  Synchronises the stream. */
+mhfp_status mhfp_update_logk(mhfp_handle h, const double* d_logk);
+
 /* Misfit of one time step (not in the paper; the objective of the gradient
  * growth): *d_J += 1/2 inv_su2 sum_top (u_z - u_z*)^2 + 1/2 inv_sp2
  * sum_cells (p - p*)^2, and d_g (n values, overwritten) = dJ/dx.  The top
@@ -224,7 +250,9 @@ mhfp_status mhfp_apply_precond_t(mhfp_handle h, const double* d_v, double* d_z);
 mhfp_status mhfp_apply_precond(mhfp_handle h, const double* d_v, double* d_z);
 
 /* One V-cycle x = V(b) of the displacement (which = 0, length n_u) or the
- * interface-pressure (which = 1, length n_pi) hierarchy. */
+ * interface-pressure (which = 1, length n_pi) hierarchy, in the precision
+ * the solve uses: with precision = 1 the FP64 b is rounded to FP32, the
+ * FP32 cycle runs, and x is its FP32 result widened to FP64. */
 mhfp_status mhfp_vcycle(mhfp_handle h, int which, const double* d_b, double* d_x);
 
 /* y = A_l x for level `level` of hierarchy `which` (lengths from

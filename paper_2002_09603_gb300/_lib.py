@@ -24,7 +24,7 @@ EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhf
            "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_operator_t", "mhfp_adjoint_solve",
            "mhfp_grad_logk", "mhfp_misfit", "mhfp_adjoint_rhs", "mhfp_apply_precond_t", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
-           "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
+           "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_update_logk", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
 
 
 class MhfpError(RuntimeError):
@@ -47,7 +47,7 @@ class Options(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_ratio", C.c_double), ("coarse_max", C.c_int), ("power_iters", C.c_int),
                 ("precision", C.c_int), ("graphs", C.c_int), ("autotune", C.c_int),
-                ("reorth", C.c_int)]
+                ("reorth", C.c_int), ("schedule", C.c_int), ("fine_blocks", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -99,6 +99,7 @@ def load(path: str | None = None):
         "mhfp_timing": (i, [vp, i]),
         "mhfp_timing_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d), C.POINTER(d)]),
         "mhfp_residual_norm_noalloc": (i, [vp, vp, vp, vp]),
+        "mhfp_update_logk": (i, [vp, vp]),
         "mhfp_solve_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, C.POINTER(Stats),
                                  C.POINTER(i)]),
         "mhfp_launch_count": (ll, []),
@@ -316,6 +317,12 @@ class Solver:
         n, ms, b = C.c_longlong(), C.c_double(), C.c_double()
         self._check(self.lib.mhfp_timing_read(self.h, int(kernel_class), C.byref(n), C.byref(ms), C.byref(b)))
         return dict(launches=n.value, total_ms=ms.value, bytes_per_launch=b.value)
+
+    def update_logk(self, logk):
+        """New per-cell log-permeability (n_T float64 device values): the
+        condensation, B~_p, C~_pi, D_s and the interface-pressure hierarchy
+        are recomputed in place (mhfp_update_logk)."""
+        self._check(self.lib.mhfp_update_logk(self.h, self._v(logk, "logk", n=self.sizes[1])))
 
     def residual_norm_noalloc(self, b, x, out=None):
         """(||D_s (b - A x)||, ||D_s b||) into a 2-element device tensor; the

@@ -1,8 +1,10 @@
 """Gradient of a time-stepped misfit with respect to the per-cell
 log-permeability, by the discrete adjoint, on the GPU.
 
-Marshalling only: every step runs in libmhfp (mhfp_build_rhs, mhfp_solve,
-mhfp_misfit, mhfp_adjoint_rhs, mhfp_adjoint_solve, mhfp_grad_logk).  The
+Marshalling only: every step runs in libmhfp (mhfp_update_logk,
+mhfp_build_rhs, mhfp_solve, mhfp_misfit, mhfp_adjoint_rhs,
+mhfp_adjoint_solve, mhfp_grad_logk).  One handle is created and set up
+once; each evaluation only updates its permeability in place.  The
 forward sweep keeps every `checkpoint_every`-th state; the reverse sweep
 recomputes each segment from its checkpoint, so device memory holds
 N / k + k states instead of N.
@@ -51,13 +53,24 @@ class MisfitGradient:
         self.stats = []
 
     def _solver(self, logk):
-        opt = default_options()
-        opt.precision = self.precision
-        opt.restart = self.restart
-        s = Solver(_with_logk(self.prob, logk))
-        s.assemble_condense()
-        s.setup_precond(opt)
-        return s
+        """The handle, created and set up on the first call; every call sets
+        its log-permeability (in place, mhfp_update_logk)."""
+        if getattr(self, "_s", None) is None:
+            opt = default_options()
+            opt.precision = self.precision
+            opt.restart = self.restart
+            s = Solver(self.prob)
+            s.assemble_condense()
+            s.setup_precond(opt)
+            self._s = s
+        t = self.torch.as_tensor(np.ascontiguousarray(logk, dtype=np.float64), device=self._s.device)
+        self._s.update_logk(t)
+        return self._s
+
+    def close(self):
+        if getattr(self, "_s", None) is not None:
+            self._s.close()
+            self._s = None
 
     def _step(self, s, x_prev):
         b = s.build_rhs(x_prev)
@@ -73,7 +86,6 @@ class MisfitGradient:
         for n in range(self.nsteps):
             x = self._step(s, x)
             s.misfit(x, self.uz_t[n], self.p_t[n], self.inv_su2, self.inv_sp2, J, g)
-        s.close()
         return float(J.item())
 
     def value_and_grad(self, logk):
@@ -107,7 +119,6 @@ class MisfitGradient:
                 s.grad_logk(lam, xn, grad)
                 lam_next = lam
         Jv = float(J.item())
-        s.close()
         return Jv, grad
 
 

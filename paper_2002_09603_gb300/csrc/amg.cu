@@ -1163,22 +1163,42 @@ __global__ void k_gj_init(int n, const double* __restrict__ A, double* __restric
   M[t] = cidx < n ? A[r * n + cidx] : (cidx - n == r ? 1.0 : 0.0);
 }
 
-// A (host, n x n row-major) -> its inverse in device memory `inv`
-void invert_dense_gpu(Ctx& c, const std::vector<double>& A, int n, double* inv) {
+// A (host, n x n row-major) -> its inverse in device memory `inv`.  With
+// keep, the elimination workspace is the handle's persistent one (allocated
+// once, for permeability updates); otherwise it is allocated and freed here.
+void invert_dense_gpu(Ctx& c, const std::vector<double>& A, int n, double* inv, bool keep = false) {
   double *dA = nullptr, *M = nullptr, *prow = nullptr, *fcol = nullptr;
   int* err = nullptr;
   auto release = [&] {
+    if (keep) return;
     cudaFree(dA);
     cudaFree(M);
     cudaFree(prow);
     cudaFree(fcol);
     cudaFree(err);
   };
-  cudaError_t e = cudaMalloc(&dA, (size_t)n * n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&M, (size_t)n * 2 * n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&prow, (size_t)2 * n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&fcol, (size_t)n * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  cudaError_t e = cudaSuccess;
+  if (keep) {
+    if (c.gj_n < n) {
+      c.gj_A = dalloc_n<double>(c, (size_t)n * n);
+      c.gj_M = dalloc_n<double>(c, (size_t)n * 2 * n);
+      c.gj_prow = dalloc_n<double>(c, (size_t)2 * n);
+      c.gj_fcol = dalloc_n<double>(c, (size_t)n);
+      if (!c.gj_err) c.gj_err = dalloc_n<int>(c, 1);
+      c.gj_n = n;
+    }
+    dA = c.gj_A;
+    M = c.gj_M;
+    prow = c.gj_prow;
+    fcol = c.gj_fcol;
+    err = c.gj_err;
+  } else {
+    e = cudaMalloc(&dA, (size_t)n * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&M, (size_t)n * 2 * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&prow, (size_t)2 * n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&fcol, (size_t)n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  }
   if (e != cudaSuccess) {
     release();
     throw Error{MHFP_ERR_OOM, "device allocation failed (dense coarsest level)"};
@@ -1239,12 +1259,13 @@ void make_dense_coarse(Ctx& c, Level& L) {
       }
     }
   }
-  L.dense_inv = dalloc_n<double>(c, (size_t)n * n);
-  invert_dense_gpu(c, A, n, L.dense_inv);
+  const bool rebuild = L.dense_inv != nullptr;
+  if (!rebuild) L.dense_inv = dalloc_n<double>(c, (size_t)n * n);
+  invert_dense_gpu(c, A, n, L.dense_inv, rebuild);
 }
 
 void finish_level(Ctx& c, Level& L) {
-  L.dinv = dalloc_n<double>(c, (size_t)L.bs * L.bs * L.npts);
+  if (!L.dinv) L.dinv = dalloc_n<double>(c, (size_t)L.bs * L.bs * L.npts);
   if (L.faces) {
     k_dinv_ell<<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.Cpi, L.dinv);
   } else {
@@ -1259,12 +1280,16 @@ void finish_level(Ctx& c, Level& L) {
   L.lmax = 1.1 * spectral_radius(c, L);
 }
 
-// one smoothed-aggregation coarsening step of a lattice level
-Level coarsen(Ctx& c, Level& L) {
+// one smoothed-aggregation coarsening step of a lattice level.  With
+// `into` (a permeability update), the next level already exists and its
+// values, its activity mask and L's prolongator are recomputed in place,
+// with the handle's persistent Galerkin scratch.
+Level coarsen(Ctx& c, Level& L, Level* into = nullptr) {
   const StructOp& A = L.A;
   const int R = stencil_radius(A.kind);
   L.R = R;
   Level Cl;
+  if (into) Cl = *into;
   Cl.bs = L.bs;
   Cl.A.Lx = (A.Lx + 2) / 3; Cl.A.Ly = (A.Ly + 2) / 3; Cl.A.Lz = (A.Lz + 2) / 3;
   Cl.A.N = (long long)Cl.A.Lx * Cl.A.Ly * Cl.A.Lz;
@@ -1276,11 +1301,20 @@ Level coarsen(Ctx& c, Level& L) {
   const Lat F = lat_of(A), Cc = lat_of(Cl.A);
   const int ns = p_slots(R), nq = q_slots(R);
   const int bs2 = L.bs * L.bs;
-  L.P = dalloc_n<double>(c, (size_t)ns * ns * ns * bs2 * F.N);
-  Cl.active = dalloc_n<unsigned char>(c, Cl.n);
-  Cl.A.val = dalloc_n<double>(c, (size_t)Cl.A.noff() * bs2 * Cc.N);
+  if (!L.P) L.P = dalloc_n<double>(c, (size_t)ns * ns * ns * bs2 * F.N);
+  if (!Cl.active) Cl.active = dalloc_n<unsigned char>(c, Cl.n);
+  if (!Cl.A.val) Cl.A.val = dalloc_n<double>(c, (size_t)Cl.A.noff() * bs2 * Cc.N);
+  const size_t q_elems = (size_t)nq * nq * nq * bs2 * F.N;
   double* Q = nullptr;
-  MHFP_CUDA(cudaMalloc(&Q, (size_t)nq * nq * nq * bs2 * F.N * sizeof(double)));
+  if (into) {
+    if (c.upd_Q_elems < q_elems) {
+      c.upd_Q = dalloc_n<double>(c, q_elems);
+      c.upd_Q_elems = q_elems;
+    }
+    Q = c.upd_Q;
+  } else {
+    MHFP_CUDA(cudaMalloc(&Q, q_elems * sizeof(double)));
+  }
   const double omega = 4.0 / (3.0 * L.lmax);
   try {
     dispatch_bs(L.bs, [&](auto BS) {
@@ -1301,10 +1335,10 @@ Level coarsen(Ctx& c, Level& L) {
     });
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
   } catch (...) {
-    cudaFree(Q);
+    if (!into) cudaFree(Q);
     throw;
   }
-  MHFP_CUDA(cudaFree(Q));
+  if (!into) MHFP_CUDA(cudaFree(Q));
   return Cl;
 }
 
@@ -1721,14 +1755,62 @@ void build_hierarchies(Ctx& c) {
   if (c.opt.autotune) {
     // the finest displacement level runs k_cheb_u0 (FP64) or the symmetric
     // FP32 sweep, whose two occupancy variants are timed; tune the others
-    if (c.opt.precision == 1 && !c.hu[0].dense_inv) autotune_fine_sym(c, c.hu[0]);
+    // (schedules fixed by the options are not tuned)
+    if (c.opt.precision == 1 && !c.hu[0].dense_inv && !c.opt.fine_blocks) autotune_fine_sym(c, c.hu[0]);
     for (auto* H : {&c.hu, &c.hpi})
       for (size_t l = 0; l < H->size(); ++l) {
         Level& L = (*H)[l];
-        if (L.faces || L.dense_inv || (H == &c.hu && l == 0)) continue;
+        if (L.faces || L.dense_inv || (H == &c.hu && l == 0) || c.opt.schedule) continue;
         if (c.opt.precision == 1) autotune_level<float>(c, L);
         else autotune_level<double>(c, L);
       }
+  }
+  // schedules forced by the options
+  if (c.opt.fine_blocks && c.opt.precision == 1 && !c.hu[0].dense_inv) c.hu[0].tpp = c.opt.fine_blocks;
+  if (c.opt.schedule)
+    for (auto* H : {&c.hu, &c.hpi})
+      for (size_t l = 0; l < H->size(); ++l) {
+        Level& L = (*H)[l];
+        if (!L.faces && !L.dense_inv && !(H == &c.hu && l == 0)) L.tpp = c.opt.schedule;
+      }
+}
+
+// The interface-pressure hierarchy after a permeability update: C~_pi has
+// new values on the same pattern, so every level keeps its size, buffers
+// and launch schedule; the diagonal inverses, lmax, prolongators, Galerkin
+// products, dense coarsest inverse and FP32 copies are recomputed in place.
+void rebuild_pi_hierarchy(Ctx& c) {
+  auto& H = c.hpi;
+  if (H.size() == 1) {
+    make_dense_coarse(c, H[0]);
+  } else {
+    finish_level(c, H[0]);
+    Level& L1 = H[1];
+    k_rap_faces<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(FaceTopo{c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy},
+                                                           c.ell_col, c.Cpi, c.pw, L1.A.val, L1.active);
+    MHFP_LAUNCH_CHECK();
+    for (size_t l = 1; l + 1 < H.size(); ++l) {
+      finish_level(c, H[l]);
+      H[l + 1] = coarsen(c, H[l], &H[l + 1]);
+    }
+    make_dense_coarse(c, H.back());
+  }
+  if (c.opt.precision == 1) {
+    auto recast = [&](float* dst, const double* src, size_t n) {
+      k_cast_f32<<<grid_for((long long)n, 256), 256, 0, c.stream>>>((long long)n, src, dst);
+      MHFP_LAUNCH_CHECK();
+    };
+    for (Level& L : H) {
+      const size_t bs2 = (size_t)L.bs * L.bs;
+      if (!L.faces && L.valf) recast(L.valf, L.A.val, (size_t)L.A.noff() * bs2 * L.A.N);
+      if (L.dinv && L.dinvf) recast(L.dinvf, L.dinv, bs2 * L.npts);
+      if (L.P && L.Pf) {
+        const int ns = p_slots(L.R);
+        recast(L.Pf, L.P, (size_t)ns * ns * ns * bs2 * L.npts);
+      }
+    }
+    recast(c.Cpif, c.Cpi, (size_t)11 * c.nF);
+    recast(c.pwf, c.pw, c.nF);
   }
 }
 
@@ -1754,6 +1836,33 @@ void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x) {
 
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y) {
   level_spmv_t<double>(c, H[l], x, nullptr, y);
+}
+
+namespace {
+__global__ void k_narrow(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+__global__ void k_widen(long long n, const float* __restrict__ x, double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)x[i];
+}
+}  // namespace
+
+// One V-cycle in the precision of the solve: FP64 directly, or, with
+// precision 1, the FP32 cycle on b rounded to FP32 (the FP32 work vectors of
+// the whole system, c.tf and c.zf, hold b and x).
+void vcycle_api(Ctx& c, std::vector<Level>& H, const double* b, double* x) {
+  if (c.opt.precision != 1) {
+    vcycle(c, H, b, x);
+    return;
+  }
+  const long long n = H[0].n;
+  k_narrow<<<grid_for(n, 256), 256, 0, c.stream>>>(n, b, c.tf);
+  MHFP_LAUNCH_CHECK();
+  vcycle(c, H, (const float*)c.tf, c.zf);
+  k_widen<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.zf, x);
+  MHFP_LAUNCH_CHECK();
 }
 
 }  // namespace mhfp

@@ -135,6 +135,8 @@ void mhfp_default_options(mhfp_options* o) {
   o->graphs = 2;
   o->autotune = 1;
   o->reorth = 1;
+  o->schedule = 0;
+  o->fine_blocks = 0;
 }
 
 const char* mhfp_status_string(mhfp_status s) {
@@ -230,7 +232,10 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
       if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
           !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
           (opt->precision != 0 && opt->precision != 1) || (opt->graphs < 0 || opt->graphs > 2) ||
-          (opt->autotune != 0 && opt->autotune != 1) || (opt->reorth != 0 && opt->reorth != 1))
+          (opt->autotune != 0 && opt->autotune != 1) || (opt->reorth != 0 && opt->reorth != 1) ||
+          (opt->schedule != 0 && opt->schedule != 1 && opt->schedule != 4 && opt->schedule != 8 &&
+           opt->schedule != 16) ||
+          (opt->fine_blocks != 0 && opt->fine_blocks != 6 && opt->fine_blocks != 8))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }
@@ -331,7 +336,7 @@ mhfp_status mhfp_vcycle(mhfp_handle h, int which, const double* d_b, double* d_x
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (which != 0 && which != 1) throw Error{MHFP_ERR_ARG, "which must be 0 or 1"};
     if (!d_b || !d_x || d_b == d_x) throw Error{MHFP_ERR_ARG, "bad vectors"};
-    mhfp::vcycle(c, which == 0 ? c.hu : c.hpi, d_b, d_x);
+    mhfp::vcycle_api(c, which == 0 ? c.hu : c.hpi, d_b, d_x);
   });
 }
 
@@ -406,6 +411,18 @@ mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launche
     if (total_ms) *total_ms = c.timing.total_ms[kernel_class];
     if (bytes_per_launch)
       *bytes_per_launch = c.timing.launches[kernel_class] ? c.timing.bytes[kernel_class] / c.timing.launches[kernel_class] : 0.0;
+  });
+}
+
+mhfp_status mhfp_update_logk(mhfp_handle h, const double* d_logk) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
+    if (!d_logk) throw Error{MHFP_ERR_ARG, "bad log-permeability vector"};
+    mhfp::update_logk_blocks(c, d_logk);  // validates before changing anything
+    mhfp::invalidate_graphs(c);
+    mhfp::rebuild_pi_hierarchy(c);
+    if (c.opt.precision == 1) mhfp::make_fp32_blocks(c);
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
   });
 }
 

@@ -919,24 +919,90 @@ void assemble_all(Ctx& c) {
   if (hflag & 2) throw Error{MHFP_ERR_MESH, "RT0 element mass matrix is not positive definite"};
 }
 
+// B~_p, A_ppi, the face operators A_pipi and C~_pi and the equilibration.
+// Buffers are allocated on the first call; a later call (after a
+// permeability update) recomputes every entry in place.
 void build_preconditioner_blocks(Ctx& c) {
   const Dims d = dims_of(c);
-  c.btilde = dalloc_n<double>(c, c.nT);
-  c.ApPi = dalloc_n<double>(c, (size_t)6 * c.nT);
+  if (!c.btilde) c.btilde = dalloc_n<double>(c, c.nT);
+  if (!c.ApPi) c.ApPi = dalloc_n<double>(c, (size_t)6 * c.nT);
   k_btilde<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.Auu.val, c.Aup, c.Seps, c.vol, c.stabc, c.sW, c.W1,
                                                       c.face_bc, c.dt, c.btilde, c.ApPi);
   MHFP_LAUNCH_CHECK();
-  c.ell_col = dalloc_n<int>(c, (size_t)11 * c.nF);
-  c.Apipi = dalloc_n<double>(c, (size_t)11 * c.nF);
-  c.Cpi = dalloc_n<double>(c, (size_t)11 * c.nF);
-  c.pw = dalloc_n<double>(c, c.nF);
+  if (!c.ell_col) {
+    c.ell_col = dalloc_n<int>(c, (size_t)11 * c.nF);
+    c.Apipi = dalloc_n<double>(c, (size_t)11 * c.nF);
+    c.Cpi = dalloc_n<double>(c, (size_t)11 * c.nF);
+    c.pw = dalloc_n<double>(c, c.nF);
+  }
   k_face_ell<<<grid_for(c.nF, 128), 128, 0, c.stream>>>(d, c.W, c.W1, c.btilde, c.face_bc, c.dt, c.ell_col, c.Apipi,
                                                         c.Cpi, c.pw);
   MHFP_LAUNCH_CHECK();
-  c.ds = dalloc_n<double>(c, c.n);
-  c.ds_inv = dalloc_n<double>(c, c.n);
+  if (!c.ds) {
+    c.ds = dalloc_n<double>(c, c.n);
+    c.ds_inv = dalloc_n<double>(c, c.n);
+  }
   k_scalings<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.btilde, c.Cpi, c.ds, c.ds_inv);
   MHFP_LAUNCH_CHECK();
+}
+
+namespace {
+// kappa_ratio[3T + q] = kappa[3T + q] / kappa[3T] (the anisotropy the
+// permeability update keeps)
+__global__ void k_kappa_ratio(long long nT, const double* __restrict__ kappa, double* __restrict__ ratio) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nT) return;
+  const double k0 = kappa[3 * t];
+  for (int q = 0; q < 3; ++q) ratio[3 * t + q] = kappa[3 * t + q] / k0;
+}
+
+// kappa_T = exp(logk_T) * ratio_T.  Pass 0 only checks (a non-finite or
+// non-positive result sets flag bit 4); pass 1, run when no cell failed,
+// writes.
+__global__ void k_set_kappa(long long nT, const double* __restrict__ logk, const double* __restrict__ ratio,
+                            double* __restrict__ kappa, int* __restrict__ flag, int write) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nT) return;
+  const double s = exp(logk[t]);
+  double k[3];
+  bool ok = isfinite(s) && s > 0.0;
+  for (int q = 0; q < 3; ++q) {
+    k[q] = s * ratio[3 * t + q];
+    ok = ok && isfinite(k[q]) && k[q] > 0.0;
+  }
+  if (!ok) atomicOr(flag, 4);
+  if (write && ok)
+    for (int q = 0; q < 3; ++q) kappa[3 * t + q] = k[q];
+}
+}  // namespace
+
+// New per-cell log-permeability: kappa_T = exp(logk_T) times the cell's
+// create-time anisotropy ratios, then the RT0 condensation (W_T, W_T 1,
+// 1^T W_T 1, Abar_pp) and the preconditioner blocks recomputed in place.
+// A_uu, A_up, |T| and the stabilization do not depend on kappa.
+void update_logk_blocks(Ctx& c, const double* logk) {
+  const Dims d = dims_of(c);
+  if (!c.kappa_ratio) {
+    c.kappa_ratio = dalloc_n<double>(c, (size_t)3 * c.nT);
+    k_kappa_ratio<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(c.nT, c.kappa, c.kappa_ratio);
+    MHFP_LAUNCH_CHECK();
+  }
+  MHFP_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+  k_set_kappa<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(c.nT, logk, c.kappa_ratio, c.kappa, c.d_flag, 0);
+  MHFP_LAUNCH_CHECK();
+  int hflag = 0;
+  MHFP_CUDA(cudaMemcpyAsync(&hflag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  if (hflag & 4) throw Error{MHFP_ERR_ARG, "log-permeability gives a non-finite or non-positive permeability"};
+  k_set_kappa<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(c.nT, logk, c.kappa_ratio, c.kappa, c.d_flag, 1);
+  MHFP_LAUNCH_CHECK();
+  k_rt0<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.coords, c.mu, c.kappa, c.Seps, c.vol, c.dt, c.W, c.W1, c.sW,
+                                                   c.Abar, c.d_flag);
+  MHFP_LAUNCH_CHECK();
+  MHFP_CUDA(cudaMemcpyAsync(&hflag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  if (hflag & 2) throw Error{MHFP_ERR_MESH, "RT0 element mass matrix is not positive definite"};
+  build_preconditioner_blocks(c);
 }
 
 void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs) {
@@ -1043,18 +1109,18 @@ __global__ void k_cast_blocks(long long n, const double* __restrict__ x, float* 
 }
 
 // FP32 copies of the blocks the mixed-precision preconditioner reads
+// (allocated on the first call, overwritten in place afterwards)
 void make_fp32_blocks(Ctx& c) {
-  auto cast = [&](const double* src, long long n) {
-    float* d = dalloc_n<float>(c, n);
-    k_cast_blocks<<<grid_for(n, 256), 256, 0, c.stream>>>(n, src, d);
+  auto cast = [&](float*& dst, const double* src, long long n) {
+    if (!dst) dst = dalloc_n<float>(c, n);
+    k_cast_blocks<<<grid_for(n, 256), 256, 0, c.stream>>>(n, src, dst);
     MHFP_LAUNCH_CHECK();
-    return d;
   };
-  c.ApPif = cast(c.ApPi, 6 * c.nT);
-  c.btildef = cast(c.btilde, c.nT);
-  c.Aupf = cast(c.Aup, 24 * c.nT);
-  c.tf = dalloc_n<float>(c, c.n);
-  c.zf = dalloc_n<float>(c, c.n);
+  cast(c.ApPif, c.ApPi, 6 * c.nT);
+  cast(c.btildef, c.btilde, c.nT);
+  cast(c.Aupf, c.Aup, 24 * c.nT);
+  if (!c.tf) c.tf = dalloc_n<float>(c, c.n);
+  if (!c.zf) c.zf = dalloc_n<float>(c, c.n);
 }
 
 }  // namespace mhfp

@@ -322,6 +322,15 @@ struct Ctx {
   double* btilde = nullptr; // [nT]
   double* ds = nullptr;     // [n] equilibration D_s
   double* ds_inv = nullptr; // [n] its inverse (multiplies instead of FP64 divisions)
+  double* kappa_ratio = nullptr;  // [3][nT] create-time kappa_q / kappa_0 (permeability updates)
+  // persistent scratch of the interface-pressure hierarchy rebuild
+  // (permeability updates): Galerkin Q and the Gauss-Jordan workspace
+  double* upd_Q = nullptr;
+  size_t upd_Q_elems = 0;
+  double *gj_A = nullptr, *gj_M = nullptr, *gj_prow = nullptr, *gj_fcol = nullptr;
+  int* gj_err = nullptr;
+  int gj_n = 0;
+  cudaGraphConditionalHandle* d_hif[2] = {nullptr, nullptr};  // IF handles of the solve graphs
 
   std::vector<Level> hu, hpi;
   // FP32 copies used by the mixed-precision preconditioner
@@ -404,12 +413,21 @@ void misfit(Ctx& c, const double* x, const double* uzt, const double* pt, double
 void adjoint_rhs(Ctx& c, const double* g, const double* lam_next, double* rhs);
 void ensure_workspace(Ctx& c);
 void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out);
+void update_logk_blocks(Ctx& c, const double* logk);
+
+// amg.cu: the interface-pressure hierarchy and the FP32 copies rebuilt in
+// place after a permeability update (same levels, same schedules)
+void rebuild_pi_hierarchy(Ctx& c);
+// krylov.cu: drop the captured CUDA graphs (their kernel arguments hold the
+// old Chebyshev coefficients); the next solve captures them again
+void invalidate_graphs(Ctx& c);
 
 // amg.cu
 void build_hierarchies(Ctx& c);
 void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x);
 void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x);
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y);
+void vcycle_api(Ctx& c, std::vector<Level>& H, const double* b, double* x);  // in the solve's precision
 
 // krylov.cu
 void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st, bool transpose = false);

@@ -841,7 +841,9 @@ void build_solve_graph(Ctx& c, bool transpose) {
   cudaGraphNode_t wnode = add_conditional(G, last, hw, cudaGraphCondTypeWhile, &W);
   std::vector<cudaGraphConditionalHandle> hif(m);
   for (int j = 0; j < m; ++j) MHFP_CUDA(cudaGraphConditionalHandleCreate(&hif[j], W, 0, 0));
-  cudaGraphConditionalHandle* d_hif = dalloc_n<cudaGraphConditionalHandle>(c, m);
+  const int ti = transpose ? 1 : 0;
+  if (!c.d_hif[ti]) c.d_hif[ti] = dalloc_n<cudaGraphConditionalHandle>(c, m);
+  cudaGraphConditionalHandle* d_hif = c.d_hif[ti];
   MHFP_CUDA(cudaMemcpy(d_hif, hif.data(), m * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice));
   // while body: the cycle
   const long long l1 = g_launches;
@@ -893,6 +895,22 @@ void build_solve_graph(Ctx& c, bool transpose) {
 }
 
 }  // namespace
+
+void invalidate_graphs(Ctx& c) {
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  for (int t = 0; t < 2; ++t) {
+    for (auto& g : c.graphs[t]) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (auto& p : g.timed) {
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
+      }
+    }
+    c.graphs[t].clear();
+    if (c.solve_exec[t]) cudaGraphExecDestroy(c.solve_exec[t]);
+    c.solve_exec[t] = nullptr;
+  }
+}
 
 void solve_device_graph_launch(Ctx& c, const double* b, double tol, bool transpose) {
   const int t = transpose ? 1 : 0;

@@ -180,3 +180,73 @@ def test_adjoint_workload_48_cubed():
         lm[T] -= h
         fd = (mg.value(lp) - mg.value(lm)) / (2 * h)
         assert np.isclose(g[T], fd, rtol=1e-4), (T, g[T], fd)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_update_logk_in_place(precision):
+    """mhfp_update_logk on a handle that has already solved (and captured its
+    solve graphs) gives bit-identical operator, M^-1, solutions and iteration
+    counts to the same update on a freshly set-up handle; both agree with a
+    handle created from the new permeability (computed on the host) and with
+    the oracle's direct solution; a non-finite log-permeability is rejected
+    and leaves the handle unchanged."""
+    from paper_2002_09603_gb300 import MhfpError, Solver, default_options
+    from paper_2002_09603_gb300.adjoint import _with_logk
+    prob = mi.random_small(6, 5, 4, seed=41, jitter=0.1, dt=0.05)
+    rng = np.random.default_rng(7)
+    logk = np.log(prob.kappa[:, 0]) + rng.normal(0.0, 1.0, prob.n_cells)
+    opt = default_options()
+    opt.precision = precision
+
+    def handle(p):
+        s = Solver(p)
+        s.assemble_condense()
+        s.setup_precond(opt)
+        return s
+
+    used = handle(prob)
+    x0, _ = used.solve(used.build_rhs(), tol=1e-10)          # captures the solve graph
+    used.adjoint_solve(used.build_rhs(), tol=1e-10)
+    lmax_before = used.hierarchy(1)["lmax"]
+    fresh = handle(prob)
+    t = _cuda(logk)
+    used.update_logk(t)
+    fresh.update_logk(t)
+    host = handle(_with_logk(prob, logk))
+    assert used.hierarchy(1)["lmax"] != lmax_before
+    assert np.allclose(used.hierarchy(1)["lmax"], host.hierarchy(1)["lmax"], rtol=1e-11)
+    v = _cuda(rng.standard_normal(used.n))
+    outs = {}
+    for name, s in (("used", used), ("fresh", fresh), ("host", host)):
+        b = s.build_rhs(x0)
+        x, st = s.solve(b, tol=1e-10)
+        lam, sta = s.adjoint_solve(b, tol=1e-10)
+        outs[name] = dict(y=s.apply_operator(v), z=s.apply_precond(v), x=x, it=st["iterations"],
+                          lam=lam, ita=sta["iterations"], ds=s.scalings()[1])
+    for k in ("y", "z", "x", "lam", "ds"):
+        assert torch.equal(outs["used"][k], outs["fresh"][k]), k
+    assert outs["used"]["it"] == outs["fresh"]["it"] and outs["used"]["ita"] == outs["fresh"]["ita"]
+    # against a handle built from the host-computed permeability (exp may
+    # differ in the last bit) and the oracle
+    Bq = oracle.assemble(_with_logk(prob, logk))
+    yref = system.system_matrix(Bq) @ v.cpu().numpy()
+    for name in ("used", "host"):
+        y = outs[name]["y"].cpu().numpy()
+        assert np.abs(y - yref).max() <= 1e-12 * np.abs(yref).max()
+    zt = 1e-10 if precision == 0 else 1e-5
+    zu, zh = outs["used"]["z"].cpu().numpy(), outs["host"]["z"].cpu().numpy()
+    assert np.abs(zu - zh).max() <= zt * np.abs(zh).max()
+    assert abs(outs["used"]["it"] - outs["host"]["it"]) <= 1
+    nU, nP, _ = Bq.sizes
+    xc = x0.cpu().numpy()
+    xd = oracle.solve_direct(Bq, system.rhs(Bq, xc[:nU], xc[nU:nU + nP]))
+    xu = outs["used"]["x"].cpu().numpy()
+    assert np.linalg.norm(xu - xd) <= 1e-7 * np.linalg.norm(xd)
+    # rejected update: nothing changes
+    bad = logk.copy()
+    bad[3] = np.nan
+    with pytest.raises(MhfpError):
+        used.update_logk(_cuda(bad))
+    assert torch.equal(used.apply_operator(v), outs["used"]["y"])
+    for s in (used, fresh, host):
+        s.close()

@@ -474,3 +474,72 @@ def test_coarse_limit_512_against_oracle():
         assert st["converged"] and st["true_rel_residual"] <= 1.05e-10
         assert _energy(B, pc, x.cpu().numpy() - xd) <= 1e-8 * _energy(B, pc, xd)
         s.close()
+
+
+# --------------------------------------------- every launch schedule, forced
+SCHED_CASE = {}
+
+
+def _sched_case():
+    """16^3 jittered heterogeneous box: the displacement hierarchy has a
+    coarse 6^3 lattice level with sweeps (3x3 blocks, 27-point stencil), the
+    interface-pressure one a 16^3 cell level (25-point stencil) and a 6^3
+    level (125-point stencil), so every coarse-sweep kernel kind runs."""
+    if not SCHED_CASE:
+        prob = mi.random_small(16, 16, 16, seed=31, jitter=0.15)
+        B = oracle.assemble(prob)
+        pc = precond.build(B, "amg")
+        assert [lv.dims for lv in pc.u_levels] == [(17, 17, 17), (6, 6, 6), (2, 2, 2)]
+        assert [lv.dims for lv in pc.pi_levels][1:] == [(16, 16, 16), (6, 6, 6), (2, 2, 2)]
+        SCHED_CASE.update(prob=prob, B=B, pc=pc)
+    return SCHED_CASE["prob"], SCHED_CASE["B"], SCHED_CASE["pc"]
+
+
+@pytest.mark.parametrize("precision,schedule,fine_blocks",
+                         [(0, 1, 0), (0, 4, 0), (0, 8, 0), (0, 16, 0),
+                          (1, 1, 6), (1, 4, 8), (1, 8, 6), (1, 16, 8)])
+def test_forced_schedules_match_oracle(precision, schedule, fine_blocks):
+    """Each launch schedule of the coarse-level sweeps and residuals (one
+    point per thread, or the stencil offsets split over 4, 8 or 16 warps) and
+    each occupancy variant of the finest FP32 displacement sweep, forced
+    through mhfp_options, gives the oracle's V-cycles and M^-1 element by
+    element: 1e-10 in FP64, 1e-5 in FP32 (relative to the largest entry)."""
+    from paper_2002_09603_gb300 import Solver, default_options
+    prob, B, pc = _sched_case()
+    opt = default_options()
+    opt.precision = precision
+    opt.schedule = schedule
+    opt.fine_blocks = fine_blocks
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    hu, hpi = s.hierarchy(0), s.hierarchy(1)
+    assert hu["schedule"][1] == schedule and hpi["schedule"][1:3] == [schedule, schedule]
+    if precision == 1:
+        assert hu["schedule"][0] == fine_blocks
+    tol = 1e-10 if precision == 0 else 1e-5
+    rng = np.random.default_rng(40 + schedule)
+    nU, nP, nPi = B.sizes
+    bu, bpi = rng.standard_normal(nU), rng.standard_normal(nPi)
+    xu = s.vcycle(0, torch.from_numpy(bu).cuda()).cpu().numpy()
+    xpi = s.vcycle(1, torch.from_numpy(bpi).cuda()).cpu().numpy()
+    ru, rpi = precond.vcycle(pc.u_levels, bu), precond.vcycle(pc.pi_levels, bpi)
+    assert np.abs(xu - ru).max() <= tol * np.abs(ru).max()
+    assert np.abs(xpi - rpi).max() <= tol * np.abs(rpi).max()
+    v = rng.standard_normal(s.n)
+    z = s.apply_precond(torch.from_numpy(v).cuda()).cpu().numpy()
+    _blockwise_close(z, pc.apply(v), B.sizes, tol)
+    s.close()
+
+
+def test_invalid_schedule_options_are_rejected():
+    from paper_2002_09603_gb300 import MhfpError, Solver, default_options
+    prob = mi.random_small(3, 3, 3, seed=2)
+    for field, value in (("schedule", 3), ("schedule", 32), ("fine_blocks", 7)):
+        opt = default_options()
+        setattr(opt, field, value)
+        s = Solver(prob)
+        s.assemble_condense()
+        with pytest.raises(MhfpError):
+            s.setup_precond(opt)
+        s.close()
