@@ -12,13 +12,20 @@ written out plainly:
   the six rigid-body modes (three translations, three rotations about the
   mesh centroid), with the rows of prescribed dofs zeroed;
 * aggregates: 3x3x3 boxes of lattice points (as in the M_II^(h) spec);
-* tentative prolongator: on each aggregate the rank-revealing (column-
-  pivoted) thin QR factorisation of N restricted to the aggregate's dofs,
-  N_K = Q_K R_K, keeping the leading r columns whose |R_ii| exceeds 1e-10
-  of the largest; Q_K becomes the aggregate's block of P_t and R_K (with its
-  columns back in mode order) the coarse near-kernel of the coarse point K,
-  so a coarse point carries up to six dofs (fewer where prescribed
-  displacements leave the aggregate fewer rigid motions);
+* tentative prolongator: on each aggregate the thin QR factorisation of N
+  restricted to the aggregate's dofs, N_K = Q_K R_K, by classical Gram-
+  Schmidt applied twice in mode order (translations x, y, z, then rotations
+  about x, y, z) with a non-negative diagonal of R_K; a mode whose norm
+  after orthogonalisation is at most 1e-10 of its norm before (or zero) is
+  one the aggregate cannot represent (prescribed displacements, or too few
+  points, leave it fewer rigid motions): its column of Q_K is zero.  Q_K
+  becomes the aggregate's block of P_t and R_K the coarse near-kernel of
+  the coarse point K.  Every coarse point carries six dofs; a dof whose
+  column is zero has no fine support and gets a unit diagonal on the
+  coarse level, as the M_II^(h) spec does for a coarse dof with no free
+  fine dof (reading: GAMG is named, not defined; without pivoting the
+  factorisation is unique, and a fixed block size keeps the coarse levels
+  lattice operators);
 * P = (I - omega D^-1 A) P_t with D the point-block diagonal and
   omega = 4 / (3 lmax), lmax = 1.1 rho(D^-1 A) by 15 power iterations from
   the same start vector as M_II^(h);
@@ -32,12 +39,12 @@ from __future__ import annotations
 from dataclasses import dataclass
 
 import numpy as np
-import scipy.linalg as sla
 import scipy.sparse as sp
 
 from . import precond
 
 QR_DROP = 1e-10
+NK = 6   # dofs per coarse point: the six rigid-body modes
 
 
 def rigid_body_modes(coords: np.ndarray, free: np.ndarray | None = None) -> np.ndarray:
@@ -100,42 +107,55 @@ def _finish(lev: RLevel):
     lev.lmax = 1.1 * rho
 
 
+def gram_schmidt_modes(NK: np.ndarray):
+    """Thin QR of the aggregate's near-kernel block NK (rows x 6) by
+    classical Gram-Schmidt applied twice, columns in mode order, R with a
+    non-negative diagonal; a column left with at most QR_DROP of its norm is
+    dropped (zero column of Q, zero row of R).  Returns Q, R, kept."""
+    m, k = NK.shape
+    Q = np.zeros((m, k))
+    R = np.zeros((k, k))
+    kept = np.zeros(k, bool)
+    for j in range(k):
+        v = NK[:, j].copy()
+        n0 = np.linalg.norm(v)
+        for _ in range(2):
+            h = Q[:, :j].T @ v
+            v -= Q[:, :j] @ h
+            R[:j, j] += h
+        nv = np.linalg.norm(v)
+        if n0 > 0.0 and nv > QR_DROP * n0:
+            Q[:, j] = v / nv
+            R[j, j] = nv
+            kept[j] = True
+    return Q, R, kept
+
+
 def _tentative(lev: RLevel, N: np.ndarray):
-    """P_t, the coarse points' dof lists, the coarse near-kernel and dims."""
+    """P_t, the coarse points' dof lists, the coarse near-kernel, the coarse
+    dofs with fine support (kept modes) and the coarse lattice dims."""
     agg, cdims = precond.aggregate_map(lev.dims)
     nc_pts = cdims[0] * cdims[1] * cdims[2]
     members = [[] for _ in range(nc_pts)]
     for p, K in enumerate(agg):
         members[K].append(p)
     rows, cols, vals = [], [], []
-    cpts, Nc_blocks = [], []
-    nxt = 0
+    Nc = np.zeros((NK * nc_pts, NK))
+    active = np.zeros(NK * nc_pts, bool)
     for K in range(nc_pts):
-        dofs = np.concatenate([np.asarray(lev.pts[p], dtype=np.int64) for p in members[K]]) if members[K] else \
-            np.zeros(0, np.int64)
-        NK = N[dofs] if len(dofs) else np.zeros((0, N.shape[1]))
-        keep_rows = np.abs(NK).sum(axis=1) > 0.0
-        dofs, NK = dofs[keep_rows], NK[keep_rows]
-        if len(dofs) == 0:
-            cpts.append(np.zeros(0, np.int64))
-            continue
-        Q, R, piv = sla.qr(NK, mode="economic", pivoting=True)
-        d = np.abs(np.diag(R))
-        q = int(np.sum(d > QR_DROP * d.max()))
-        Q = Q[:, :q]
-        Rk = np.zeros((q, NK.shape[1]))
-        Rk[:, piv] = R[:q, :]
-        R = Rk
-        rr, cc = np.meshgrid(dofs, nxt + np.arange(q), indexing="ij")
+        dofs = np.concatenate([np.asarray(lev.pts[p], dtype=np.int64) for p in members[K]])
+        Q, R, kept = gram_schmidt_modes(N[dofs])
+        rr, cc = np.meshgrid(dofs, NK * K + np.arange(NK), indexing="ij")
         rows.append(rr.ravel())
         cols.append(cc.ravel())
         vals.append(Q.ravel())
-        cpts.append(nxt + np.arange(q))
-        Nc_blocks.append(R)
-        nxt += q
+        Nc[NK * K:NK * K + NK] = R
+        active[NK * K:NK * K + NK] = kept
     Pt = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                       shape=(lev.A.shape[0], nxt))
-    return Pt, cpts, np.vstack(Nc_blocks), cdims
+                       shape=(lev.A.shape[0], NK * nc_pts))
+    Pt.eliminate_zeros()
+    cpts = [np.arange(NK * K, NK * K + NK) for K in range(nc_pts)]
+    return Pt, cpts, Nc, active, cdims
 
 
 def build_u_hierarchy(B, coarse_max=precond.COARSE_MAX):
@@ -147,12 +167,14 @@ def build_u_hierarchy(B, coarse_max=precond.COARSE_MAX):
     levels = [lev]
     while dims[0] * dims[1] * dims[2] > coarse_max:
         _finish(lev)
-        Pt, cpts, Nc, dims = _tentative(lev, N)
+        Pt, cpts, Nc, active, dims = _tentative(lev, N)
         omega = 4.0 / (3.0 * lev.lmax)
         P = (Pt - omega * (lev.Dm @ (lev.A @ Pt))).tocsr()
         lev.Pt, lev.P = Pt, P
         Ac = (P.T @ lev.A @ P).tocsr()
         Ac = (0.5 * (Ac + Ac.T)).tocsr()  # exact in real arithmetic; removes rounding asymmetry
+        Ac = (Ac + sp.diags(np.where(active, 0.0, 1.0))).tocsr()
+        Ac.sum_duplicates()
         lev = RLevel(Ac, cpts, dims)
         N = Nc
         levels.append(lev)

@@ -578,11 +578,20 @@ def test_m3_tentative_prolongator_reproduces_the_rigid_body_modes():
     lev = rbm.RLevel(B.Auu.tocsr(), [np.arange(3 * q, 3 * q + 3) for q in range(B.mesh.n_nodes)],
                      (8, 7, 9))
     N = rbm.rigid_body_modes(B.mesh.coords, ~B.u_fixed)
-    Pt, cpts, Nc, cdims = rbm._tentative(lev, N)
-    assert cdims == (3, 3, 3) and len(cpts) == 27
+    Pt, cpts, Nc, active, cdims = rbm._tentative(lev, N)
+    assert cdims == (3, 3, 3) and len(cpts) == 27 and Pt.shape[1] == 6 * 27
     G = (Pt.T @ Pt).toarray()
-    assert np.abs(G - np.eye(G.shape[0])).max() <= 1e-12
-    assert np.abs(Pt @ Nc - N).max() <= 1e-12 * np.abs(N).max()
+    assert np.abs(G - np.diag(active.astype(float))).max() <= 1e-12
+    assert np.abs(Pt @ Nc - N).max() <= 1e-10 * np.abs(N).max()
+    # the 1-node-thick aggregates on the y = 1 rollers (u_y fixed) cannot
+    # move along y: their translation-y dof has no fine support
+    assert not active.all() and active.sum() >= 6 * 18
+    # no pivoting: the factorisation is the Gram-Schmidt one, so R_K is upper
+    # triangular with a non-negative diagonal and Q_K's kept columns span
+    # the modes in order
+    for K in range(27):
+        R = Nc[6 * K:6 * K + 6]
+        assert np.allclose(np.tril(R, -1), 0.0) and np.all(np.diag(R) >= 0)
 
 
 def test_m3_vcycle_is_a_symmetric_contraction_and_fgmres_reaches_the_direct_solution():
