@@ -3,10 +3,13 @@
 poromechanics system (FGMRES + block-triangular multigrid preconditioner,
 FP64) on one GB300, to a 1e-8 relative residual of the equilibrated system.
 
-Default workload: 64^3 unit cube, log-normal permeability (ln kappa ~
-N(ln 1e-13, 2^2), exponential covariance of 8 cells, seed 2), S_eps = 0,
-dt = 1e-3 s, consolidation-column boundaries; 1,884,739 unknowns.  A "step"
-is one time step: right-hand side from the previous state + FGMRES solve.
+Default workload: the largest single-GPU configuration, 128^3 unit cube
+with interior node jitter U(+-0.2h), 8 horizontal layers (kappa log-U
+[1e-18, 1e-12] m^2, E log-U[1e8, 1e10] Pa, nu U[0.2, 0.35]), S_eps = 0,
+dt = 0.1 s, consolidation-column boundaries; 14,877,827 unknowns.  The 64^3
+log-normal workload (1,884,739 unknowns) is measured in the same run and
+reported inside config.  A "step" is one time step: right-hand side from
+the previous state + FGMRES solve.
 The operator and the preconditioner are built once (constant dt), timed
 separately as setup_ms.
 
@@ -33,11 +36,17 @@ METRIC = "time-to-solve per step to 1e-8 rel. residual"
 TOL = 1e-8
 FALLBACK_HBM_GBS = 6800.0
 
+# gpu_iters: FGMRES iterations per step the GPU solve takes on the workload
+# (measured; the CPU legs scale their samples to it, the oracle being the
+# same algorithm)
 WORKLOADS = {
-    "lognormal64": dict(n=64, restart=12, desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
-    "lognormal32": dict(n=32, desc="32^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
-    "lognormal96": dict(n=96, desc="96^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
-    "layered128": dict(n=128, gen="layered", restart=20,
+    "lognormal64": dict(n=64, restart=12, gpu_iters=32,
+                        desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "lognormal32": dict(n=32, gpu_iters=28,
+                        desc="32^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "lognormal96": dict(n=96, gpu_iters=36,
+                        desc="96^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
+    "layered128": dict(n=128, gen="layered", restart=20, gpu_iters=54,
                        desc="128^3 hex, interior node jitter U(+-0.2h), 8 z-layers: kappa log-U[1e-18,1e-12] m^2, "
                             "E log-U[1e8,1e10] Pa, nu U[0.2,0.35]; S_eps=0, dt=0.1 s (seed 3)"),
     "batch48": dict(n=0, desc="48 cubes n ~ U{16..64} (seed 4), own log-normal kappa (sigma 1.5), loads x0.5/1/2/4, "
@@ -60,9 +69,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lognormal64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="layered128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-64", action="store_true", help="skip the 64^3 workload measured beside the 128^3 one")
     ap.add_argument("--restart", type=int, default=None,
                     help="FGMRES restart length (default: the fastest measured for the workload, 12 at 64^3, "
                          "20 at 128^3)")
@@ -74,8 +84,6 @@ def parse():
                          "residuals on the workloads), 1 DGKS reorthogonalisation when needed")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="both: mixed headline with FP64-plain beside it (default)")
-    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
-    ap.add_argument("--oracle-target", type=str, default="", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.restart is None:
         args.restart = WORKLOADS[args.workload].get("restart", 12)
@@ -86,18 +94,107 @@ SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_N
                      "NUMEXPR_NUM_THREADS": "1"}
 
 
-def oracle_sample_subprocess(workload, n_target_dofs, gpu_iters, sample_n=32):
-    """Run the oracle sample in a fresh interpreter pinned to one BLAS/OpenMP
-    thread (so the reported core count is exact), not forked from this
-    CUDA process."""
-    env = dict(os.environ, **SINGLE_THREAD_ENV)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", workload,
-                        "--oracle-sample", str(sample_n),
-                        "--oracle-target", f"{n_target_dofs},{gpu_iters}"], env=env, capture_output=True,
-                       text=True, timeout=600)
-    if r.returncode != 0:
-        return {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker(workload, sample_n, seed_shift, nsteps, barrier, out):
+    """One host core's share of the oracle leg: the workload's generator at
+    sample_n^3 (assembly and preconditioner set-up untimed), then `nsteps`
+    backward-Euler steps, each started at the shared barrier and timed."""
+    for k, v in SINGLE_THREAD_ENV.items():
+        os.environ[k] = v
+    import oracle
+    from oracle import fgmres, precond, system
+    prob = make_problem(workload, sample_n)
+    B = oracle.assemble(prob)
+    pc = precond.build(B, "amg", coarse_max=512)
+    A = system.system_matrix(B)
+    sc = precond.equilibration(B, pc.Bt, pc.C)
+    nU, nP, _ = B.sizes
+    n_s = sum(B.sizes)
+    m = WORKLOADS[workload].get("restart", 12)
+    xprev = None
+    for k in range(nsteps):
+        barrier.wait()
+        t0 = time.perf_counter()
+        b = system.rhs(B, None if xprev is None else xprev[:nU], None if xprev is None else xprev[nU:nU + nP])
+        x, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=TOL, restart=m, scale=sc)
+        out.put((seed_shift, k, sample_n, n_s, info["iters"], time.perf_counter() - t0))
+        xprev = x
+
+
+def oracle_leg(workload, samples, nsteps, on_step=None):
+    """Run the oracle as it stands on the host cores: one spawned process
+    per entry of `samples` (a sample size each), all stepping together.
+    Returns per step a list of (sample_n, unknowns, iterations, seconds) and
+    the step's wall time."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(len(samples) + 1)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(workload, n, i, nsteps, barrier, out), daemon=True)
+             for i, n in enumerate(samples)]
+    for p in procs:
+        p.start()
+    steps = []
+    try:
+        for k in range(nsteps):
+            barrier.wait(timeout=900)
+            t0 = time.perf_counter()
+            got = [out.get(timeout=900) for _ in samples]
+            wall = time.perf_counter() - t0
+            steps.append(([g[2:] for g in sorted(got)], wall))
+            if on_step:
+                on_step(k, steps[-1])
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    return steps
+
+
+def full_estimate_ms(workload, step, iters_full):
+    """The oracle's time for one step of the full workload from a step of
+    concurrent samples: every core's rate (unknowns x FGMRES iterations per
+    second) measured while all cores run, summed, and the full workload's
+    unknowns x iterations divided by it (the same rule for both CPU legs;
+    the full workload's iteration count is the GPU's, the same algorithm)."""
+    rate = sum(n_s * it / sec for _, n_s, it, sec in step)
+    n_full = sum(make_problem_sizes(workload))
+    return n_full * iters_full / rate * 1e3
+
+
+def cpu_baseline_leg(workload, iters_full):
+    """cpu_baseline of our arm: one step of the oracle on every host core at
+    the 32^3 sample of the workload's generator, plus one core at 48^3 to
+    check that the cost per unknown and iteration holds as the sample grows."""
+    cores = host_cores()
+    ncore = max(1, min(cores, 16))
+    samples = [48] + [32] * (ncore - 1) if ncore > 1 else [32]
+    t0 = time.perf_counter()
+    (step, wall), = oracle_leg(workload, samples, 1)
+    total = time.perf_counter() - t0
+    per = {}
+    for n_s_mesh, n_s, it, sec in step:
+        per.setdefault(n_s_mesh, []).append((n_s, it, sec))
+    cost = {f"{k}^3": {"unknowns": v[0][0], "iterations": v[0][1],
+                       "us_per_unknown_iteration": 1e6 * statistics.mean(sec / (n_s * it) for n_s, it, sec in v)}
+            for k, v in per.items()}
+    value = full_estimate_ms(workload, step, iters_full)
+    return {"value": value, "unit": "ms", "cores": len(samples), "kind": "oracle",
+            "extrapolated": True,
+            "sample": (f"one backward-Euler step of the workload's generator on each of {len(samples)} host "
+                       f"processes (one per core, one BLAS thread each; {samples.count(32)} at 32^3, "
+                       f"{samples.count(48)} at 48^3), assembly and set-up untimed, {wall:.1f} s of wall time; "
+                       f"the summed per-core rate (unknowns x FGMRES iterations / s) scaled to the full "
+                       f"workload's unknowns x the GPU's {iters_full:.0f} iterations"),
+            "oracle_iterations_in_sample": {k: v["iterations"] for k, v in cost.items()},
+            "cost_per_unknown_iteration": cost, "leg_seconds": total}
 
 
 def measured_peaks():
@@ -153,90 +250,55 @@ def clocks_stop(proc, path):
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(workload, n_target_dofs, gpu_iters, sample_n=32, nsteps=1):
-    """The FP64 oracle (as it stands) on a bounded sample of the workload:
-    `nsteps` time steps of the same generator at sample_n^3 (setup not
-    timed), scaled to the full workload by unknowns x FGMRES iterations."""
-    import oracle
-    from oracle import fgmres, precond, system
-    prob = make_problem(workload, sample_n)
-    B = oracle.assemble(prob)
-    pc = precond.build(B, "amg")
-    A = system.system_matrix(B)
-    sc = precond.equilibration(B, pc.Bt, pc.C)
-    nU, nP, _ = B.sizes
-    n_s = sum(B.sizes)
-    xprev = None
-    secs, iters = [], []
-    for _ in range(nsteps):
-        t0 = time.perf_counter()
-        b = system.rhs(B, None if xprev is None else xprev[:nU], None if xprev is None else xprev[nU:nU + nP])
-        x, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=TOL, scale=sc)
-        secs.append(time.perf_counter() - t0)
-        iters.append(info["iters"])
-        xprev = x
-    per_dof_iter = sum(secs) / (n_s * sum(iters))
-    ms = per_dof_iter * n_target_dofs * gpu_iters * 1e3
-    return dict(value=ms, unit="ms", cores=1, kind="oracle",
-                sample=(f"{nsteps} time step(s) of the same workload generator at {sample_n}^3 ({n_s} unknowns, "
-                        f"{sum(iters)} FGMRES iterations, {sum(secs):.2f} s, setup untimed) on one host core "
-                        f"(scipy.sparse is single-threaded), scaled by unknowns x iterations to the full "
-                        f"workload's {gpu_iters:.1f} iterations"),
-                sample_seconds=sum(secs), sample_iters=iters), secs
-
-
 def run_reference(args):
-    """--impl reference: the oracle timed on the host cores, each step a
-    bounded sample of the workload, scaled to the metric's unit."""
+    """--impl reference: the oracle as it stands on the host cores (one
+    process per core), each step one backward-Euler step of every process's
+    24^3 sample of the workload's generator; the step's time is scaled to the
+    full workload by the rule of full_estimate_ms, with the full workload's
+    iteration count the GPU's measured one for this workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     n_full = sum(make_problem_sizes(args.workload))
-    import oracle
-    from oracle import fgmres, precond, system
-    sample_n = 24
-    prob = make_problem(args.workload, sample_n)
-    B = oracle.assemble(prob)
-    pc = precond.build(B, "amg")
-    A = system.system_matrix(B)
-    sc = precond.equilibration(B, pc.Bt, pc.C)
-    nU, nP, _ = B.sizes
-    n_s = sum(B.sizes)
-    xprev = None
-    per_step = []
-    total_iters = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        b = system.rhs(B, None if xprev is None else xprev[:nU], None if xprev is None else xprev[nU:nU + nP])
-        x, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=TOL, scale=sc)
-        dt = time.perf_counter() - t0
-        xprev = x
-        if k >= args.warmup:
-            per_step.append(dt * n_full / n_s * 1e3)
-            total_iters.append(info["iters"])
+    iters_full = WORKLOADS[args.workload]["gpu_iters"]
+    ncore = max(1, min(host_cores(), 16))
+    samples = [24] * ncore
+    steps = oracle_leg(args.workload, samples, args.warmup + args.steps)
+    timed = steps[args.warmup:]
+    per_step = [full_estimate_ms(args.workload, st, iters_full) for st, _ in timed]
+    walls = [w for _, w in timed]
+    its = sorted({it for st, _ in timed for _, _, it, _ in st})
     ms = sum(per_step) / len(per_step)
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": n_full, "tol": TOL,
                        "parallelism": "replicas"},
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": (f"each step = one time step of the same generator at {sample_n}^3 "
-                                        f"({n_s} unknowns, {total_iters} FGMRES iterations), scaled by unknowns "
-                                        f"to the full workload; one host core")},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": ncore, "kind": "oracle", "extrapolated": True,
+                             "sample": (f"each step = one backward-Euler step on each of {ncore} host processes "
+                                        f"(one per core, one BLAS thread each) of the workload's generator at "
+                                        f"24^3 ({sum(make_problem_sizes_n(args.workload, 24))} unknowns, oracle "
+                                        f"FGMRES iterations {its}), {statistics.mean(walls):.2f} s of wall time "
+                                        f"per step; the summed per-core rate scaled to the full workload's "
+                                        f"{n_full} unknowns x {iters_full} iterations (the GPU's count)"),
+                             "wall_s_per_step": statistics.mean(walls)},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def make_problem_sizes(name):
-    n = WORKLOADS[name]["n"]
+    return make_problem_sizes_n(name, WORKLOADS[name]["n"])
+
+
+def make_problem_sizes_n(name, n):
     return (3 * (n + 1) ** 3, n ** 3, 3 * n * n * (n + 1))
 
 
-def traffic_for(kernel):
-    """dram read+write bytes per launch of `kernel` at the 64^3 workload, from
-    the committed ncu summary, or None if the kernel's source region changed
-    since the counters were taken."""
+def traffic_for(kernel, workload, bytes_per_launch):
+    """DRAM read+write bytes per launch of `kernel` from the committed ncu
+    summary (profiles/traffic.json), scaled to this workload's launch by the
+    ratio of algorithmic bytes when the capture ran on a smaller case; None
+    if there is no capture or the kernel's source region changed since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -250,7 +312,11 @@ def traffic_for(kernel):
     except ValueError:
         return None
     sha = hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
-    return d["bytes_per_launch"] if sha == d["region_sha"] else None
+    if sha != d["region_sha"]:
+        return None
+    if d.get("workload", "lognormal64") == workload or not d.get("algorithmic_bytes"):
+        return d["bytes_per_launch"] if d.get("workload", "lognormal64") == workload else None
+    return d["bytes_per_launch"] * bytes_per_launch / d["algorithmic_bytes"]
 
 
 # FP64 peak of the part: ~2 FP64 FMA per clock per SM (from the pipe
@@ -272,6 +338,83 @@ def cheb_u0_flops(n):
     blocks = (3 * L - 2) ** 3
     nodes = L ** 3
     return 2 * 9 * blocks + 2 * 9 * nodes + 4 * 3 * nodes
+
+
+def operator_flops(n):
+    """Algorithmic FP64 flops of one operator apply A_H x on an n^3 mesh:
+    2 per stored coefficient the three row kernels multiply -- A_uu's valid
+    (node, neighbour) 3x3 blocks, A_up and A_pu (24 per cell each), the
+    p-block (diagonal and three macro partners per cell), A_ppi and A_pip
+    (6 per cell each) and the 11 ELL slots of A_pipi per face."""
+    L = n + 1
+    nT, nF = n ** 3, 3 * n * n * L
+    nnz = 9 * (3 * L - 2) ** 3 + 48 * nT + 4 * nT + 12 * nT + 11 * nF
+    return 2 * nnz
+
+
+# ------------------------------------------------------ step-level bytes
+# Algorithmic HBM bytes of one time step (each stored value, inverse
+# diagonal block and vector touched once per kernel; coarse levels counted
+# the same way although they sit in L2).  Per lattice level of N points
+# with b unknowns per point, K stencil offsets and s bytes per value:
+# values V = K b^2 s (the finest FP32 displacement level stores the
+# symmetric half, 14 of 27 blocks), inverse diagonal D = b^2 s, a vector
+# v = b s per point.
+STENCIL = {"box1": 27, "diamond2": 25, "box2": 125, "faces": 11}
+
+
+def _vcycle_bytes(levels, s, fine_sym):
+    """One V(1,1) cycle with Chebyshev(2) smoothing: per non-last level a
+    zero-start step (D + 3v), three stencil steps (V + D + 5v each), a
+    residual (V + 3v), the restriction and prolongation (prolongator values
+    or face weights plus 3v); the last level is the FP64 dense inverse
+    (n^2 x 8 B) and two vectors."""
+    total = 0.0
+    for i, (kind, N, b) in enumerate(levels):
+        v, D = b * s * N, b * b * s * N
+        if i == len(levels) - 1:
+            n = N * b
+            total += n * n * 8 + 2 * v
+            break
+        K = 14 if (fine_sym and i == 0) else STENCIL[kind]
+        V = K * b * b * s * N
+        slots = 8 if kind == "box1" else 27
+        Pb = (s * N) if kind == "faces" else slots * b * b * s * N
+        total += (D + 3 * v) + 3 * (V + D + 5 * v) + (V + 3 * v) + 2 * (Pb + 3 * v)
+    return total
+
+
+def step_bytes(n_mesh, hu_points, hpi_points, precision, m, iters_per_step):
+    """Algorithmic bytes of one time step (right-hand side + FGMRES solve).
+
+    Per Arnoldi step j: the preconditioner (precision conversions, the
+    interface-pressure V-cycle, the two Schur steps, the displacement
+    V-cycle), the FP64 operator, one classical Gram-Schmidt pass over the
+    j + 1 basis vectors (dots, update, normalisation) and the Givens step.
+    Per restart cycle: the residual (operator + norm) and x += Z y."""
+    L = n_mesh + 1
+    nN, nT = L ** 3, n_mesh ** 3
+    nF = 3 * n_mesh * n_mesh * L
+    n = 3 * nN + nT + nF
+    s = 4 if precision == 1 else 8
+    hu = [("box1", N, 3) for N in hu_points]
+    hpi = [("faces", hpi_points[0], 1)] + [("diamond2" if i == 1 else "box2", N, 1)
+                                           for i, N in enumerate(hpi_points) if i > 0]
+    conv = (20 + 12) * n if precision == 1 else 24 * n
+    schur = (6 * s + 3 * s) * nT + nF * s + 24 * s * nT + s * nT + 6 * s * nN
+    prec = conv + _vcycle_bytes(hpi, s, False) + schur + _vcycle_bytes(hu, s, precision == 1)
+    op = 27 * 9 * 8 * nN + 2 * 24 * 8 * nT + 11 * 8 * nF + 17 * 8 * nT + 16 * n
+    total = 16.0 * n  # right-hand side (reads the previous state, writes b)
+    k = 0
+    while k < iters_per_step:
+        steps = min(m, iters_per_step - k)
+        total += op + 16 * n            # residual of the cycle and its norm
+        for j in range(steps):
+            total += prec + op + (2 * (j + 1) + 4) * 8 * n
+        total += (steps + 2) * 8 * n    # x += Z y
+        k += steps
+    total += op + 16 * n                # true residual at exit
+    return total
 
 
 # ------------------------------------------------------------------ ranks
@@ -355,6 +498,32 @@ def _solver(prob, precision, torch, restart=50, reorth=1, coarse_max=125):
     return s, e0.elapsed_time(e1)
 
 
+def _measure_workload(args, name, world, dist, torch, launch_count, local, precisions):
+    """Both forms of one workload: FP64 plain, then mixed (the headline),
+    each with its timed pass and a second pass with the kernel events on."""
+    prob = make_problem(name)
+    restart = args.restart if name == args.workload else WORKLOADS[name].get("restart", 12)
+    out = {}
+    for precision in precisions:
+        s, setup = _solver(prob, precision, torch, restart, args.reorth, args.coarse_max)
+        r = _timed_steps(s, args, world, dist, torch, launch_count, precision == precisions[-1], local)
+        rk = _timed_steps(s, args, world, dist, torch, launch_count, False, local, True)
+        r["kt"], r["kernel_pass_ms"], r["setup_ms"] = rk["kt"], rk["ms"], setup
+        r["op"] = s.timing_read(1)
+        r["hu"], r["hpi"] = s.hierarchy(0)["points"], s.hierarchy(1)["points"]
+        r["restart"] = restart
+        out[precision] = (s, r)
+        if precision != precisions[-1]:
+            s.close()
+    return out
+
+
+def _sweep_roofline(kt, peak):
+    avg_ms = kt["total_ms"] / max(kt["launches"], 1)
+    gbs = kt["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9 if kt["launches"] else None
+    return avg_ms, gbs
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -372,30 +541,14 @@ def run_ours(args):
         dist.barrier()
     from paper_2002_09603_gb300 import launch_count
 
-    prob = make_problem(args.workload)
     n_mesh = WORKLOADS[args.workload]["n"]
     peak, peak_kind = measured_peaks()
-
-    # FP64-plain form first (reported beside the headline), then the
-    # mixed form (FP32 V-cycles and Schur steps inside FP64 FGMRES)
-    r64, setup64 = None, None
-    if args.precision in ("both", "fp64"):
-        s64, setup64 = _solver(prob, 0, torch, args.restart, args.reorth, args.coarse_max)
-        r64 = _timed_steps(s64, args, world, dist, torch, launch_count, args.precision == "fp64", local)
-        r64["kt"] = _timed_steps(s64, args, world, dist, torch, launch_count, False, local, True)["kt"]
-        if args.precision == "fp64":
-            s, setup_ms, r32 = s64, setup64, r64
-        else:
-            s64.close()
-            del s64
-    if args.precision in ("both", "mixed"):
-        s, setup_ms = _solver(prob, 1, torch, args.restart, args.reorth, args.coarse_max)
-        r32 = _timed_steps(s, args, world, dist, torch, launch_count, True, local)
-        # second pass over the same steps with the kernel events on (roofline)
-        rk = _timed_steps(s, args, world, dist, torch, launch_count, False, local, True)
-        r32["kt"] = rk["kt"]
-        r32["kernel_pass_ms"] = rk["ms"]
+    precisions = {"both": (0, 1), "mixed": (1,), "fp64": (0,)}[args.precision]
+    res = _measure_workload(args, args.workload, world, dist, torch, launch_count, local, precisions)
+    s, r32 = res[precisions[-1]]
+    r64 = res[0][1] if 0 in res else None
     ms = r32["ms"]
+    setup_ms = r32["setup_ms"]
 
     # end to end through the C ABI with host buffers: the previous state comes
     # from pinned host memory and the solution goes back to it every step
@@ -420,38 +573,74 @@ def run_ours(args):
         e2e = {"value": aggregate_time(e2e_ms, world), "unit": "ms", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    # roofline of the dominant sweep of the headline (mixed) form:
-    # k_cheb_u0_sym<float>, HBM-bound
-    kt = r32["kt"]
-    avg_ms = kt["total_ms"] / max(kt["launches"], 1)
-    gbs = kt["bytes_per_launch"] / (avg_ms * 1e-3) / 1e9 if kt["launches"] else None
+    # roofline of the dominant sweep of the headline form
+    headline_mixed = precisions[-1] == 1
+    kname = "k_cheb_u0_sym<float>" if headline_mixed else "k_cheb_u0<double>"
+    avg_ms, gbs = _sweep_roofline(r32["kt"], peak)
     roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                 "frac": gbs / peak if gbs else None,
-                "traffic": traffic_for("k_cheb_u0_sym<float>") if args.workload == "lognormal64" else None,
-                "kernel": "k_cheb_u0_sym<float> (Chebyshev sweep, finest displacement level, 27-point 3x3-block "
-                          "stencil, FP32, symmetric storage: 14 of the 27 blocks per node)",
-                "launches": kt["launches"], "avg_launch_us": avg_ms * 1e3, "bytes_per_launch": kt["bytes_per_launch"],
+                "traffic": traffic_for(kname, args.workload, r32["kt"]["bytes_per_launch"]),
+                "kernel": (kname + " (Chebyshev sweep, finest displacement level, 27-point 3x3-block stencil"
+                           + (", FP32, symmetric storage: 14 of the 27 blocks per node)" if headline_mixed
+                              else ", FP64)")),
+                "launches": r32["kt"]["launches"], "avg_launch_us": avg_ms * 1e3,
+                "bytes_per_launch": r32["kt"]["bytes_per_launch"],
                 "measured_in": "a second timed pass over the same K steps with the library's kernel events on "
                                f"(per-step graph replays, {r32.get('kernel_pass_ms', float('nan')):.2f} ms/step); the "
                                "headline pass runs each solve as one device-driven graph, which cannot hold event nodes",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
-    # the FP64-plain form's dominant kernel is bound by the FP64 pipe
-    k64 = (r64 or r32)["kt"]
-    avg64 = k64["total_ms"] / max(k64["launches"], 1)
+    # the operator A_H x (FP64 in both forms, the largest single kernel of
+    # the headline step) is bound by the FP64 pipe
     sm_max = ((r32["clocks"] or {}).get("sm_max_mhz") or 2070.0)
     fpk = fp64_peak_tflops(sm_max)
-    tf64 = cheb_u0_flops(n_mesh) / (avg64 * 1e-3) / 1e12 if k64["launches"] else None
-    roofline_fp64 = {"bound": "alu", "achieved": tf64, "peak": fpk, "unit": "TFLOP/s",
-                     "frac": tf64 / fpk if tf64 else None,
-                     "traffic": traffic_for("k_cheb_u0<double>") if args.workload == "lognormal64" else None,
-                     "kernel": "k_cheb_u0<double>", "avg_launch_us": avg64 * 1e3,
-                     "hbm_achieved_gbs": k64["bytes_per_launch"] / (avg64 * 1e-3) / 1e9 if k64["launches"] else None,
+    op = r32["op"]
+    op_ms = op["total_ms"] / max(op["launches"], 1)
+    op_tf = operator_flops(n_mesh) / (op_ms * 1e-3) / 1e12 if op["launches"] else None
+    roofline_fp64 = {"bound": "alu", "achieved": op_tf, "peak": fpk, "unit": "TFLOP/s",
+                     "frac": op_tf / fpk if op_tf else None, "traffic": None,
+                     "kernel": "operator A_H x (k_apply_u + k_apply_p + k_apply_pi, FP64)",
+                     "launches": op["launches"], "avg_launch_us": op_ms * 1e3,
+                     "flops_per_launch": operator_flops(n_mesh),
+                     "hbm_achieved_gbs": op["bytes_per_launch"] / (op_ms * 1e-3) / 1e9 if op["launches"] else None,
                      "peak_source": "derived FP64 pipe peak: 152 SMs x 2 FMA/clk x 2 flop x max SM clock"}
+    # the whole step against the bandwidth roofline
+    mean_iters = statistics.mean(r32["iters"])
+    sb = step_bytes(n_mesh, r32["hu"], r32["hpi"], precisions[-1], r32["restart"], int(round(mean_iters)))
+    step_roof = {"bytes_per_step": sb, "achieved_gbs": sb / (ms * 1e-3) / 1e9, "peak": peak,
+                 "frac": sb / (ms * 1e-3) / 1e9 / peak,
+                 "model": "algorithmic bytes of every kernel of the step (bench.step_bytes), FP64 coarsest "
+                          "inverse and L2-resident coarse levels included"}
+
+    fp64_plain = None
+    if r64 is not None and r64 is not r32:
+        a64, g64 = _sweep_roofline(r64["kt"], peak)
+        t64 = cheb_u0_flops(n_mesh) / (a64 * 1e-3) / 1e12 if r64["kt"]["launches"] else None
+        sb64 = step_bytes(n_mesh, r64["hu"], r64["hpi"], 0, r64["restart"], int(round(statistics.mean(r64["iters"]))))
+        fp64_plain = {"ms_per_step": r64["ms"], "iterations_per_step": r64["iters"], "setup_ms": r64["setup_ms"],
+                      "gpu_launches": r64["launches"],
+                      "sweep_roofline": {"kernel": "k_cheb_u0<double>", "bound": "alu", "achieved": t64, "peak": fpk,
+                                         "unit": "TFLOP/s", "frac": t64 / fpk if t64 else None,
+                                         "hbm_achieved_gbs": g64, "avg_launch_us": a64 * 1e3},
+                      "step_frac_of_hbm": sb64 / (r64["ms"] * 1e-3) / 1e9 / peak}
+
+    # the 64^3 log-normal workload, measured in the same run
+    other = None
+    if args.workload == "layered128" and world == 1 and not args.no_64:
+        o = _measure_workload(args, "lognormal64", world, dist, torch, launch_count, local, precisions)
+        so, ro = o[precisions[-1]]
+        ao, go = _sweep_roofline(ro["kt"], peak)
+        other = {"workload": WORKLOADS["lognormal64"]["desc"], "unknowns": so.n, "restart": ro["restart"],
+                 "ms_per_step": ro["ms"], "iterations_per_step": ro["iters"], "setup_ms": ro["setup_ms"],
+                 "sweep_frac_of_hbm": go / peak if go else None,
+                 "step_frac_of_hbm": step_bytes(64, ro["hu"], ro["hpi"], precisions[-1], ro["restart"],
+                                                int(round(statistics.mean(ro["iters"])))) / (ro["ms"] * 1e-3) / 1e9 / peak,
+                 "fp64_plain_ms_per_step": o[0][1]["ms"] if 0 in o and len(precisions) > 1 else None}
+        so.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample_subprocess(args.workload, s.n, statistics.mean(r32["iters"]))
+        cpu = cpu_baseline_leg(args.workload, mean_iters)
 
     nU, nP, nPi = s.sizes
     auu_mb = 27 * 9 * 8 * (n_mesh + 1) ** 3 / 1e6  # 27 3x3 FP64 blocks per node
@@ -459,7 +648,9 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": aggregate_time(ms, world), "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)",
+            "vs_baseline": None,
+            "dtype": ("f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)" if headline_mixed
+                      else "f64"),
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
                        "n_pi": nPi, "tol": TOL, "restart": args.restart, "reorth": args.reorth,
@@ -467,14 +658,14 @@ def run_ours(args):
                        "setup_ms": setup_ms, "precision": {"both": "FP32 V-cycles inside FP64 FGMRES",
                                                            "mixed": "FP32 V-cycles inside FP64 FGMRES",
                                                            "fp64": "FP64 throughout"}[args.precision],
-                       "fp64_plain": None if r64 is None else {
-                           "ms_per_step": r64["ms"], "iterations_per_step": r64["iters"], "setup_ms": setup64,
-                           "gpu_launches": r64["launches"]},
+                       "fp64_plain": fp64_plain,
                        "l2": (f"inputs larger than L2 (A_uu alone is {auu_mb:.0f} MB in FP64, "
                               f"{auu_mb * 14 / 27 / 2:.0f} MB as the symmetric FP32 half)"),
                        "parallelism": "replicas",
-                       "hierarchy_u": s.hierarchy(0)["points"], "hierarchy_pi": s.hierarchy(1)["points"]},
-            "roofline": roofline, "roofline_fp64": roofline_fp64, "cpu_baseline": cpu, "e2e": e2e,
+                       "hierarchy_u": r32["hu"], "hierarchy_pi": r32["hpi"],
+                       "lognormal64": other},
+            "roofline": roofline, "roofline_fp64": roofline_fp64, "step_roofline": step_roof,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": r32["launches"], "clocks": r32["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -539,11 +730,6 @@ def main():
     args = parse()
     if args.workload == "batch48":
         run_batch(args)
-        return
-    if args.oracle_sample:
-        tgt, it = args.oracle_target.split(",")
-        d, _ = oracle_sample(args.workload, int(tgt), float(it), sample_n=args.oracle_sample)
-        print(json.dumps(d), flush=True)
         return
     if args.impl == "reference":
         os.environ.update(SINGLE_THREAD_ENV)  # before numpy is imported

@@ -113,6 +113,14 @@ typedef struct {
   int fine_blocks;      /* 0 (default): autotuned (size rule without it); 6 or */
                         /* 8: resident blocks per SM of the finest FP32        */
                         /* displacement sweep and residual (precision = 1)     */
+  int near_kernel;      /* near-kernel of the displacement multigrid (Section  */
+                        /* 5): 0 (default) the three translations per          */
+                        /* aggregate, separate displacement components         */
+                        /* (M_II^(h)); 1 the six rigid-body modes (M_III^(h)): */
+                        /* per aggregate a Gram-Schmidt factorisation of the   */
+                        /* modes restricted to its dofs, six dofs per coarse   */
+                        /* point (a mode the aggregate cannot represent leaves */
+                        /* a decoupled dof with a unit diagonal)               */
 } mhfp_options;
 
 typedef struct {
@@ -127,7 +135,8 @@ typedef struct {
 typedef struct {
   int levels;           /* number of levels (>= 1)                             */
   long long points[8];  /* lattice points (or faces) per level                 */
-  int block[8];         /* unknowns per point (3 for u, 1 for pi)              */
+  int block[8];         /* unknowns per point (3 for u, 6 on the coarse u      */
+                        /* levels with the rigid-body modes, 1 for pi)         */
   double lmax[8];       /* 1.1 * rho(D^-1 A) per level (0 on the last level)   */
   int schedule[8];      /* launch schedule of the level's sweeps: 1 = one point */
                         /* per thread, 4/8/16 = offsets split over that many    */

@@ -47,7 +47,8 @@ class Options(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_ratio", C.c_double), ("coarse_max", C.c_int), ("power_iters", C.c_int),
                 ("precision", C.c_int), ("graphs", C.c_int), ("autotune", C.c_int),
-                ("reorth", C.c_int), ("schedule", C.c_int), ("fine_blocks", C.c_int)]
+                ("reorth", C.c_int), ("schedule", C.c_int), ("fine_blocks", C.c_int),
+                ("near_kernel", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -14,7 +14,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmhfp.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["assemble.cu", "amg.cu", "krylov.cu", "api.cu"]
+# (source, extra flags, object): the coarse-level sweeps compile once per
+# value type, so the largest translation units build in parallel
+SOURCES = [("assemble.cu", [], "assemble.o"), ("amg.cu", [], "amg.o"), ("krylov.cu", [], "krylov.o"),
+           ("api.cu", [], "api.o"), ("sweep.cu", ["-DMHFP_SWEEP_T=float"], "sweep_f32.o"),
+           ("sweep.cu", ["-DMHFP_SWEEP_T=double"], "sweep_f64.o")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-O3"]
@@ -27,9 +31,10 @@ def nvcc() -> str:
     return p
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(entry, verbose: bool) -> str:
+    src, extra, name = entry
+    obj = os.path.join(BUILD, name)
+    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

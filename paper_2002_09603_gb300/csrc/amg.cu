@@ -17,7 +17,7 @@
 // Galerkin products are formed in two deterministic gather passes, Q = A P
 // on the fine lattice and A_c = P^T Q per coarse point: no atomics, no
 // sparse-matrix hashing.
-#include "common.cuh"
+#include "lattice.cuh"
 
 #include <type_traits>
 
@@ -27,143 +27,6 @@
 namespace mhfp {
 
 namespace {
-
-static __constant__ signed char c_dia[25][3] = {
-    {0, 0, -2}, {0, -1, -1}, {-1, 0, -1}, {0, 0, -1}, {1, 0, -1}, {0, 1, -1}, {0, -2, 0}, {-1, -1, 0}, {0, -1, 0},
-    {1, -1, 0}, {-2, 0, 0},  {-1, 0, 0},  {0, 0, 0},  {1, 0, 0},  {2, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
-    {0, 2, 0},  {0, -1, 1},  {-1, 0, 1},  {0, 0, 1},  {1, 0, 1},  {0, 1, 1},  {0, 0, 2}};
-static __constant__ signed char c_dia_idx[125] = {
-    -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 0,  -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
-    -1, -1, -1, -1, -1, -1, -1, 1,  -1, -1, -1, 2,  3,  4,  -1, -1, -1, 5,  -1, -1, -1, -1, -1, -1, -1,
-    -1, -1, 6,  -1, -1, -1, 7,  8,  9,  -1, 10, 11, 12, 13, 14, -1, 15, 16, 17, -1, -1, -1, 18, -1, -1,
-    -1, -1, -1, -1, -1, -1, -1, 19, -1, -1, -1, 20, 21, 22, -1, -1, -1, 23, -1, -1, -1, -1, -1, -1, -1,
-    -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 24, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
-
-template <int KIND>
-struct St;
-template <>
-struct St<ST_BOX1> {
-  static constexpr int N = 27, R = 1, C = 13;
-  __device__ static void off(int o, int& x, int& y, int& z) { x = o % 3 - 1; y = (o / 3) % 3 - 1; z = o / 9 - 1; }
-  __device__ static int idx(int x, int y, int z) {
-    if (x < -1 || x > 1 || y < -1 || y > 1 || z < -1 || z > 1) return -1;
-    return (x + 1) + 3 * ((y + 1) + 3 * (z + 1));
-  }
-};
-template <>
-struct St<ST_DIAMOND2> {
-  static constexpr int N = 25, R = 2, C = 12;
-  __device__ static void off(int o, int& x, int& y, int& z) { x = c_dia[o][0]; y = c_dia[o][1]; z = c_dia[o][2]; }
-  __device__ static int idx(int x, int y, int z) {
-    if (x < -2 || x > 2 || y < -2 || y > 2 || z < -2 || z > 2) return -1;
-    return c_dia_idx[(x + 2) + 5 * ((y + 2) + 5 * (z + 2))];
-  }
-};
-template <>
-struct St<ST_BOX2> {
-  static constexpr int N = 125, R = 2, C = 62;
-  __device__ static void off(int o, int& x, int& y, int& z) { x = o % 5 - 2; y = (o / 5) % 5 - 2; z = o / 25 - 2; }
-  __device__ static int idx(int x, int y, int z) {
-    if (x < -2 || x > 2 || y < -2 || y > 2 || z < -2 || z > 2) return -1;
-    return (x + 2) + 5 * ((y + 2) + 5 * (z + 2));
-  }
-};
-
-struct Lat {
-  int Lx, Ly, Lz;
-  long long N;
-  __device__ void ijk(long long p, int& i, int& j, int& k) const {
-    i = (int)(p % Lx);
-    const long long r = p / Lx;
-    j = (int)(r % Ly);
-    k = (int)(r / Ly);
-  }
-  __device__ bool in(int i, int j, int k) const { return i >= 0 && i < Lx && j >= 0 && j < Ly && k >= 0 && k < Lz; }
-  __device__ long long id(int i, int j, int k) const { return i + (long long)Lx * (j + (long long)Ly * k); }
-};
-
-Lat lat_of(const StructOp& A) { return Lat{A.Lx, A.Ly, A.Lz, A.N}; }
-
-// ------------------------------------------------------------------ SpMV
-// y = A x (or r = b - A x) on a lattice level; thread per lattice point.
-template <int BS, int KIND, typename T>
-__device__ __forceinline__ void spmv_body(const Lat& L, const T* __restrict__ val, const T* __restrict__ x,
-                                          const T* __restrict__ b, T* __restrict__ y) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= L.N) return;
-  int i, j, k;
-  L.ijk(p, i, j, k);
-  T acc[BS];
-#pragma unroll
-  for (int r = 0; r < BS; ++r) acc[r] = T(0);
-#pragma unroll
-  for (int o = 0; o < St<KIND>::N; ++o) {
-    int dx, dy, dz;
-    St<KIND>::off(o, dx, dy, dz);
-    if (!L.in(i + dx, j + dy, k + dz)) continue;
-    const long long q = p + dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
-    const T* v = val + (long long)o * BS * BS * L.N + p;
-#pragma unroll
-    for (int r = 0; r < BS; ++r)
-#pragma unroll
-      for (int s = 0; s < BS; ++s) acc[r] += v[(long long)(r * BS + s) * L.N] * x[BS * q + s];
-  }
-#pragma unroll
-  for (int r = 0; r < BS; ++r) y[BS * p + r] = b ? b[BS * p + r] - acc[r] : acc[r];
-}
-
-// ------------------------------------------------------- lattice helpers
-// 32-bit lattice indexing for the coarse levels (see the coarse-level sweeps
-// below).
-struct Lat32 {
-  int Lx, Ly, Lz, N, LxLy;
-  Div32 dx, dy;
-  __device__ __forceinline__ void ijk(unsigned p, int& i, int& j, int& k) const {
-    const unsigned r = dx.div(p);
-    i = (int)(p - r * (unsigned)Lx);
-    k = (int)dy.div(r);
-    j = (int)(r - (unsigned)k * (unsigned)Ly);
-  }
-};
-
-// box index (x+2) + 5 (y+2) + 25 (z+2) of the o-th offset with |d|_1 <= 2,
-// in box order (the order of stencil_offset for ST_DIAMOND2)
-__host__ __device__ constexpr int dia_box(int o) { return o == 0 ? 12 : o == 1 ? 32 : o == 2 ? 36 : o == 3 ? 37 : o == 4 ? 38 : o == 5 ? 42 : o == 6 ? 52 : o == 7 ? 56 : o == 8 ? 57 : o == 9 ? 58 : o == 10 ? 60 : o == 11 ? 61 : o == 12 ? 62 : o == 13 ? 63 : o == 14 ? 64 : o == 15 ? 66 : o == 16 ? 67 : o == 17 ? 68 : o == 18 ? 72 : o == 19 ? 82 : o == 20 ? 86 : o == 21 ? 87 : o == 22 ? 88 : o == 23 ? 92 : 112; }
-constexpr bool dia_table_matches_box_order() {
-  int n = 0;
-  for (int b = 0; b < 125; ++b) {
-    const int x = b % 5 - 2, y = (b / 5) % 5 - 2, z = b / 25 - 2;
-    if ((x < 0 ? -x : x) + (y < 0 ? -y : y) + (z < 0 ? -z : z) > 2) continue;
-    if (dia_box(n++) != b) return false;
-  }
-  return n == 25;
-}
-static_assert(dia_table_matches_box_order(), "diamond offset table out of box order");
-
-// compile-time offsets of each stencil kind
-template <int KIND>
-struct Sf;
-template <>
-struct Sf<ST_BOX1> {
-  static constexpr int N = 27, R = 1;
-  __device__ static constexpr int x(int o) { return o % 3 - 1; }
-  __device__ static constexpr int y(int o) { return (o / 3) % 3 - 1; }
-  __device__ static constexpr int z(int o) { return o / 9 - 1; }
-};
-template <>
-struct Sf<ST_BOX2> {
-  static constexpr int N = 125, R = 2;
-  __device__ static constexpr int x(int o) { return o % 5 - 2; }
-  __device__ static constexpr int y(int o) { return (o / 5) % 5 - 2; }
-  __device__ static constexpr int z(int o) { return o / 25 - 2; }
-};
-template <>
-struct Sf<ST_DIAMOND2> {
-  static constexpr int N = 25, R = 2;
-  __device__ static constexpr int x(int o) { return dia_box(o) % 5 - 2; }
-  __device__ static constexpr int y(int o) { return (dia_box(o) / 5) % 5 - 2; }
-  __device__ static constexpr int z(int o) { return dia_box(o) / 25 - 2; }
-};
 
 // <hot:k_cheb_u0> (bench.py hashes this region to tell whether profiles/traffic.json still applies)
 // Chebyshev step: r = b - A xin (r = b when xin is null), d = cd d + cr D^-1 r,
@@ -308,191 +171,17 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
 
 // </hot:k_cheb_u0_sym>
 
-// ------------------------------------------------------- coarse-level sweeps
-// Sweeps and residuals of the coarse lattice levels and of the interface-
-// pressure cell levels.  Their data is a few to a few tens of MB, so the cost
-// is latency and issue, not bytes: index arithmetic is 32-bit (the lattice
-// point is split with multiply-high division by invariant integers,
-// Granlund & Montgomery 1994, no 64-bit division), stencil offsets are
-// compile-time constants, bounds are three small per-axis masks, and every
-// offset of a chunk issues its loads before any is used (an out-of-lattice
-// neighbour reads the point itself and is then replaced by 0).
-
-// r -= sum over the offsets o with o % step == first of A(p, p + e_o) x(p + e_o)
-template <int BS, int KIND, int CHUNK, typename T>
-__device__ __forceinline__ void coarse_residual(const Lat32& L, unsigned p, const T* __restrict__ val,
-                                                const T* __restrict__ x, T r[BS], int first, int step) {
-  constexpr int R = Sf<KIND>::R, NO = Sf<KIND>::N;
-  int i, j, k;
-  L.ijk(p, i, j, k);
-  bool mx[2 * R + 1], my[2 * R + 1], mz[2 * R + 1];
-#pragma unroll
-  for (int t = -R; t <= R; ++t) {
-    mx[t + R] = (unsigned)(i + t) < (unsigned)L.Lx;
-    my[t + R] = (unsigned)(j + t) < (unsigned)L.Ly;
-    mz[t + R] = (unsigned)(k + t) < (unsigned)L.Lz;
-  }
-  const unsigned N = (unsigned)L.N;
-#pragma unroll
-  for (int o0 = 0; o0 < NO; o0 += CHUNK) {
-    T vv[CHUNK][BS * BS], xx[CHUNK][BS];
-#pragma unroll
-    for (int c = 0; c < CHUNK; ++c) {
-      const int o = o0 + c;
-      if (o < NO && o % step == first) {
-        const int dx = Sf<KIND>::x(o), dy = Sf<KIND>::y(o), dz = Sf<KIND>::z(o);
-        const bool in = mx[dx + R] && my[dy + R] && mz[dz + R];
-        const unsigned q = in ? p + (unsigned)(dx + L.Lx * dy + L.LxLy * dz) : p;
-        const T* row = val + (size_t)o * BS * BS * N;
-#pragma unroll
-        for (int e = 0; e < BS * BS; ++e) vv[c][e] = row[e * N + p];
-#pragma unroll
-        for (int s = 0; s < BS; ++s) {
-          const T xs = x[BS * q + s];
-          xx[c][s] = in ? xs : T(0);  // a select, not a multiply (no FP64 pipe work)
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < CHUNK; ++c)
-      if (o0 + c < NO && (o0 + c) % step == first)
-#pragma unroll
-        for (int a = 0; a < BS; ++a)
-#pragma unroll
-          for (int s = 0; s < BS; ++s) r[a] -= vv[c][a * BS + s] * xx[c][s];
-  }
-}
-
-// one point per thread: loads of CHUNK offsets in flight at once
-template <int BS, typename T>
-constexpr int f_chunk() { return sizeof(T) == 4 ? (BS == 1 ? 25 : 3) : (BS == 1 ? 8 : 1); }
-
-// y = b - A x, or y = A x when b is null
-template <int BS, int KIND, typename T>
-__global__ void __launch_bounds__(256) k_spmv_f(Lat32 L, const T* __restrict__ val, const T* __restrict__ x,
-                                                const T* __restrict__ b, T* __restrict__ y) {
-  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (unsigned)L.N) return;
-  T r[BS];
-#pragma unroll
-  for (int a = 0; a < BS; ++a) r[a] = T(0);
-  coarse_residual<BS, KIND, f_chunk<BS, T>(), T>(L, p, val, x, r, 0, 1);
-#pragma unroll
-  for (int a = 0; a < BS; ++a) y[BS * p + a] = b ? b[BS * p + a] + r[a] : -r[a];
-}
-
-// Chebyshev step: r = b - A xin (r = b when xin is null), d = cd d + cr D^-1 r, xout = xin + d
-template <typename T, int BS>
-__device__ __forceinline__ void cheb_update(unsigned p, unsigned N, const T r[BS], const T* __restrict__ dinv,
-                                            const T* __restrict__ xin, T* __restrict__ xout, T* __restrict__ d, T cd,
-                                            T cr) {
-#pragma unroll
-  for (int a = 0; a < BS; ++a) {
-    T z = T(0);
-#pragma unroll
-    for (int s = 0; s < BS; ++s) z += dinv[(a * BS + s) * N + p] * r[s];
-    const T dn = (cd != T(0)) ? cd * d[BS * p + a] + cr * z : cr * z;
-    d[BS * p + a] = dn;
-    xout[BS * p + a] = (xin ? xin[BS * p + a] : T(0)) + dn;
-  }
-}
-
-template <int BS, int KIND, typename T>
-__global__ void __launch_bounds__(256) k_cheb_f(Lat32 L, const T* __restrict__ val, const T* __restrict__ dinv,
-                                                const T* __restrict__ b, const T* __restrict__ xin,
-                                                T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
-  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (unsigned)L.N) return;
-  T r[BS];
-#pragma unroll
-  for (int a = 0; a < BS; ++a) r[a] = b[BS * p + a];
-  coarse_residual<BS, KIND, f_chunk<BS, T>(), T>(L, p, val, xin, r, 0, 1);
-  cheb_update<T, BS>(p, (unsigned)L.N, r, dinv, xin, xout, d, cd, cr);
-}
-
-// the first Chebyshev step from x = 0: d = cr D^-1 b, xout = d (no stencil)
-template <int BS, typename T>
-__global__ void __launch_bounds__(256) k_cheb_zero(long long npts, const T* __restrict__ dinv,
-                                                   const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ d,
-                                                   T cr) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npts) return;
-  T r[BS];
-#pragma unroll
-  for (int a = 0; a < BS; ++a) r[a] = b[BS * p + a];
-#pragma unroll
-  for (int a = 0; a < BS; ++a) {
-    T z = T(0);
-#pragma unroll
-    for (int s = 0; s < BS; ++s) z += dinv[(a * BS + s) * npts + p] * r[s];
-    d[BS * p + a] = cr * z;
-    xout[BS * p + a] = cr * z;
-  }
-}
-
-// Warp-split offsets: blockDim = (32, W); warp y takes the offsets o with
-// o % W == y for 32 consecutive points, so every load instruction reads one
-// stored row for 32 consecutive points; the W partial sums meet in shared
-// memory and are added in a fixed order.
-template <int BS, typename T>
-constexpr int w_chunk() { return sizeof(T) == 4 ? (BS == 1 ? 8 : 2) : (BS == 1 ? 4 : 1); }
-
-template <int BS, int KIND, int W, typename T>
-__device__ __forceinline__ bool wsplit_residual(const Lat32& L, const T* __restrict__ val, const T* __restrict__ x,
-                                                T (&part)[W][BS][32], unsigned& p, T r[BS]) {
-  p = blockIdx.x * 32 + threadIdx.x;
-  const bool valid = p < (unsigned)L.N;
-  T acc[BS];
-#pragma unroll
-  for (int a = 0; a < BS; ++a) acc[a] = T(0);
-  if (valid && x) coarse_residual<BS, KIND, w_chunk<BS, T>(), T>(L, p, val, x, acc, threadIdx.y, W);
-#pragma unroll
-  for (int a = 0; a < BS; ++a) part[threadIdx.y][a][threadIdx.x] = acc[a];
-  __syncthreads();
-  if (threadIdx.y != 0 || !valid) return false;
-#pragma unroll
-  for (int a = 0; a < BS; ++a) {
-    T s = T(0);
-#pragma unroll
-    for (int u = 0; u < W; ++u) s += part[u][a][threadIdx.x];
-    r[a] = s;  // = -(A x)_a
-  }
-  return true;
-}
-
-template <int BS, int KIND, int W, typename T>
-__global__ void __launch_bounds__(32 * W) k_spmv_w(Lat32 L, const T* __restrict__ val, const T* __restrict__ x,
-                                                   const T* __restrict__ b, T* __restrict__ y) {
-  __shared__ T part[W][BS][32];
-  unsigned p;
-  T r[BS];
-  if (!wsplit_residual<BS, KIND, W, T>(L, val, x, part, p, r)) return;
-#pragma unroll
-  for (int a = 0; a < BS; ++a) y[BS * p + a] = b ? b[BS * p + a] + r[a] : -r[a];
-}
-
-template <int BS, int KIND, int W, typename T>
-__global__ void __launch_bounds__(32 * W) k_cheb_w(Lat32 L, const T* __restrict__ val, const T* __restrict__ dinv,
-                                                   const T* __restrict__ b, const T* __restrict__ xin,
-                                                   T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
-  __shared__ T part[W][BS][32];
-  unsigned p;
-  T r[BS];
-  if (!wsplit_residual<BS, KIND, W, T>(L, val, xin, part, p, r)) return;
-#pragma unroll
-  for (int a = 0; a < BS; ++a) r[a] += b[BS * p + a];
-  cheb_update<T, BS>(p, (unsigned)L.N, r, dinv, xin, xout, d, cd, cr);
-}
-
 // ---------------------------------------------------------------- transfers
 // Prolongation x += P x_c and restriction b_c = P^T r between lattice levels,
 // with the same 32-bit indexing and batched loads as the sweeps.  P is
-// stored [ns^3 slots][bs^2][fine points]; slot (sx, sy, sz) of fine point
-// (a, b, c) is coarse point (p_lo(a) + sx, p_lo(b) + sy, p_lo(c) + sz).  An
-// absent coarse point contributes 0 (a select, not a multiply).
-template <int BS, int R, int CH, typename T>
+// stored [ns^3 slots][BF x BC][fine points] (BF unknowns per fine point, BC
+// per coarse point: 3 x 3 or 1 x 1 for M_II^(h), 3 x 6 and 6 x 6 with the
+// rigid-body modes); slot (sx, sy, sz) of fine point (a, b, c) is coarse
+// point (p_lo(a) + sx, p_lo(b) + sy, p_lo(c) + sz).  An absent coarse point
+// contributes 0 (a select, not a multiply).
+template <int BF, int BC, int R, int CH, typename T>
 __device__ __forceinline__ void prolong_sum(const Lat32& F, const Lat32& C, unsigned p, const T* __restrict__ P,
-                                            const T* __restrict__ xc, T acc[BS], int first, int step) {
+                                            const T* __restrict__ xc, T acc[BF], int first, int step) {
   constexpr int ns = (2 + 2 * R) / 3 + 1, NS = ns * ns * ns;
   int a, b, c;
   F.ijk(p, a, b, c);
@@ -507,7 +196,7 @@ __device__ __forceinline__ void prolong_sum(const Lat32& F, const Lat32& C, unsi
   const unsigned N = (unsigned)F.N;
 #pragma unroll
   for (int s0 = 0; s0 < NS; s0 += CH) {
-    T pv[CH][BS * BS], xv[CH][BS];
+    T pv[CH][BF * BC], xv[CH][BC];
 #pragma unroll
     for (int q = 0; q < CH; ++q) {
       const int sl = s0 + q;
@@ -516,13 +205,13 @@ __device__ __forceinline__ void prolong_sum(const Lat32& F, const Lat32& C, unsi
         const bool in = vx[sx] && vy[sy] && vz[sz];
         const unsigned J = in ? (unsigned)(lx + sx) + (unsigned)C.Lx * ((unsigned)(ly + sy) + (unsigned)C.Ly * (unsigned)(lz + sz)) : 0u;
 #pragma unroll
-        for (int e = 0; e < BS * BS; ++e) {
-          const T v = P[(unsigned)(sl * BS * BS + e) * N + p];
+        for (int e = 0; e < BF * BC; ++e) {
+          const T v = P[(unsigned)(sl * BF * BC + e) * N + p];
           pv[q][e] = in ? v : T(0);
         }
 #pragma unroll
-        for (int t = 0; t < BS; ++t) {
-          const T v = xc[BS * J + t];
+        for (int t = 0; t < BC; ++t) {
+          const T v = xc[BC * J + t];
           xv[q][t] = in ? v : T(0);
         }
       }
@@ -531,106 +220,111 @@ __device__ __forceinline__ void prolong_sum(const Lat32& F, const Lat32& C, unsi
     for (int q = 0; q < CH; ++q)
       if (s0 + q < NS && (s0 + q) % step == first)
 #pragma unroll
-        for (int r = 0; r < BS; ++r)
+        for (int r = 0; r < BF; ++r)
 #pragma unroll
-          for (int t = 0; t < BS; ++t) acc[r] += pv[q][r * BS + t] * xv[q][t];
+          for (int t = 0; t < BC; ++t) acc[r] += pv[q][r * BC + t] * xv[q][t];
   }
 }
 
-template <int BS>
-constexpr int prolong_chunk() { return BS == 1 ? 9 : 4; }
+template <int BF, int BC>
+constexpr int prolong_chunk() { return BF * BC == 1 ? 9 : (BF * BC <= 9 ? 4 : 1); }
 
 // one fine point per thread
-template <int BS, int R, typename T>
+template <int BF, int BC, int R, typename T>
 __global__ void __launch_bounds__(256) k_prolong_f(Lat32 F, Lat32 C, const T* __restrict__ P,
                                                    const T* __restrict__ xc, T* __restrict__ x) {
   const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (unsigned)F.N) return;
-  T acc[BS];
+  T acc[BF];
 #pragma unroll
-  for (int r = 0; r < BS; ++r) acc[r] = T(0);
-  prolong_sum<BS, R, prolong_chunk<BS>(), T>(F, C, p, P, xc, acc, 0, 1);
+  for (int r = 0; r < BF; ++r) acc[r] = T(0);
+  prolong_sum<BF, BC, R, prolong_chunk<BF, BC>(), T>(F, C, p, P, xc, acc, 0, 1);
 #pragma unroll
-  for (int r = 0; r < BS; ++r) x[BS * p + r] += acc[r];
+  for (int r = 0; r < BF; ++r) x[BF * p + r] += acc[r];
 }
 
 // small fine levels: the slots split over W warps for 32 consecutive fine
 // points, partial sums added in a fixed order through shared memory
-template <int BS, int R, int W, typename T>
+template <int BF, int BC, int R, int W, typename T>
 __global__ void __launch_bounds__(32 * W) k_prolong_w(Lat32 F, Lat32 C, const T* __restrict__ P,
                                                       const T* __restrict__ xc, T* __restrict__ x) {
-  __shared__ T part[W][BS][32];
+  __shared__ T part[W][BF][32];
   const unsigned p = blockIdx.x * 32 + threadIdx.x;
   const bool valid = p < (unsigned)F.N;
-  T acc[BS];
+  T acc[BF];
 #pragma unroll
-  for (int r = 0; r < BS; ++r) acc[r] = T(0);
-  if (valid) prolong_sum<BS, R, 2, T>(F, C, p, P, xc, acc, threadIdx.y, W);
+  for (int r = 0; r < BF; ++r) acc[r] = T(0);
+  if (valid) prolong_sum<BF, BC, R, (BF * BC > 9 ? 1 : 2), T>(F, C, p, P, xc, acc, threadIdx.y, W);
 #pragma unroll
-  for (int r = 0; r < BS; ++r) part[threadIdx.y][r][threadIdx.x] = acc[r];
+  for (int r = 0; r < BF; ++r) part[threadIdx.y][r][threadIdx.x] = acc[r];
   __syncthreads();
   if (threadIdx.y != 0 || !valid) return;
 #pragma unroll
-  for (int r = 0; r < BS; ++r) {
+  for (int r = 0; r < BF; ++r) {
     T sum = T(0);
 #pragma unroll
     for (int u = 0; u < W; ++u) sum += part[u][r][threadIdx.x];
-    x[BS * p + r] += sum;
+    x[BF * p + r] += sum;
   }
 }
 
 // restriction b_c = P^T r, one warp per coarse point: the lanes split the
 // (3 + 2R)^3 fine box around it, each lane issuing the loads of all its box
 // points before the sums, then a fixed-order xor reduction over the warp
-template <int BS, int R, typename T>
+template <int BF, int BC, int R, typename T>
 __global__ void __launch_bounds__(256) k_restrict_f(Lat32 F, Lat32 C, const T* __restrict__ P,
                                                     const T* __restrict__ r, T* __restrict__ bc) {
   constexpr int ns = (2 + 2 * R) / 3 + 1, w = 3 + 2 * R, NB = w * w * w, PER = (NB + 31) / 32;
+  // blocks larger than 3 x 3 keep one box point's loads in flight at a time
+  constexpr int KB = BF * BC > 9 ? 1 : PER;
   const unsigned J = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const bool valid = J < (unsigned)C.N;
-  T acc[BS];
+  T acc[BC];
 #pragma unroll
-  for (int q = 0; q < BS; ++q) acc[q] = T(0);
+  for (int q = 0; q < BC; ++q) acc[q] = T(0);
   if (valid) {
     int I, Jj, K;
     C.ijk(J, I, Jj, K);
     const unsigned N = (unsigned)F.N;
-    T pv[PER][BS * BS], rv[PER][BS];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int e = lane + 32 * k;
-      const int ex = e % w, ey = (e / w) % w, ez = e / (w * w);
-      const int a = 3 * I - R + ex, b = 3 * Jj - R + ey, c = 3 * K - R + ez;
-      const bool in = e < NB && (unsigned)a < (unsigned)F.Lx && (unsigned)b < (unsigned)F.Ly &&
-                      (unsigned)c < (unsigned)F.Lz;
-      const int sx = I - p_lo(a, R), sy = Jj - p_lo(b, R), sz = K - p_lo(c, R);
-      const bool ok = in && (unsigned)sx < (unsigned)ns && (unsigned)sy < (unsigned)ns && (unsigned)sz < (unsigned)ns;
-      const unsigned fp = ok ? (unsigned)a + (unsigned)F.Lx * ((unsigned)b + (unsigned)F.Ly * (unsigned)c) : 0u;
-      const int sl = ok ? sx + ns * (sy + ns * sz) : 0;
+    for (int k0 = 0; k0 < PER; k0 += KB) {
+      T pv[KB][BF * BC], rv[KB][BF];
 #pragma unroll
-      for (int t = 0; t < BS * BS; ++t) {
-        const T v = P[(unsigned)(sl * BS * BS + t) * N + fp];
-        pv[k][t] = ok ? v : T(0);
+      for (int kk = 0; kk < KB; ++kk) {
+        const int e = lane + 32 * (k0 + kk);
+        const int ex = e % w, ey = (e / w) % w, ez = e / (w * w);
+        const int a = 3 * I - R + ex, b = 3 * Jj - R + ey, c = 3 * K - R + ez;
+        const bool in = e < NB && (unsigned)a < (unsigned)F.Lx && (unsigned)b < (unsigned)F.Ly &&
+                        (unsigned)c < (unsigned)F.Lz;
+        const int sx = I - p_lo(a, R), sy = Jj - p_lo(b, R), sz = K - p_lo(c, R);
+        const bool ok = in && (unsigned)sx < (unsigned)ns && (unsigned)sy < (unsigned)ns && (unsigned)sz < (unsigned)ns;
+        const unsigned fp = ok ? (unsigned)a + (unsigned)F.Lx * ((unsigned)b + (unsigned)F.Ly * (unsigned)c) : 0u;
+        const int sl = ok ? sx + ns * (sy + ns * sz) : 0;
+#pragma unroll
+        for (int t = 0; t < BF * BC; ++t) {
+          const T v = P[(unsigned)(sl * BF * BC + t) * N + fp];
+          pv[kk][t] = ok ? v : T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < BF; ++t) {
+          const T v = r[BF * fp + t];
+          rv[kk][t] = ok ? v : T(0);
+        }
       }
 #pragma unroll
-      for (int t = 0; t < BS; ++t) {
-        const T v = r[BS * fp + t];
-        rv[k][t] = ok ? v : T(0);
-      }
+      for (int kk = 0; kk < KB; ++kk)
+#pragma unroll
+        for (int q = 0; q < BC; ++q)
+#pragma unroll
+          for (int t = 0; t < BF; ++t) acc[q] += pv[kk][t * BC + q] * rv[kk][t];
     }
-#pragma unroll
-    for (int k = 0; k < PER; ++k)
-#pragma unroll
-      for (int q = 0; q < BS; ++q)
-#pragma unroll
-        for (int t = 0; t < BS; ++t) acc[q] += pv[k][t * BS + q] * rv[k][t];
   }
 #pragma unroll
-  for (int q = 0; q < BS; ++q) {
+  for (int q = 0; q < BC; ++q) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], m);
-    if (valid && lane == 0) bc[BS * J + q] = acc[q];
+    if (valid && lane == 0) bc[BC * J + q] = acc[q];
   }
 }
 
@@ -784,6 +478,26 @@ __global__ void k_dinv(Lat L, const double* __restrict__ val, double* __restrict
   const double* v = val + (long long)St<KIND>::C * BS * BS * L.N + p;
   if (BS == 1) {
     dinv[p] = 1.0 / v[0];
+  } else if (BS != 3) {
+    // the SPD point block of the rigid-body-mode levels (6 x 6): Gauss-
+    // Jordan elimination without pivoting (positive pivots of an SPD block)
+    double m[BS][2 * BS];
+    for (int r = 0; r < BS; ++r)
+      for (int c = 0; c < BS; ++c) {
+        m[r][c] = v[(long long)(r * BS + c) * L.N];
+        m[r][BS + c] = (r == c) ? 1.0 : 0.0;
+      }
+    for (int c = 0; c < BS; ++c) {
+      const double ip = 1.0 / m[c][c];
+      for (int k = 0; k < 2 * BS; ++k) m[c][k] *= ip;
+      for (int r = 0; r < BS; ++r) {
+        if (r == c) continue;
+        const double f = m[r][c];
+        for (int k = 0; k < 2 * BS; ++k) m[r][k] -= f * m[c][k];
+      }
+    }
+    for (int r = 0; r < BS; ++r)
+      for (int c = 0; c < BS; ++c) dinv[(long long)(r * BS + c) * L.N + p] = m[r][BS + c];
   } else {
     double a[9];
     for (int q = 0; q < 9; ++q) a[q] = v[(long long)q * L.N];
@@ -886,8 +600,9 @@ __global__ void k_active_coarse(Lat F, Lat Cc, const unsigned char* __restrict__
   for (int q = 0; q < BS; ++q) ac[BS * J + q] = m[q] ? 1 : 0;
 }
 
-// Q[a, J] = sum_o A[a, a+o] P[a+o, J]   (fine point a, coarse J in its Q range)
-template <int BS, int KIND>
+// Q[a, J] = sum_o A[a, a+o] P[a+o, J]   (fine point a, coarse J in its Q range;
+// A blocks BF x BF, P and Q blocks BF x BC)
+template <int BF, int BC, int KIND>
 __global__ void k_build_Q(Lat F, Lat Cc, const double* __restrict__ val, const double* __restrict__ P,
                           double* __restrict__ Q) {
   const int R = St<KIND>::R;
@@ -900,8 +615,8 @@ __global__ void k_build_Q(Lat F, Lat Cc, const double* __restrict__ val, const d
   int a, b, c;
   F.ijk(p, a, b, c);
   const int I = q_lo(a, R) + s % nq, J = q_lo(b, R) + (s / nq) % nq, K = q_lo(c, R) + s / (nq * nq);
-  double out[BS * BS];
-  for (int q = 0; q < BS * BS; ++q) out[q] = 0.0;
+  double out[BF * BC];
+  for (int q = 0; q < BF * BC; ++q) out[q] = 0.0;
   if (Cc.in(I, J, K)) {
     for (int o = 0; o < St<KIND>::N; ++o) {
       int dx, dy, dz;
@@ -912,21 +627,21 @@ __global__ void k_build_Q(Lat F, Lat Cc, const double* __restrict__ val, const d
       if (px < 0 || px >= ns || py < 0 || py >= ns || pz < 0 || pz >= ns) continue;
       const long long q = F.id(na, nb, nc);
       const int ps = px + ns * (py + ns * pz);
-      const double* v = val + (long long)o * BS * BS * F.N + p;
-      const double* pv = P + (long long)ps * BS * BS * F.N + q;
-      for (int r = 0; r < BS; ++r)
-        for (int t = 0; t < BS; ++t) {
+      const double* v = val + (long long)o * BF * BF * F.N + p;
+      const double* pv = P + (long long)ps * BF * BC * F.N + q;
+      for (int r = 0; r < BF; ++r)
+        for (int t = 0; t < BC; ++t) {
           double z = 0.0;
-          for (int u = 0; u < BS; ++u) z += v[(long long)(r * BS + u) * F.N] * pv[(long long)(u * BS + t) * F.N];
-          out[r * BS + t] += z;
+          for (int u = 0; u < BF; ++u) z += v[(long long)(r * BF + u) * F.N] * pv[(long long)(u * BC + t) * F.N];
+          out[r * BC + t] += z;
         }
     }
   }
-  for (int q = 0; q < BS * BS; ++q) Q[((long long)s * BS * BS + q) * F.N + p] = out[q];
+  for (int q = 0; q < BF * BC; ++q) Q[((long long)s * BF * BC + q) * F.N + p] = out[q];
 }
 
-// A_c[J, J+oc] = sum_{a in box(J)} P[a, J]^T Q[a, J+oc]
-template <int BS, int CKIND>
+// A_c[J, J+oc] = sum_{a in box(J)} P[a, J]^T Q[a, J+oc]   (BC x BC blocks)
+template <int BF, int BC, int CKIND>
 __global__ void k_rap(Lat F, Lat Cc, int R, const double* __restrict__ P, const double* __restrict__ Q,
                       const unsigned char* __restrict__ ac, double* __restrict__ Ac) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -938,8 +653,8 @@ __global__ void k_rap(Lat F, Lat Cc, int R, const double* __restrict__ P, const 
   int ox, oy, oz;
   St<CKIND>::off(oc, ox, oy, oz);
   const int I2 = I + ox, J2 = Jj + oy, K2 = K + oz;
-  double out[BS * BS];
-  for (int q = 0; q < BS * BS; ++q) out[q] = 0.0;
+  double out[BC * BC];
+  for (int q = 0; q < BC * BC; ++q) out[q] = 0.0;
   if (Cc.in(I2, J2, K2)) {
     const int ns = p_slots(R), nq = q_slots(R);
     for (int c = 3 * K - R; c <= 3 * K + 2 + R; ++c) {
@@ -955,22 +670,201 @@ __global__ void k_rap(Lat F, Lat Cc, int R, const double* __restrict__ P, const 
           const int px = I - p_lo(a, R), qx = I2 - q_lo(a, R);
           if (px < 0 || px >= ns || qx < 0 || qx >= nq) continue;
           const long long p = F.id(a, b, c);
-          const double* pv = P + (long long)(px + ns * (py + ns * pz)) * BS * BS * F.N + p;
-          const double* qv = Q + (long long)(qx + nq * (qy + nq * qz)) * BS * BS * F.N + p;
-          for (int r = 0; r < BS; ++r)
-            for (int t = 0; t < BS; ++t) {
+          const double* pv = P + (long long)(px + ns * (py + ns * pz)) * BF * BC * F.N + p;
+          const double* qv = Q + (long long)(qx + nq * (qy + nq * qz)) * BF * BC * F.N + p;
+          for (int r = 0; r < BC; ++r)
+            for (int t = 0; t < BC; ++t) {
               double z = 0.0;
-              for (int u = 0; u < BS; ++u) z += pv[(long long)(u * BS + r) * F.N] * qv[(long long)(u * BS + t) * F.N];
-              out[r * BS + t] += z;
+              for (int u = 0; u < BF; ++u) z += pv[(long long)(u * BC + r) * F.N] * qv[(long long)(u * BC + t) * F.N];
+              out[r * BC + t] += z;
             }
         }
       }
     }
   }
   if (ox == 0 && oy == 0 && oz == 0)
-    for (int r = 0; r < BS; ++r)
-      if (!ac[BS * J + r]) out[r * BS + r] = 1.0;
-  for (int q = 0; q < BS * BS; ++q) Ac[((long long)oc * BS * BS + q) * Cc.N + J] = out[q];
+    for (int r = 0; r < BC; ++r)
+      if (!ac[BC * J + r]) out[r * BC + r] = 1.0;
+  for (int q = 0; q < BC * BC; ++q) Ac[((long long)oc * BC * BC + q) * Cc.N + J] = out[q];
+}
+
+// ------------------------------------------- rigid-body-mode near-kernel
+// M_III^(h) (Section 5: smoothed aggregation with the six rigid-body modes
+// as the near-kernel of A_uu).  Per aggregate (3x3x3 box of lattice points)
+// one warp factorises the near-kernel restricted to the aggregate's dofs,
+// N_K = Q_K R_K, by classical Gram-Schmidt applied twice in mode order
+// (translations x, y, z, rotations about x, y, z); a mode left with at
+// most 1e-10 of its norm is dropped (zero column of Q_K, zero row of R_K,
+// the coarse dof inactive).  The lanes hold the rows (lane l: rows l,
+// l + 32, ...), dot products are fixed-order xor butterflies.  Q_K is
+// stored per fine point, Pt[(a BC + j)][p] = Q_K(row of dof a of point p, j);
+// R_K as the coarse point's near-kernel, Nc[(a 6 + j)][K] = R_K(a, j).
+constexpr int RBM_K = 6;
+constexpr double RBM_DROP = 1e-10;
+
+__device__ __forceinline__ double warp_sum_xor(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// near-kernel rows of the aggregate's dofs: the fine level (BF = 3) takes
+// the rigid-body modes of the node coordinates (about the centroid cen,
+// rows of prescribed dofs zero); a coarse level (BF = 6) takes the previous
+// level's R blocks
+template <int BF>
+__device__ __forceinline__ void rbm_rows(const Lat& F, int I, int J, int K, int row, const double* __restrict__ coords,
+                                         const unsigned char* __restrict__ active, const double* __restrict__ Nprev,
+                                         double cx, double cy, double cz, double n[RBM_K], long long& p, int& a,
+                                         bool& ok) {
+  // row = local point (box order, i fastest) * BF + dof
+  const int lp = row / BF;
+  a = row - lp * BF;
+  const int ex = lp % 3, ey = (lp / 3) % 3, ez = lp / 9;
+  const int i = 3 * I + ex, j = 3 * J + ey, k = 3 * K + ez;
+  ok = lp < 27 && F.in(i, j, k);
+  p = ok ? F.id(i, j, k) : 0;
+  for (int m = 0; m < RBM_K; ++m) n[m] = 0.0;
+  if (!ok || !active[BF * p + a]) return;
+  if (BF == 3) {
+    const double x = coords[3 * p] - cx, y = coords[3 * p + 1] - cy, z = coords[3 * p + 2] - cz;
+    n[a] = 1.0;
+    // rotation about x: (0, -z, y); about y: (z, 0, -x); about z: (-y, x, 0)
+    if (a == 0) { n[4] = z; n[5] = -y; }
+    if (a == 1) { n[3] = -z; n[5] = x; }
+    if (a == 2) { n[3] = y; n[4] = -x; }
+  } else {
+    for (int m = 0; m < RBM_K; ++m) n[m] = Nprev[(long long)(a * RBM_K + m) * F.N + p];
+  }
+}
+
+template <int BF, int RPL>
+__global__ void __launch_bounds__(128) k_rbm_tentative(Lat F, Lat Cc, const double* __restrict__ coords,
+                                                        const unsigned char* __restrict__ active,
+                                                        const double* __restrict__ Nprev, double cx, double cy,
+                                                        double cz, double* __restrict__ Pt, double* __restrict__ Nc,
+                                                        unsigned char* __restrict__ ac) {
+  const long long Kc = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (Kc >= Cc.N) return;  // whole warps leave together
+  int I, J, K;
+  Cc.ijk(Kc, I, J, K);
+  double v[RPL][RBM_K], q[RPL][RBM_K];
+  long long pp[RPL];
+  int aa[RPL];
+  bool ok[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    rbm_rows<BF>(F, I, J, K, lane + 32 * t, coords, active, Nprev, cx, cy, cz, v[t], pp[t], aa[t], ok[t]);
+#pragma unroll
+    for (int m = 0; m < RBM_K; ++m) q[t][m] = 0.0;
+  }
+  double R[RBM_K][RBM_K];
+#pragma unroll
+  for (int a = 0; a < RBM_K; ++a)
+#pragma unroll
+    for (int b = 0; b < RBM_K; ++b) R[a][b] = 0.0;
+  bool kept[RBM_K];
+#pragma unroll
+  for (int j = 0; j < RBM_K; ++j) {
+    double w[RPL];
+    double s0 = 0.0;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      w[t] = v[t][j];
+      s0 += w[t] * w[t];
+    }
+    const double n0 = sqrt(warp_sum_xor(s0));
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+      double h[RBM_K];
+#pragma unroll
+      for (int i = 0; i < RBM_K; ++i) {
+        if (i >= j) break;
+        double d = 0.0;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) d += q[t][i] * w[t];
+        h[i] = warp_sum_xor(d);
+      }
+#pragma unroll
+      for (int i = 0; i < RBM_K; ++i) {
+        if (i >= j) break;
+        R[i][j] += h[i];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) w[t] -= h[i] * q[t][i];
+      }
+    }
+    double s1 = 0.0;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) s1 += w[t] * w[t];
+    const double nv = sqrt(warp_sum_xor(s1));
+    kept[j] = n0 > 0.0 && nv > RBM_DROP * n0;
+    const double inv = kept[j] ? 1.0 / nv : 0.0;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) q[t][j] = kept[j] ? w[t] * inv : 0.0;
+    R[j][j] = kept[j] ? nv : 0.0;
+  }
+#pragma unroll
+  for (int t = 0; t < RPL; ++t)
+    if (ok[t])
+#pragma unroll
+      for (int j = 0; j < RBM_K; ++j) Pt[(long long)(aa[t] * RBM_K + j) * F.N + pp[t]] = q[t][j];
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < RBM_K; ++a) {
+#pragma unroll
+      for (int b = 0; b < RBM_K; ++b) Nc[(long long)(a * RBM_K + b) * Cc.N + Kc] = R[a][b];
+      ac[RBM_K * Kc + a] = kept[a] ? 1 : 0;
+    }
+  }
+}
+
+// Smoothed prolongator from the per-point tentative blocks:
+// P[a, J] = Pt[a] [agg(a) = J] - omega D_a^-1 sum_{b ~ a, agg(b) = J} A_ab Pt[b]
+template <int BF, int BC, int KIND>
+__global__ void k_build_P_t(Lat F, Lat Cc, const double* __restrict__ val, const double* __restrict__ dinv,
+                            const double* __restrict__ Pt, double omega, double* __restrict__ P) {
+  const int R = St<KIND>::R;
+  const int ns = p_slots(R);
+  const int nslot = ns * ns * ns;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= F.N * nslot) return;
+  const int s = (int)(tid / F.N);
+  const long long p = tid - (long long)s * F.N;
+  int a, b, c;
+  F.ijk(p, a, b, c);
+  const int sx = s % ns, sy = (s / ns) % ns, sz = s / (ns * ns);
+  const int I = p_lo(a, R) + sx, J = p_lo(b, R) + sy, K = p_lo(c, R) + sz;
+  double out[BF * BC];
+  for (int q = 0; q < BF * BC; ++q) out[q] = 0.0;
+  if (Cc.in(I, J, K)) {
+    double ap[BF * BC];
+    for (int q = 0; q < BF * BC; ++q) ap[q] = 0.0;
+    for (int o = 0; o < St<KIND>::N; ++o) {
+      int dx, dy, dz;
+      St<KIND>::off(o, dx, dy, dz);
+      const int na = a + dx, nb = b + dy, nc = c + dz;
+      if (!F.in(na, nb, nc)) continue;
+      if (na / 3 != I || nb / 3 != J || nc / 3 != K) continue;
+      const long long q = F.id(na, nb, nc);
+      const double* v = val + (long long)o * BF * BF * F.N + p;
+      for (int r = 0; r < BF; ++r)
+        for (int t = 0; t < BC; ++t) {
+          double z = 0.0;
+          for (int u = 0; u < BF; ++u) z += v[(long long)(r * BF + u) * F.N] * Pt[(long long)(u * BC + t) * F.N + q];
+          ap[r * BC + t] += z;
+        }
+    }
+    for (int r = 0; r < BF; ++r)
+      for (int t = 0; t < BC; ++t) {
+        double z = 0.0;
+        for (int u = 0; u < BF; ++u) z += dinv[(long long)(r * BF + u) * F.N + p] * ap[u * BC + t];
+        out[r * BC + t] = -omega * z;
+      }
+    if (a / 3 == I && b / 3 == J && c / 3 == K)
+      for (int q = 0; q < BF * BC; ++q) out[q] += Pt[(long long)q * F.N + p];
+  }
+  for (int q = 0; q < BF * BC; ++q) P[((long long)s * BF * BC + q) * F.N + p] = out[q];
 }
 
 // Galerkin faces -> cells: A_1[T, T'] = sum_{f in T, g} pw_f C_fg pw_g [T' adjacent to g]
@@ -1006,76 +900,16 @@ __global__ void k_rap_faces(FaceTopo d, const int* __restrict__ col, const doubl
 }
 
 // ------------------------------------------------------------------ host helpers
-template <class F>
-void dispatch_kind(int kind, F&& f) {
-  if (kind == ST_BOX1) f(std::integral_constant<int, ST_BOX1>{});
-  else if (kind == ST_DIAMOND2) f(std::integral_constant<int, ST_DIAMOND2>{});
-  else f(std::integral_constant<int, ST_BOX2>{});
-}
-
-template <class F>
-void dispatch_bs(int bs, F&& f) {
-  if (bs == 3) f(std::integral_constant<int, 3>{});
-  else f(std::integral_constant<int, 1>{});
-}
-
-template <class F>
-void dispatch_r(int R, F&& f) {
-  if (R == 2) f(std::integral_constant<int, 2>{});
-  else f(std::integral_constant<int, 1>{});
-}
-
 // the face level's topology for the sweeps and transfers (32-bit: nF < 2^31)
 FaceTopo32 face_topo(const Ctx& c) {
   if (c.nF >= (1LL << 31) / 11) throw Error{MHFP_ERR_ARG, "too many faces for 32-bit face indexing"};
   return FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy);
 }
 
-// 32-bit lattice view for the coarse-level kernels (their indices e N + p
-// and bs q + s stay below 2^31)
-Lat32 lat32_of(const StructOp& A) {
-  if ((long long)A.bs * A.bs * A.N >= (1LL << 31))
-    throw Error{MHFP_ERR_ARG, "lattice level too large for 32-bit indexing"};
-  Lat32 L;
-  L.Lx = A.Lx;
-  L.Ly = A.Ly;
-  L.Lz = A.Lz;
-  L.N = (int)A.N;
-  L.LxLy = A.Lx * A.Ly;
-  L.dx = Div32::make((unsigned)A.Lx);
-  L.dy = Div32::make((unsigned)A.Ly);
-  return L;
-}
-
-// Launch schedule of a level's sweeps and residuals: 1 = one point per
-// thread, W = 4, 8, 16 = warp-split offsets over W warps.  The set-up
-// autotuner times all four; without it, scalar levels of 64K points and up
-// take one point per thread and the others eight warps.
-int default_schedule(long long npts, int bs) { return (bs == 1 && npts >= 65536) ? 1 : 8; }
-
-template <class F>
-void dispatch_sched(int sched, F&& f) {
-  if (sched == 1) f(std::integral_constant<int, 1>{});
-  else if (sched == 4) f(std::integral_constant<int, 4>{});
-  else if (sched == 16) f(std::integral_constant<int, 16>{});
-  else f(std::integral_constant<int, 8>{});
-}
-
 // y = b - A x (y = A x when b is null) on a lattice level with schedule sched
 template <typename T>
 void launch_spmv(Ctx& c, const StructOp& A, int bs, const T* val, const T* x, const T* b, T* y, int sched) {
-  const Lat32 L = lat32_of(A);
-  dispatch_bs(bs, [&](auto BS) {
-    dispatch_kind(A.kind, [&](auto K) {
-      dispatch_sched(sched, [&](auto S) {
-        if constexpr (S.value == 1)
-          k_spmv_f<BS.value, K.value, T><<<grid_for(A.N, 256), 256, 0, c.stream>>>(L, val, x, b, y);
-        else
-          k_spmv_w<BS.value, K.value, S.value, T><<<grid_for(A.N, 32), dim3(32, S.value), 0, c.stream>>>(L, val, x,
-                                                                                                          b, y);
-      });
-    });
-  });
+  sweep_spmv<T>(c.stream, A, bs, val, x, b, y, sched);
 }
 
 void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
@@ -1108,10 +942,9 @@ double spectral_radius(Ctx& c, Level& L) {
   double rho = 0.0;
   for (int it = 0; it < c.opt.power_iters; ++it) {
     level_spmv(c, L, v, nullptr, L.r);
-    if (L.bs == 3)
-      k_apply_dinv<3><<<grid_for(L.npts, 256), 256, 0, c.stream>>>(L.npts, L.dinv, L.r, w);
-    else
-      k_apply_dinv<1><<<grid_for(L.npts, 256), 256, 0, c.stream>>>(L.npts, L.dinv, L.r, w);
+    dispatch_bs(L.bs, [&](auto BS) {
+      k_apply_dinv<BS.value><<<grid_for(L.npts, 256), 256, 0, c.stream>>>(L.npts, L.dinv, L.r, w);
+    });
     MHFP_LAUNCH_CHECK();
     rho = device_norm2(c, w, n);
     k_scale_by<<<grid_for(n, 256), 256, 0, c.stream>>>(n, 1.0 / rho, w);
@@ -1271,7 +1104,7 @@ void finish_level(Ctx& c, Level& L) {
   } else {
     const Lat lat = lat_of(L.A);
     dispatch_bs(L.bs, [&](auto BS) {
-      dispatch_kind(L.A.kind, [&](auto K) {
+      dispatch_kind_bs<BS.value>(L.A.kind, [&](auto K) {
         k_dinv<BS.value, K.value><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.A.val, L.dinv);
       });
     });
@@ -1288,6 +1121,7 @@ Level coarsen(Ctx& c, Level& L, Level* into = nullptr) {
   const StructOp& A = L.A;
   const int R = stencil_radius(A.kind);
   L.R = R;
+  L.cbs = L.bs;
   Level Cl;
   if (into) Cl = *into;
   Cl.bs = L.bs;
@@ -1317,20 +1151,25 @@ Level coarsen(Ctx& c, Level& L, Level* into = nullptr) {
   }
   const double omega = 4.0 / (3.0 * L.lmax);
   try {
-    dispatch_bs(L.bs, [&](auto BS) {
-      dispatch_kind(A.kind, [&](auto K) {
+    dispatch_bs13(L.bs, [&](auto BS) {
+      dispatch_kind_bs<BS.value>(A.kind, [&](auto K) {
         k_build_P<BS.value, K.value><<<grid_for(F.N * ns * ns * ns, 256), 256, 0, c.stream>>>(F, Cc, A.val, L.dinv,
                                                                                              L.active, omega, L.P);
         MHFP_LAUNCH_CHECK();
         k_active_coarse<BS.value><<<grid_for(Cc.N, 256), 256, 0, c.stream>>>(F, Cc, L.active, Cl.active);
         MHFP_LAUNCH_CHECK();
-        k_build_Q<BS.value, K.value><<<grid_for(F.N * nq * nq * nq, 256), 256, 0, c.stream>>>(F, Cc, A.val, L.P, Q);
+        k_build_Q<BS.value, BS.value, K.value><<<grid_for(F.N * nq * nq * nq, 256), 256, 0, c.stream>>>(F, Cc, A.val,
+                                                                                                     L.P, Q);
         MHFP_LAUNCH_CHECK();
       });
-      if (Cl.A.kind == ST_BOX1)
-        k_rap<BS.value, ST_BOX1><<<grid_for(Cc.N * 27, 128), 128, 0, c.stream>>>(F, Cc, R, L.P, Q, Cl.active, Cl.A.val);
+      // coarse levels of the 27-point displacement lattice stay 27-point; the
+      // scalar levels become 125-point
+      if constexpr (BS.value == 3)
+        k_rap<BS.value, BS.value, ST_BOX1><<<grid_for(Cc.N * 27, 128), 128, 0, c.stream>>>(F, Cc, R, L.P, Q,
+                                                                                           Cl.active, Cl.A.val);
       else
-        k_rap<BS.value, ST_BOX2><<<grid_for(Cc.N * 125, 128), 128, 0, c.stream>>>(F, Cc, R, L.P, Q, Cl.active, Cl.A.val);
+        k_rap<BS.value, BS.value, ST_BOX2><<<grid_for(Cc.N * 125, 128), 128, 0, c.stream>>>(F, Cc, R, L.P, Q,
+                                                                                             Cl.active, Cl.A.val);
       MHFP_LAUNCH_CHECK();
     });
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
@@ -1342,7 +1181,7 @@ Level coarsen(Ctx& c, Level& L, Level* into = nullptr) {
   return Cl;
 }
 
-void build_u(Ctx& c) {
+void build_u_level0(Ctx& c) {
   c.hu.clear();
   Level L0;
   L0.bs = 3;
@@ -1361,11 +1200,101 @@ void build_u(Ctx& c) {
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
   }
   c.hu.push_back(L0);
+}
+
+void build_u(Ctx& c) {
+  build_u_level0(c);
   while (c.hu.back().npts > c.opt.coarse_max && c.hu.size() < 8) {
     Level& L = c.hu.back();
     alloc_work(c, L);
     finish_level(c, L);
     Level Cl = coarsen(c, L);
+    c.hu.push_back(Cl);
+  }
+  Level& last = c.hu.back();
+  alloc_work(c, last);
+  make_dense_coarse(c, last);
+}
+
+// The displacement hierarchy of M_III^(h): the same aggregates, with the six
+// rigid-body modes as the near-kernel.  Level 0 is A_uu (3 dofs per node);
+// every coarse point carries 6 dofs (a mode its aggregate cannot represent
+// leaves an inactive dof with a unit diagonal).  P = (I - omega D^-1 A) P_t
+// with P_t the Gram-Schmidt factors of the aggregates, Galerkin coarse
+// operators in the same two gather passes as M_II^(h).
+void build_u_rbm(Ctx& c) {
+  build_u_level0(c);
+  // centroid of the nodes (the rotations' axis point), summed in node order
+  double cen[3] = {0, 0, 0};
+  {
+    std::vector<double> xyz(3 * c.nN);
+    MHFP_CUDA(cudaMemcpyAsync(xyz.data(), c.coords, xyz.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    for (long long p = 0; p < c.nN; ++p)
+      for (int a = 0; a < 3; ++a) cen[a] += xyz[3 * p + a];
+    for (int a = 0; a < 3; ++a) cen[a] /= (double)c.nN;
+  }
+  const double* Nprev = nullptr;
+  while (c.hu.back().npts > c.opt.coarse_max && c.hu.size() < 8) {
+    Level& L = c.hu.back();
+    alloc_work(c, L);
+    finish_level(c, L);
+    const int BFv = L.bs;
+    const StructOp& A = L.A;
+    L.R = 1;
+    L.cbs = RBM_K;
+    Level Cl;
+    Cl.bs = RBM_K;
+    Cl.A.Lx = (A.Lx + 2) / 3; Cl.A.Ly = (A.Ly + 2) / 3; Cl.A.Lz = (A.Lz + 2) / 3;
+    Cl.A.N = (long long)Cl.A.Lx * Cl.A.Ly * Cl.A.Lz;
+    Cl.A.bs = RBM_K;
+    Cl.A.kind = ST_BOX1;
+    Cl.npts = Cl.A.N;
+    Cl.n = Cl.A.N * RBM_K;
+    Cl.R = 1;
+    const Lat F = lat_of(A), Cc = lat_of(Cl.A);
+    const int ns = p_slots(1), nq = q_slots(1);
+    const int pb = BFv * RBM_K;
+    double* Pt = dalloc_n<double>(c, (size_t)pb * F.N);
+    double* Nc = dalloc_n<double>(c, (size_t)RBM_K * RBM_K * Cc.N);
+    Cl.active = dalloc_n<unsigned char>(c, Cl.n);
+    L.P = dalloc_n<double>(c, (size_t)ns * ns * ns * pb * F.N);
+    Cl.A.val = dalloc_n<double>(c, (size_t)27 * RBM_K * RBM_K * Cc.N);
+    MHFP_CUDA(cudaMemsetAsync(Pt, 0, (size_t)pb * F.N * sizeof(double), c.stream));
+    const double omega = 4.0 / (3.0 * L.lmax);
+    double* Q = nullptr;
+    MHFP_CUDA(cudaMalloc(&Q, (size_t)nq * nq * nq * pb * F.N * sizeof(double)));
+    try {
+      const unsigned warps = grid_for(Cc.N * 32, 128);
+      auto galerkin = [&](auto BF) {
+        constexpr int bf = decltype(BF)::value;
+        k_build_P_t<bf, RBM_K, ST_BOX1><<<grid_for(F.N * ns * ns * ns, 256), 256, 0, c.stream>>>(F, Cc, A.val, L.dinv,
+                                                                                                 Pt, omega, L.P);
+        MHFP_LAUNCH_CHECK();
+        k_build_Q<bf, RBM_K, ST_BOX1><<<grid_for(F.N * nq * nq * nq, 256), 256, 0, c.stream>>>(F, Cc, A.val, L.P, Q);
+        MHFP_LAUNCH_CHECK();
+        k_rap<bf, RBM_K, ST_BOX1><<<grid_for(Cc.N * 27, 128), 128, 0, c.stream>>>(F, Cc, 1, L.P, Q, Cl.active,
+                                                                                   Cl.A.val);
+        MHFP_LAUNCH_CHECK();
+      };
+      if (BFv == 3) {
+        k_rbm_tentative<3, 3><<<warps, 128, 0, c.stream>>>(F, Cc, c.coords, L.active, nullptr, cen[0], cen[1], cen[2],
+                                                           Pt, Nc, Cl.active);
+        MHFP_LAUNCH_CHECK();
+        galerkin(std::integral_constant<int, 3>{});
+      } else {
+        k_rbm_tentative<RBM_K, 6><<<warps, 128, 0, c.stream>>>(F, Cc, c.coords, L.active, Nprev, cen[0], cen[1],
+                                                               cen[2], Pt, Nc, Cl.active);
+        MHFP_LAUNCH_CHECK();
+        galerkin(std::integral_constant<int, RBM_K>{});
+      }
+      MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    } catch (...) {
+      cudaFree(Q);
+      throw;
+    }
+    MHFP_CUDA(cudaFree(Q));
+    Nprev = Nc;
     c.hu.push_back(Cl);
   }
   Level& last = c.hu.back();
@@ -1445,24 +1374,10 @@ void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
 template <typename T>
 void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* out, T cd, T cr, int sched) {
   if (!xin) {
-    dispatch_bs(L.bs, [&](auto BS) {
-      k_cheb_zero<BS.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(L.A.N, v.dinv, b, out, v.d, cr);
-    });
+    sweep_cheb_zero<T>(c.stream, L.A.N, L.bs, v.dinv, b, out, v.d, cr);
     return;
   }
-  const Lat32 lat = lat32_of(L.A);
-  dispatch_bs(L.bs, [&](auto BS) {
-    dispatch_kind(L.A.kind, [&](auto K) {
-      dispatch_sched(sched, [&](auto S) {
-        if constexpr (S.value == 1)
-          k_cheb_f<BS.value, K.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out,
-                                                                                     v.d, cd, cr);
-        else
-          k_cheb_w<BS.value, K.value, S.value, T><<<grid_for(L.A.N, 32), dim3(32, S.value), 0, c.stream>>>(
-              lat, v.val, v.dinv, b, xin, out, v.d, cd, cr);
-      });
-    });
-  });
+  sweep_cheb<T>(c.stream, L.A, L.bs, v.val, v.dinv, b, xin, out, v.d, cd, cr, sched);
 }
 
 // The symmetric FP32 sweep and residual of the finest displacement level
@@ -1479,7 +1394,7 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
                      float cr) {
   const Lat lat = lat_of(L.A);
   if (!xin) {  // the first step from zero has no stencil work
-    k_cheb_zero<3, float><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat.N, L.dinvf, b, xout, d, cr);
+    sweep_cheb_zero<float>(c.stream, lat.N, 3, L.dinvf, b, xout, d, cr);
     MHFP_LAUNCH_CHECK();
     return;
   }
@@ -1676,9 +1591,10 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
     k_restrict_faces<T><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb);
   } else {
     const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
-    dispatch_bs(L.bs, [&](auto BS) {
+    dispatch_pair(L.bs, C.bs, [&](auto BF, auto BC) {
       dispatch_r(L.R, [&](auto RR) {
-        k_restrict_f<BS.value, RR.value, T><<<grid_for(C.A.N * 32, 256), 256, 0, c.stream>>>(F, Cc, v.P, v.r, cb);
+        k_restrict_f<BF.value, BC.value, RR.value, T><<<grid_for(C.A.N * 32, 256), 256, 0, c.stream>>>(F, Cc, v.P,
+                                                                                                       v.r, cb);
       });
     });
   }
@@ -1689,12 +1605,13 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   } else {
     // one fine point per thread on large levels, slots split over 8 warps on small ones
     const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
-    dispatch_bs(L.bs, [&](auto BS) {
+    dispatch_pair(L.bs, C.bs, [&](auto BF, auto BC) {
       dispatch_r(L.R, [&](auto RR) {
         if (L.A.N >= 65536)
-          k_prolong_f<BS.value, RR.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(F, Cc, v.P, cx, x);
+          k_prolong_f<BF.value, BC.value, RR.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(F, Cc, v.P, cx, x);
         else
-          k_prolong_w<BS.value, RR.value, 8, T><<<grid_for(L.A.N, 32), dim3(32, 8), 0, c.stream>>>(F, Cc, v.P, cx, x);
+          k_prolong_w<BF.value, BC.value, RR.value, 8, T><<<grid_for(L.A.N, 32), dim3(32, 8), 0, c.stream>>>(
+              F, Cc, v.P, cx, x);
       });
     });
   }
@@ -1731,7 +1648,7 @@ void make_fp32(Ctx& c, std::vector<Level>& H, bool fine_sym) {
     if (L.dinv) L.dinvf = cast_copy(c, L.dinv, bs2 * L.npts);
     if (L.P) {
       const int ns = p_slots(L.R);
-      L.Pf = cast_copy(c, L.P, (size_t)ns * ns * ns * bs2 * L.npts);
+      L.Pf = cast_copy(c, L.P, (size_t)ns * ns * ns * L.bs * L.cbs * L.npts);
     }
     L.xf = dalloc_n<float>(c, L.n);
     L.bf = dalloc_n<float>(c, L.n);
@@ -1744,7 +1661,8 @@ void make_fp32(Ctx& c, std::vector<Level>& H, bool fine_sym) {
 }  // namespace
 
 void build_hierarchies(Ctx& c) {
-  build_u(c);
+  if (c.opt.near_kernel == 1) build_u_rbm(c);
+  else build_u(c);
   build_pi(c);
   if (c.opt.precision == 1) {
     make_fp32(c, c.hu, true);
@@ -1806,7 +1724,7 @@ void rebuild_pi_hierarchy(Ctx& c) {
       if (L.dinv && L.dinvf) recast(L.dinvf, L.dinv, bs2 * L.npts);
       if (L.P && L.Pf) {
         const int ns = p_slots(L.R);
-        recast(L.Pf, L.P, (size_t)ns * ns * ns * bs2 * L.npts);
+        recast(L.Pf, L.P, (size_t)ns * ns * ns * L.bs * L.cbs * L.npts);
       }
     }
     recast(c.Cpif, c.Cpi, (size_t)11 * c.nF);

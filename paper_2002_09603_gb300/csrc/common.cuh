@@ -234,6 +234,7 @@ struct Level {
   // prolongator to the next level (lattice levels only): [p_slots^3][bs*bs][npts]
   double* P = nullptr;
   int R = 1;                  // stencil radius of A (L_inf)
+  int cbs = 0;                // unknowns per point of the next level (P blocks are bs x cbs)
   int tpp = 0;                // launch schedule chosen by the autotuner (0: default rule):
                               // 1 = one point per thread, 4/8/16 = warps splitting the
                               // offsets; finest FP32 displacement level: blocks per SM (6, 8)
