@@ -110,9 +110,12 @@ typedef struct {
                         /* rule when autotune = 0); 1, 4, 8 or 16: every       */
                         /* coarse lattice level uses that schedule (1 = one    */
                         /* point per thread, W = offsets over W warps)         */
-  int fine_blocks;      /* 0 (default): autotuned (size rule without it); 6 or */
-                        /* 8: resident blocks per SM of the finest FP32        */
-                        /* displacement sweep and residual (precision = 1)     */
+  int fine_blocks;      /* finest FP32 displacement sweep and residual         */
+                        /* (precision = 1): 0 (default) autotuned (size rule   */
+                        /* without it); 6 or 8: one node per thread with that  */
+                        /* many resident blocks of 256 per SM; 4: persistent   */
+                        /* CTAs (4 per SM) fed by bulk copies of the stored    */
+                        /* rows into shared memory (same sums, same order)     */
   int near_kernel;      /* near-kernel of the displacement multigrid (Section  */
                         /* 5): 0 (default) the three translations per          */
                         /* aggregate, separate displacement components         */
@@ -140,8 +143,8 @@ typedef struct {
   double lmax[8];       /* 1.1 * rho(D^-1 A) per level (0 on the last level)   */
   int schedule[8];      /* launch schedule of the level's sweeps: 1 = one point */
                         /* per thread, 4/8/16 = offsets split over that many    */
-                        /* warps; finest FP32 displacement level: resident     */
-                        /* blocks per SM (6 or 8); 0 = not a lattice sweep     */
+                        /* warps; finest FP32 displacement level: fine_blocks  */
+                        /* (4, 6 or 8); 0 = not a lattice sweep                */
   double sweep_us[8];   /* set-up autotuner's time of one sweep under that     */
                         /* schedule, microseconds (0 when not timed)           */
 } mhfp_hierarchy_info;

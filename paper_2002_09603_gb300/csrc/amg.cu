@@ -171,6 +171,193 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
 
 // </hot:k_cheb_u0_sym>
 
+// <hot:k_cheb_u0_tma> (hashed like the regions above)
+// The same FP32 symmetric-storage sweep and residual, fed by bulk copies.
+// A persistent CTA of TMA_NB threads takes node blocks of TMA_NB
+// consecutive nodes; for each block it streams the 14 stored slots u: the
+// 9 rows of the node's own blocks A(p, p + e_u) and, for u >= 1, the 9 rows
+// of the neighbours' blocks A(p - e_u, p) (read transposed), each row one
+// cp.async.bulk copy of TMA_NB (+4) floats from global into shared memory,
+// TMA_S slots in flight behind an mbarrier each.  The products are summed
+// in the order of sym_residual, so results are bit-identical to it.  Every
+// mbarrier wait is bounded: after about 2^31 clocks the CTA records
+// MHFP_WAIT_TIMEOUT in *err, drains what it issued (again bounded) and
+// returns.
+constexpr int TMA_NB = 128;                  // nodes (threads) per node block
+constexpr int TMA_S = 5;                     // slots in flight
+constexpr int TMA_ROW_OWN = TMA_NB;          // floats per own row
+constexpr int TMA_ROW_TR = TMA_NB + 4;       // floats per transposed row (aligned superset)
+constexpr int TMA_STAGE = 9 * TMA_ROW_OWN + 9 * TMA_ROW_TR;  // floats per stage
+constexpr int MHFP_WAIT_TIMEOUT = 8;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+struct TmaSweep {
+  const float* up;   // symmetric half [14][9][ld] (+ padding)
+  long long ld;
+  const float* dinv; // [9][N]
+  const float *b, *xin;
+  float *xout, *d;
+  float cd, cr;
+  int* err;
+};
+
+// issue the copies of stage (node block wb, slot u) into buf
+__device__ __forceinline__ void tma_issue(const TmaSweep& a, int wb, int u, int su, float* buf,
+                                          unsigned long long* bar) {
+  const long long p0 = (long long)wb * TMA_NB;
+  const unsigned own_bytes = TMA_ROW_OWN * 4;
+  const unsigned tr_bytes = TMA_ROW_TR * 4;
+  mbar_expect_tx(bar, u == 0 ? 9 * own_bytes : 9 * (own_bytes + tr_bytes));
+  const float* slot = a.up + (long long)u * 9 * a.ld;
+#pragma unroll 1
+  for (int e = 0; e < 9; ++e) bulk_to_smem(buf + e * TMA_ROW_OWN, slot + e * a.ld + p0, own_bytes, bar);
+  if (u > 0) {
+    // rows of nodes p0 - su ..: from the 16-byte boundary at or below
+    const long long q0 = ((p0 - su) >> 2) << 2;
+#pragma unroll 1
+    for (int e = 0; e < 9; ++e)
+      bulk_to_smem(buf + 9 * TMA_ROW_OWN + e * TMA_ROW_TR, slot + e * a.ld + q0, tr_bytes, bar);
+  }
+}
+
+template <bool CHEB>
+__global__ void __launch_bounds__(TMA_NB, 4) k_sym_tma(Lat L, TmaSweep a) {
+  __shared__ __align__(128) float stage[TMA_S][TMA_STAGE];
+  __shared__ __align__(8) unsigned long long full[TMA_S];
+  const int t = threadIdx.x;
+  const int nblocks = (int)((L.N + TMA_NB - 1) / TMA_NB);
+  const int my = (nblocks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // node blocks of this CTA
+  const int units = my * 14;
+  // lattice shift of slot u (node p's stored neighbour is p + shift)
+  auto shift = [&](int u) {
+    int dx, dy, dz;
+    St<ST_BOX1>::off(13 + u, dx, dy, dz);
+    return u == 0 ? 0 : dx + L.Lx * (dy + L.Ly * dz);
+  };
+  if (t == 0) {
+    for (int s = 0; s < TMA_S; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0)
+    for (int g = 0; g < TMA_S && g < units; ++g)
+      tma_issue(a, (int)blockIdx.x + (g / 14) * (int)gridDim.x, g % 14, shift(g % 14), stage[g], &full[g]);
+  bool ok = true;
+  int g = 0;
+  for (int k = 0; k < my && ok; ++k) {
+    const int wb = (int)blockIdx.x + k * (int)gridDim.x;
+    const long long p = (long long)wb * TMA_NB + t;
+    const bool valid = p < L.N;
+    const long long pc = valid ? p : L.N - 1;
+    int i, j, kk;
+    L.ijk(pc, i, j, kk);
+    float r[3] = {a.b[3 * pc], a.b[3 * pc + 1], a.b[3 * pc + 2]};
+    for (int u = 0; u < 14; ++u, ++g) {
+      const int buf = g % TMA_S;
+      // a thread whose wait ran out still reads (in-bounds) shared memory;
+      // the vote below makes the whole CTA stop together
+      const bool arrived = mbar_wait(&full[buf], (unsigned)(g / TMA_S) & 1u);
+      const float* st = stage[buf];
+      if (u == 0) {
+        const float x0 = a.xin[3 * pc], x1 = a.xin[3 * pc + 1], x2 = a.xin[3 * pc + 2];
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+          r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * x0 + st[(3 * e + 1) * TMA_ROW_OWN + t] * x1 +
+                  st[(3 * e + 2) * TMA_ROW_OWN + t] * x2;
+      } else {
+        int dx, dy, dz;
+        St<ST_BOX1>::off(13 + u, dx, dy, dz);
+        const int su = dx + L.Lx * (dy + L.Ly * dz);
+        const bool inp = L.in(i + dx, j + dy, kk + dz), inm = L.in(i - dx, j - dy, kk - dz);
+        if (inp) {
+          const long long q = pc + su;
+          const float x0 = a.xin[3 * q], x1 = a.xin[3 * q + 1], x2 = a.xin[3 * q + 2];
+#pragma unroll
+          for (int e = 0; e < 3; ++e)
+            r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * x0 + st[(3 * e + 1) * TMA_ROW_OWN + t] * x1 +
+                    st[(3 * e + 2) * TMA_ROW_OWN + t] * x2;
+        }
+        if (inm) {
+          const long long q = pc - su;
+          const long long p0 = (long long)wb * TMA_NB;
+          const int off = (int)((p0 - su) - (((p0 - su) >> 2) << 2)) + t;
+          const float* tr = st + 9 * TMA_ROW_OWN;
+          const float x0 = a.xin[3 * q], x1 = a.xin[3 * q + 1], x2 = a.xin[3 * q + 2];
+#pragma unroll
+          for (int e = 0; e < 3; ++e)
+            r[e] -= tr[e * TMA_ROW_TR + off] * x0 + tr[(3 + e) * TMA_ROW_TR + off] * x1 +
+                    tr[(6 + e) * TMA_ROW_TR + off] * x2;
+        }
+      }
+      // every thread is done with this buffer (and every copy arrived)
+      if (!__syncthreads_and(arrived)) {
+        ok = false;
+        ++g;
+        break;
+      }
+      if (t == 0 && g + TMA_S < units) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int gn = g + TMA_S;
+        tma_issue(a, (int)blockIdx.x + (gn / 14) * (int)gridDim.x, gn % 14, shift(gn % 14), stage[buf], &full[buf]);
+      }
+    }
+    if (!ok) break;
+    if (valid) {
+      if (CHEB) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const float z = a.dinv[(3 * e) * L.N + p] * r[0] + a.dinv[(3 * e + 1) * L.N + p] * r[1] +
+                          a.dinv[(3 * e + 2) * L.N + p] * r[2];
+          const float dn = (a.cd != 0.f) ? a.cd * a.d[3 * p + e] + a.cr * z : a.cr * z;
+          a.d[3 * p + e] = dn;
+          a.xout[3 * p + e] = a.xin[3 * p + e] + dn;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) a.xout[3 * p + e] = r[e];
+      }
+    }
+  }
+  if (!ok) {
+    // a copy did not arrive in time: report, then drain what was issued
+    // (units up to g - 1 + TMA_S; the failed one, g - 1, included)
+    if (t == 0) atomicOr(a.err, MHFP_WAIT_TIMEOUT);
+    for (int h = g - 1; h < units && h < g - 1 + TMA_S; ++h)
+      mbar_wait(&full[h % TMA_S], (unsigned)(h / TMA_S) & 1u);
+  }
+}
+// </hot:k_cheb_u0_tma>
+
 // ---------------------------------------------------------------- transfers
 // Prolongation x += P x_c and restriction b_c = P^T r between lattice levels,
 // with the same 32-bit indexing and batched loads as the sweeps.  P is
@@ -1387,8 +1574,20 @@ void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* 
 // 256 threads per SM (0: 8 when one wave of 8 blocks per SM covers the
 // level, else 6)
 int sym_minb(const Level& L) {
-  if (L.tpp == 6 || L.tpp == 8) return L.tpp;
+  if (L.tpp == 4 || L.tpp == 6 || L.tpp == 8) return L.tpp;
   return L.A.N <= 152LL * 8 * 256 ? 8 : 6;
+}
+
+// the bulk-copy-fed variant (schedule 4): persistent CTAs, 4 per SM
+void launch_sym_tma(Ctx& c, const Level& L, bool cheb, const float* b, const float* xin, float* xout, float* d,
+                    float cd, float cr) {
+  const Lat lat = lat_of(L.A);
+  if (lat.N >= (1LL << 31) - TMA_NB) throw Error{MHFP_ERR_ARG, "level too large for the bulk-copy sweep"};
+  const long long nblocks = (lat.N + TMA_NB - 1) / TMA_NB;
+  const unsigned grid = (unsigned)std::min<long long>(nblocks, 4LL * c.n_sm);
+  TmaSweep a{L.symf, L.sym_ld, L.dinvf, b, xin, xout, d, cd, cr, c.d_flag};
+  if (cheb) k_sym_tma<true><<<grid, TMA_NB, 0, c.stream>>>(lat, a);
+  else k_sym_tma<false><<<grid, TMA_NB, 0, c.stream>>>(lat, a);
 }
 void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, float* xout, float* d, float cd,
                      float cr) {
@@ -1398,7 +1597,9 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
     MHFP_LAUNCH_CHECK();
     return;
   }
-  if (sym_minb(L) == 8)
+  if (sym_minb(L) == 4)
+    launch_sym_tma(c, L, true, b, xin, xout, d, cd, cr);
+  else if (sym_minb(L) == 8)
     k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
                                                                         d, cd, cr);
   else
@@ -1408,7 +1609,9 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
 }
 void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, float* y) {
   const Lat lat = lat_of(L.A);
-  if (sym_minb(L) == 8)
+  if (sym_minb(L) == 4)
+    launch_sym_tma(c, L, false, b, x, y, nullptr, 0.f, 0.f);
+  else if (sym_minb(L) == 8)
     k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
   else
     k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
@@ -1475,7 +1678,7 @@ void autotune_fine_sym(Ctx& c, Level& L) {
   MHFP_CUDA(cudaMemsetAsync(L.df, 0, L.n * sizeof(float), c.stream));
   float best = 1e30f;
   int best_minb = 0;
-  for (int minb : {8, 6}) {
+  for (int minb : {8, 6, 4}) {
     L.tpp = minb;
     const float us = graph_time_us(c, 5, [&] { launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f); });
     if (us < best) {
@@ -1638,8 +1841,11 @@ void make_fp32(Ctx& c, std::vector<Level>& H, bool fine_sym) {
     if (fine_sym && l == 0 && !L.dense_inv) {
       const long long N = L.A.N;
       L.sym_ld = (N + 63) / 64 * 64;  // rows start on 256-byte boundaries
-      L.symf = dalloc_n<float>(c, (size_t)126 * L.sym_ld);
-      MHFP_CUDA(cudaMemsetAsync(L.symf, 0, (size_t)126 * L.sym_ld * sizeof(float), c.stream));
+      // zeroed tail: the bulk-copy sweep reads whole node blocks, up to one
+      // block past the last row
+      const size_t sym_elems = (size_t)126 * L.sym_ld + 2 * TMA_NB;
+      L.symf = dalloc_n<float>(c, sym_elems);
+      MHFP_CUDA(cudaMemsetAsync(L.symf, 0, sym_elems * sizeof(float), c.stream));
       k_cast_f32_rows<<<grid_for(126 * N, 256), 256, 0, c.stream>>>(126, N, L.A.val + 13 * 9 * N, L.symf, L.sym_ld);
       MHFP_LAUNCH_CHECK();
     } else if (!L.faces) {

@@ -195,6 +195,7 @@ mhfp_status mhfp_create(const mhfp_mesh* mesh, const mhfp_materials* mat, double
     int dev = 0;
     MHFP_CUDA(cudaGetDevice(&dev));
     c.device = dev;
+    MHFP_CUDA(cudaDeviceGetAttribute(&c.n_sm, cudaDevAttrMultiProcessorCount, dev));
     for (long long i = 0; i < 3 * c.nN; ++i)
       if (!std::isfinite(mesh->coords[i])) throw Error{MHFP_ERR_ARG, "non-finite node coordinate"};
     c.coords = upload(c, mesh->coords, 3 * c.nN);
@@ -236,7 +237,7 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
           (opt->autotune != 0 && opt->autotune != 1) || (opt->reorth != 0 && opt->reorth != 1) ||
           (opt->schedule != 0 && opt->schedule != 1 && opt->schedule != 4 && opt->schedule != 8 &&
            opt->schedule != 16) ||
-          (opt->fine_blocks != 0 && opt->fine_blocks != 6 && opt->fine_blocks != 8) ||
+          (opt->fine_blocks != 0 && opt->fine_blocks != 4 && opt->fine_blocks != 6 && opt->fine_blocks != 8) ||
           (opt->near_kernel != 0 && opt->near_kernel != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;

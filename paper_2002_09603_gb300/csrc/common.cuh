@@ -290,6 +290,7 @@ struct Timing {
 
 struct Ctx {
   int device = 0;
+  int n_sm = 152;           // multiprocessors of the device
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0, nz = 0;
   long long nN = 0, nT = 0, nF = 0, nFx = 0, nFy = 0, nU = 0, n = 0;

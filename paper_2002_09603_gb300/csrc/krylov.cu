@@ -946,10 +946,29 @@ void solve_device_graph_finish(Ctx& c, double* x, mhfp_stats* st) {
   if (!h.converged) throw Error{MHFP_ERR_NOT_CONVERGED, "FGMRES reached maxit before the tolerance"};
 }
 
+// The bulk-copy sweep records a wait that ran out of time in bit 8 of the
+// handle's device flag instead of hanging; read it after a solve.
+void check_wait_flag(Ctx& c) {
+  if (c.hu.empty() || c.hu[0].tpp != 4 || c.opt.precision != 1) return;
+  int h = 0;
+  MHFP_CUDA(cudaMemcpyAsync(&h, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  if (h & 8) {
+    MHFP_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+    throw Error{MHFP_ERR_CUDA, "a bulk copy of the finest displacement sweep did not arrive in time"};
+  }
+}
+
 void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st, bool transpose) {
   if (c.opt.graphs == 2 && !c.timing.enabled) {
     solve_device_graph_launch(c, b, tol, transpose);
-    solve_device_graph_finish(c, x, st);
+    try {
+      solve_device_graph_finish(c, x, st);
+    } catch (...) {
+      check_wait_flag(c);
+      throw;
+    }
+    check_wait_flag(c);
     return;
   }
   FgState f;
@@ -961,9 +980,11 @@ void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st
     }
   } catch (const Error& e) {
     if (st) *st = f.stats;
+    check_wait_flag(c);
     throw;
   }
   if (st) *st = f.stats;
+  check_wait_flag(c);
 }
 
 }  // namespace mhfp
