@@ -196,6 +196,27 @@ mhfp_status mhfp_solve(mhfp_handle h, const double* d_rhs, double* d_x, double t
 mhfp_status mhfp_solve_batch(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
                              double tol, mhfp_stats* stats, mhfp_status* statuses);
 
+/* Many solves in one CUDA graph launch (not in the paper: batching of its
+ * solve over parameter samples, meshes and loads).  Entry i solves handle
+ * hs[i] for d_rhs[i] into d_x[i] (device vectors of that handle's size) with
+ * the algorithm of mhfp_solve.  Entries of one handle run one after another
+ * in list order (they share its Krylov workspace); entries of different
+ * handles are independent branches of the graph and run concurrently.  The
+ * graph is built and instantiated once by mhfp_batch_create (the device-
+ * driven solve of mhfp_solve, with the copies of b and x and the control
+ * block's reset as graph nodes), and every mhfp_batch_run is one
+ * cudaGraphLaunch on `stream` (NULL: the legacy default stream) followed by
+ * a synchronisation; the handles' own streams are synchronised first.  The
+ * vector pointers are fixed at creation.  After mhfp_update_logk on any of
+ * its handles a batch reports MHFP_ERR_STATE and must be created again.
+ * stats / statuses: count entries each (may be NULL); solve_ms is the whole
+ * launch's wall time.  Returns the first non-OK status. */
+typedef struct mhfp_batch_s* mhfp_batch;
+mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
+                              double tol, mhfp_batch* out);
+mhfp_status mhfp_batch_run(mhfp_batch b, void* stream, mhfp_stats* stats, mhfp_status* statuses);
+void mhfp_batch_destroy(mhfp_batch b);
+
 /* y = A_H x (Eq. stab_A, hybrid form), unscaled. */
 mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y);
 

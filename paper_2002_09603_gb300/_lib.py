@@ -24,7 +24,8 @@ EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhf
            "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_operator_t", "mhfp_adjoint_solve",
            "mhfp_grad_logk", "mhfp_misfit", "mhfp_adjoint_rhs", "mhfp_apply_precond_t", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
-           "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_update_logk", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
+           "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_update_logk",
+           "mhfp_batch_create", "mhfp_batch_run", "mhfp_batch_destroy", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
 
 
 class MhfpError(RuntimeError):
@@ -101,6 +102,9 @@ def load(path: str | None = None):
         "mhfp_timing_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d), C.POINTER(d)]),
         "mhfp_residual_norm_noalloc": (i, [vp, vp, vp, vp]),
         "mhfp_update_logk": (i, [vp, vp]),
+        "mhfp_batch_create": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, C.POINTER(vp)]),
+        "mhfp_batch_run": (i, [vp, vp, C.POINTER(Stats), C.POINTER(i)]),
+        "mhfp_batch_destroy": (None, [vp]),
         "mhfp_solve_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, C.POINTER(Stats),
                                  C.POINTER(i)]),
         "mhfp_launch_count": (ll, []),
@@ -363,6 +367,52 @@ def solve_batch(solvers, rhs, tol=1e-8, out=None):
     codes = (C.c_int * n)()
     load().mhfp_solve_batch(n, H, R, X, float(tol), st, codes)
     return xs, [s.as_dict() for s in st], list(codes)
+
+
+class Batch:
+    """Many solves as one CUDA graph launch (mhfp_batch_*): entry i solves
+    solvers[i] for rhs[i] into out[i]; entries of one solver run in order,
+    different solvers concurrently.  The tensors are bound at creation."""
+
+    def __init__(self, solvers, rhs, out, tol=1e-8):
+        n = len(solvers)
+        if n == 0 or len(rhs) != n or len(out) != n:
+            raise ValueError("Batch: one right-hand side and one output per entry")
+        for i, s in enumerate(solvers):
+            check_vec(rhs[i], s.n, s.device, f"rhs[{i}]")
+            check_vec(out[i], s.n, s.device, f"out[{i}]")
+        self.lib = load()
+        self.solvers, self.rhs, self.out = list(solvers), list(rhs), list(out)
+        H = (C.c_void_p * n)(*[s.h.value for s in solvers])
+        R = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
+        X = (C.c_void_p * n)(*[t.data_ptr() for t in out])
+        b = C.c_void_p()
+        code = self.lib.mhfp_batch_create(n, H, R, X, float(tol), C.byref(b))
+        if code != MHFP_OK:
+            raise MhfpError(code, self.lib.mhfp_last_error(solvers[0].h).decode())
+        self.b = b
+
+    def run(self, stream=None):
+        """One graph launch; returns (stats, statuses)."""
+        n = len(self.solvers)
+        st = (Stats * n)()
+        codes = (C.c_int * n)()
+        sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        code = self.lib.mhfp_batch_run(self.b, sp, st, codes)
+        if code not in (MHFP_OK, 5, 6):  # a solve that did not converge is reported per entry
+            raise MhfpError(code, self.lib.mhfp_last_error(self.solvers[0].h).decode())
+        return [x.as_dict() for x in st], list(codes)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mhfp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def prepare(prob, options: Options | None = None, stream=None) -> Solver:

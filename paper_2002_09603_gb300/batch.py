@@ -1,12 +1,15 @@
-"""Many independent systems solved together (mhfp_solve_batch).
+"""Many independent systems solved together.
 
-Marshalling only: one handle per instance, each on its own CUDA stream, so
-the per-step CUDA-graph replays of different instances overlap on the
-device; every right-hand side of a round is solved in one batched call.
+Marshalling only: one handle per instance.  `solve_loads_one_launch` binds
+every (instance, load) pair into one CUDA graph (mhfp_batch_create) and
+solves them all with one launch (mhfp_batch_run): the loads of an instance
+run one after another in its branch, the instances concurrently.
+`solve_loads` is the earlier form: per load, one mhfp_solve_batch call that
+launches each instance's solve graph on its own stream.
 """
 from __future__ import annotations
 
-from ._lib import Solver, default_options, solve_batch
+from ._lib import Batch, Solver, default_options, solve_batch
 
 
 def prepare_batch(problems, precision=1, restart=12, autotune=1, reorth=1):
@@ -39,3 +42,32 @@ def solve_loads(solvers, load_scales, tol=1e-8):
         out.append(solve_batch(solvers, rhs, tol=tol))
     torch.cuda.synchronize()
     return out
+
+
+class LoadBatch:
+    """Every instance x every load scale as one graph launch.  The right-hand
+    sides are built once (mhfp_build_rhs); `run()` solves them all."""
+
+    def __init__(self, solvers, load_scales, tol=1e-8):
+        import torch
+        self.solvers = solvers
+        self.scales = tuple(load_scales)
+        entries, rhs, out = [], [], []
+        for s in solvers:
+            for scale in self.scales:
+                entries.append(s)
+                rhs.append(s.build_rhs(None, load_scale=scale))
+                out.append(s.empty())
+        for s in solvers:
+            s.stream.synchronize()
+        torch.cuda.synchronize()
+        self.rhs, self.out = rhs, out
+        self.batch = Batch(entries, rhs, out, tol=tol)
+
+    def run(self, stream=None):
+        """Returns (solutions, stats, statuses), entry order instance-major."""
+        stats, codes = self.batch.run(stream)
+        return self.out, stats, codes
+
+    def close(self):
+        self.batch.close()

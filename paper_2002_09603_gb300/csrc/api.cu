@@ -1,6 +1,7 @@
 // C ABI of libmhfp: argument validation, handle life cycle, dispatch.
 #include "common.cuh"
 
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -514,6 +515,98 @@ mhfp_status mhfp_solve_batch(int count, const mhfp_handle* hs, const double* con
     if (first == MHFP_OK && code[i] != MHFP_OK) first = code[i];
   }
   return first;
+}
+
+struct mhfp_batch_s {
+  std::vector<mhfp_handle> hs;
+  std::vector<int> gen;
+  int device = 0;
+  mhfp::BatchGraph g;
+};
+
+mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
+                              double tol, mhfp_batch* out) {
+  if (!out) return MHFP_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || !hs || !d_rhs || !d_x || !(tol > 0.0) || !(tol < 1.0)) return MHFP_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !d_rhs[i] || !d_x[i]) return MHFP_ERR_ARG;
+    if (!hs[i]->c.prepared) return MHFP_ERR_STATE;
+    if (hs[i]->c.device != hs[0]->c.device) return MHFP_ERR_ARG;
+    if (hs[i]->c.timing.enabled) return MHFP_ERR_STATE;
+  }
+  mhfp_batch b = new (std::nothrow) mhfp_batch_s;
+  if (!b) return MHFP_ERR_OOM;
+  b->device = hs[0]->c.device;
+  std::vector<Ctx*> cs;
+  std::vector<const double*> r;
+  std::vector<double*> x;
+  for (int i = 0; i < count; ++i) {
+    b->hs.push_back(hs[i]);
+    b->gen.push_back(hs[i]->c.graph_gen);
+    cs.push_back(&hs[i]->c);
+    r.push_back(d_rhs[i]);
+    x.push_back(d_x[i]);
+  }
+  try {
+    MHFP_CUDA(cudaSetDevice(b->device));
+    for (Ctx* c : cs) MHFP_CUDA(cudaStreamSynchronize(c->stream));
+    mhfp::build_batch_graph(b->g, cs, r, x, tol);
+  } catch (const Error& e) {
+    hs[0]->c.err = e.msg;
+    mhfp::destroy_batch_graph(b->g);
+    delete b;
+    return e.status;
+  }
+  *out = b;
+  return MHFP_OK;
+}
+
+mhfp_status mhfp_batch_run(mhfp_batch b, void* stream, mhfp_stats* stats, mhfp_status* statuses) {
+  if (!b) return MHFP_ERR_ARG;
+  const int count = (int)b->hs.size();
+  for (int i = 0; i < count; ++i)
+    if (b->hs[i]->c.graph_gen != b->gen[i]) {
+      b->hs[i]->c.err = "a handle of the batch changed (mhfp_update_logk); create the batch again";
+      return MHFP_ERR_STATE;
+    }
+  const auto t0 = std::chrono::steady_clock::now();
+  try {
+    MHFP_CUDA(cudaSetDevice(b->device));
+    for (mhfp_handle h : b->hs) MHFP_CUDA(cudaStreamSynchronize(h->c.stream));
+    mhfp::run_batch_graph(b->g, (cudaStream_t)stream);
+  } catch (const Error& e) {
+    b->hs[0]->c.err = e.msg;
+    return e.status;
+  }
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  mhfp_status first = MHFP_OK;
+  for (int i = 0; i < count; ++i) {
+    const mhfp::DevCtl& h = b->g.host_ctl[i];
+    mhfp_status code = MHFP_OK;
+    if (h.status == (int)MHFP_ERR_NONFINITE) code = MHFP_ERR_NONFINITE;
+    else if (!h.converged) code = MHFP_ERR_NOT_CONVERGED;
+    if (stats) {
+      mhfp_stats s{};
+      s.iterations = h.total;
+      s.restarts = h.cycles;
+      s.converged = h.converged;
+      s.rel_residual = h.est;
+      s.true_rel_residual = h.true_rel;
+      s.solve_ms = ms;
+      stats[i] = s;
+    }
+    if (statuses) statuses[i] = code;
+    if (first == MHFP_OK && code != MHFP_OK) first = code;
+  }
+  return first;
+}
+
+void mhfp_batch_destroy(mhfp_batch b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  mhfp::destroy_batch_graph(b->g);
+  delete b;
 }
 
 long long mhfp_launch_count(void) { return mhfp::g_launches; }

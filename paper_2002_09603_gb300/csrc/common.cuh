@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cstdint>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "../../include/mhfp.h"
@@ -361,6 +362,7 @@ struct Ctx {
   long long solve_step_kernels[2] = {0, 0};   // kernels of one Arnoldi step
   int solve_pending = 0;
   std::chrono::steady_clock::time_point solve_t0;
+  int graph_gen = 0;                     // bumped whenever captured graphs are dropped
   DevCtl* ctl = nullptr;                 // device control block
   DevCtl* host_ctl = nullptr;            // pinned copy
   double *bcur = nullptr, *xcur = nullptr;
@@ -432,6 +434,18 @@ void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* 
 void vcycle_api(Ctx& c, std::vector<Level>& H, const double* b, double* x);  // in the solve's precision
 
 // krylov.cu
+// one graph over many solves (mhfp_batch_*)
+struct BatchGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  DevCtl* host_ctl = nullptr;                        // pinned, one per entry
+  std::vector<cudaGraphConditionalHandle*> d_hif;    // per entry
+  std::vector<std::array<long long, 3>> counts;      // kernels: start, per cycle, per step
+};
+void build_batch_graph(BatchGraph& B, const std::vector<Ctx*>& cs, const std::vector<const double*>& rhs,
+                       const std::vector<double*>& x, double tol);
+void run_batch_graph(BatchGraph& B, cudaStream_t stream);
+void destroy_batch_graph(BatchGraph& B);
 void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st, bool transpose = false);
 void fgmres_begin(Ctx& c, FgState& f, const double* b, double* x, double tol, bool transpose);
 void fgmres_advance(Ctx& c, FgState& f);

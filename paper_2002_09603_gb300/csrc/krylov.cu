@@ -811,39 +811,56 @@ cudaGraphNode_t add_conditional(cudaGraph_t parent, cudaGraphNode_t dep, cudaGra
   return node;
 }
 
-void build_solve_graph(Ctx& c, bool transpose) {
-  ensure_workspace(c);
+__global__ void k_ctl_reset(DevCtl* __restrict__ ctl, double tol, int maxit, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevCtl h{};
+  h.tol = tol;
+  h.maxit = maxit;
+  h.m = m;
+  *ctl = h;
+}
+
+// Add one whole device-driven solve of handle c to graph G after `dep`:
+// [b -> bcur, control block reset] x = 0, ||D_s b||, the control block's
+// start, the WHILE node of the restart cycles (Arnoldi steps in IF nodes),
+// [xcur -> x] and the control block -> host_slot.  The bracketed parts are
+// added when rhs / x are given (batched graphs); the single-solve graph
+// leaves them to the host.  d_hif: device array of `restart` IF handles for
+// this solve.  Returns the last node; the kernel counts go to *cnt.
+struct SolveCounts {
+  long long start = 0, cycle = 0, step = 0;
+};
+
+cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool transpose,
+                          cudaGraphConditionalHandle* d_hif, const double* rhs, double* x, double tol,
+                          DevCtl* host_slot, SolveCounts* cnt) {
   const int m = c.opt.restart;
   const long long n = c.n;
-  if (!c.ctl) {
-    c.ctl = dalloc_n<DevCtl>(c, 1);
-    MHFP_CUDA(cudaMallocHost(&c.host_ctl, sizeof(DevCtl)));
-    c.bcur = dalloc_n<double>(c, n);
-    c.xcur = dalloc_n<double>(c, n);
-  }
   const long long l0 = g_launches;
-  cudaGraph_t G;
-  MHFP_CUDA(cudaGraphCreate(&G, 0));
   // the WHILE node sits in G, the IF nodes in the WHILE body: each handle is
   // created on the graph that contains its node
   cudaGraphConditionalHandle hw;
   MHFP_CUDA(cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault));
   DevCtl* ctl = c.ctl;
+  cudaGraphNode_t last = dep;
+  if (rhs) {
+    cudaGraphNode_t cp;
+    MHFP_CUDA(cudaGraphAddMemcpyNode1D(&cp, G, last ? &last : nullptr, last ? 1 : 0, c.bcur, rhs,
+                                       n * sizeof(double), cudaMemcpyDeviceToDevice));
+    last = add_kernel(G, cp, k_ctl_reset, dim3(1), dim3(32), ctl, tol, c.opt.maxit, m);
+  }
   // x = 0, ||D_s b|| and the control block
-  cudaGraphNode_t last = add_child(G, nullptr, capture_piece(c, [&] {
+  last = add_child(G, last, capture_piece(c, [&] {
     MHFP_CUDA(cudaMemsetAsync(c.xcur, 0, n * sizeof(double), c.stream));
     vec_scale(c, c.bcur, c.ds, false, c.tmp, n);
     norm2_dev(c, c.tmp, n, c.scal + 4);
   }));
-  const long long nk_start = g_launches - l0;
   last = add_kernel(G, last, k_ctl_init, dim3(1), dim3(32), ctl, (const double*)(c.scal + 4), hw);
+  const long long nk_start = g_launches - l0;
   cudaGraph_t W;
   cudaGraphNode_t wnode = add_conditional(G, last, hw, cudaGraphCondTypeWhile, &W);
   std::vector<cudaGraphConditionalHandle> hif(m);
   for (int j = 0; j < m; ++j) MHFP_CUDA(cudaGraphConditionalHandleCreate(&hif[j], W, 0, 0));
-  const int ti = transpose ? 1 : 0;
-  if (!c.d_hif[ti]) c.d_hif[ti] = dalloc_n<cudaGraphConditionalHandle>(c, m);
-  cudaGraphConditionalHandle* d_hif = c.d_hif[ti];
   MHFP_CUDA(cudaMemcpy(d_hif, hif.data(), m * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice));
   // while body: the cycle
   const long long l1 = g_launches;
@@ -878,26 +895,118 @@ void build_solve_graph(Ctx& c, bool transpose) {
     MHFP_LAUNCH_CHECK();
   }));
   const long long nk_end = g_launches - l3;
+  last = wnode;
+  if (x) {
+    cudaGraphNode_t cp;
+    MHFP_CUDA(cudaGraphAddMemcpyNode1D(&cp, G, &last, 1, x, c.xcur, n * sizeof(double), cudaMemcpyDeviceToDevice));
+    last = cp;
+  }
   // after the loop: the control block back to pinned host memory
   cudaGraphNode_t fin;
-  MHFP_CUDA(cudaGraphAddMemcpyNode1D(&fin, G, &wnode, 1, c.host_ctl, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost));
+  MHFP_CUDA(cudaGraphAddMemcpyNode1D(&fin, G, &last, 1, host_slot, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost));
+  cnt->start = nk_start;
+  cnt->cycle = nk_cycle + nk_end;
+  cnt->step = nk_step;
+  return fin;
+}
+
+// the handle's device-side solve state (control block, current b and x)
+void ensure_solve_state(Ctx& c) {
+  ensure_workspace(c);
+  if (!c.ctl) {
+    c.ctl = dalloc_n<DevCtl>(c, 1);
+    MHFP_CUDA(cudaMallocHost(&c.host_ctl, sizeof(DevCtl)));
+    c.bcur = dalloc_n<double>(c, c.n);
+    c.xcur = dalloc_n<double>(c, c.n);
+  }
+}
+
+void build_solve_graph(Ctx& c, bool transpose) {
+  ensure_solve_state(c);
+  const int ti = transpose ? 1 : 0;
+  if (!c.d_hif[ti]) c.d_hif[ti] = dalloc_n<cudaGraphConditionalHandle>(c, c.opt.restart);
+  const long long l0 = g_launches;
+  cudaGraph_t G;
+  MHFP_CUDA(cudaGraphCreate(&G, 0));
+  SolveCounts cnt;
+  try {
+    add_solve(c, G, nullptr, transpose, c.d_hif[ti], nullptr, nullptr, 0.0, c.host_ctl, &cnt);
+  } catch (...) {
+    g_launches = l0;
+    cudaGraphDestroy(G);
+    throw;
+  }
   g_launches = l0;  // nothing ran during the build
   cudaGraphExec_t exec;
   cudaError_t e = cudaGraphInstantiate(&exec, G, 0);
   cudaGraphDestroy(G);
   MHFP_CUDA(e);
-  const int t = transpose ? 1 : 0;
-  c.solve_exec[t] = exec;
+  c.solve_exec[ti] = exec;
   // launches of one solve = start + per cycle (cycle + end) + per step
-  c.solve_nkernels[t] = nk_start + 1;
-  c.solve_cycle_kernels[t] = nk_cycle + nk_end;
-  c.solve_step_kernels[t] = nk_step;
+  c.solve_nkernels[ti] = cnt.start;
+  c.solve_cycle_kernels[ti] = cnt.cycle;
+  c.solve_step_kernels[ti] = cnt.step;
 }
 
 }  // namespace
 
+// One CUDA graph for many solves: every handle's entries run in list order
+// in a branch of their own (they share its Krylov workspace); branches of
+// different handles are independent, so one launch runs them all.
+void build_batch_graph(BatchGraph& B, const std::vector<Ctx*>& cs, const std::vector<const double*>& rhs,
+                       const std::vector<double*>& x, double tol) {
+  const long long l0 = g_launches;
+  MHFP_CUDA(cudaGraphCreate(&B.graph, 0));
+  const int count = (int)cs.size();
+  B.counts.assign(count, {0, 0, 0});
+  MHFP_CUDA(cudaMallocHost(&B.host_ctl, (size_t)std::max(count, 1) * sizeof(DevCtl)));
+  std::vector<std::pair<Ctx*, cudaGraphNode_t>> tail;  // last node of each handle's branch
+  try {
+    for (int i = 0; i < count; ++i) {
+      Ctx& c = *cs[i];
+      ensure_solve_state(c);
+      cudaGraphConditionalHandle* d_hif = nullptr;
+      MHFP_CUDA(cudaMalloc(&d_hif, (size_t)c.opt.restart * sizeof(cudaGraphConditionalHandle)));
+      B.d_hif.push_back(d_hif);
+      cudaGraphNode_t dep = nullptr;
+      size_t slot = tail.size();
+      for (size_t t = 0; t < tail.size(); ++t)
+        if (tail[t].first == &c) slot = t;
+      if (slot < tail.size()) dep = tail[slot].second;
+      SolveCounts cnt;
+      const cudaGraphNode_t last = add_solve(c, B.graph, dep, false, d_hif, rhs[i], x[i], tol, &B.host_ctl[i], &cnt);
+      B.counts[i] = {cnt.start + 1, cnt.cycle, cnt.step};  // + the control-block reset
+      if (slot < tail.size()) tail[slot].second = last;
+      else tail.push_back({&c, last});
+    }
+    g_launches = l0;
+    MHFP_CUDA(cudaGraphInstantiate(&B.exec, B.graph, 0));
+  } catch (...) {
+    g_launches = l0;
+    throw;
+  }
+}
+
+void run_batch_graph(BatchGraph& B, cudaStream_t stream) {
+  MHFP_CUDA(cudaGraphLaunch(B.exec, stream));
+  MHFP_CUDA(cudaStreamSynchronize(stream));
+  for (size_t i = 0; i < B.counts.size(); ++i) {
+    const DevCtl& h = B.host_ctl[i];
+    g_launches += B.counts[i][0] + (long long)(h.cycles + 1) * B.counts[i][1] + (long long)h.total * B.counts[i][2];
+  }
+}
+
+void destroy_batch_graph(BatchGraph& B) {
+  if (B.exec) cudaGraphExecDestroy(B.exec);
+  if (B.graph) cudaGraphDestroy(B.graph);
+  for (auto* p : B.d_hif) cudaFree(p);
+  if (B.host_ctl) cudaFreeHost(B.host_ctl);
+  B = BatchGraph{};
+}
+
 void invalidate_graphs(Ctx& c) {
   MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  ++c.graph_gen;
   for (int t = 0; t < 2; ++t) {
     for (auto& g : c.graphs[t]) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
