@@ -74,7 +74,10 @@ typedef struct {
 typedef struct {
   int restart;          /* FGMRES restart length m, 1..63 (default 50)         */
   int maxit;            /* maximum total FGMRES iterations (default 1000)      */
-  int cheb_degree;      /* Chebyshev smoother degree (default 2)               */
+  int cheb_degree;      /* Chebyshev smoother degree (default 2); 0: chosen by */
+                        /* the set-up autotuner (autotune = 1 required): the   */
+                        /* step's load right-hand side is solved to 1e-8 with  */
+                        /* degrees 1, 2 and 3 and the fastest is kept          */
   double cheb_ratio;    /* lmax / lmin of the smoother interval (default 10)   */
   int coarse_max;       /* coarsen while a level has more lattice points       */
                         /* (default 125, at most 4096); the last level is      */
@@ -147,6 +150,7 @@ typedef struct {
                         /* (4, 6 or 8); 0 = not a lattice sweep                */
   double sweep_us[8];   /* set-up autotuner's time of one sweep under that     */
                         /* schedule, microseconds (0 when not timed)           */
+  int cheb_degree;      /* Chebyshev degree of the smoothers in use            */
 } mhfp_hierarchy_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -240,15 +240,15 @@ def chebyshev(lev: Level, b, x, degree=CHEB_DEGREE):
     return x
 
 
-def vcycle(levels, b, l=0):
+def vcycle(levels, b, l=0, degree=CHEB_DEGREE):
     lev = levels[l]
     if lev.dense_inv is not None:
         return lev.dense_inv @ b
-    x = chebyshev(lev, b, np.zeros_like(b))
+    x = chebyshev(lev, b, np.zeros_like(b), degree)
     r = b - lev.A @ x
-    xc = vcycle(levels, lev.P.T @ r, l + 1)
+    xc = vcycle(levels, lev.P.T @ r, l + 1, degree)
     x = x + lev.P @ xc
-    return chebyshev(lev, b, x)
+    return chebyshev(lev, b, x, degree)
 
 
 @dataclass

@@ -62,7 +62,8 @@ class Stats(C.Structure):
 
 class HierInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("points", C.c_longlong * 8), ("block", C.c_int * 8),
-                ("lmax", C.c_double * 8), ("schedule", C.c_int * 8), ("sweep_us", C.c_double * 8)]
+                ("lmax", C.c_double * 8), ("schedule", C.c_int * 8), ("sweep_us", C.c_double * 8),
+                ("cheb_degree", C.c_int)]
 
 
 _lib = None
@@ -303,7 +304,8 @@ class Solver:
         self._check(self.lib.mhfp_hierarchy(self.h, int(which), C.byref(info)))
         L = info.levels
         return dict(levels=L, points=list(info.points[:L]), block=list(info.block[:L]), lmax=list(info.lmax[:L]),
-                    schedule=list(info.schedule[:L]), sweep_us=list(info.sweep_us[:L]))
+                    schedule=list(info.schedule[:L]), sweep_us=list(info.sweep_us[:L]),
+                    cheb_degree=info.cheb_degree)
 
     def uz_target_size(self):
         """Top-plane node count (nx+1)(ny+1), the length of a u_z target."""

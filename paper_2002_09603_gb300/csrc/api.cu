@@ -232,7 +232,8 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
     if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
     if (c.prepared) throw Error{MHFP_ERR_STATE, "preconditioner already set up"};
     if (opt) {
-      if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 1 || opt->cheb_degree > 8 ||
+      if (opt->restart < 1 || opt->restart > 63 || opt->maxit < 1 || opt->cheb_degree < 0 || opt->cheb_degree > 8 ||
+          (opt->cheb_degree == 0 && opt->autotune != 1) ||
           !(opt->cheb_ratio > 1.0) || opt->coarse_max < 1 || opt->coarse_max > 4096 || opt->power_iters < 1 ||
           (opt->precision != 0 && opt->precision != 1) || (opt->graphs < 0 || opt->graphs > 2) ||
           (opt->autotune != 0 && opt->autotune != 1) || (opt->reorth != 0 && opt->reorth != 1) ||
@@ -243,11 +244,22 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }
+    const bool tune_degree = c.opt.cheb_degree == 0;
+    if (tune_degree) c.opt.cheb_degree = 2;  // the hierarchy's set-up timings use degree 2
     mhfp::build_preconditioner_blocks(c);
     mhfp::build_hierarchies(c);
     if (c.opt.precision == 1) mhfp::make_fp32_blocks(c);
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
     c.prepared = true;
+    if (tune_degree) {
+      try {
+        mhfp::autotune_cheb_degree(c);
+      } catch (...) {
+        c.prepared = false;
+        throw;
+      }
+      MHFP_CUDA(cudaStreamSynchronize(c.stream));
+    }
   });
 }
 
@@ -362,6 +374,7 @@ mhfp_status mhfp_hierarchy(mhfp_handle h, int which, mhfp_hierarchy_info* info) 
     auto& H = which == 0 ? c.hu : c.hpi;
     std::memset(info, 0, sizeof(*info));
     info->levels = (int)H.size();
+    info->cheb_degree = c.opt.cheb_degree;
     for (size_t l = 0; l < H.size() && l < 8; ++l) {
       info->points[l] = H[l].npts;
       info->block[l] = H[l].bs;

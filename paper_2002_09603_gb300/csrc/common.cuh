@@ -445,6 +445,7 @@ struct BatchGraph {
 void build_batch_graph(BatchGraph& B, const std::vector<Ctx*>& cs, const std::vector<const double*>& rhs,
                        const std::vector<double*>& x, double tol);
 void run_batch_graph(BatchGraph& B, cudaStream_t stream);
+void autotune_cheb_degree(Ctx& c);
 void destroy_batch_graph(BatchGraph& B);
 void fgmres_solve(Ctx& c, const double* rhs, double* x, double tol, mhfp_stats* st, bool transpose = false);
 void fgmres_begin(Ctx& c, FgState& f, const double* b, double* x, double tol, bool transpose);

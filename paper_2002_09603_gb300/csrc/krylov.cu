@@ -1068,6 +1068,55 @@ void check_wait_flag(Ctx& c) {
   }
 }
 
+// Set-up autotuner of the Chebyshev degree (cheb_degree = 0 in the
+// options): solve the step's load right-hand side (previous state zero) to
+// 1e-8 with degrees 1, 2 and 3, each after one warm-up solve, and keep the
+// fastest.  The captured graphs hold the degree's sweeps, so they are
+// dropped between candidates and after the choice.
+void autotune_cheb_degree(Ctx& c) {
+  double* b = dalloc_n<double>(c, c.n);
+  double* x = dalloc_n<double>(c, c.n);
+  build_rhs(c, nullptr, 1.0, b);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MHFP_CUDA(cudaEventCreate(&e0));
+  MHFP_CUDA(cudaEventCreate(&e1));
+  int best = 2;
+  float best_ms = 1e30f;
+  try {
+    for (int deg = 1; deg <= 3; ++deg) {
+      c.opt.cheb_degree = deg;
+      invalidate_graphs(c);
+      mhfp_stats st{};
+      float ms = 1e30f;
+      bool ok = true;
+      for (int rep = 0; rep < 2 && ok; ++rep) {
+        MHFP_CUDA(cudaEventRecord(e0, c.stream));
+        try {
+          fgmres_solve(c, b, x, 1e-8, &st);
+        } catch (const Error& e) {
+          if (e.status != MHFP_ERR_NOT_CONVERGED) throw;
+          ok = false;
+        }
+        MHFP_CUDA(cudaEventRecord(e1, c.stream));
+        MHFP_CUDA(cudaEventSynchronize(e1));
+        MHFP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ok && ms < best_ms) {
+        best_ms = ms;
+        best = deg;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.opt.cheb_degree = best;
+  invalidate_graphs(c);
+}
+
 void fgmres_solve(Ctx& c, const double* b, double* x, double tol, mhfp_stats* st, bool transpose) {
   if (c.opt.graphs == 2 && !c.timing.enabled) {
     solve_device_graph_launch(c, b, tol, transpose);

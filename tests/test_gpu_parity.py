@@ -574,3 +574,52 @@ def test_bulk_copy_sweep_matches_the_thread_per_node_sweep(dims):
         a, b = out[8][k], out[4][k]
         assert (a - b).abs().max().item() <= 1e-6 * a.abs().max().item(), k
     assert out[8][3] == out[4][3]
+
+
+@pytest.mark.parametrize("degree", [1, 3])
+def test_chebyshev_degree_matches_oracle(degree):
+    """The smoother degree is an option (the set-up autotuner may pick 1, 2
+    or 3): both V-cycles at degree 1 and 3 against the oracle's (1e-10)."""
+    from paper_2002_09603_gb300 import Solver, default_options
+    prob, B, pc = _sched_case()
+    opt = default_options()
+    opt.cheb_degree = degree
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    assert s.hierarchy(0)["cheb_degree"] == degree
+    rng = np.random.default_rng(50 + degree)
+    nU, nP, nPi = B.sizes
+    bu, bpi = rng.standard_normal(nU), rng.standard_normal(nPi)
+    xu = s.vcycle(0, torch.from_numpy(bu).cuda()).cpu().numpy()
+    xpi = s.vcycle(1, torch.from_numpy(bpi).cuda()).cpu().numpy()
+    ru = precond.vcycle(pc.u_levels, bu, degree=degree)
+    rpi = precond.vcycle(pc.pi_levels, bpi, degree=degree)
+    assert np.abs(xu - ru).max() <= 1e-10 * np.abs(ru).max()
+    assert np.abs(xpi - rpi).max() <= 1e-10 * np.abs(rpi).max()
+    s.close()
+
+
+def test_chebyshev_degree_autotuner():
+    """cheb_degree = 0: the set-up solves the step's load with degrees 1-3
+    and keeps the fastest; the chosen handle still reaches the direct
+    solution."""
+    from paper_2002_09603_gb300 import MhfpError, Solver, default_options
+    prob = mi.random_small(9, 8, 7, seed=35, jitter=0.1)
+    opt = default_options()
+    opt.cheb_degree = 0
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    assert s.hierarchy(0)["cheb_degree"] in (1, 2, 3)
+    B = oracle.assemble(prob)
+    xd = oracle.solve_direct(B, system.rhs(B))
+    x, st = s.solve(s.build_rhs(), tol=1e-10)
+    assert st["converged"] and np.linalg.norm(x.cpu().numpy() - xd) <= 1e-7 * np.linalg.norm(xd)
+    s.close()
+    opt.autotune = 0
+    s = Solver(prob)
+    s.assemble_condense()
+    with pytest.raises(MhfpError):
+        s.setup_precond(opt)
+    s.close()
