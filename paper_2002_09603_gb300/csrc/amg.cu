@@ -173,21 +173,27 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
 
 // <hot:k_cheb_u0_tma> (hashed like the regions above)
 // The same FP32 symmetric-storage sweep and residual, fed by bulk copies.
-// A persistent CTA of TMA_NB threads takes node blocks of TMA_NB
-// consecutive nodes; for each block it streams the 14 stored slots u: the
-// 9 rows of the node's own blocks A(p, p + e_u) and, for u >= 1, the 9 rows
-// of the neighbours' blocks A(p - e_u, p) (read transposed), each row one
-// cp.async.bulk copy of TMA_NB (+4) floats from global into shared memory,
-// TMA_S slots in flight behind an mbarrier each.  The products are summed
-// in the order of sym_residual, so results are bit-identical to it.  Every
-// mbarrier wait is bounded: after about 2^31 clocks the CTA records
-// MHFP_WAIT_TIMEOUT in *err, drains what it issued (again bounded) and
-// returns.
-constexpr int TMA_NB = 128;                  // nodes (threads) per node block
-constexpr int TMA_S = 5;                     // slots in flight
+// A persistent CTA takes node blocks of TMA_NB consecutive nodes.  Its
+// producer warp streams, for each block, the 14 stored slots u: the 9 rows
+// of the nodes' own blocks A(p, p + e_u) and, for u >= 1, the 9 rows of the
+// neighbours' blocks A(p - e_u, p) (read transposed), each row one
+// cp.async.bulk copy of TMA_NB (+4) floats into shared memory, TMA_S slots
+// in flight; a "full" mbarrier per slot buffer counts the bytes, an "empty"
+// one the consumer warps that are done with it.  The TMA_NW consumer warps
+// (one node per lane) never wait for one another: each waits only for its
+// data, and loads the next slot's neighbour x before it waits.  The
+// products are summed in the order of sym_residual, so results are
+// bit-identical to it.  Every mbarrier wait is bounded: after about 2^31
+// clocks the warp records MHFP_WAIT_TIMEOUT in *err and stops; the
+// producer waits (bounded) for every copy it issued before the CTA exits.
+constexpr int TMA_NW = 8;                    // consumer warps
+constexpr int TMA_NB = 32 * TMA_NW;          // nodes per node block
+constexpr int TMA_S = 4;                     // slot buffers
 constexpr int TMA_ROW_OWN = TMA_NB;          // floats per own row
 constexpr int TMA_ROW_TR = TMA_NB + 4;       // floats per transposed row (aligned superset)
 constexpr int TMA_STAGE = 9 * TMA_ROW_OWN + 9 * TMA_ROW_TR;  // floats per stage
+constexpr int TMA_THREADS = 32 * (TMA_NW + 1);
+constexpr size_t TMA_SMEM = (size_t)TMA_S * TMA_STAGE * sizeof(float) + 2 * TMA_S * sizeof(unsigned long long);
 constexpr int MHFP_WAIT_TIMEOUT = 8;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -197,6 +203,9 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned coun
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -231,8 +240,15 @@ struct TmaSweep {
   int* err;
 };
 
+// lattice shift of slot u (node p's stored neighbour is p + shift)
+__device__ __forceinline__ int sym_shift(const Lat& L, int u) {
+  int dx, dy, dz;
+  St<ST_BOX1>::off(13 + u, dx, dy, dz);
+  return u == 0 ? 0 : dx + L.Lx * (dy + L.Ly * dz);
+}
+
 // issue the copies of stage (node block wb, slot u) into buf
-__device__ __forceinline__ void tma_issue(const TmaSweep& a, int wb, int u, int su, float* buf,
+__device__ __forceinline__ void tma_issue(const TmaSweep& a, const Lat& L, int wb, int u, float* buf,
                                           unsigned long long* bar) {
   const long long p0 = (long long)wb * TMA_NB;
   const unsigned own_bytes = TMA_ROW_OWN * 4;
@@ -242,119 +258,143 @@ __device__ __forceinline__ void tma_issue(const TmaSweep& a, int wb, int u, int 
 #pragma unroll 1
   for (int e = 0; e < 9; ++e) bulk_to_smem(buf + e * TMA_ROW_OWN, slot + e * a.ld + p0, own_bytes, bar);
   if (u > 0) {
-    // rows of nodes p0 - su ..: from the 16-byte boundary at or below
-    const long long q0 = ((p0 - su) >> 2) << 2;
+    // rows of nodes p0 - s_u ..: from the 16-byte boundary at or below
+    const long long q0 = ((p0 - sym_shift(L, u)) >> 2) << 2;
 #pragma unroll 1
     for (int e = 0; e < 9; ++e)
       bulk_to_smem(buf + 9 * TMA_ROW_OWN + e * TMA_ROW_TR, slot + e * a.ld + q0, tr_bytes, bar);
   }
 }
 
+// x of node pc's neighbours in slot u (+s and -s; 0 outside the lattice)
+__device__ __forceinline__ void sym_x(const Lat& L, const float* __restrict__ x, long long pc, int i, int j, int k,
+                                      int u, float xp[3], float xm[3]) {
+  int dx, dy, dz;
+  St<ST_BOX1>::off(13 + u, dx, dy, dz);
+  const int su = sym_shift(L, u);
+  const bool inp = u == 0 || L.in(i + dx, j + dy, k + dz), inm = u > 0 && L.in(i - dx, j - dy, k - dz);
+  const long long qp = inp ? pc + su : pc, qm = inm ? pc - su : pc;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const float vp = x[3 * qp + e], vm = x[3 * qm + e];
+    xp[e] = inp ? vp : 0.f;
+    xm[e] = inm ? vm : 0.f;
+  }
+}
+
 template <bool CHEB>
-__global__ void __launch_bounds__(TMA_NB, 4) k_sym_tma(Lat L, TmaSweep a) {
-  __shared__ __align__(128) float stage[TMA_S][TMA_STAGE];
-  __shared__ __align__(8) unsigned long long full[TMA_S];
-  const int t = threadIdx.x;
+__global__ void __launch_bounds__(TMA_THREADS, 3) k_sym_tma(Lat L, TmaSweep a) {
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  float* stage = (float*)tma_smem;
+  unsigned long long* full = (unsigned long long*)(tma_smem + (size_t)TMA_S * TMA_STAGE * sizeof(float));
+  unsigned long long* empty = full + TMA_S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblocks = (int)((L.N + TMA_NB - 1) / TMA_NB);
   const int my = (nblocks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // node blocks of this CTA
   const int units = my * 14;
-  // lattice shift of slot u (node p's stored neighbour is p + shift)
-  auto shift = [&](int u) {
-    int dx, dy, dz;
-    St<ST_BOX1>::off(13 + u, dx, dy, dz);
-    return u == 0 ? 0 : dx + L.Lx * (dy + L.Ly * dz);
-  };
-  if (t == 0) {
-    for (int s = 0; s < TMA_S; ++s) mbar_init(&full[s], 1);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TMA_S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], TMA_NW);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (t == 0)
-    for (int g = 0; g < TMA_S && g < units; ++g)
-      tma_issue(a, (int)blockIdx.x + (g / 14) * (int)gridDim.x, g % 14, shift(g % 14), stage[g], &full[g]);
-  bool ok = true;
-  int g = 0;
-  for (int k = 0; k < my && ok; ++k) {
-    const int wb = (int)blockIdx.x + k * (int)gridDim.x;
-    const long long p = (long long)wb * TMA_NB + t;
-    const bool valid = p < L.N;
-    const long long pc = valid ? p : L.N - 1;
-    int i, j, kk;
-    L.ijk(pc, i, j, kk);
-    float r[3] = {a.b[3 * pc], a.b[3 * pc + 1], a.b[3 * pc + 2]};
-    for (int u = 0; u < 14; ++u, ++g) {
-      const int buf = g % TMA_S;
-      // a thread whose wait ran out still reads (in-bounds) shared memory;
-      // the vote below makes the whole CTA stop together
-      const bool arrived = mbar_wait(&full[buf], (unsigned)(g / TMA_S) & 1u);
-      const float* st = stage[buf];
-      if (u == 0) {
-        const float x0 = a.xin[3 * pc], x1 = a.xin[3 * pc + 1], x2 = a.xin[3 * pc + 2];
-#pragma unroll
-        for (int e = 0; e < 3; ++e)
-          r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * x0 + st[(3 * e + 1) * TMA_ROW_OWN + t] * x1 +
-                  st[(3 * e + 2) * TMA_ROW_OWN + t] * x2;
-      } else {
-        int dx, dy, dz;
-        St<ST_BOX1>::off(13 + u, dx, dy, dz);
-        const int su = dx + L.Lx * (dy + L.Ly * dz);
-        const bool inp = L.in(i + dx, j + dy, kk + dz), inm = L.in(i - dx, j - dy, kk - dz);
-        if (inp) {
-          const long long q = pc + su;
-          const float x0 = a.xin[3 * q], x1 = a.xin[3 * q + 1], x2 = a.xin[3 * q + 2];
-#pragma unroll
-          for (int e = 0; e < 3; ++e)
-            r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * x0 + st[(3 * e + 1) * TMA_ROW_OWN + t] * x1 +
-                    st[(3 * e + 2) * TMA_ROW_OWN + t] * x2;
-        }
-        if (inm) {
-          const long long q = pc - su;
-          const long long p0 = (long long)wb * TMA_NB;
-          const int off = (int)((p0 - su) - (((p0 - su) >> 2) << 2)) + t;
-          const float* tr = st + 9 * TMA_ROW_OWN;
-          const float x0 = a.xin[3 * q], x1 = a.xin[3 * q + 1], x2 = a.xin[3 * q + 2];
-#pragma unroll
-          for (int e = 0; e < 3; ++e)
-            r[e] -= tr[e * TMA_ROW_TR + off] * x0 + tr[(3 + e) * TMA_ROW_TR + off] * x1 +
-                    tr[(6 + e) * TMA_ROW_TR + off] * x2;
-        }
+  if (warp == TMA_NW) {
+    // producer: lane 0 issues every unit once its buffer is free
+    if (lane == 0) {
+      bool ok = true;
+      int g = 0;
+      for (; g < units && ok; ++g) {
+        const int buf = g % TMA_S;
+        if (g >= TMA_S) ok = mbar_wait(&empty[buf], (unsigned)(g / TMA_S - 1) & 1u);
+        if (!ok) break;
+        tma_issue(a, L, (int)blockIdx.x + (g / 14) * (int)gridDim.x, g % 14, stage + (size_t)buf * TMA_STAGE,
+                  &full[buf]);
       }
-      // every thread is done with this buffer (and every copy arrived)
-      if (!__syncthreads_and(arrived)) {
-        ok = false;
-        ++g;
-        break;
-      }
-      if (t == 0 && g + TMA_S < units) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const int gn = g + TMA_S;
-        tma_issue(a, (int)blockIdx.x + (gn / 14) * (int)gridDim.x, gn % 14, shift(gn % 14), stage[buf], &full[buf]);
-      }
+      // every issued copy lands before the CTA may exit
+      for (int h = (g > TMA_S ? g - TMA_S : 0); h < g; ++h)
+        if (!mbar_wait(&full[h % TMA_S], (unsigned)(h / TMA_S) & 1u)) ok = false;
+      if (!ok) atomicOr(a.err, MHFP_WAIT_TIMEOUT);
     }
-    if (!ok) break;
-    if (valid) {
-      if (CHEB) {
+  } else {
+    bool ok = true;
+    int g = 0;
+    const int t = warp * 32 + lane;
+    for (int k = 0; k < my && ok; ++k) {
+      const int wb = (int)blockIdx.x + k * (int)gridDim.x;
+      const long long p0 = (long long)wb * TMA_NB;
+      const long long p = p0 + t;
+      const bool valid = p < L.N;
+      const long long pc = valid ? p : L.N - 1;
+      int i, j, kk;
+      L.ijk(pc, i, j, kk);
+      float r[3] = {a.b[3 * pc], a.b[3 * pc + 1], a.b[3 * pc + 2]};
+      float xp[3], xm[3];
+      sym_x(L, a.xin, pc, i, j, kk, 0, xp, xm);
+      for (int u = 0; u < 14; ++u, ++g) {
+        const int buf = g % TMA_S;
+        // the next slot's x, in flight while this slot's rows are waited for
+        float np[3], nm[3];
+        sym_x(L, a.xin, pc, i, j, kk, u < 13 ? u + 1 : 13, np, nm);
+        // the warp decides together (every lane's wait is bounded)
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[buf], (unsigned)(g / TMA_S) & 1u))) {
+          ok = false;
+          break;
+        }
+        const float* st = stage + (size_t)buf * TMA_STAGE;
+        if (u == 0) {
+#pragma unroll
+          for (int e = 0; e < 3; ++e)
+            r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * xp[0] + st[(3 * e + 1) * TMA_ROW_OWN + t] * xp[1] +
+                    st[(3 * e + 2) * TMA_ROW_OWN + t] * xp[2];
+        } else {
+          int dx, dy, dz;
+          St<ST_BOX1>::off(13 + u, dx, dy, dz);
+          if (L.in(i + dx, j + dy, kk + dz)) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+              r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * xp[0] + st[(3 * e + 1) * TMA_ROW_OWN + t] * xp[1] +
+                      st[(3 * e + 2) * TMA_ROW_OWN + t] * xp[2];
+          }
+          if (L.in(i - dx, j - dy, kk - dz)) {
+            const long long sh = p0 - sym_shift(L, u);
+            const int off = (int)(sh - ((sh >> 2) << 2)) + t;
+            const float* tr = st + 9 * TMA_ROW_OWN;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+              r[e] -= tr[e * TMA_ROW_TR + off] * xm[0] + tr[(3 + e) * TMA_ROW_TR + off] * xm[1] +
+                      tr[(6 + e) * TMA_ROW_TR + off] * xm[2];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[buf]);  // this warp is done with the buffer
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-          const float z = a.dinv[(3 * e) * L.N + p] * r[0] + a.dinv[(3 * e + 1) * L.N + p] * r[1] +
-                          a.dinv[(3 * e + 2) * L.N + p] * r[2];
-          const float dn = (a.cd != 0.f) ? a.cd * a.d[3 * p + e] + a.cr * z : a.cr * z;
-          a.d[3 * p + e] = dn;
-          a.xout[3 * p + e] = a.xin[3 * p + e] + dn;
+          xp[e] = np[e];
+          xm[e] = nm[e];
         }
-      } else {
+      }
+      if (!ok) break;
+      if (valid) {
+        if (CHEB) {
 #pragma unroll
-        for (int e = 0; e < 3; ++e) a.xout[3 * p + e] = r[e];
+          for (int e = 0; e < 3; ++e) {
+            const float z = a.dinv[(3 * e) * L.N + p] * r[0] + a.dinv[(3 * e + 1) * L.N + p] * r[1] +
+                            a.dinv[(3 * e + 2) * L.N + p] * r[2];
+            const float dn = (a.cd != 0.f) ? a.cd * a.d[3 * p + e] + a.cr * z : a.cr * z;
+            a.d[3 * p + e] = dn;
+            a.xout[3 * p + e] = a.xin[3 * p + e] + dn;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 3; ++e) a.xout[3 * p + e] = r[e];
+        }
       }
     }
+    if (!ok && lane == 0) atomicOr(a.err, MHFP_WAIT_TIMEOUT);
   }
-  if (!ok) {
-    // a copy did not arrive in time: report, then drain what was issued
-    // (units up to g - 1 + TMA_S; the failed one, g - 1, included)
-    if (t == 0) atomicOr(a.err, MHFP_WAIT_TIMEOUT);
-    for (int h = g - 1; h < units && h < g - 1 + TMA_S; ++h)
-      mbar_wait(&full[h % TMA_S], (unsigned)(h / TMA_S) & 1u);
-  }
+  __syncthreads();  // no warp leaves while copies into this CTA's shared memory may be in flight
 }
 // </hot:k_cheb_u0_tma>
 
@@ -1584,10 +1624,16 @@ void launch_sym_tma(Ctx& c, const Level& L, bool cheb, const float* b, const flo
   const Lat lat = lat_of(L.A);
   if (lat.N >= (1LL << 31) - TMA_NB) throw Error{MHFP_ERR_ARG, "level too large for the bulk-copy sweep"};
   const long long nblocks = (lat.N + TMA_NB - 1) / TMA_NB;
-  const unsigned grid = (unsigned)std::min<long long>(nblocks, 4LL * c.n_sm);
+  const unsigned grid = (unsigned)std::min<long long>(nblocks, 3LL * c.n_sm);
+  static bool attr = false;  // the dynamic shared memory above 48 KB, once per process
+  if (!attr) {
+    MHFP_CUDA(cudaFuncSetAttribute(k_sym_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM));
+    MHFP_CUDA(cudaFuncSetAttribute(k_sym_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM));
+    attr = true;
+  }
   TmaSweep a{L.symf, L.sym_ld, L.dinvf, b, xin, xout, d, cd, cr, c.d_flag};
-  if (cheb) k_sym_tma<true><<<grid, TMA_NB, 0, c.stream>>>(lat, a);
-  else k_sym_tma<false><<<grid, TMA_NB, 0, c.stream>>>(lat, a);
+  if (cheb) k_sym_tma<true><<<grid, TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a);
+  else k_sym_tma<false><<<grid, TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a);
 }
 void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, float* xout, float* d, float cd,
                      float cr) {
