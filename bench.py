@@ -49,6 +49,9 @@ WORKLOADS = {
     "layered128": dict(n=128, gen="layered", restart=20, gpu_iters=54,
                        desc="128^3 hex, interior node jitter U(+-0.2h), 8 z-layers: kappa log-U[1e-18,1e-12] m^2, "
                             "E log-U[1e8,1e10] Pa, nu U[0.2,0.35]; S_eps=0, dt=0.1 s (seed 3)"),
+    "adjoint48": dict(n=48, desc="48^3 hex, log-normal ln kappa (sigma 1, seed 5), 10 backward-Euler steps dt=0.1 s, "
+                                 "misfit of top u_z and cell p against a second seeded field; J and dJ/d ln kappa "
+                                 "(110,592 cells) by the checkpointed discrete adjoint, solves to 1e-10"),
     "batch48": dict(n=0, desc="48 cubes n ~ U{16..64} (seed 4), own log-normal kappa (sigma 1.5), loads x0.5/1/2/4, "
                               "FP32 V-cycles in FP64 FGMRES(12), all 192 systems in one CUDA graph launch"),
 }
@@ -674,6 +677,67 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Auxiliary workload: one evaluation of J and its gradient with respect
+    to the per-cell log-permeability (forward sweep, checkpointed reverse
+    sweep with adjoint solves), on one handle whose permeability is updated
+    in place (mhfp_update_logk) for every evaluation."""
+    import numpy as np
+    import torch
+    import mhfp_inputs as mi
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_09603_gb300 import Solver, launch_count
+    from paper_2002_09603_gb300.adjoint import MisfitGradient
+    n, nsteps = 48, 10
+    prob = mi.lognormal_cube(n, seed=5, sigma=1.0, dt=0.1)
+    q = mi.lognormal_cube(n, seed=55, sigma=1.0, dt=0.1)
+    s = Solver(q)
+    s.assemble_condense()
+    s.setup_precond()
+    nU, nP, _ = s.sizes
+    nodes = np.arange((n + 1) ** 3)
+    top = nodes[nodes // ((n + 1) ** 2) == n]
+    x, uz, pp = None, [], []
+    for _ in range(nsteps):
+        x, _ = s.solve(s.build_rhs(x), tol=1e-13)
+        xc = x.cpu().numpy()
+        uz.append(xc[3 * top + 2])
+        pp.append(xc[nU:nU + nP])
+    s.close()
+    mg = MisfitGradient(prob, nsteps, uz, pp, tol=1e-10, checkpoint_every=3, precision=1, restart=20)
+    logk = np.log(prob.kappa[:, 0])
+    rng = np.random.default_rng(6)
+    t0 = time.perf_counter()
+    mg.value_and_grad(logk)  # creates and sets up the handle once
+    torch.cuda.synchronize()
+    first = time.perf_counter() - t0
+    times = []
+    l0 = launch_count()
+    for k in range(max(1, args.steps)):
+        lk = logk + 0.1 * rng.standard_normal(logk.shape)
+        mg.stats = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, g = mg.value_and_grad(lk)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    solves = len(mg.stats)
+    line = {"metric": "time per J + dJ/d ln kappa evaluation (adjoint)", "value": statistics.mean(times) * 1e3,
+            "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": statistics.mean(times) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["adjoint48"]["desc"], "cells": int(prob.n_cells), "steps": nsteps,
+                       "checkpoint_every": 3, "solves_per_evaluation": solves,
+                       "iterations_per_solve_min_max": [min(st["iterations"] for st in mg.stats),
+                                                        max(st["iterations"] for st in mg.stats)],
+                       "first_evaluation_ms_with_setup": first * 1e3,
+                       "parameter_update": "mhfp_update_logk on one handle (no re-creation)"},
+            "gpu_launches": (launch_count() - l0) // max(1, args.steps)}
+    print(json.dumps(line), flush=True)
+    mg.close()
+
+
 def run_batch(args):
     """Auxiliary workload: many uneven instances x 4 loads; reports the time
     per solved system with all instances batched (concurrent streams and
@@ -752,6 +816,9 @@ def main():
     args = parse()
     if args.workload == "batch48":
         run_batch(args)
+        return
+    if args.workload == "adjoint48":
+        run_adjoint(args)
         return
     if args.impl == "reference":
         os.environ.update(SINGLE_THREAD_ENV)  # before numpy is imported
