@@ -115,8 +115,9 @@ typedef struct {
                         /* point per thread, W = offsets over W warps)         */
   int fine_blocks;      /* finest FP32 displacement sweep and residual         */
                         /* (precision = 1): 0 (default) autotuned (size rule   */
-                        /* without it); 6 or 8: one node per thread with that  */
-                        /* many resident blocks of 256 per SM; 4: persistent   */
+                        /* without it); 5, 6, 7 or 8: one node per thread with */
+                        /* that many resident blocks of 256 per SM (5: two     */
+                        /* neighbour slots per loop iteration); 4: persistent  */
                         /* CTAs (4 per SM) fed by bulk copies of the stored    */
                         /* rows into shared memory (same sums, same order)     */
   int near_kernel;      /* near-kernel of the displacement multigrid (Section  */

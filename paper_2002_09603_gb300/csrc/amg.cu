@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
 // A(n, n - e_o) = A(n - e_o, n)^T, slot u of node n - e_o.  Each stored
 // block is read by its owner and by one neighbour at most a lattice plane
 // apart, so the second read hits L2 and HBM carries each value once.
-template <typename T>
+// UNR slots per loop iteration: 2 keeps two slots' loads in flight (the
+// 5-blocks-per-SM variant has the registers for it), 1 one slot.
+template <typename T, int UNR = 1>
 __device__ __forceinline__ void sym_residual(const Lat& L, long long ld, long long p, const T* __restrict__ up,
                                              const T* __restrict__ x, T r[3]) {
   const long long N = ld;  // row stride of the stored values (>= number of nodes)
@@ -113,7 +115,7 @@ __device__ __forceinline__ void sym_residual(const Lat& L, long long ld, long lo
 #pragma unroll
     for (int a = 0; a < 3; ++a) r[a] -= v[(3 * a) * N] * x0 + v[(3 * a + 1) * N] * x1 + v[(3 * a + 2) * N] * x2;
   }
-#pragma unroll 1
+#pragma unroll UNR
   for (int u = 1; u <= 13; ++u) {
     int dx, dy, dz;
     St<ST_BOX1>::off(13 + u, dx, dy, dz);
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, long long ld,
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
-  sym_residual<T>(L, ld, p, up, x, r);
+  sym_residual<T, (MINB <= 5 ? 2 : 1)>(L, ld, p, up, x, r);
 #pragma unroll
   for (int a = 0; a < 3; ++a) y[3 * p + a] = r[a];
 }
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
-  if (xin) sym_residual<T>(L, ld, p, up, xin, r);
+  if (xin) sym_residual<T, (MINB <= 5 ? 2 : 1)>(L, ld, p, up, xin, r);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const T z = dinv[(3 * a) * L.N + p] * r[0] + dinv[(3 * a + 1) * L.N + p] * r[1] + dinv[(3 * a + 2) * L.N + p] * r[2];
@@ -1614,7 +1616,7 @@ void launch_cheb(Ctx& c, Level& L, const LV<T>& v, const T* b, const T* xin, T* 
 // 256 threads per SM (0: 8 when one wave of 8 blocks per SM covers the
 // level, else 6)
 int sym_minb(const Level& L) {
-  if (L.tpp == 4 || L.tpp == 6 || L.tpp == 8) return L.tpp;
+  if (L.tpp >= 4 && L.tpp <= 8) return L.tpp;
   return L.A.N <= 152LL * 8 * 256 ? 8 : 6;
 }
 
@@ -1643,9 +1645,16 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
     MHFP_LAUNCH_CHECK();
     return;
   }
-  if (sym_minb(L) == 4)
+  const int mb = sym_minb(L);
+  if (mb == 4)
     launch_sym_tma(c, L, true, b, xin, xout, d, cd, cr);
-  else if (sym_minb(L) == 8)
+  else if (mb == 5)
+    k_cheb_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+                                                                        d, cd, cr);
+  else if (mb == 7)
+    k_cheb_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+                                                                        d, cd, cr);
+  else if (mb == 8)
     k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
                                                                         d, cd, cr);
   else
@@ -1655,9 +1664,14 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
 }
 void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, float* y) {
   const Lat lat = lat_of(L.A);
-  if (sym_minb(L) == 4)
+  const int mb = sym_minb(L);
+  if (mb == 4)
     launch_sym_tma(c, L, false, b, x, y, nullptr, 0.f, 0.f);
-  else if (sym_minb(L) == 8)
+  else if (mb == 5)
+    k_resid_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
+  else if (mb == 7)
+    k_resid_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
+  else if (mb == 8)
     k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
   else
     k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
@@ -1724,7 +1738,7 @@ void autotune_fine_sym(Ctx& c, Level& L) {
   MHFP_CUDA(cudaMemsetAsync(L.df, 0, L.n * sizeof(float), c.stream));
   float best = 1e30f;
   int best_minb = 0;
-  for (int minb : {8, 6, 4}) {
+  for (int minb : {8, 7, 6, 5, 4}) {
     L.tpp = minb;
     const float us = graph_time_us(c, 5, [&] { launch_cheb_sym(c, L, L.bf, L.xf, L.yf, L.df, 0.5f, 0.5f); });
     if (us < best) {

@@ -239,7 +239,7 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
           (opt->autotune != 0 && opt->autotune != 1) || (opt->reorth != 0 && opt->reorth != 1) ||
           (opt->schedule != 0 && opt->schedule != 1 && opt->schedule != 4 && opt->schedule != 8 &&
            opt->schedule != 16) ||
-          (opt->fine_blocks != 0 && opt->fine_blocks != 4 && opt->fine_blocks != 6 && opt->fine_blocks != 8) ||
+          (opt->fine_blocks != 0 && (opt->fine_blocks < 4 || opt->fine_blocks > 8)) ||
           (opt->near_kernel != 0 && opt->near_kernel != 1))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;

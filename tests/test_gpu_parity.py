@@ -547,16 +547,17 @@ def test_invalid_schedule_options_are_rejected():
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (13, 9, 21)])
 def test_bulk_copy_sweep_matches_the_thread_per_node_sweep(dims):
-    """The finest FP32 displacement sweep fed by bulk copies (fine_blocks =
-    4: persistent CTAs, stored rows streamed through shared memory behind
-    mbarriers) sums the same products in the same order as the one-node-
-    per-thread kernel (fine_blocks = 8): the V-cycle, M^-1 and a whole solve
-    agree to FP32 rounding, on meshes of many node blocks with a ragged last
-    block."""
+    """Every variant of the finest FP32 displacement sweep sums the same
+    products in the same order as the one-node-per-thread kernel with 8
+    blocks per SM: the bulk-copy form (fine_blocks = 4: persistent CTAs,
+    stored rows streamed through shared memory behind mbarriers), two slots
+    per iteration (5) and the 6- and 7-block variants.  The V-cycle, M^-1 and
+    a whole solve agree to FP32 rounding, on meshes of many node blocks with
+    a ragged last block."""
     from paper_2002_09603_gb300 import Solver, default_options
     prob = mi.random_small(*dims, seed=33, jitter=0.1)
     out = {}
-    for fb in (8, 4):
+    for fb in (8, 4, 5, 6, 7):
         opt = default_options()
         opt.precision = 1
         opt.fine_blocks = fb
@@ -570,10 +571,11 @@ def test_bulk_copy_sweep_matches_the_thread_per_node_sweep(dims):
         x, st = s.solve(s.build_rhs(), tol=1e-10)
         out[fb] = (s.vcycle(0, bu), s.apply_precond(v), x, st["iterations"])
         s.close()
-    for k in range(3):
-        a, b = out[8][k], out[4][k]
-        assert (a - b).abs().max().item() <= 1e-6 * a.abs().max().item(), k
-    assert out[8][3] == out[4][3]
+    for fb in (4, 5, 6, 7):
+        for k in range(3):
+            a, b = out[8][k], out[fb][k]
+            assert (a - b).abs().max().item() <= 1e-6 * a.abs().max().item(), (fb, k)
+        assert out[8][3] == out[fb][3]
 
 
 @pytest.mark.parametrize("degree", [1, 3])
