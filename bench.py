@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--reorth", type=int, choices=[0, 1], default=0,
                     help="Gram-Schmidt: 0 one classical pass (PETSc's GMRES default; same iterations and "
                          "residuals on the workloads), 1 DGKS reorthogonalisation when needed")
+    ap.add_argument("--cheb-degree", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="Chebyshev smoother degree; 0 (default): chosen by the set-up autotuner, which solves the "
+                         "step's load with degrees 1-3 and keeps the fastest")
     ap.add_argument("--precision", choices=["both", "mixed", "fp64"], default="both",
                     help="both: mixed headline with FP64-plain beside it (default)")
     args = ap.parse_args()
@@ -482,13 +485,14 @@ def _timed_steps(s, args, world, dist, torch, launch_count, sample_clocks, local
     return dict(ms=ms, iters=iters, launches=launches, clocks=clocks, kt=kt)
 
 
-def _solver(prob, precision, torch, restart=50, reorth=1, coarse_max=125):
+def _solver(prob, precision, torch, restart=50, reorth=1, coarse_max=125, cheb_degree=2):
     from paper_2002_09603_gb300 import Solver, default_options
     opt = default_options()
     opt.precision = precision
     opt.restart = restart
     opt.reorth = reorth
     opt.coarse_max = coarse_max
+    opt.cheb_degree = cheb_degree
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -508,12 +512,13 @@ def _measure_workload(args, name, world, dist, torch, launch_count, local, preci
     restart = args.restart if name == args.workload else WORKLOADS[name].get("restart", 12)
     out = {}
     for precision in precisions:
-        s, setup = _solver(prob, precision, torch, restart, args.reorth, args.coarse_max)
+        s, setup = _solver(prob, precision, torch, restart, args.reorth, args.coarse_max, args.cheb_degree)
         r = _timed_steps(s, args, world, dist, torch, launch_count, precision == precisions[-1], local)
         rk = _timed_steps(s, args, world, dist, torch, launch_count, False, local, True)
         r["kt"], r["kernel_pass_ms"], r["setup_ms"] = rk["kt"], rk["ms"], setup
         r["op"] = s.timing_read(1)
         r["hu"], r["hpi"] = s.hierarchy(0)["points"], s.hierarchy(1)["points"]
+        r["cheb_degree"] = s.hierarchy(0)["cheb_degree"]
         r["restart"] = restart
         out[precision] = (s, r)
         if precision != precisions[-1]:
@@ -621,7 +626,7 @@ def run_ours(args):
         t64 = cheb_u0_flops(n_mesh) / (a64 * 1e-3) / 1e12 if r64["kt"]["launches"] else None
         sb64 = step_bytes(n_mesh, r64["hu"], r64["hpi"], 0, r64["restart"], int(round(statistics.mean(r64["iters"]))))
         fp64_plain = {"ms_per_step": r64["ms"], "iterations_per_step": r64["iters"], "setup_ms": r64["setup_ms"],
-                      "gpu_launches": r64["launches"],
+                      "gpu_launches": r64["launches"], "cheb_degree": r64["cheb_degree"],
                       "sweep_roofline": {"kernel": "k_cheb_u0<double>", "bound": "alu", "achieved": t64, "peak": fpk,
                                          "unit": "TFLOP/s", "frac": t64 / fpk if t64 else None,
                                          "hbm_achieved_gbs": g64, "avg_launch_us": a64 * 1e3},
@@ -635,6 +640,7 @@ def run_ours(args):
         ao, go = _sweep_roofline(ro["kt"], peak)
         other = {"workload": WORKLOADS["lognormal64"]["desc"], "unknowns": so.n, "restart": ro["restart"],
                  "ms_per_step": ro["ms"], "iterations_per_step": ro["iters"], "setup_ms": ro["setup_ms"],
+                 "cheb_degree": ro["cheb_degree"],
                  "sweep_frac_of_hbm": go / peak if go else None,
                  "step_frac_of_hbm": step_bytes(64, ro["hu"], ro["hpi"], precisions[-1], ro["restart"],
                                                 int(round(statistics.mean(ro["iters"])))) / (ro["ms"] * 1e-3) / 1e9 / peak,
@@ -658,6 +664,8 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload]["desc"], "unknowns": s.n, "n_u": nU, "n_p": nP,
                        "n_pi": nPi, "tol": TOL, "restart": args.restart, "reorth": args.reorth,
                        "coarse_max": args.coarse_max, "iterations_per_step": r32["iters"],
+                       "cheb_degree": r32["cheb_degree"],
+                       "cheb_degree_source": "set-up autotuner" if args.cheb_degree == 0 else "option",
                        "setup_ms": setup_ms, "precision": {"both": "FP32 V-cycles inside FP64 FGMRES",
                                                            "mixed": "FP32 V-cycles inside FP64 FGMRES",
                                                            "fp64": "FP64 throughout"}[args.precision],

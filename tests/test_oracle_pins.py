@@ -198,32 +198,10 @@ def test_static_condensation_matches_uncondensed_hybrid():
     assert np.allclose(x4[nU:nU + nW], w.ravel(), rtol=0, atol=1e-10 * np.abs(w).max())
 
 
-def _mixed_system(p, B):
-    """Eq. (mfeSys) with stabilization (Eq. stab_A): continuous RT0 fluxes
-    q, one per face not on a no-flow boundary, oriented along +axis."""
-    mesh = B.mesh
-    nU, nP, nPi = B.sizes
-    Aww = B.Aww_cells
-    nT = mesh.n_cells
-    # sign of the cell-local outward basis relative to the face's +axis
-    sgn = np.tile(np.array([-1.0, 1.0, -1.0, 1.0, -1.0, 1.0]), (nT, 1))
-    cf = mesh.cell_faces
-    R = np.repeat(cf, 6, axis=1).ravel()
-    C = np.tile(cf, (1, 6)).ravel()
-    V = (sgn[:, :, None] * Aww * sgn[:, None, :]).ravel()
-    Aqq = sp.csr_matrix((V, (R, C)), shape=(nPi, nPi))
-    Aqp = sp.csr_matrix((-sgn.ravel(), (cf.ravel(), np.repeat(np.arange(nT), 6))), shape=(nPi, nP))
-    Apq = (-Aqp.T).tocsr()
-    keep = np.flatnonzero(~((p.face_bc & 4) != 0))
-    Aqq, Aqp, Apq = Aqq[keep][:, keep], Aqp[keep], Apq[:, keep]
-    A = sp.bmat([[B.Auu, None, B.Aup], [None, Aqq, Aqp], [B.Apu, B.dt * Apq, B.App + B.Astab]],
-                format="csr")
-    return A, len(keep)
-
-
 def test_hybrid_equals_mixed_formulation():
     """Hybridization is an algebraic reformulation of the mixed method:
     (u, p) of Eq. (mfeSys)+stabilization equal those of Eq. (A_33H)."""
+    from oracle import mixed
     p = mi.random_small(4, 3, 2, seed=3, jitter=0.15)
     B = oracle.assemble(p)
     nU, nP, nPi = B.sizes
@@ -233,11 +211,73 @@ def test_hybrid_equals_mixed_formulation():
     p0 = rng.standard_normal(nP)
     b = system.rhs(B, u0, p0)
     x = oracle.solve_direct(B, b)
-    Am, nq = _mixed_system(p, B)
-    xm = spla.spsolve(Am.tocsc(), np.concatenate([b[:nU], np.zeros(nq), b[nU:nU + nP]]))
+    M = mixed.assemble_mixed(B, p.face_bc)
+    xm = mixed.solve_direct(M, b)         # f_q = 0: the same right-hand side
     u, pp, _ = system.split(B, x)
     assert np.allclose(xm[:nU], u, rtol=0, atol=1e-10 * np.abs(u).max())
-    assert np.allclose(xm[nU + nq:], pp, rtol=0, atol=1e-10 * np.abs(pp).max())
+    assert np.allclose(xm[nU:nU + nP], pp, rtol=0, atol=1e-10 * np.abs(pp).max())
+    # the fluxes: q on a face equals the outward flux of the cell below it
+    w = system.reconstruct_fluxes(B, pp, x[nU + nP:])
+    fc, fl = B.mesh.face_cells, B.mesh.face_local
+    q = xm[nU + nP:]
+    has0 = (fc[:, 0] >= 0) & ~M.q_fixed
+    assert np.allclose(q[has0], w[fc[has0, 0], fl[has0, 0]], rtol=0, atol=1e-9 * np.abs(q).max())
+
+
+def test_btp_with_exact_blocks_has_a_unit_spectrum():
+    """Eq. (prec): with exact inner solves and the exact Schur complement
+    C_p = A_stab + A_pp - A_pu A_uu^-1 A_up - dt A_pq A_qq^-1 A_qp the BTP is
+    the lower block factor of A_M = M U with U unit upper triangular, so
+    A_M M^-1 has every eigenvalue 1 and (A_M M^-1 - I)^2 = 0.  Pins the signs
+    and dt factors of the coupling blocks and of C_p."""
+    from oracle import mixed
+    p = mi.random_small(2, 3, 2, seed=8, jitter=0.1, dt=0.3)
+    B = oracle.assemble(p)
+    M = mixed.assemble_mixed(B, p.face_bc)
+    A = mixed.mixed_matrix(M).toarray()
+    Auu, Aqq = B.Auu.toarray(), M.Aqq.toarray()
+    Cp = ((B.App + B.Astab).toarray() - B.Apu.toarray() @ np.linalg.solve(Auu, B.Aup.toarray())
+          - B.dt * M.Apq.toarray() @ np.linalg.solve(Aqq, M.Aqp.toarray()))
+    pc = mixed.BTP(M, sp.csr_matrix(Cp), "exact")
+    T = A @ np.linalg.inv(pc.matrix().toarray())
+    E = T - np.eye(T.shape[0])
+    assert np.abs(np.linalg.eigvals(T) - 1).max() <= 1e-6
+    assert np.abs(E @ E).max() <= 1e-8 * np.abs(E).max()
+    # and GMRES stops after two iterations
+    _, info = fgmres.fgmres(lambda v: A @ v, lambda v: np.linalg.solve(pc.matrix().toarray(), v),
+                            mixed.mixed_matrix(M) @ np.ones(A.shape[0]), tol=1e-10, restart=10)
+    assert info["iters"] <= 2
+
+
+def test_btp_amg_reaches_the_direct_solution():
+    """M_II^(m) (V-cycles on A_uu and C~_p, Chebyshev on A_qq) inside FGMRES
+    reaches the mixed system's direct solution; with the lumped C~_p and
+    exact inner solves (M_I^(m)) on the cantilever the count is stable under
+    refinement and within the paper's MFE column of Table tab:can_1."""
+    from oracle import mixed
+    p = mi.random_small(7, 6, 7, seed=13, jitter=0.2)
+    B = oracle.assemble(p)
+    M = mixed.assemble_mixed(B, p.face_bc)
+    A = mixed.mixed_matrix(M)
+    b = system.rhs(B)
+    x = mixed.solve_direct(M, b)
+    pc = mixed.build_btp(M, "amg")
+    assert len(pc.u_levels) >= 2 and len(pc.p_levels) >= 2
+    s = mixed.equilibration(M, pc.Cp)
+    xx, info = fgmres.fgmres(lambda v: A @ v, pc.apply, b, tol=1e-10, scale=s)
+    assert info["converged"] and np.linalg.norm(xx - x) <= 1e-8 * np.linalg.norm(x)
+    its = {}
+    for n in (6, 12):
+        q = mi.cantilever_cube(n, dt=0.1)
+        Bq = oracle.assemble(q)
+        Mq = mixed.assemble_mixed(Bq, q.face_bc)
+        pcq = mixed.build_btp(Mq, "exact")
+        Aq = mixed.mixed_matrix(Mq)
+        _, iq = fgmres.fgmres(lambda v: Aq @ v, pcq.apply, system.rhs(Bq), tol=1e-6, restart=200,
+                              scale=mixed.equilibration(Mq, pcq.Cp))
+        assert iq["converged"]
+        its[n] = iq["iters"]
+    assert its[12] <= 1.25 * its[6] and its[6] <= 47, its
 
 
 def test_condensed_block_identities():
