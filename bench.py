@@ -52,6 +52,9 @@ WORKLOADS = {
     "adjoint48": dict(n=48, desc="48^3 hex, log-normal ln kappa (sigma 1, seed 5), 10 backward-Euler steps dt=0.1 s, "
                                  "misfit of top u_z and cell p against a second seeded field; J and dJ/d ln kappa "
                                  "(110,592 cells) by the checkpointed discrete adjoint, solves to 1e-10"),
+    "cantilever_can3": dict(n=0, desc="Test 2 cantilever (unit cube clamped at x=0, unit load on top, no-flow, E=1e5 Pa, "
+                                      "nu=0.4, kappa=1e-7 m^2, mu=1e-3 Pa s) at 1/h = 64 and 128, dt = 0.1 and 1e-5 s: "
+                                      "M_II^(m) (mixed form) beside M_II^(h) and M_III^(h), FP64, tol 1e-6"),
     "batch48": dict(n=0, desc="48 cubes n ~ U{16..64} (seed 4), own log-normal kappa (sigma 1.5), loads x0.5/1/2/4, "
                               "FP32 V-cycles in FP64 FGMRES(12), all 192 systems in one CUDA graph launch"),
 }
@@ -820,8 +823,65 @@ def run_batch(args):
         sv.close()
 
 
+def run_table(args):
+    """Auxiliary workload, the comparison of Section 5 (Table tab:can_3): the
+    cantilever at the paper's two finest single-GPU grids and both time
+    steps, solved with the mixed formulation's M_II^(m) and the hybrid
+    formulation's M_II^(h) and M_III^(h): FGMRES iterations, set-up time
+    T_p, solve time T_s (CUDA events around the library calls; the first
+    solve of each set-up is a warm-up)."""
+    import torch
+    import mhfp_inputs as mi
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2002_09603_gb300 import Solver, default_options, launch_count
+    variants = [("M_II^(m)", 1, 0), ("M_II^(h)", 0, 0), ("M_III^(h)", 0, 1)]
+    rows = []
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    l0 = launch_count()
+    for n in (64, 128):
+        for dt in (0.1, 1e-5):
+            prob = mi.cantilever_cube(n, dt=dt)
+            for label, form, nk in variants:
+                opt = default_options()
+                opt.formulation, opt.near_kernel, opt.restart = form, nk, 60
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                s = Solver(prob)
+                s.assemble_condense()
+                s.setup_precond(opt)
+                ev[1].record(stream)
+                b = s.build_rhs()
+                x, st = s.solve(b, tol=1e-6)
+                ts = []
+                for _ in range(max(1, args.steps)):
+                    ev[2].record(stream)
+                    x, st = s.solve(b, tol=1e-6, out=x)
+                    ev[3].record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(ev[2].elapsed_time(ev[3]))
+                rows.append({"inv_h": n, "dofs": s.n, "dt": dt, "preconditioner": label,
+                             "iterations": st["iterations"], "converged": bool(st["converged"]),
+                             "T_p_ms": ev[0].elapsed_time(ev[1]), "T_s_ms": statistics.median(ts),
+                             "T_t_ms": ev[0].elapsed_time(ev[1]) + statistics.median(ts)})
+                s.close()
+                del x, b
+    main_ts = [r["T_s_ms"] for r in rows if r["inv_h"] == 128 and r["preconditioner"] == "M_II^(m)"]
+    line = {"metric": "solve time, Test 2 cantilever 1/h=128, M_II^(m) (mean of both dt)",
+            "value": statistics.mean(main_ts), "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "ms_per_step": statistics.mean(main_ts), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["cantilever_can3"]["desc"], "restart": 60, "rows": rows},
+            "gpu_launches": launch_count() - l0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "cantilever_can3":
+        run_table(args)
+        return
     if args.workload == "batch48":
         run_batch(args)
         return

@@ -128,6 +128,19 @@ typedef struct {
                         /* modes restricted to its dofs, six dofs per coarse   */
                         /* point (a mode the aggregate cannot represent leaves */
                         /* a decoupled dof with a unit diagonal)               */
+  int formulation;      /* 0 (default): the hybridized system [u | p | pi]     */
+                        /* (Eq. hmfeSys) with M_II^(h) / M_III^(h); 1: the     */
+                        /* mixed system [u | p | q] (Eq. mfeSys, one RT0 flux  */
+                        /* per face, q = 0 imposed on no-flow faces) with the  */
+                        /* block-triangular preconditioner M_II^(m) of         */
+                        /* Eq. (prec): a displacement V-cycle, Chebyshev on    */
+                        /* A_qq preconditioned by its diagonal, and a V-cycle  */
+                        /* on C~_p = A_pp + A_stab + the fixed-stress diagonal */
+                        /* - dt A_pq L_qq^-1 A_qp (L_qq the lumped A_qq).      */
+                        /* Same vector length as 0; the face entries are the   */
+                        /* fluxes.  Needs precision = 0; the transposed,       */
+                        /* adjoint, gradient, permeability-update and no-      */
+                        /* allocation residual calls return MHFP_ERR_STATE     */
 } mhfp_options;
 
 typedef struct {
@@ -284,24 +297,31 @@ mhfp_status mhfp_adjoint_rhs(mhfp_handle h, const double* d_g, const double* d_l
 mhfp_status mhfp_apply_precond_t(mhfp_handle h, const double* d_v, double* d_z);
 
 /* z = M^-1 v with the multigrid inner solves (Eq. hybridPrec back
- * substitution: pi, then p, then u), unscaled. */
+ * substitution: pi, then p, then u), unscaled.  With formulation = 1 the
+ * block-triangular M_II^(m) of Eq. (prec) by forward substitution: u and q,
+ * then p. */
 mhfp_status mhfp_apply_precond(mhfp_handle h, const double* d_v, double* d_z);
 
 /* One V-cycle x = V(b) of the displacement (which = 0, length n_u) or the
  * interface-pressure (which = 1, length n_pi) hierarchy, in the precision
  * the solve uses: with precision = 1 the FP64 b is rounded to FP32, the
- * FP32 cycle runs, and x is its FP32 result widened to FP64. */
+ * FP32 cycle runs, and x is its FP32 result widened to FP64.  With
+ * formulation = 1, which = 1 is the hierarchy of C~_p (length n_p). */
 mhfp_status mhfp_vcycle(mhfp_handle h, int which, const double* d_b, double* d_x);
 
 /* y = A_l x for level `level` of hierarchy `which` (lengths from
- * mhfp_hierarchy).  Level 0 of which = 1 is C~_pi. */
+ * mhfp_hierarchy).  Level 0 of which = 1 is C~_pi (C~_p with formulation =
+ * 1); with formulation = 1, which = 2 is the one-level A_qq (length n_pi)
+ * that the flux block's Chebyshev smoother runs on. */
 mhfp_status mhfp_level_apply(mhfp_handle h, int which, int level, const double* d_x, double* d_y);
 
-/* Hierarchy description (after mhfp_setup_precond). */
+/* Hierarchy description (after mhfp_setup_precond); which as for
+ * mhfp_level_apply. */
 mhfp_status mhfp_hierarchy(mhfp_handle h, int which, mhfp_hierarchy_info* info);
 
-/* Copy the diagonal approximation B~_p (n_p values) and the equilibration
- * scaling D_s (n values) into device buffers (either may be NULL). */
+/* Copy the diagonal approximation B~_p (n_p values; with formulation = 1
+ * the diagonal of C~_p) and the equilibration scaling D_s (n values) into
+ * device buffers (either may be NULL). */
 mhfp_status mhfp_get_scalings(mhfp_handle h, double* d_btilde, double* d_ds);
 
 /* Sizes: n_u = 3 (nx+1)(ny+1)(nz+1), n_p = nx ny nz, n_pi = number of faces

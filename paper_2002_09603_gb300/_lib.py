@@ -49,7 +49,7 @@ class Options(C.Structure):
                 ("cheb_ratio", C.c_double), ("coarse_max", C.c_int), ("power_iters", C.c_int),
                 ("precision", C.c_int), ("graphs", C.c_int), ("autotune", C.c_int),
                 ("reorth", C.c_int), ("schedule", C.c_int), ("fine_blocks", C.c_int),
-                ("near_kernel", C.c_int)]
+                ("near_kernel", C.c_int), ("formulation", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -223,6 +223,7 @@ class Solver:
 
     def setup_precond(self, options: Options | None = None):
         self._check(self.lib.mhfp_setup_precond(self.h, None if options is None else C.byref(options)))
+        self.formulation = 0 if options is None else int(options.formulation)
 
     def build_rhs(self, x_prev=None, load_scale=1.0, out=None):
         out = self.empty() if out is None else out
@@ -287,7 +288,10 @@ class Solver:
         return out
 
     def vcycle(self, which, b, out=None):
-        n = self.sizes[0] if int(which) == 0 else self.sizes[2]
+        # which = 1: the interface-pressure hierarchy (n_pi), or C~_p's (n_p)
+        # with the mixed formulation
+        mixed = getattr(self, "formulation", 0) == 1
+        n = self.sizes[0] if int(which) == 0 else self.sizes[1 if mixed else 2]
         out = self.empty(n) if out is None else out
         self._check(self.lib.mhfp_vcycle(self.h, int(which), self._v(b, "b", n=n), self._v(out, "out", n=n)))
         return out

@@ -1143,7 +1143,7 @@ void launch_spmv(Ctx& c, const StructOp& A, int bs, const T* val, const T* x, co
 
 void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
   if (L.faces) {
-    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), c.Cpi, x, b, y);
+    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), L.ell ? L.ell : c.Cpi, x, b, y);
   } else {
     launch_spmv<double>(c, L.A, L.bs, L.A.val, x, b, y, default_schedule(L.A.N, L.bs));
   }
@@ -1329,7 +1329,7 @@ void make_dense_coarse(Ctx& c, Level& L) {
 void finish_level(Ctx& c, Level& L) {
   if (!L.dinv) L.dinv = dalloc_n<double>(c, (size_t)L.bs * L.bs * L.npts);
   if (L.faces) {
-    k_dinv_ell<<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, c.Cpi, L.dinv);
+    k_dinv_ell<<<grid_for(L.n, 256), 256, 0, c.stream>>>(L.n, L.ell ? L.ell : c.Cpi, L.dinv);
   } else {
     const Lat lat = lat_of(L.A);
     dispatch_bs(L.bs, [&](auto BS) {
@@ -1580,7 +1580,9 @@ struct LV {
   const T *val, *dinv, *P, *ell, *pw;
   T *r, *d, *y;
 };
-LV<double> view(Ctx& c, Level& L, double) { return {L.A.val, L.dinv, L.P, c.Cpi, c.pw, L.r, L.d, L.y}; }
+LV<double> view(Ctx& c, Level& L, double) {
+  return {L.A.val, L.dinv, L.P, L.ell ? L.ell : c.Cpi, c.pw, L.r, L.d, L.y};
+}
 LV<float> view(Ctx& c, Level& L, float) { return {L.valf, L.dinvf, L.Pf, c.Cpif, c.pwf, L.rf, L.df, L.yf}; }
 double* bvec(Level& L, double) { return L.b; }
 float* bvec(Level& L, float) { return L.bf; }
@@ -1996,6 +1998,66 @@ void rebuild_pi_hierarchy(Ctx& c) {
     recast(c.Cpif, c.Cpi, (size_t)11 * c.nF);
     recast(c.pwf, c.pw, c.nF);
   }
+}
+
+// The mixed formulation's inner solvers (opt.formulation = 1): the
+// displacement hierarchy as for the hybrid form, A_qq as a single face level
+// (its Chebyshev smoother stands for the paper's incomplete Cholesky), and
+// the smoothed-aggregation hierarchy of C~_p started on the cell lattice.
+void build_mixed_hierarchies(Ctx& c) {
+  if (c.opt.near_kernel == 1) build_u_rbm(c);
+  else build_u(c);
+  c.hq.clear();
+  Level Q;
+  Q.faces = true;
+  Q.bs = 1;
+  Q.npts = c.nF;
+  Q.n = c.nF;
+  Q.ell = c.Aqq;
+  c.hq.push_back(Q);
+  alloc_work(c, c.hq.back());
+  finish_level(c, c.hq.back());
+  c.hcp.clear();
+  Level L0;
+  L0.bs = 1;
+  L0.A.Lx = c.nx; L0.A.Ly = c.ny; L0.A.Lz = c.nz;
+  L0.A.N = c.nT; L0.A.bs = 1; L0.A.kind = ST_DIAMOND2;
+  L0.A.val = c.Cp;
+  L0.npts = c.nT;
+  L0.n = c.nT;
+  L0.R = 2;
+  L0.active = dalloc_n<unsigned char>(c, c.nT);
+  MHFP_CUDA(cudaMemsetAsync(L0.active, 1, c.nT, c.stream));
+  c.hcp.push_back(L0);
+  while (c.hcp.back().npts > c.opt.coarse_max && c.hcp.size() < 8) {
+    Level& L = c.hcp.back();
+    alloc_work(c, L);
+    finish_level(c, L);
+    Level Cl = coarsen(c, L);
+    c.hcp.push_back(Cl);
+  }
+  Level& last = c.hcp.back();
+  alloc_work(c, last);
+  make_dense_coarse(c, last);
+  if (c.opt.autotune)
+    for (auto* H : {&c.hu, &c.hcp})
+      for (size_t l = 0; l < H->size(); ++l) {
+        Level& L = (*H)[l];
+        if (L.faces || L.dense_inv || (H == &c.hu && l == 0) || c.opt.schedule) continue;
+        autotune_level<double>(c, L);
+      }
+  if (c.opt.schedule)
+    for (auto* H : {&c.hu, &c.hcp})
+      for (size_t l = 0; l < H->size(); ++l) {
+        Level& L = (*H)[l];
+        if (!L.faces && !L.dense_inv && !(H == &c.hu && l == 0)) L.tpp = c.opt.schedule;
+      }
+}
+
+// x = the Chebyshev smoother of level 0 of H applied to b from x = 0 (the
+// mixed formulation's A_qq solve)
+void chebyshev_from_zero(Ctx& c, std::vector<Level>& H, const double* b, double* x) {
+  smooth<double>(c, H, 0, b, x, true, false);
 }
 
 int level_schedule(Ctx& c, std::vector<Level>& H, int l) {

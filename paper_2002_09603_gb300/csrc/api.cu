@@ -113,6 +113,19 @@ mhfp_status guarded(mhfp_handle h, F&& f) {
   }
 }
 
+// which = 0: displacement; 1: interface pressure (C~_p with the mixed
+// formulation); 2: the mixed formulation's A_qq level
+std::vector<mhfp::Level>& hierarchy_of(Ctx& c, int which) {
+  if (which == 0) return c.hu;
+  if (c.opt.formulation == 1) return which == 1 ? c.hcp : c.hq;
+  return c.hpi;
+}
+
+// the calls that only the hybridized system has
+void hybrid_only(const Ctx& c) {
+  if (c.opt.formulation == 1) throw Error{MHFP_ERR_STATE, "not available with the mixed formulation"};
+}
+
 template <class T>
 T* upload(Ctx& c, const T* host, size_t n) {
   T* d = mhfp::dalloc_n<T>(c, n);
@@ -139,6 +152,7 @@ void mhfp_default_options(mhfp_options* o) {
   o->schedule = 0;
   o->fine_blocks = 0;
   o->near_kernel = 0;
+  o->formulation = 0;
 }
 
 const char* mhfp_status_string(mhfp_status s) {
@@ -240,14 +254,20 @@ mhfp_status mhfp_setup_precond(mhfp_handle h, const mhfp_options* opt) {
           (opt->schedule != 0 && opt->schedule != 1 && opt->schedule != 4 && opt->schedule != 8 &&
            opt->schedule != 16) ||
           (opt->fine_blocks != 0 && (opt->fine_blocks < 4 || opt->fine_blocks > 8)) ||
-          (opt->near_kernel != 0 && opt->near_kernel != 1))
+          (opt->near_kernel != 0 && opt->near_kernel != 1) ||
+          (opt->formulation != 0 && opt->formulation != 1) || (opt->formulation == 1 && opt->precision != 0))
         throw Error{MHFP_ERR_ARG, "invalid options"};
       c.opt = *opt;
     }
     const bool tune_degree = c.opt.cheb_degree == 0;
     if (tune_degree) c.opt.cheb_degree = 2;  // the hierarchy's set-up timings use degree 2
     mhfp::build_preconditioner_blocks(c);
-    mhfp::build_hierarchies(c);
+    if (c.opt.formulation == 1) {
+      mhfp::build_mixed_blocks(c);
+      mhfp::build_mixed_hierarchies(c);
+    } else {
+      mhfp::build_hierarchies(c);
+    }
     if (c.opt.precision == 1) mhfp::make_fp32_blocks(c);
     MHFP_CUDA(cudaStreamSynchronize(c.stream));
     c.prepared = true;
@@ -289,6 +309,7 @@ mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y) {
 
 mhfp_status mhfp_apply_operator_t(mhfp_handle h, const double* d_x, double* d_y) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.assembled || !c.prepared) throw Error{MHFP_ERR_STATE, "operator needs assemble + setup"};
     if (!d_x || !d_y || d_x == d_y) throw Error{MHFP_ERR_ARG, "bad vectors"};
     mhfp::apply_operator(c, d_x, d_y, nullptr, nullptr, true);
@@ -297,6 +318,7 @@ mhfp_status mhfp_apply_operator_t(mhfp_handle h, const double* d_x, double* d_y)
 
 mhfp_status mhfp_adjoint_solve(mhfp_handle h, const double* d_g, double* d_lambda, double tol, mhfp_stats* stats) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (!d_g || !d_lambda || !(tol > 0.0) || !(tol < 1.0)) throw Error{MHFP_ERR_ARG, "bad adjoint argument"};
     mhfp::fgmres_solve(c, d_g, d_lambda, tol, stats, true);
@@ -305,6 +327,7 @@ mhfp_status mhfp_adjoint_solve(mhfp_handle h, const double* d_g, double* d_lambd
 
 mhfp_status mhfp_grad_logk(mhfp_handle h, const double* d_lambda, const double* d_x, double* d_grad) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
     if (!d_lambda || !d_x || !d_grad) throw Error{MHFP_ERR_ARG, "bad gradient argument"};
     mhfp::grad_logk(c, d_lambda, d_x, d_grad);
@@ -325,6 +348,7 @@ mhfp_status mhfp_misfit(mhfp_handle h, const double* d_x, const double* d_uz_tar
 
 mhfp_status mhfp_adjoint_rhs(mhfp_handle h, const double* d_g, const double* d_lambda_next, double* d_rhs) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.assembled) throw Error{MHFP_ERR_STATE, "mhfp_assemble_condense must come first"};
     if (!d_g || !d_rhs) throw Error{MHFP_ERR_ARG, "bad adjoint rhs argument"};
     mhfp::adjoint_rhs(c, d_g, d_lambda_next, d_rhs);
@@ -333,6 +357,7 @@ mhfp_status mhfp_adjoint_rhs(mhfp_handle h, const double* d_g, const double* d_l
 
 mhfp_status mhfp_apply_precond_t(mhfp_handle h, const double* d_v, double* d_z) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (!d_v || !d_z || d_v == d_z) throw Error{MHFP_ERR_ARG, "bad vectors"};
     mhfp::apply_precond(c, d_v, d_z, true);
@@ -352,15 +377,16 @@ mhfp_status mhfp_vcycle(mhfp_handle h, int which, const double* d_b, double* d_x
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (which != 0 && which != 1) throw Error{MHFP_ERR_ARG, "which must be 0 or 1"};
     if (!d_b || !d_x || d_b == d_x) throw Error{MHFP_ERR_ARG, "bad vectors"};
-    mhfp::vcycle_api(c, which == 0 ? c.hu : c.hpi, d_b, d_x);
+    mhfp::vcycle_api(c, hierarchy_of(c, which), d_b, d_x);
   });
 }
 
 mhfp_status mhfp_level_apply(mhfp_handle h, int which, int level, const double* d_x, double* d_y) {
   return guarded(h, [&](Ctx& c) {
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
-    if (which != 0 && which != 1) throw Error{MHFP_ERR_ARG, "which must be 0 or 1"};
-    auto& H = which == 0 ? c.hu : c.hpi;
+    if (which != 0 && which != 1 && !(which == 2 && c.opt.formulation == 1))
+      throw Error{MHFP_ERR_ARG, "which must be 0 or 1 (or 2 with the mixed formulation)"};
+    auto& H = hierarchy_of(c, which);
     if (level < 0 || level >= (int)H.size()) throw Error{MHFP_ERR_ARG, "level out of range"};
     if (!d_x || !d_y || d_x == d_y) throw Error{MHFP_ERR_ARG, "bad vectors"};
     mhfp::level_apply(c, H, level, d_x, d_y);
@@ -370,8 +396,9 @@ mhfp_status mhfp_level_apply(mhfp_handle h, int which, int level, const double* 
 mhfp_status mhfp_hierarchy(mhfp_handle h, int which, mhfp_hierarchy_info* info) {
   return guarded(h, [&](Ctx& c) {
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
-    if ((which != 0 && which != 1) || !info) throw Error{MHFP_ERR_ARG, "bad argument"};
-    auto& H = which == 0 ? c.hu : c.hpi;
+    if ((which != 0 && which != 1 && !(which == 2 && c.opt.formulation == 1)) || !info)
+      throw Error{MHFP_ERR_ARG, "bad argument"};
+    auto& H = hierarchy_of(c, which);
     std::memset(info, 0, sizeof(*info));
     info->levels = (int)H.size();
     info->cheb_degree = c.opt.cheb_degree;
@@ -390,7 +417,8 @@ mhfp_status mhfp_get_scalings(mhfp_handle h, double* d_btilde, double* d_ds) {
   return guarded(h, [&](Ctx& c) {
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (d_btilde)
-      MHFP_CUDA(cudaMemcpyAsync(d_btilde, c.btilde, c.nT * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      MHFP_CUDA(cudaMemcpyAsync(d_btilde, c.opt.formulation == 1 ? c.Cp + (size_t)12 * c.nT : c.btilde,
+                                c.nT * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     if (d_ds) MHFP_CUDA(cudaMemcpyAsync(d_ds, c.ds, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
   });
 }
@@ -433,6 +461,7 @@ mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launche
 
 mhfp_status mhfp_update_logk(mhfp_handle h, const double* d_logk) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (!d_logk) throw Error{MHFP_ERR_ARG, "bad log-permeability vector"};
     mhfp::update_logk_blocks(c, d_logk);  // validates before changing anything
@@ -445,6 +474,7 @@ mhfp_status mhfp_update_logk(mhfp_handle h, const double* d_logk) {
 
 mhfp_status mhfp_residual_norm_noalloc(mhfp_handle h, const double* d_b, const double* d_x, double* d_out) {
   return guarded(h, [&](Ctx& c) {
+    hybrid_only(c);
     if (!c.prepared) throw Error{MHFP_ERR_STATE, "mhfp_setup_precond must come first"};
     if (!d_b || !d_x || !d_out) throw Error{MHFP_ERR_ARG, "bad vectors"};
     mhfp::residual_norm_noalloc(c, d_b, d_x, d_out);

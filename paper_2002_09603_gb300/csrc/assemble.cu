@@ -178,7 +178,7 @@ __global__ void k_rt0(Dims d, const double* __restrict__ coords, const double* _
                       const double* __restrict__ kappa, const double* __restrict__ Seps,
                       const double* __restrict__ vol, double dt, double* __restrict__ Wout,
                       double* __restrict__ W1out, double* __restrict__ sWout, double* __restrict__ Abar,
-                      int* __restrict__ flag) {
+                      int* __restrict__ flag, double* __restrict__ Aww_out = nullptr) {
   const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= d.nT) return;
   double X[8][3];
@@ -213,6 +213,9 @@ __global__ void k_rt0(Dims d, const double* __restrict__ coords, const double* _
     for (int f = 0; f < 6; ++f)
       for (int g = 0; g < 6; ++g) A[f][g] += M[f >> 1][g >> 1] * val[f] * val[g];
   }
+  if (Aww_out)
+    for (int f = 0; f < 6; ++f)
+      for (int g = 0; g < 6; ++g) Aww_out[(long long)(6 * f + g) * d.nT + T] = A[f][g];
   // Cholesky A = L L^T, then W = A^-1 column by column
   double L[6][6];
   for (int i = 0; i < 6; ++i)
@@ -670,6 +673,30 @@ __global__ void __launch_bounds__(256) k_apply_pi(FaceTopo32 t, long long nU, co
   y[r] = finish(s, r, so, bsub);
 }
 
+// t_p = v_p - A_pu z_u - dt A_pq z_q (A_pu z_u = -sum A_up^T z_u, as in the p
+// rows of the operator)
+__global__ void __launch_bounds__(256) k_btp_p(FaceTopo32 t, const double* __restrict__ Aup,
+                                               const double* __restrict__ Apq, double dt,
+                                               const double* __restrict__ vp, const double* __restrict__ zu,
+                                               const double* __restrict__ zq, double* __restrict__ tp) {
+  const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= t.nT) return;
+  const unsigned q = t.d_nx.div(T);
+  const int i = (int)(T - q * (unsigned)t.nx), k = (int)t.d_ny.div(q), j = (int)(q - (unsigned)k * (unsigned)t.ny);
+  const unsigned Lx = (unsigned)t.nx + 1, Ly = (unsigned)t.ny + 1;
+  double su = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const unsigned n = (unsigned)(i + (a & 1)) + Lx * ((unsigned)(j + ((a >> 1) & 1)) + Ly * (unsigned)(k + (a >> 2)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) su -= Aup[(unsigned)(3 * a + c) * t.nT + T] * zu[3 * n + c];
+  }
+  double cq = 0.0;
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) cq += Apq[(unsigned)lf * t.nT + T] * zq[t.face(i, j, k, lf)];
+  tp[T] = vp[T] - su - dt * cq;
+}
+
 // preconditioner pieces: z_p = B~^-1 (v_p - dt A_ppi z_pi), t_u = v_u - A_up z_p
 // (FP64, or FP32 in the mixed-precision preconditioner)
 template <typename R>
@@ -869,6 +896,112 @@ __global__ void k_adjoint_rhs(Dims d, const double* __restrict__ Aup, const doub
   rhs[r] = v;
 }
 
+// ---------------------------------------------------------------- mixed form
+// Eq. (mfeSys) with continuous RT0 fluxes q, one per face oriented along the
+// face's +axis: the cell's local face lf carries the sign s_lf = -1 on its
+// lower side (lf even) and +1 on its upper side.  On a no-flow face q = 0:
+// its row and column are zeroed and the diagonal kept.
+__device__ __forceinline__ double face_sign(int lf) { return (lf & 1) ? 1.0 : -1.0; }
+
+// per cell face: A_qp = -s_lf, A_pq = +s_lf (0 on no-flow faces); A_pp = S|T|
+__global__ void k_mixed_cells(Dims d, const unsigned char* __restrict__ face_bc, const double* __restrict__ Seps,
+                              const double* __restrict__ vol, double* __restrict__ Aqp, double* __restrict__ Apq,
+                              double* __restrict__ Spp) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  for (int lf = 0; lf < 6; ++lf) {
+    const long long f = cell_face(d, i, j, k, lf);
+    const bool noflow = face_bc[f] & 4;
+    Aqp[(long long)lf * d.nT + T] = noflow ? 0.0 : -face_sign(lf);
+    Apq[(long long)lf * d.nT + T] = noflow ? 0.0 : face_sign(lf);
+  }
+  Spp[T] = Seps[T] * vol[T];
+}
+
+// A_qq in the ELL slots of the face operators (slot 0 the face itself; slot
+// 1 + 5 s + q the q-th other local face of the cell on side s), from the cell
+// mass matrices A_ww,T and the face signs; lumped[f] = sum of |row|.
+__global__ void k_mixed_faces(Dims d, const double* __restrict__ Aww, const unsigned char* __restrict__ face_bc,
+                              double* __restrict__ Aqq, double* __restrict__ lumped) {
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.nF) return;
+  long long cell[2];
+  int lf[2], ijk[2][3];
+  face_cells(d, f, cell, lf, ijk);
+  const bool fixed = face_bc[f] & 4;
+  double diag = 0.0, lsum = 0.0;
+  const long long nF = d.nF, nT = d.nT;
+  for (int s = 0; s < 2; ++s) {
+    if (cell[s] < 0) {
+      for (int q = 0; q < 5; ++q) Aqq[(1 + 5 * s + q) * nF + f] = 0.0;
+      continue;
+    }
+    const long long T = cell[s];
+    const int l = lf[s];
+    diag += Aww[(long long)(6 * l + l) * nT + T];
+    int q = 0;
+    for (int m = 0; m < 6; ++m) {
+      if (m == l) continue;
+      const long long g = cell_face(d, ijk[s][0], ijk[s][1], ijk[s][2], m);
+      double v = face_sign(l) * face_sign(m) * Aww[(long long)(6 * l + m) * nT + T];
+      if (fixed || (face_bc[g] & 4)) v = 0.0;
+      Aqq[(1 + 5 * s + q) * nF + f] = v;
+      lsum += fabs(v);
+      ++q;
+    }
+  }
+  Aqq[f] = diag;
+  lumped[f] = lsum + fabs(diag);
+}
+
+// C~_p = A_pp + A_stab + diag(A_up^T diag(A_uu)^-1 A_up) - dt A_pq L^-1 A_qp
+// on the cell lattice (25-point slots; the non-zeros are the cell and its six
+// face neighbours): the diagonal gains dt / L_f per flowing face, a
+// neighbour across face f gets -dt / L_f, a macro partner -beta_M |M|.
+__global__ void k_mixed_cp(Dims d, const double* __restrict__ Auu, const double* __restrict__ Aup,
+                           const double* __restrict__ Spp, const double* __restrict__ stabc,
+                           const unsigned char* __restrict__ face_bc, const double* __restrict__ lumped, double dt,
+                           double* __restrict__ Cp) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= d.nT) return;
+  const int i = (int)(T % d.nx), j = (int)((T / d.nx) % d.ny), k = (int)(T / ((long long)d.nx * d.ny));
+  double fs = 0.0;
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_id(d, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    for (int c = 0; c < 3; ++c) {
+      const double v = Aup[(long long)(3 * a + c) * d.nT + T];
+      const double dg = Auu[(long long)(13 * 9 + 4 * c) * d.nN + n];
+      fs += v * v / dg;
+    }
+  }
+  double out[25];
+  for (int o = 0; o < 25; ++o) out[o] = 0.0;
+  const double sx = stabc[T], sy = stabc[d.nT + T], sz = stabc[2 * d.nT + T];
+  double diag = Spp[T] + (sx + sy + sz) + fs;
+  // 25-point slot of the offset (dx, dy, dz) with |d|_1 <= 1: the diamond
+  // order lists (0,0,-1) at 3, (0,-1,0) at 8, (-1,0,0) at 11, the cell at 12,
+  // (1,0,0) at 13, (0,1,0) at 16, (0,0,1) at 21
+  const int slot_of_lf[6] = {11, 13, 8, 16, 3, 21};
+  for (int lf = 0; lf < 6; ++lf) {
+    const long long f = cell_face(d, i, j, k, lf);
+    if (face_bc[f] & 4) continue;
+    const double c1 = dt / lumped[f];
+    diag += c1;
+    const int ax = lf >> 1, up = lf & 1;
+    const int ni = i + (ax == 0 ? (up ? 1 : -1) : 0), nj = j + (ax == 1 ? (up ? 1 : -1) : 0),
+              nk = k + (ax == 2 ? (up ? 1 : -1) : 0);
+    if (ni < 0 || ni >= d.nx || nj < 0 || nj >= d.ny || nk < 0 || nk >= d.nz) continue;
+    out[slot_of_lf[lf]] -= c1;
+  }
+  // macro partners (i ^ 1, j, k) ... are face neighbours
+  if (sx != 0.0) out[(i & 1) ? 11 : 13] -= sx;
+  if (sy != 0.0) out[(j & 1) ? 8 : 16] -= sy;
+  if (sz != 0.0) out[(k & 1) ? 3 : 21] -= sz;
+  out[12] = diag;
+  for (int o = 0; o < 25; ++o) Cp[(long long)o * d.nT + T] = out[o];
+}
+
 Dims dims_of(const Ctx& c) {
   return Dims{c.nx, c.ny, c.nz, c.nN, c.nT, c.nF, c.nFx, c.nFy};
 }
@@ -1005,6 +1138,72 @@ void update_logk_blocks(Ctx& c, const double* logk) {
   build_preconditioner_blocks(c);
 }
 
+// The mixed formulation's blocks (opt.formulation = 1): A_ww again from
+// the RT0 element kernel, A_qq and its lumped diagonal, A_qp / A_pq per
+// cell face, A_pp, C~_p on the cell lattice and the equilibration
+// D_s = diag(A_uu, C~_p, A_qq)^(-1/2).
+void build_mixed_blocks(Ctx& c) {
+  const Dims d = dims_of(c);
+  double* Aww = dalloc_n<double>(c, (size_t)36 * c.nT);
+  MHFP_CUDA(cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream));
+  k_rt0<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.coords, c.mu, c.kappa, c.Seps, c.vol, c.dt, c.W, c.W1, c.sW,
+                                                   c.Abar, c.d_flag, Aww);
+  MHFP_LAUNCH_CHECK();
+  c.Aqp_c = dalloc_n<double>(c, (size_t)6 * c.nT);
+  c.Apq_c = dalloc_n<double>(c, (size_t)6 * c.nT);
+  c.Spp = dalloc_n<double>(c, c.nT);
+  k_mixed_cells<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(d, c.face_bc, c.Seps, c.vol, c.Aqp_c, c.Apq_c, c.Spp);
+  MHFP_LAUNCH_CHECK();
+  c.Aqq = dalloc_n<double>(c, (size_t)11 * c.nF);
+  double* lumped = dalloc_n<double>(c, c.nF);
+  k_mixed_faces<<<grid_for(c.nF, 128), 128, 0, c.stream>>>(d, Aww, c.face_bc, c.Aqq, lumped);
+  MHFP_LAUNCH_CHECK();
+  c.Cp = dalloc_n<double>(c, (size_t)25 * c.nT);
+  k_mixed_cp<<<grid_for(c.nT, 128), 128, 0, c.stream>>>(d, c.Auu.val, c.Aup, c.Spp, c.stabc, c.face_bc, lumped, c.dt,
+                                                        c.Cp);
+  MHFP_LAUNCH_CHECK();
+  if (!c.ds) {
+    c.ds = dalloc_n<double>(c, c.n);
+    c.ds_inv = dalloc_n<double>(c, c.n);
+  }
+  k_scalings<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.Auu.val, c.Cp + (size_t)12 * c.nT, c.Aqq, c.ds,
+                                                       c.ds_inv);
+  MHFP_LAUNCH_CHECK();
+  int hflag = 0;
+  MHFP_CUDA(cudaMemcpyAsync(&hflag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  MHFP_CUDA(cudaStreamSynchronize(c.stream));
+  // the cell mass matrices are consumed by the face rows; release them now
+  for (auto it = c.allocs.begin(); it != c.allocs.end(); ++it)
+    if (*it == (void*)Aww) { c.allocs.erase(it); break; }
+  MHFP_CUDA(cudaFree(Aww));
+  if (hflag & 2) throw Error{MHFP_ERR_MESH, "RT0 element mass matrix is not positive definite"};
+}
+
+// y = A_M x (or D_s (b - A_M x)) for the mixed formulation [u | p | q]: the
+// u rows as for the hybrid system; p rows A_pu x_u + (A_pp + A_stab) x_p +
+// dt A_pq x_q; q rows A_qp x_p + A_qq x_q
+void apply_operator_mixed(Ctx& c, const double* x, double* y, const double* so, const double* bsub) {
+  const Dims d = dims_of(c);
+  timing_begin(c, 1);
+  k_apply_u<<<grid_for(c.nN, APPLY_U_NODES), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
+                                                                                    bsub, 1.0);
+  MHFP_LAUNCH_CHECK();
+  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Spp, c.stabc, c.Apq_c, c.dt, x, y, so,
+                                                       bsub, 1.0);
+  MHFP_LAUNCH_CHECK();
+  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(topo32(c), 3 * c.nN, c.Aqp_c, c.Aqq, x, y, so, bsub, 1.0);
+  MHFP_LAUNCH_CHECK();
+  const double bytes = 27.0 * 9 * 8 * c.nN + 2.0 * 24 * 8 * c.nT + 11.0 * 8 * c.nF + 17.0 * 8 * c.nT + 16.0 * c.n;
+  timing_end(c, 1, bytes);
+}
+
+// the block-triangular preconditioner's p right-hand side (Eq. prec, forward
+// substitution): t_p = v_p - A_pu z_u - dt A_pq z_q
+void btp_p_rhs(Ctx& c, const double* vp, const double* zu, const double* zq, double* tp) {
+  k_btp_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Apq_c, c.dt, vp, zu, zq, tp);
+  MHFP_LAUNCH_CHECK();
+}
+
 void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs) {
   const Dims d = dims_of(c);
   k_rhs<<<grid_for(c.n, 256), 256, 0, c.stream>>>(d, c.fu, c.Aup, c.Seps, c.vol, xprev, scale, rhs);
@@ -1012,6 +1211,11 @@ void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs) {
 }
 
 void apply_operator(Ctx& c, const double* x, double* y, const double* so, const double* bsub, bool transpose) {
+  if (c.opt.formulation == 1) {
+    if (transpose) throw Error{MHFP_ERR_STATE, "the mixed formulation has no transposed solve"};
+    apply_operator_mixed(c, x, y, so, bsub);
+    return;
+  }
   const Dims d = dims_of(c);
   timing_begin(c, 1);
   const double sgn = transpose ? -1.0 : 1.0;

@@ -236,6 +236,7 @@ struct Level {
   double* P = nullptr;
   int R = 1;                  // stencil radius of A (L_inf)
   int cbs = 0;                // unknowns per point of the next level (P blocks are bs x cbs)
+  const double* ell = nullptr; // face level: its ELL values (null: C~_pi)
   int tpp = 0;                // launch schedule chosen by the autotuner (0: default rule):
                               // 1 = one point per thread, 4/8/16 = warps splitting the
                               // offsets; finest FP32 displacement level: blocks per SM (6, 8)
@@ -336,6 +337,13 @@ struct Ctx {
   cudaGraphConditionalHandle* d_hif[2] = {nullptr, nullptr};  // IF handles of the solve graphs
 
   std::vector<Level> hu, hpi;
+  // the mixed formulation (opt.formulation = 1), unknowns [u | p | q]
+  double* Aqq = nullptr;     // [11][nF] A_qq (ELL, the face operators' slots)
+  double* Aqp_c = nullptr;   // [6][nT] A_qp per cell face (-s_lf; 0 on no-flow faces)
+  double* Apq_c = nullptr;   // [6][nT] A_pq per cell face (+s_lf; 0 on no-flow faces)
+  double* Spp = nullptr;     // [nT] A_pp = S_eps |T|
+  double* Cp = nullptr;      // [25][nT] C~_p on the cell lattice (25-point slots)
+  std::vector<Level> hq, hcp;  // A_qq's Chebyshev level; C~_p's hierarchy
   // FP32 copies used by the mixed-precision preconditioner
   float *Cpif = nullptr, *pwf = nullptr, *ApPif = nullptr, *btildef = nullptr, *Aupf = nullptr;
   float *tf = nullptr, *zf = nullptr;
@@ -418,6 +426,9 @@ void adjoint_rhs(Ctx& c, const double* g, const double* lam_next, double* rhs);
 void ensure_workspace(Ctx& c);
 void residual_norm_noalloc(Ctx& c, const double* b, const double* x, double* out);
 void update_logk_blocks(Ctx& c, const double* logk);
+void build_mixed_blocks(Ctx& c);   // A_qq, A_qp, A_pq, S|T|, C~_p, D_s of the mixed formulation
+void apply_operator_mixed(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub);
+void btp_p_rhs(Ctx& c, const double* vp, const double* zu, const double* zq, double* tp);
 
 // amg.cu: the interface-pressure hierarchy and the FP32 copies rebuilt in
 // place after a permeability update (same levels, same schedules)
@@ -431,6 +442,8 @@ void build_hierarchies(Ctx& c);
 void vcycle(Ctx& c, std::vector<Level>& H, const double* b, double* x);
 void vcycle(Ctx& c, std::vector<Level>& H, const float* b, float* x);
 void level_apply(Ctx& c, std::vector<Level>& H, int l, const double* x, double* y);
+void build_mixed_hierarchies(Ctx& c);
+void chebyshev_from_zero(Ctx& c, std::vector<Level>& H, const double* b, double* x);
 void vcycle_api(Ctx& c, std::vector<Level>& H, const double* b, double* x);  // in the solve's precision
 
 // krylov.cu

@@ -409,7 +409,31 @@ void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z, 
   timing_end(c, 3, 0.0);
 }
 
+// M_II^(m) of Eq. (prec) for the mixed formulation [u | p | q], by forward
+// substitution: z_u = V_u(v_u), z_q = Chebyshev(A_qq) v_q, then
+// z_p = V_Cp(v_p - A_pu z_u - dt A_pq z_q)
+void apply_precond_btp(Ctx& c, const double* v, double* z) {
+  const double* vu = v;
+  const double* vp = v + c.nU;
+  const double* vq = vp + c.nT;
+  double* zu = z;
+  double* zp = z + c.nU;
+  double* zq = zp + c.nT;
+  timing_begin(c, 3);
+  vcycle(c, c.hu, vu, zu);
+  chebyshev_from_zero(c, c.hq, vq, zq);
+  double* tp = c.hcp[0].b;  // level 0's right-hand-side buffer is free here
+  btp_p_rhs(c, vp, zu, zq, tp);
+  vcycle(c, c.hcp, (const double*)tp, zp);
+  timing_end(c, 3, 0.0);
+}
+
 void apply_precond(Ctx& c, const double* v, double* z, bool transpose) {
+  if (c.opt.formulation == 1) {
+    if (transpose) throw Error{MHFP_ERR_STATE, "the mixed formulation has no transposed preconditioner"};
+    apply_precond_btp(c, v, z);
+    return;
+  }
   if (c.opt.precision == 1) {
     apply_precond_mixed(c, v, nullptr, z, transpose);
     return;
