@@ -101,39 +101,78 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
 // A(n, n - e_o) = A(n - e_o, n)^T, slot u of node n - e_o.  Each stored
 // block is read by its owner and by one neighbour at most a lattice plane
 // apart, so the second read hits L2 and HBM carries each value once.
+// Node-blocked layout: nodes in blocks of 32; a block holds its 126 rows
+// (slot u, entry e: row 9 u + e) of 32 values each, so the rows a warp
+// streams are one contiguous 16 KB range (sym_base).
 // UNR slots per loop iteration: 2 keeps two slots' loads in flight (the
 // 5-blocks-per-SM variant has the registers for it), 1 one slot.
+__device__ __forceinline__ long long sym_base(long long q) { return (q >> 5) * (126 * 32) + (q & 31); }
+// lanes of p's warp that hold a node (blocks are whole warps of 32 nodes)
+__device__ __forceinline__ unsigned sym_lanes(const Lat& L, long long p) {
+  const long long left = L.N - (p & ~31LL);
+  return left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
+}
+
+// Slot 1 is the +x neighbour, so node p's lower block of that slot is the
+// own block of node p - 1, the previous lane's: every lane loads its own
+// slot-1 block and the lower one arrives by warp shuffle (lane 0 loads it).
+// `mask` holds the lanes of the warp with a node (all lanes call this).
 template <typename T, int UNR = 1>
-__device__ __forceinline__ void sym_residual(const Lat& L, long long ld, long long p, const T* __restrict__ up,
-                                             const T* __restrict__ x, T r[3]) {
-  const long long N = ld;  // row stride of the stored values (>= number of nodes)
+__device__ __forceinline__ void sym_residual(const Lat& L, long long p, const T* __restrict__ up,
+                                             const T* __restrict__ x, T r[3], unsigned mask) {
   int i, j, k;
   L.ijk(p, i, j, k);
+  const T* own = up + sym_base(p);
   {
-    const T* v = up + p;
     const T x0 = x[3 * p], x1 = x[3 * p + 1], x2 = x[3 * p + 2];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) r[a] -= v[(3 * a) * N] * x0 + v[(3 * a + 1) * N] * x1 + v[(3 * a + 2) * N] * x2;
+    for (int a = 0; a < 3; ++a) r[a] -= own[(3 * a) * 32] * x0 + own[(3 * a + 1) * 32] * x1 + own[(3 * a + 2) * 32] * x2;
+  }
+  {
+    T v[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) v[e] = own[(9 + e) * 32];
+    if (i + 1 < L.Lx) {
+      const long long q = p + 1;
+      const T x0 = x[3 * q], x1 = x[3 * q + 1], x2 = x[3 * q + 2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) r[a] -= v[3 * a] * x0 + v[3 * a + 1] * x1 + v[3 * a + 2] * x2;
+    }
+    const bool first = (threadIdx.x & 31) == 0;
+    const T* w = up + sym_base(first && i > 0 ? p - 1 : p) + 9 * 32;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T t0 = __shfl_up_sync(mask, v[a], 1), t1 = __shfl_up_sync(mask, v[3 + a], 1),
+        t2 = __shfl_up_sync(mask, v[6 + a], 1);
+      if (first) {
+        t0 = w[a * 32];
+        t1 = w[(3 + a) * 32];
+        t2 = w[(6 + a) * 32];
+      }
+      if (i > 0) {
+        const long long q = p - 1;
+        r[a] -= t0 * x[3 * q] + t1 * x[3 * q + 1] + t2 * x[3 * q + 2];
+      }
+    }
   }
 #pragma unroll UNR
-  for (int u = 1; u <= 13; ++u) {
+  for (int u = 2; u <= 13; ++u) {
     int dx, dy, dz;
     St<ST_BOX1>::off(13 + u, dx, dy, dz);
     const long long s = dx + (long long)L.Lx * (dy + (long long)L.Ly * dz);
-    const T* vu = up + (long long)u * 9 * N;
     if (L.in(i + dx, j + dy, k + dz)) {
       const long long q = p + s;
-      const T* v = vu + p;
+      const T* v = own + u * 9 * 32;
       const T x0 = x[3 * q], x1 = x[3 * q + 1], x2 = x[3 * q + 2];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) r[a] -= v[(3 * a) * N] * x0 + v[(3 * a + 1) * N] * x1 + v[(3 * a + 2) * N] * x2;
+      for (int a = 0; a < 3; ++a) r[a] -= v[(3 * a) * 32] * x0 + v[(3 * a + 1) * 32] * x1 + v[(3 * a + 2) * 32] * x2;
     }
     if (L.in(i - dx, j - dy, k - dz)) {
       const long long q = p - s;
-      const T* v = vu + q;
+      const T* v = up + sym_base(q) + u * 9 * 32;
       const T x0 = x[3 * q], x1 = x[3 * q + 1], x2 = x[3 * q + 2];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) r[a] -= v[a * N] * x0 + v[(3 + a) * N] * x1 + v[(6 + a) * N] * x2;
+      for (int a = 0; a < 3; ++a) r[a] -= v[a * 32] * x0 + v[(3 + a) * 32] * x1 + v[(6 + a) * 32] * x2;
     }
   }
 }
@@ -142,26 +181,26 @@ __device__ __forceinline__ void sym_residual(const Lat& L, long long ld, long lo
 // when the level has at most 152 x 2048 nodes; 6 (40 registers) keeps more
 // loads in flight per thread on larger levels.  The set-up autotuner picks.
 template <typename T, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, long long ld, const T* __restrict__ up,
+__global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, const T* __restrict__ up,
                                                             const T* __restrict__ x, const T* __restrict__ b,
                                                             T* __restrict__ y) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
-  sym_residual<T, (MINB <= 5 ? 2 : 1)>(L, ld, p, up, x, r);
+  sym_residual<T, (MINB <= 5 ? 2 : 1)>(L, p, up, x, r, sym_lanes(L, p));
 #pragma unroll
   for (int a = 0; a < 3; ++a) y[3 * p + a] = r[a];
 }
 
 template <typename T, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, const T* __restrict__ up,
+__global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, const T* __restrict__ up,
                                                            const T* __restrict__ dinv, const T* __restrict__ b,
                                                            const T* __restrict__ xin, T* __restrict__ xout,
                                                            T* __restrict__ d, T cd, T cr) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
-  if (xin) sym_residual<T, (MINB <= 5 ? 2 : 1)>(L, ld, p, up, xin, r);
+  if (xin) sym_residual<T, (MINB <= 5 ? 2 : 1)>(L, p, up, xin, r, sym_lanes(L, p));
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const T z = dinv[(3 * a) * L.N + p] * r[0] + dinv[(3 * a + 1) * L.N + p] * r[1] + dinv[(3 * a + 2) * L.N + p] * r[2];
@@ -178,10 +217,12 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
 // A persistent CTA takes node blocks of TMA_NB consecutive nodes.  Its
 // producer warp streams, for each block, the 14 stored slots u: the 9 rows
 // of the nodes' own blocks A(p, p + e_u) and, for u >= 1, the 9 rows of the
-// neighbours' blocks A(p - e_u, p) (read transposed), each row one
-// cp.async.bulk copy of TMA_NB (+4) floats into shared memory, TMA_S slots
-// in flight; a "full" mbarrier per slot buffer counts the bytes, an "empty"
-// one the consumer warps that are done with it.  The TMA_NW consumer warps
+// neighbours' blocks A(p - e_u, p) (read transposed).  In the node-blocked
+// layout a slot's 9 rows of one 32-node block are 1152 contiguous bytes, one
+// cp.async.bulk copy: 8 for the own rows, 8 or 9 for the transposed ones
+// (the node range p - s_u starts anywhere); TMA_S slots in flight; a "full"
+// mbarrier per slot buffer counts the bytes, an "empty" one the consumer
+// warps that are done with it.  The TMA_NW consumer warps
 // (one node per lane) never wait for one another: each waits only for its
 // data, and loads the next slot's neighbour x before it waits.  The
 // products are summed in the order of sym_residual, so results are
@@ -190,10 +231,9 @@ __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, long long ld, 
 // producer waits (bounded) for every copy it issued before the CTA exits.
 constexpr int TMA_NW = 8;                    // consumer warps
 constexpr int TMA_NB = 32 * TMA_NW;          // nodes per node block
-constexpr int TMA_S = 4;                     // slot buffers
-constexpr int TMA_ROW_OWN = TMA_NB;          // floats per own row
-constexpr int TMA_ROW_TR = TMA_NB + 4;       // floats per transposed row (aligned superset)
-constexpr int TMA_STAGE = 9 * TMA_ROW_OWN + 9 * TMA_ROW_TR;  // floats per stage
+constexpr int TMA_S = 3;                     // slot buffers
+constexpr int TMA_CH = 9 * 32;               // floats of one slot of one 32-node block
+constexpr int TMA_STAGE = (2 * TMA_NW + 1) * TMA_CH;  // floats per stage: 8 own + 9 transposed chunks
 constexpr int TMA_THREADS = 32 * (TMA_NW + 1);
 constexpr size_t TMA_SMEM = (size_t)TMA_S * TMA_STAGE * sizeof(float) + 2 * TMA_S * sizeof(unsigned long long);
 constexpr int MHFP_WAIT_TIMEOUT = 8;
@@ -233,8 +273,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 struct TmaSweep {
-  const float* up;   // symmetric half [14][9][ld] (+ padding)
-  long long ld;
+  const float* up;   // symmetric half, node-blocked (+ 8 zeroed blocks)
   const float* dinv; // [9][N]
   const float *b, *xin;
   float *xout, *d;
@@ -249,23 +288,30 @@ __device__ __forceinline__ int sym_shift(const Lat& L, int u) {
   return u == 0 ? 0 : dx + L.Lx * (dy + L.Ly * dz);
 }
 
-// issue the copies of stage (node block wb, slot u) into buf
+// issue the copies of stage (node block wb, slot u) into buf: own chunks
+// 0..7 (the zeroed padding covers the last node block), then the chunks
+// holding nodes p0 - s_u .. p0 - s_u + 255, first chunk index clo =
+// (p0 - s_u) >> 5; chunks before node 0 are not copied (never read)
 __device__ __forceinline__ void tma_issue(const TmaSweep& a, const Lat& L, int wb, int u, float* buf,
                                           unsigned long long* bar) {
   const long long p0 = (long long)wb * TMA_NB;
-  const unsigned own_bytes = TMA_ROW_OWN * 4;
-  const unsigned tr_bytes = TMA_ROW_TR * 4;
-  mbar_expect_tx(bar, u == 0 ? 9 * own_bytes : 9 * (own_bytes + tr_bytes));
-  const float* slot = a.up + (long long)u * 9 * a.ld;
-#pragma unroll 1
-  for (int e = 0; e < 9; ++e) bulk_to_smem(buf + e * TMA_ROW_OWN, slot + e * a.ld + p0, own_bytes, bar);
+  const long long c0 = p0 >> 5;
+  const unsigned ch_bytes = TMA_CH * 4;
+  long long clo = 0;
+  int first = 0, last = -1;
   if (u > 0) {
-    // rows of nodes p0 - s_u ..: from the 16-byte boundary at or below
-    const long long q0 = ((p0 - sym_shift(L, u)) >> 2) << 2;
-#pragma unroll 1
-    for (int e = 0; e < 9; ++e)
-      bulk_to_smem(buf + 9 * TMA_ROW_OWN + e * TMA_ROW_TR, slot + e * a.ld + q0, tr_bytes, bar);
+    const long long q0 = p0 - sym_shift(L, u);
+    clo = q0 >> 5;
+    last = (int)(((q0 + TMA_NB - 1) >> 5) - clo);
+    first = clo < 0 ? (int)(-clo) : 0;
   }
+  const int ntr = last >= first ? last - first + 1 : 0;
+  mbar_expect_tx(bar, (unsigned)(TMA_NW + ntr) * ch_bytes);
+#pragma unroll 1
+  for (int w = 0; w < TMA_NW; ++w) bulk_to_smem(buf + w * TMA_CH, a.up + ((c0 + w) * 126 + u * 9) * 32, ch_bytes, bar);
+#pragma unroll 1
+  for (int m = first; m <= last; ++m)
+    bulk_to_smem(buf + (TMA_NW + m) * TMA_CH, a.up + ((clo + m) * 126 + u * 9) * 32, ch_bytes, bar);
 }
 
 // x of node pc's neighbours in slot u (+s and -s; 0 outside the lattice)
@@ -345,28 +391,27 @@ __global__ void __launch_bounds__(TMA_THREADS, 3) k_sym_tma(Lat L, TmaSweep a) {
           break;
         }
         const float* st = stage + (size_t)buf * TMA_STAGE;
+        const float* own = st + warp * TMA_CH + lane;
         if (u == 0) {
 #pragma unroll
           for (int e = 0; e < 3; ++e)
-            r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * xp[0] + st[(3 * e + 1) * TMA_ROW_OWN + t] * xp[1] +
-                    st[(3 * e + 2) * TMA_ROW_OWN + t] * xp[2];
+            r[e] -= own[(3 * e) * 32] * xp[0] + own[(3 * e + 1) * 32] * xp[1] + own[(3 * e + 2) * 32] * xp[2];
         } else {
           int dx, dy, dz;
           St<ST_BOX1>::off(13 + u, dx, dy, dz);
           if (L.in(i + dx, j + dy, kk + dz)) {
 #pragma unroll
             for (int e = 0; e < 3; ++e)
-              r[e] -= st[(3 * e) * TMA_ROW_OWN + t] * xp[0] + st[(3 * e + 1) * TMA_ROW_OWN + t] * xp[1] +
-                      st[(3 * e + 2) * TMA_ROW_OWN + t] * xp[2];
+              r[e] -= own[(3 * e) * 32] * xp[0] + own[(3 * e + 1) * 32] * xp[1] + own[(3 * e + 2) * 32] * xp[2];
           }
           if (L.in(i - dx, j - dy, kk - dz)) {
-            const long long sh = p0 - sym_shift(L, u);
-            const int off = (int)(sh - ((sh >> 2) << 2)) + t;
-            const float* tr = st + 9 * TMA_ROW_OWN;
+            const long long su = sym_shift(L, u);
+            const long long q = p - su;  // >= 0 here
+            const int m = (int)((q >> 5) - ((p0 - su) >> 5));
+            const float* tr = st + (TMA_NW + m) * TMA_CH + (int)(q & 31);
 #pragma unroll
             for (int e = 0; e < 3; ++e)
-              r[e] -= tr[e * TMA_ROW_TR + off] * xm[0] + tr[(3 + e) * TMA_ROW_TR + off] * xm[1] +
-                      tr[(6 + e) * TMA_ROW_TR + off] * xm[2];
+              r[e] -= tr[e * 32] * xm[0] + tr[(3 + e) * 32] * xm[1] + tr[(6 + e) * 32] * xm[2];
           }
         }
         __syncwarp();
@@ -692,11 +737,13 @@ __global__ void k_cast_f32(long long n, const double* __restrict__ x, float* __r
 }
 
 // rows x n FP64 values (row stride n) to FP32 with row stride ld >= n
-__global__ void k_cast_f32_rows(int rows, long long n, const double* __restrict__ x, float* __restrict__ y,
-                                long long ld) {
+// rows 0..125 of the FP64 offset-major values ([row][n]) into the
+// node-blocked FP32 layout of the symmetric sweep
+__global__ void k_cast_f32_sym(long long n, const double* __restrict__ x, float* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= rows * n) return;
-  y[(i / n) * ld + i % n] = (float)x[i];
+  if (i >= 126 * n) return;
+  const long long row = i / n, q = i % n;
+  y[((q >> 5) * 126 + row) * 32 + (q & 31)] = (float)x[i];
 }
 
 // ------------------------------------------------------------------ setup
@@ -1635,7 +1682,7 @@ void launch_sym_tma(Ctx& c, const Level& L, bool cheb, const float* b, const flo
     MHFP_CUDA(cudaFuncSetAttribute(k_sym_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM));
     attr = true;
   }
-  TmaSweep a{L.symf, L.sym_ld, L.dinvf, b, xin, xout, d, cd, cr, c.d_flag};
+  TmaSweep a{L.symf, L.dinvf, b, xin, xout, d, cd, cr, c.d_flag};
   if (cheb) k_sym_tma<true><<<grid, TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a);
   else k_sym_tma<false><<<grid, TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a);
 }
@@ -1651,16 +1698,16 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
   if (mb == 4)
     launch_sym_tma(c, L, true, b, xin, xout, d, cd, cr);
   else if (mb == 5)
-    k_cheb_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+    k_cheb_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
                                                                         d, cd, cr);
   else if (mb == 7)
-    k_cheb_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+    k_cheb_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
                                                                         d, cd, cr);
   else if (mb == 8)
-    k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+    k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
                                                                         d, cd, cr);
   else
-    k_cheb_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, L.dinvf, b, xin, xout,
+    k_cheb_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
                                                                         d, cd, cr);
   MHFP_LAUNCH_CHECK();
 }
@@ -1670,13 +1717,13 @@ void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, fl
   if (mb == 4)
     launch_sym_tma(c, L, false, b, x, y, nullptr, 0.f, 0.f);
   else if (mb == 5)
-    k_resid_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
+    k_resid_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
   else if (mb == 7)
-    k_resid_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
+    k_resid_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
   else if (mb == 8)
-    k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
+    k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
   else
-    k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.sym_ld, L.symf, x, b, y);
+    k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
   MHFP_LAUNCH_CHECK();
 }
 
@@ -1902,13 +1949,12 @@ void make_fp32(Ctx& c, std::vector<Level>& H, bool fine_sym) {
     const size_t bs2 = (size_t)L.bs * L.bs;
     if (fine_sym && l == 0 && !L.dense_inv) {
       const long long N = L.A.N;
-      L.sym_ld = (N + 63) / 64 * 64;  // rows start on 256-byte boundaries
-      // zeroed tail: the bulk-copy sweep reads whole node blocks, up to one
-      // block past the last row
-      const size_t sym_elems = (size_t)126 * L.sym_ld + 2 * TMA_NB;
+      // node-blocked: ceil(N / 32) blocks of 126 x 32 values, plus 8 zeroed
+      // blocks that the bulk-copy sweep's last node block reads past the end
+      const size_t sym_elems = (size_t)((N + 31) / 32 + TMA_NW) * 126 * 32;
       L.symf = dalloc_n<float>(c, sym_elems);
       MHFP_CUDA(cudaMemsetAsync(L.symf, 0, sym_elems * sizeof(float), c.stream));
-      k_cast_f32_rows<<<grid_for(126 * N, 256), 256, 0, c.stream>>>(126, N, L.A.val + 13 * 9 * N, L.symf, L.sym_ld);
+      k_cast_f32_sym<<<grid_for(126 * N, 256), 256, 0, c.stream>>>(N, L.A.val + 13 * 9 * N, L.symf);
       MHFP_LAUNCH_CHECK();
     } else if (!L.faces) {
       L.valf = cast_copy(c, L.A.val, (size_t)L.A.noff() * bs2 * L.A.N);

@@ -247,8 +247,7 @@ struct Level {
   double* dense_inv = nullptr;
   // FP32 copies for the mixed-precision cycle (precision == 1)
   float *valf = nullptr, *dinvf = nullptr, *Pf = nullptr;
-  float* symf = nullptr;      // finest displacement level, FP32: symmetric half [14][9][sym_ld]
-  long long sym_ld = 0;       // row stride of symf: the node count rounded up to 64
+  float* symf = nullptr;      // finest displacement level, FP32: symmetric half, node blocks of 32 x 126 rows
   double sweep_us = 0.0;      // autotuner's time of one sweep under the chosen schedule
   float *xf = nullptr, *bf = nullptr, *rf = nullptr, *df = nullptr, *yf = nullptr;
 };

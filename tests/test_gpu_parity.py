@@ -535,7 +535,7 @@ def test_forced_schedules_match_oracle(precision, schedule, fine_blocks):
 def test_invalid_schedule_options_are_rejected():
     from paper_2002_09603_gb300 import MhfpError, Solver, default_options
     prob = mi.random_small(3, 3, 3, seed=2)
-    for field, value in (("schedule", 3), ("schedule", 32), ("fine_blocks", 7)):
+    for field, value in (("schedule", 3), ("schedule", 32), ("fine_blocks", 3), ("fine_blocks", 9)):
         opt = default_options()
         setattr(opt, field, value)
         s = Solver(prob)
