@@ -238,6 +238,14 @@ void mhfp_batch_destroy(mhfp_batch b);
 /* y = A_H x (Eq. stab_A, hybrid form), unscaled. */
 mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y);
 
+/* y = A_H x as the mixed-precision solve's Arnoldi step forms it
+ * (precision = 1 set-ups only, else MHFP_ERR_STATE): float-float arithmetic
+ * (every FP64 coefficient as a pair of FP32 words, exact products, sums
+ * carried as unevaluated pairs) from x rounded to FP32 (the Arnoldi step's
+ * vectors are FP32 values).  Relative error about 2^-44 of the sum of the
+ * |terms| of a row.  The handle's FP32 work vector is overwritten. */
+mhfp_status mhfp_apply_operator_ff(mhfp_handle h, const double* d_x, double* d_y);
+
 /* y = A_H^T x.  The condensed operator satisfies A_H^T = D A_H D^-1 with
  * D = diag(I, -I, -dt I) (A_pu = -A_up^T, A_pip = A_ppi^T; A_uu, A_pipi,
  * Abar_pp + A_stab symmetric; Section 2 and the remark on symmetrisation

@@ -21,7 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "out of memory",
 
 # every symbol include/mhfp.h declares
 EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhfp_setup_precond",
-           "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_operator_t", "mhfp_adjoint_solve",
+           "mhfp_build_rhs", "mhfp_solve", "mhfp_apply_operator", "mhfp_apply_operator_ff", "mhfp_apply_operator_t", "mhfp_adjoint_solve",
            "mhfp_grad_logk", "mhfp_misfit", "mhfp_adjoint_rhs", "mhfp_apply_precond_t", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
            "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_update_logk",
@@ -87,6 +87,7 @@ def load(path: str | None = None):
         "mhfp_build_rhs": (i, [vp, vp, d, vp]),
         "mhfp_solve": (i, [vp, vp, vp, d, C.POINTER(Stats)]),
         "mhfp_apply_operator": (i, [vp, vp, vp]),
+        "mhfp_apply_operator_ff": (i, [vp, vp, vp]),
         "mhfp_apply_precond": (i, [vp, vp, vp]),
         "mhfp_apply_operator_t": (i, [vp, vp, vp]),
         "mhfp_adjoint_solve": (i, [vp, vp, vp, d, C.POINTER(Stats)]),
@@ -242,6 +243,13 @@ class Solver:
     def apply_operator(self, x, out=None):
         out = self.empty() if out is None else out
         self._check(self.lib.mhfp_apply_operator(self.h, self._v(x, "x"), self._v(out, "out")))
+        return out
+
+    def apply_operator_ff(self, x, out=None):
+        """y = A_H x as the mixed-precision Arnoldi step forms it: u rows in
+        float-float arithmetic from x rounded to FP32 (mhfp_apply_operator_ff)."""
+        out = self.empty() if out is None else out
+        self._check(self.lib.mhfp_apply_operator_ff(self.h, self._v(x, "x"), self._v(out, "out")))
         return out
 
     def apply_operator_t(self, x, out=None):

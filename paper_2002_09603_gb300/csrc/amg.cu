@@ -106,7 +106,6 @@ __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ va
 // streams are one contiguous 16 KB range (sym_base).
 // UNR slots per loop iteration: 2 keeps two slots' loads in flight (the
 // 5-blocks-per-SM variant has the registers for it), 1 one slot.
-__device__ __forceinline__ long long sym_base(long long q) { return (q >> 5) * (126 * 32) + (q & 31); }
 // lanes of p's warp that hold a node (blocks are whole warps of 32 nodes)
 __device__ __forceinline__ unsigned sym_lanes(const Lat& L, long long p) {
   const long long left = L.N - (p & ~31LL);
@@ -743,7 +742,7 @@ __global__ void k_cast_f32_sym(long long n, const double* __restrict__ x, float*
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 126 * n) return;
   const long long row = i / n, q = i % n;
-  y[((q >> 5) * 126 + row) * 32 + (q & 31)] = (float)x[i];
+  y[sym_base(q) + 32 * row] = (float)x[i];
 }
 
 // ------------------------------------------------------------------ setup

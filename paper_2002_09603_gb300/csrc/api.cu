@@ -307,6 +307,17 @@ mhfp_status mhfp_apply_operator(mhfp_handle h, const double* d_x, double* d_y) {
   });
 }
 
+mhfp_status mhfp_apply_operator_ff(mhfp_handle h, const double* d_x, double* d_y) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.assembled || !c.prepared) throw Error{MHFP_ERR_STATE, "operator needs assemble + setup"};
+    if (c.opt.precision != 1 || c.opt.formulation != 0 || !c.auu_h)
+      throw Error{MHFP_ERR_STATE, "the float-float operator needs a precision = 1 set-up"};
+    if (!d_x || !d_y || d_x == d_y) throw Error{MHFP_ERR_ARG, "bad vectors"};
+    mhfp::narrow_to_f32(c, d_x, c.zf, c.n);
+    mhfp::apply_operator_arnoldi(c, d_x, c.zf, d_y, nullptr, false);
+  });
+}
+
 mhfp_status mhfp_apply_operator_t(mhfp_handle h, const double* d_x, double* d_y) {
   return guarded(h, [&](Ctx& c) {
     hybrid_only(c);

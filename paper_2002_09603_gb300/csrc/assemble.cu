@@ -697,6 +697,202 @@ __global__ void __launch_bounds__(256) k_btp_p(FaceTopo32 t, const double* __res
   tp[T] = vp[T] - su - dt * cq;
 }
 
+// ---------------------------------------------------------------- float-float
+// The Arnoldi step's operator rows for u in float-float arithmetic: every
+// FP64 coefficient a is held as a_h + a_l (two FP32 values, a_h = fl32(a),
+// a_l = fl32(a - a_h): 48 significand bits), every product a z is formed
+// exactly by an error-free transformation (TwoProduct with an FMA) and the
+// sum is kept as an unevaluated pair (TwoSum, Knuth), the rounding error of
+// each step carried in the low word.  z is the FP32 output of the
+// preconditioner, so its low word is zero.  The relative error of a row is
+// about 2^-44 of the sum of |terms|, against 2^-50 in FP64; FGMRES needs the
+// Arnoldi products only to well below its tolerance, and the stopping test
+// and restarts use the FP64 operator.  GB300 issues FP32 at about 60x its
+// FP64 rate, which moves this kernel off the FP64 pipe.
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float ah, float al, float z) {
+  const float pr = __fmul_rn(ah, z);
+  float e = __fmaf_rn(ah, z, -pr);  // ah z = pr + e exactly
+  e = __fmaf_rn(al, z, e);
+  const float t = __fadd_rn(sh, pr);
+  const float bp = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(pr, bp));  // sh + pr = t + err exactly
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// y_u = A_uu z_u + cup A_up z_p (then finish: D_s and b as in k_apply_u), one
+// thread per node and its three rows; A_uu's symmetric half (hi, lo) in the
+// node-blocked layout, the lower blocks read transposed from their owners.
+__global__ void __launch_bounds__(256, 4) k_apply_u_ff(Dims d, const float* __restrict__ uh,
+                                                       const float* __restrict__ ul, const float* __restrict__ aph,
+                                                       const float* __restrict__ apl, const float* __restrict__ z,
+                                                       double* __restrict__ y, const double* __restrict__ so,
+                                                       const double* __restrict__ bsub, float cup) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= d.nN) return;
+  const int Lx = d.nx + 1, Ly = d.ny + 1, Lz = d.nz + 1;
+  const int i = (int)(p % Lx), j = (int)((p / Lx) % Ly), k = (int)(p / ((long long)Lx * Ly));
+  auto in = [&](int a, int b, int c) { return a >= 0 && a < Lx && b >= 0 && b < Ly && c >= 0 && c < Lz; };
+  float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
+  const long long ob = sym_base(p);
+#pragma unroll 1
+  for (int u = 0; u <= 13; ++u) {
+    const int o = 13 + u, dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const long long s = dx + (long long)Lx * (dy + (long long)Ly * dz);
+    // own block A(p, p + e_u): row a, column c at entry 3 a + c
+    if (in(i + dx, j + dy, k + dz)) {
+      const long long q = p + s;
+      const float z0 = z[3 * q], z1 = z[3 * q + 1], z2 = z[3 * q + 2];
+      const float* h = uh + ob + u * 9 * 32;
+      const float* l = ul + ob + u * 9 * 32;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ff_mac(sh[a], sl[a], h[(3 * a) * 32], l[(3 * a) * 32], z0);
+        ff_mac(sh[a], sl[a], h[(3 * a + 1) * 32], l[(3 * a + 1) * 32], z1);
+        ff_mac(sh[a], sl[a], h[(3 * a + 2) * 32], l[(3 * a + 2) * 32], z2);
+      }
+    }
+    // lower block A(p, p - e_u) = A(p - e_u, p)^T: row a, column c at entry 3 c + a
+    if (u > 0 && in(i - dx, j - dy, k - dz)) {
+      const long long q = p - s;
+      const float z0 = z[3 * q], z1 = z[3 * q + 1], z2 = z[3 * q + 2];
+      const long long qb = sym_base(q) + u * 9 * 32;
+      const float* h = uh + qb;
+      const float* l = ul + qb;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ff_mac(sh[a], sl[a], h[a * 32], l[a * 32], z0);
+        ff_mac(sh[a], sl[a], h[(3 + a) * 32], l[(3 + a) * 32], z1);
+        ff_mac(sh[a], sl[a], h[(6 + a) * 32], l[(6 + a) * 32], z2);
+      }
+    }
+  }
+  // cup A_up z_p over the (up to) eight cells of the node
+  const float* zp = z + 3 * d.nN;
+  for (int cz = k - 1; cz <= k; ++cz) {
+    if (cz < 0 || cz >= d.nz) continue;
+    for (int cy = j - 1; cy <= j; ++cy) {
+      if (cy < 0 || cy >= d.ny) continue;
+      for (int cx = i - 1; cx <= i; ++cx) {
+        if (cx < 0 || cx >= d.nx) continue;
+        const long long T = cell_id(d, cx, cy, cz);
+        const int a = (i - cx) + 2 * (j - cy) + 4 * (k - cz);
+        const float zt = cup * zp[T];
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp)
+          ff_mac(sh[comp], sl[comp], aph[(long long)(3 * a + comp) * d.nT + T], apl[(long long)(3 * a + comp) * d.nT + T],
+                 zt);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long r = 3 * p + a;
+    y[r] = finish((double)sh[a] + (double)sl[a], r, so, bsub);
+  }
+}
+
+// p rows in float-float: cpu A_pu z_u + (Abar + A_stab) z_p + cpi A_ppi z_pi,
+// each of the three sums carried as a pair and combined in FP64
+__global__ void __launch_bounds__(256) k_apply_p_ff(FaceTopo32 t, const float* __restrict__ aph,
+                                                    const float* __restrict__ apl, const float* __restrict__ pdh,
+                                                    const float* __restrict__ pdl, const float* __restrict__ sth,
+                                                    const float* __restrict__ stl, const float* __restrict__ pph,
+                                                    const float* __restrict__ ppl, double cpi,
+                                                    const float* __restrict__ z, double* __restrict__ y,
+                                                    const double* __restrict__ so, double cpu) {
+  const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= t.nT) return;
+  const unsigned q = t.d_nx.div(T);
+  const int i = (int)(T - q * (unsigned)t.nx), k = (int)t.d_ny.div(q), j = (int)(q - (unsigned)k * (unsigned)t.ny);
+  const unsigned Lx = (unsigned)t.nx + 1, Ly = (unsigned)t.ny + 1;
+  const unsigned nU = 3 * Lx * Ly * ((unsigned)t.nz + 1);
+  float uh = 0.f, ul = 0.f;  // A_up^T z_u (the row is its negative)
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const unsigned n = (unsigned)(i + (a & 1)) + Lx * ((unsigned)(j + ((a >> 1) & 1)) + Ly * (unsigned)(k + (a >> 2)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      ff_mac(uh, ul, aph[(unsigned)(3 * a + c) * t.nT + T], apl[(unsigned)(3 * a + c) * t.nT + T], z[3 * n + c]);
+  }
+  const float* zp = z + nU;
+  float ph = 0.f, pl = 0.f;
+  ff_mac(ph, pl, pdh[T], pdl[T], zp[T]);
+  const unsigned nb[3] = {t.cell(i ^ 1, j, k), t.cell(i, j ^ 1, k), t.cell(i, j, k ^ 1)};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float ch = sth[d * t.nT + T];
+    if (ch != 0.f) ff_mac(ph, pl, -ch, -stl[d * t.nT + T], zp[nb[d]]);
+  }
+  const float* zpi = zp + t.nT;
+  float ch = 0.f, cl = 0.f;
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) ff_mac(ch, cl, pph[lf * t.nT + T], ppl[lf * t.nT + T], zpi[t.face(i, j, k, lf)]);
+  const double s = -cpu * ((double)uh + (double)ul) + ((double)ph + (double)pl) + cpi * ((double)ch + (double)cl);
+  const long long r = (long long)nU + T;
+  y[r] = finish(s, r, so, nullptr);
+}
+
+// pi rows in float-float: cpp A_pip z_p + A_pipi z_pi (ELL, 11 slots)
+__global__ void __launch_bounds__(256) k_apply_pi_ff(FaceTopo32 t, long long nU, const float* __restrict__ pph,
+                                                     const float* __restrict__ ppl, const float* __restrict__ eh,
+                                                     const float* __restrict__ el, const float* __restrict__ z,
+                                                     double* __restrict__ y, const double* __restrict__ so,
+                                                     double cpp) {
+  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= t.nF) return;
+  int c[2][3], lf[2];
+  bool ok[2];
+  t.cells(f, c, ok, lf);
+  const float* zp = z + nU;
+  const float* zpi = zp + t.nT;
+  float ph = 0.f, pl = 0.f;
+  for (int q = 0; q < 2; ++q)
+    if (ok[q]) {
+      const unsigned T = t.cell(c[q][0], c[q][1], c[q][2]);
+      ff_mac(ph, pl, pph[(long long)lf[q] * t.nT + T], ppl[(long long)lf[q] * t.nT + T], zp[T]);
+    }
+  unsigned col[11];
+  t.ell_cols(f, col);
+  float ah = 0.f, al = 0.f;
+#pragma unroll
+  for (int q = 0; q < 11; ++q) ff_mac(ah, al, eh[(long long)q * t.nF + f], el[(long long)q * t.nF + f], zpi[col[q]]);
+  const double s = cpp * ((double)ph + (double)pl) + ((double)ah + (double)al);
+  const long long r = nU + t.nT + f;
+  y[r] = finish(s, r, so, nullptr);
+}
+
+// the p block's diagonal Abar + sum of the three stabilization coefficients
+__global__ void k_pdiag(long long nT, const double* __restrict__ Abar, const double* __restrict__ stabc,
+                        double* __restrict__ out) {
+  const long long T = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T < nT) out[T] = Abar[T] + (stabc[T] + stabc[nT + T] + stabc[2 * nT + T]);
+}
+__global__ void k_split(long long n, const double* __restrict__ x, float* __restrict__ h, float* __restrict__ l) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const float vh = __double2float_rn(x[t]);
+  h[t] = vh;
+  l[t] = __double2float_rn(x[t] - (double)vh);
+}
+
+// FP64 rows into the node-blocked float-float layout (hi = fl32(v), lo =
+// fl32(v - hi)); and the lo words of a block array whose hi words exist
+__global__ void k_split_sym(long long n, const double* __restrict__ x, float* __restrict__ h, float* __restrict__ l) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 126 * n) return;
+  const long long row = t / n, q = t % n;
+  const double v = x[t];
+  const float vh = __double2float_rn(v);
+  h[sym_base(q) + 32 * row] = vh;
+  l[sym_base(q) + 32 * row] = __double2float_rn(v - (double)vh);
+}
+__global__ void k_split_lo(long long n, const double* __restrict__ x, const float* __restrict__ h,
+                           float* __restrict__ l) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) l[t] = __double2float_rn(x[t] - (double)h[t]);
+}
+
 // preconditioner pieces: z_p = B~^-1 (v_p - dt A_ppi z_pi), t_u = v_u - A_up z_p
 // (FP64, or FP32 in the mixed-precision preconditioner)
 template <typename R>
@@ -1325,6 +1521,79 @@ void make_fp32_blocks(Ctx& c) {
   cast(c.Aupf, c.Aup, 24 * c.nT);
   if (!c.tf) c.tf = dalloc_n<float>(c, c.n);
   if (!c.zf) c.zf = dalloc_n<float>(c, c.n);
+  // float-float A_uu (symmetric half) and A_up for the Arnoldi step (A_uu and
+  // A_up do not depend on the permeability: built once)
+  if (!c.auu_h) {
+    const long long N = c.nN;
+    const size_t elems = (size_t)((N + 31) / 32) * 126 * 32;
+    c.auu_h = dalloc_n<float>(c, elems);
+    c.auu_l = dalloc_n<float>(c, elems);
+    MHFP_CUDA(cudaMemsetAsync(c.auu_h, 0, elems * sizeof(float), c.stream));
+    MHFP_CUDA(cudaMemsetAsync(c.auu_l, 0, elems * sizeof(float), c.stream));
+    k_split_sym<<<grid_for(126 * N, 256), 256, 0, c.stream>>>(N, c.Auu.val + 13 * 9 * N, c.auu_h, c.auu_l);
+    MHFP_LAUNCH_CHECK();
+    c.aup_l = dalloc_n<float>(c, 24 * c.nT);
+    k_split_lo<<<grid_for(24 * c.nT, 256), 256, 0, c.stream>>>(24 * c.nT, c.Aup, c.Aupf, c.aup_l);
+    MHFP_LAUNCH_CHECK();
+    c.pd_h = dalloc_n<float>(c, c.nT);
+    c.pd_l = dalloc_n<float>(c, c.nT);
+    c.st_h = dalloc_n<float>(c, 3 * c.nT);
+    c.st_l = dalloc_n<float>(c, 3 * c.nT);
+    c.appi_h = dalloc_n<float>(c, 6 * c.nT);
+    c.appi_l = dalloc_n<float>(c, 6 * c.nT);
+    c.apipi_h = dalloc_n<float>(c, 11 * c.nF);
+    c.apipi_l = dalloc_n<float>(c, 11 * c.nF);
+  }
+  // the permeability-dependent blocks of the p and pi rows, every call
+  double* pd = c.tmp_pd ? c.tmp_pd : (c.tmp_pd = dalloc_n<double>(c, c.nT));
+  k_pdiag<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(c.nT, c.Abar, c.stabc, pd);
+  MHFP_LAUNCH_CHECK();
+  auto split = [&](const double* x, float* h, float* l, long long n) {
+    k_split<<<grid_for(n, 256), 256, 0, c.stream>>>(n, x, h, l);
+    MHFP_LAUNCH_CHECK();
+  };
+  split(pd, c.pd_h, c.pd_l, c.nT);
+  split(c.stabc, c.st_h, c.st_l, 3 * c.nT);
+  split(c.ApPi, c.appi_h, c.appi_l, 6 * c.nT);
+  split(c.Apipi, c.apipi_h, c.apipi_l, 11 * c.nF);
+}
+
+namespace {
+__global__ void k_narrow_f32(long long n, const double* __restrict__ x, float* __restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = __double2float_rn(x[t]);
+}
+}  // namespace
+void narrow_to_f32(Ctx& c, const double* x, float* y, long long n) {
+  k_narrow_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, x, y);
+  MHFP_LAUNCH_CHECK();
+}
+
+void apply_operator_arnoldi(Ctx& c, const double* z, const float* zf, double* y, const double* so, bool transpose) {
+  if (c.opt.precision != 1 || c.opt.formulation != 0 || !c.auu_h) {
+    apply_operator(c, z, y, so, nullptr, transpose);
+    return;
+  }
+  const Dims d = dims_of(c);
+  timing_begin(c, 1);
+  k_apply_u_ff<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.auu_h, c.auu_l, c.Aupf, c.aup_l, zf, y, so, nullptr,
+                                                           transpose ? -1.f : 1.f);
+  MHFP_LAUNCH_CHECK();
+  k_apply_p_ff<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aupf, c.aup_l, c.pd_h, c.pd_l, c.st_h, c.st_l,
+                                                          c.appi_h, c.appi_l, transpose ? 1.0 : c.dt, zf, y, so,
+                                                          transpose ? -1.0 : 1.0);
+  MHFP_LAUNCH_CHECK();
+  k_apply_pi_ff<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(topo32(c), 3 * c.nN, c.appi_h, c.appi_l, c.apipi_h,
+                                                           c.apipi_l, zf, y, so, transpose ? c.dt : 1.0);
+  MHFP_LAUNCH_CHECK();
+  // algorithmic bytes, every coefficient a hi + lo pair (8 B): A_uu's
+  // symmetric half (126 per node) and A_up (24 per cell) by the u rows, A_up
+  // again, the p block (1 + 3) and A_ppi (6) by the p rows, A_ppi (6 per
+  // cell) and A_pipi (11 per face) by the pi rows; z read in FP32, y written
+  // in FP64
+  const double bytes = 8.0 * (126.0 * c.nN + (24.0 + 24.0 + 4.0 + 6.0 + 6.0) * c.nT + 11.0 * c.nF) + 4.0 * c.n +
+                       8.0 * c.n;
+  timing_end(c, 1, bytes);
 }
 
 }  // namespace mhfp

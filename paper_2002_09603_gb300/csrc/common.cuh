@@ -12,6 +12,12 @@
 #include "../../include/mhfp.h"
 
 namespace mhfp {
+// Node-blocked layout of a finest-level symmetric half (the diagonal 3x3
+// block and the 13 blocks of the neighbours after it in stencil order):
+// nodes in blocks of 32, each block its 126 rows (slot u, entry e: row
+// 9 u + e) of 32 values; value (row, q) at sym_base(q) + 32 row.
+__host__ __device__ inline long long sym_base(long long q) { return (q >> 5) * (126 * 32) + (q & 31); }
+
 
 // ------------------------------------------------------------ error handling
 struct Error {
@@ -346,6 +352,16 @@ struct Ctx {
   // FP32 copies used by the mixed-precision preconditioner
   float *Cpif = nullptr, *pwf = nullptr, *ApPif = nullptr, *btildef = nullptr, *Aupf = nullptr;
   float *tf = nullptr, *zf = nullptr;
+  // float-float (hi + lo FP32 pairs) copies for the Arnoldi step's operator
+  // in the mixed-precision solve: A_uu's symmetric half in the node-blocked
+  // layout (sym_base) and the lo parts of A_up (the hi parts are Aupf)
+  float *auu_h = nullptr, *auu_l = nullptr, *aup_l = nullptr;
+  // and for its p and pi rows (recomputed after a permeability update): the
+  // p block's diagonal Abar + sum of the stabilization coefficients, the
+  // stabilization coefficients, A_ppi and A_pipi (ELL), each hi and lo
+  float *pd_h = nullptr, *pd_l = nullptr, *st_h = nullptr, *st_l = nullptr, *appi_h = nullptr, *appi_l = nullptr,
+        *apipi_h = nullptr, *apipi_l = nullptr;
+  double* tmp_pd = nullptr;
 
   // Krylov workspace
   int m_alloc = 0;
@@ -409,6 +425,11 @@ void build_preconditioner_blocks(Ctx& c);
 void build_rhs(Ctx& c, const double* xprev, double scale, double* rhs);
 void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out, const double* bsub,
                     bool transpose = false);
+// the Arnoldi step's w = D_s A z: with precision = 1 the u rows in float-float
+// arithmetic from the FP32 preconditioner output zf (z = zf exactly)
+void apply_operator_arnoldi(Ctx& c, const double* z, const float* zf, double* y, const double* scale_out,
+                            bool transpose);
+void narrow_to_f32(Ctx& c, const double* x, float* y, long long n);  // y = fl32(x)
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp);
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu);
 void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp);

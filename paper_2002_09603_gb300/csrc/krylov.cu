@@ -456,7 +456,7 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
     vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
     apply_precond(c, c.t, zj, transpose);
   }
-  apply_operator(c, zj, c.w, c.ds, nullptr, transpose);  // w = D_s A z_j
+  apply_operator_arnoldi(c, zj, c.zf, c.w, c.ds, transpose);  // w = D_s A z_j
   timing_begin(c, 2);
   // classical Gram-Schmidt with the DGKS reorthogonalisation test:
   // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the

@@ -57,7 +57,7 @@ def test_check_vec_accepts_and_rejects():
         _lib.check_vec(_good(7), 7, torch.device("meta"), "v")
 
 
-@pytest.mark.parametrize("call", ["apply_operator", "apply_operator_t", "apply_precond", "apply_precond_t"])
+@pytest.mark.parametrize("call", ["apply_operator", "apply_operator_ff", "apply_operator_t", "apply_precond", "apply_precond_t"])
 def test_operator_wrappers_validate_before_calling(call):
     s = _solver()
     getattr(s, call)(_good(s.n), out=_good(s.n))

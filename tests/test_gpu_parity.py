@@ -625,3 +625,39 @@ def test_chebyshev_degree_autotuner():
     with pytest.raises(MhfpError):
         s.setup_precond(opt)
     s.close()
+
+
+@pytest.mark.parametrize("dims,smooth", [((16, 16, 16), False), ((13, 9, 21), False), ((16, 16, 16), True)])
+def test_float_float_arnoldi_operator(dims, smooth):
+    """The mixed-precision Arnoldi step's operator (float-float arithmetic
+    from z in FP32): every row within 2^-40 of the sum of its |terms| (|A| |z|
+    row by row, from the oracle's matrix: the float-float bound is about
+    2^-44 of it), also for a smooth z whose displacement rows cancel."""
+    from paper_2002_09603_gb300 import Solver, default_options
+    prob = mi.random_small(*dims, seed=41, jitter=0.1)
+    B = oracle.assemble(prob)
+    A = system.system_matrix(B)
+    opt = default_options()
+    opt.precision = 1
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    rng = np.random.default_rng(12)
+    nU, nP, nPi = B.sizes
+    if smooth:
+        xyz = B.mesh.coords
+        zu = np.stack([np.sin(xyz[:, 0] + 2 * xyz[:, 1]), np.cos(xyz[:, 2]), xyz[:, 0] * xyz[:, 1]], axis=1).ravel()
+        z = np.concatenate([zu, np.ones(nP), np.ones(nPi)])
+    else:
+        z = rng.standard_normal(s.n)
+    z = z.astype(np.float32).astype(np.float64)  # the Arnoldi step's z is FP32-exact
+    zt = torch.from_numpy(z).cuda()
+    yff = s.apply_operator_ff(zt).cpu().numpy()
+    y64 = s.apply_operator(zt).cpu().numpy()
+    ref = A @ z
+    bound = 2.0 ** -40 * (abs(A) @ np.abs(z))
+    err = np.abs(yff - ref)
+    assert np.all(err <= bound + 1e-300), [(o, n, float((err[o:o + n] / (bound[o:o + n] + 1e-300)).max()))
+                                           for o, n in ((0, nU), (nU, nP), (nU + nP, nPi))]
+    assert np.abs(y64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    s.close()
