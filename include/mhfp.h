@@ -338,12 +338,13 @@ mhfp_status mhfp_sizes(mhfp_handle h, long long* n_u, long long* n_p, long long*
 
 /* Per-kernel-class device time accumulated with CUDA events on the
  * handle's stream while timing is enabled (kernel classes: 0 = Chebyshev
- * sweeps of the finest displacement level; 1 = operator apply; 2 =
+ * sweeps of the finest displacement level; 1 = FP64 operator apply; 2 =
  * Gram-Schmidt; 3 = preconditioner apply M^-1 with its precision
  * conversions; 4 = displacement V-cycle; 5 = interface-pressure V-cycle;
- * classes 4, 5 and 0 lie inside 3).  bytes_per_launch is the algorithmic
- * traffic of classes 0-2 (matrix values, inverse diagonal blocks and vectors
- * touched once) and 0 for classes 3-5.
+ * classes 4, 5 and 0 lie inside 3; 6 = the float-float operator of the
+ * mixed-precision Arnoldi step).  bytes_per_launch is the algorithmic
+ * traffic of classes 0-2 and 6 (matrix values, inverse diagonal blocks and
+ * vectors touched once) and 0 for classes 3-5.
  * mhfp_timing(h, 1) resets and enables, mhfp_timing(h, 0) disables. */
 mhfp_status mhfp_timing(mhfp_handle h, int enable);
 mhfp_status mhfp_timing_read(mhfp_handle h, int kernel_class, long long* launches,

@@ -269,7 +269,7 @@ struct TimedPair {
 // Timed classes: 0 finest displacement Chebyshev sweeps, 1 operator apply,
 // 2 Gram-Schmidt, 3 preconditioner apply M^-1, 4 displacement V-cycle,
 // 5 interface-pressure V-cycle
-constexpr int TIMING_CLASSES = 6;
+constexpr int TIMING_CLASSES = 7;
 
 // FGMRES control block kept in device memory by the device-driven solve
 struct DevCtl {

@@ -407,7 +407,10 @@ def test_invalid_reorth_is_rejected():
 def test_timing_classes_nest():
     """With timing on, every class records one interval per event: the
     preconditioner apply (3) holds both V-cycles (4, 5), and the displacement
-    V-cycle holds the timed finest-level sweeps (0); class 6 does not exist."""
+    V-cycle holds the timed finest-level sweeps (0); the Arnoldi step's
+    float-float operator (6) runs once per iteration, the FP64 operator (1)
+    for the residual of each restart cycle and at exit; class 7 does not
+    exist."""
     from paper_2002_09603_gb300 import MhfpError, Solver, default_options
     opt = default_options()
     opt.precision = 1
@@ -418,11 +421,12 @@ def test_timing_classes_nest():
     b = s.build_rhs()
     s.timing(True)
     x, st = s.solve(b, tol=1e-8)
-    r = [s.timing_read(k) for k in range(6)]
+    r = [s.timing_read(k) for k in range(7)]
     s.timing(False)
     its = st["iterations"]
     assert r[3]["launches"] == its and r[4]["launches"] == its and r[5]["launches"] == its
-    assert r[1]["launches"] >= its and r[2]["launches"] == its
+    assert r[6]["launches"] == its and r[2]["launches"] == its
+    assert 1 <= r[1]["launches"] <= st["restarts"] + 3
     # Chebyshev(2): the first pre-smoothing sweep starts from zero and is not
     # a stencil sweep; the second and both post-smoothing sweeps are timed
     assert r[0]["launches"] == 3 * its
@@ -430,7 +434,7 @@ def test_timing_classes_nest():
     assert r[3]["total_ms"] >= r[4]["total_ms"] + r[5]["total_ms"]
     assert r[4]["total_ms"] >= r[0]["total_ms"]
     with pytest.raises(MhfpError):
-        s.timing_read(6)
+        s.timing_read(7)
     s.close()
 
 
