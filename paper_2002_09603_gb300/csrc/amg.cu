@@ -1388,6 +1388,12 @@ void finish_level(Ctx& c, Level& L) {
   L.lmax = 1.1 * spectral_radius(c, L);
 }
 
+// the transfer kernels index the prolongator [slot][entry][fine point] in
+// 32-bit unsigned arithmetic: refuse levels where that would wrap
+void check_transfer_index(long long rows, long long n) {
+  if (rows * n >= (1LL << 32)) throw Error{MHFP_ERR_ARG, "level too large for 32-bit transfer indexing"};
+}
+
 // one smoothed-aggregation coarsening step of a lattice level.  With
 // `into` (a permeability update), the next level already exists and its
 // values, its activity mask and L's prolongator are recomputed in place,
@@ -1410,6 +1416,7 @@ Level coarsen(Ctx& c, Level& L, Level* into = nullptr) {
   const Lat F = lat_of(A), Cc = lat_of(Cl.A);
   const int ns = p_slots(R), nq = q_slots(R);
   const int bs2 = L.bs * L.bs;
+  check_transfer_index((long long)ns * ns * ns * bs2, F.N);
   if (!L.P) L.P = dalloc_n<double>(c, (size_t)ns * ns * ns * bs2 * F.N);
   if (!Cl.active) Cl.active = dalloc_n<unsigned char>(c, Cl.n);
   if (!Cl.A.val) Cl.A.val = dalloc_n<double>(c, (size_t)Cl.A.noff() * bs2 * Cc.N);
@@ -1533,6 +1540,7 @@ void build_u_rbm(Ctx& c) {
     double* Pt = dalloc_n<double>(c, (size_t)pb * F.N);
     double* Nc = dalloc_n<double>(c, (size_t)RBM_K * RBM_K * Cc.N);
     Cl.active = dalloc_n<unsigned char>(c, Cl.n);
+    check_transfer_index((long long)ns * ns * ns * pb, F.N);
     L.P = dalloc_n<double>(c, (size_t)ns * ns * ns * pb * F.N);
     Cl.A.val = dalloc_n<double>(c, (size_t)27 * RBM_K * RBM_K * Cc.N);
     MHFP_CUDA(cudaMemsetAsync(Pt, 0, (size_t)pb * F.N * sizeof(double), c.stream));
