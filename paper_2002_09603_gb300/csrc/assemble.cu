@@ -1574,7 +1574,7 @@ void narrow_to_f32(Ctx& c, const double* x, float* y, long long n) {
 }
 
 void apply_operator_arnoldi(Ctx& c, const double* z, const float* zf, double* y, const double* so, bool transpose) {
-  if (c.opt.precision != 1 || c.opt.formulation != 0 || !c.auu_h) {
+  if (!ff_krylov(c)) {
     apply_operator(c, z, y, so, nullptr, transpose);
     return;
   }

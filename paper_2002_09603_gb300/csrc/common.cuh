@@ -366,6 +366,7 @@ struct Ctx {
   // Krylov workspace
   int m_alloc = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *tmp = nullptr;
+  float* Zf = nullptr;  // the mixed-precision solve's Z: the preconditioner outputs are FP32 values
   double *h = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
          *partials = nullptr, *scal = nullptr;
   int* dflag = nullptr;  // DGKS decision of the current Arnoldi step
@@ -430,6 +431,8 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* scale_out,
 void apply_operator_arnoldi(Ctx& c, const double* z, const float* zf, double* y, const double* scale_out,
                             bool transpose);
 void narrow_to_f32(Ctx& c, const double* x, float* y, long long n);  // y = fl32(x)
+// the mixed-precision solve: FP32 preconditioner, float-float Arnoldi operator
+inline bool ff_krylov(const Ctx& c) { return c.opt.precision == 1 && c.opt.formulation == 0 && c.auu_h != nullptr; }
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp);
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu);
 void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp);

@@ -204,6 +204,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_norm_partials(long long n, cons
 }
 
 // x += Z y
+// x += Z y with an FP32 Z (every product exact in FP64, the same sums as
+// with the widened columns)
+__global__ void k_gemv_add_f(long long n, const float* __restrict__ Z, int ncols, const double* __restrict__ y,
+                             double* __restrict__ x) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double s = x[r];
+  for (int c = 0; c < ncols; ++c) s += (double)Z[(long long)c * n + r] * y[c];
+  x[r] = s;
+}
+
 __global__ void k_gemv_add(long long n, const double* __restrict__ Z, int ncols, const double* __restrict__ y,
                            double* __restrict__ x) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,7 +342,6 @@ void ensure_workspace(Ctx& c) {
   if (c.m_alloc == m) return;
   if (c.m_alloc != 0) throw Error{MHFP_ERR_STATE, "restart length cannot change after the first solve"};
   c.V = dalloc_n<double>(c, (size_t)(m + 1) * c.n);
-  c.Z = dalloc_n<double>(c, (size_t)m * c.n);
   c.w = dalloc_n<double>(c, c.n);
   c.t = dalloc_n<double>(c, c.n);
   c.tmp = dalloc_n<double>(c, c.n);
@@ -347,6 +357,18 @@ void ensure_workspace(Ctx& c) {
   c.dflag = dalloc_n<int>(c, 4);
   if (!c.host_scal) MHFP_CUDA(cudaMallocHost(&c.host_scal, 8 * sizeof(double)));
   c.m_alloc = m;
+}
+
+// the preconditioned basis Z in the form the set-up asks for (FP32 in the
+// mixed-precision solve, FP64 otherwise), allocated on first use
+void ensure_zbasis(Ctx& c) {
+  ensure_workspace(c);
+  const size_t nz = (size_t)c.opt.restart * c.n;
+  if (ff_krylov(c)) {
+    if (!c.Zf) c.Zf = dalloc_n<float>(c, nz);
+  } else if (!c.Z) {
+    c.Z = dalloc_n<double>(c, nz);
+  }
 }
 
 double device_norm2(Ctx& c, const double* x, long long n) {
@@ -396,16 +418,22 @@ void precond_blocks(Ctx& c, const T* t, T* z, T* work_u, T* work_pi, bool transp
   }
 }
 
-// z = M^-1 (v .* mul) (or M^-T) with the FP32 V-cycles and Schur steps; v, z FP64
-void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z, bool transpose) {
+// z = M^-1 (v .* mul) (or M^-T) with the FP32 V-cycles and Schur steps; v
+// FP64; the FP32 result in zf_out (default: the handle's FP32 work vector)
+// and, when z is given, widened into z
+void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z, bool transpose,
+                         float* zf_out = nullptr) {
   const long long n = c.n;
+  float* zo = zf_out ? zf_out : c.zf;
   timing_begin(c, 3);
   k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, mul, c.tf);
   MHFP_LAUNCH_CHECK();
   // level-0 right-hand-side buffers are free at the finest levels
-  precond_blocks<float>(c, c.tf, c.zf, c.hu[0].bf, c.hpi[0].bf, transpose);
-  k_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.zf, z);
-  MHFP_LAUNCH_CHECK();
+  precond_blocks<float>(c, c.tf, zo, c.hu[0].bf, c.hpi[0].bf, transpose);
+  if (z) {
+    k_to_f64<<<grid_for(n, 256), 256, 0, c.stream>>>(n, zo, z);
+    MHFP_LAUNCH_CHECK();
+  }
   timing_end(c, 3, 0.0);
 }
 
@@ -449,14 +477,22 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
   const int m = c.opt.restart;
   const long long n = c.n;
   double* vj = c.V + (long long)j * n;
-  double* zj = c.Z + (long long)j * n;
-  if (c.opt.precision == 1) {
-    apply_precond_mixed(c, vj, c.ds_inv, zj, transpose);  // unscale into the FP32 preconditioner
+  if (ff_krylov(c)) {
+    // z_j stays in FP32 (it is the FP32 preconditioner's output): the
+    // float-float operator reads it, and x += Z y widens it
+    float* zfj = c.Zf + (long long)j * n;
+    apply_precond_mixed(c, vj, c.ds_inv, nullptr, transpose, zfj);  // unscale into the FP32 preconditioner
+    apply_operator_arnoldi(c, nullptr, zfj, c.w, c.ds, transpose);  // w = D_s A z_j
   } else {
-    vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
-    apply_precond(c, c.t, zj, transpose);
+    double* zj = c.Z + (long long)j * n;
+    if (c.opt.precision == 1) {
+      apply_precond_mixed(c, vj, c.ds_inv, zj, transpose);  // unscale into the FP32 preconditioner
+    } else {
+      vec_scale(c, vj, c.ds_inv, false, c.t, n);  // unscale into the preconditioner
+      apply_precond(c, c.t, zj, transpose);
+    }
+    apply_operator_arnoldi(c, zj, c.zf, c.w, c.ds, transpose);  // w = D_s A z_j
   }
-  apply_operator_arnoldi(c, zj, c.zf, c.w, c.ds, transpose);  // w = D_s A z_j
   timing_begin(c, 2);
   // classical Gram-Schmidt with the DGKS reorthogonalisation test:
   // h1 = V^T w and ||w||^2; w -= V h1 and ||w||^2; then, only if the
@@ -570,7 +606,7 @@ void fgmres_begin(Ctx& c, FgState& f, const double* b, double* x, double tol, bo
   f.tol = tol;
   f.transpose = transpose;
   f.t0 = std::chrono::steady_clock::now();
-  ensure_workspace(c);
+  ensure_zbasis(c);
   MHFP_CUDA(cudaMemsetAsync(x, 0, c.n * sizeof(double), c.stream));
   vec_scale(c, b, c.ds, false, c.tmp, c.n);
   norm2_dev(c, c.tmp, c.n, c.scal + 4);
@@ -639,7 +675,10 @@ void fgmres_advance(Ctx& c, FgState& f) {
       if (resid <= f.tol * f.bnorm || f.total >= c.opt.maxit || k == m) {
         k_lsq<<<1, 32, 0, c.stream>>>(k, m, c.H, c.g, c.yv);
         MHFP_LAUNCH_CHECK();
-        k_gemv_add<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, k, c.yv, f.x);
+        if (ff_krylov(c))
+          k_gemv_add_f<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Zf, k, c.yv, f.x);
+        else
+          k_gemv_add<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, k, c.yv, f.x);
         MHFP_LAUNCH_CHECK();
         ++f.cycles;
         enqueue_residual(c, f);
@@ -758,13 +797,14 @@ __global__ void k_lsq_dev(const DevCtl* __restrict__ ctl, const double* __restri
   }
 }
 
-__global__ void k_gemv_add_dev(long long n, const double* __restrict__ Z, const DevCtl* __restrict__ ctl,
+template <typename ZT>
+__global__ void k_gemv_add_dev(long long n, const ZT* __restrict__ Z, const DevCtl* __restrict__ ctl,
                                const double* __restrict__ y, double* __restrict__ x) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int k = ctl->k;
   double s = x[r];
-  for (int c = 0; c < k; ++c) s += Z[(long long)c * n + r] * y[c];
+  for (int c = 0; c < k; ++c) s += (double)Z[(long long)c * n + r] * y[c];
   x[r] = s;
 }
 
@@ -913,7 +953,10 @@ cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool trans
   b = add_child(W, b, capture_piece(c, [&] {
     k_lsq_dev<<<1, 32, 0, c.stream>>>(ctl, c.H, c.g, c.yv);
     MHFP_LAUNCH_CHECK();
-    k_gemv_add_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, ctl, c.yv, c.xcur);
+    if (ff_krylov(c))
+      k_gemv_add_dev<float><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Zf, ctl, c.yv, c.xcur);
+    else
+      k_gemv_add_dev<double><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, ctl, c.yv, c.xcur);
     MHFP_LAUNCH_CHECK();
     k_cycle_end<<<1, 32, 0, c.stream>>>(ctl);
     MHFP_LAUNCH_CHECK();
@@ -936,7 +979,7 @@ cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool trans
 
 // the handle's device-side solve state (control block, current b and x)
 void ensure_solve_state(Ctx& c) {
-  ensure_workspace(c);
+  ensure_zbasis(c);
   if (!c.ctl) {
     c.ctl = dalloc_n<DevCtl>(c, 1);
     MHFP_CUDA(cudaMallocHost(&c.host_ctl, sizeof(DevCtl)));

@@ -61,6 +61,11 @@ def test_operator_rows_full_size(full):
         assert np.abs(y[o:o + n] - ref[o:o + n]).max() <= 1e-12 * np.abs(ref[o:o + n]).max()
         o += n
     assert np.allclose(s.scalings()[1].cpu().numpy(), ds, rtol=1e-12, atol=0)
+    # the float-float Arnoldi operator of the bench handle, from z in FP32:
+    # every row within 2^-40 of the sum of its |terms|
+    z = x.astype(np.float32).astype(np.float64)
+    yff = s.apply_operator_ff(torch.from_numpy(z).cuda()).cpu().numpy()
+    assert np.all(np.abs(yff - A @ z) <= 2.0 ** -40 * (abs(A) @ np.abs(z)) + 1e-300)
 
 
 def _bench_options(precision, restart=12):
@@ -176,7 +181,8 @@ def test_layered_jittered_128_cubed():
     six decades, E over two, S_eps = 0, dt = 0.1 s) at full size, in the
     bench's launch configuration.  Against the oracle on 8^3-cell windows
     (every complete row): A_H x for a seeded x and the right-hand side at
-    1e-12, D_s at 1e-12 where the row's B~_p and C~_pi diagonal are local to
+    1e-12, the float-float Arnoldi operator within 2^-40 of each row's sum of
+    |terms|, D_s at 1e-12 where the row's B~_p and C~_pi diagonal are local to
     the window, and the residual b - A x of the mixed and FP64 solutions
     (relative to the size of its terms).  Properties at any size: both forms
     reach 1e-8, the no-allocation residual agrees, they agree with each
@@ -212,6 +218,11 @@ def test_layered_jittered_128_cubed():
         xx = x.cpu().numpy()
         if precision == 1:
             y = s.apply_operator(torch.from_numpy(xseed).cuda()).cpu().numpy()
+            zseed = xseed.astype(np.float32).astype(np.float64)
+            yff = s.apply_operator_ff(torch.from_numpy(zseed).cuda()).cpu().numpy()
+            for sub, Bw, Aw, rows, ok, dsw, bw in wins:
+                err = np.abs(yff[rows] - Aw @ zseed[rows])[ok]
+                assert np.all(err <= 2.0 ** -40 * (abs(Aw) @ np.abs(zseed[rows]))[ok] + 1e-300)
             ds = s.scalings()[1].cpu().numpy()
             for sub, Bw, Aw, rows, ok, dsw, bw in wins:
                 ref = Aw @ xseed[rows]
