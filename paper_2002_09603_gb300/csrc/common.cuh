@@ -367,6 +367,7 @@ struct Ctx {
   int m_alloc = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *t = nullptr, *tmp = nullptr;
   float* Zf = nullptr;  // the mixed-precision solve's Z: the preconditioner outputs are FP32 values
+  long long ldz = 0;    // its column stride: n rounded up to a multiple of 4 (16-byte aligned columns)
   double *h = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *yv = nullptr,
          *partials = nullptr, *scal = nullptr;
   int* dflag = nullptr;  // DGKS decision of the current Arnoldi step

@@ -206,12 +206,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_norm_partials(long long n, cons
 // x += Z y
 // x += Z y with an FP32 Z (every product exact in FP64, the same sums as
 // with the widened columns)
-__global__ void k_gemv_add_f(long long n, const float* __restrict__ Z, int ncols, const double* __restrict__ y,
-                             double* __restrict__ x) {
+__global__ void k_gemv_add_f(long long n, long long ld, const float* __restrict__ Z, int ncols,
+                             const double* __restrict__ y, double* __restrict__ x) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   double s = x[r];
-  for (int c = 0; c < ncols; ++c) s += (double)Z[(long long)c * n + r] * y[c];
+  for (int c = 0; c < ncols; ++c) s += (double)Z[(long long)c * ld + r] * y[c];
   x[r] = s;
 }
 
@@ -365,7 +365,10 @@ void ensure_zbasis(Ctx& c) {
   ensure_workspace(c);
   const size_t nz = (size_t)c.opt.restart * c.n;
   if (ff_krylov(c)) {
-    if (!c.Zf) c.Zf = dalloc_n<float>(c, nz);
+    if (!c.Zf) {
+      c.ldz = (c.n + 3) & ~3LL;
+      c.Zf = dalloc_n<float>(c, (size_t)c.opt.restart * c.ldz);
+    }
   } else if (!c.Z) {
     c.Z = dalloc_n<double>(c, nz);
   }
@@ -480,7 +483,7 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
   if (ff_krylov(c)) {
     // z_j stays in FP32 (it is the FP32 preconditioner's output): the
     // float-float operator reads it, and x += Z y widens it
-    float* zfj = c.Zf + (long long)j * n;
+    float* zfj = c.Zf + (long long)j * c.ldz;
     apply_precond_mixed(c, vj, c.ds_inv, nullptr, transpose, zfj);  // unscale into the FP32 preconditioner
     apply_operator_arnoldi(c, nullptr, zfj, c.w, c.ds, transpose);  // w = D_s A z_j
   } else {
@@ -676,7 +679,7 @@ void fgmres_advance(Ctx& c, FgState& f) {
         k_lsq<<<1, 32, 0, c.stream>>>(k, m, c.H, c.g, c.yv);
         MHFP_LAUNCH_CHECK();
         if (ff_krylov(c))
-          k_gemv_add_f<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Zf, k, c.yv, f.x);
+          k_gemv_add_f<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.ldz, c.Zf, k, c.yv, f.x);
         else
           k_gemv_add<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, k, c.yv, f.x);
         MHFP_LAUNCH_CHECK();
@@ -798,13 +801,13 @@ __global__ void k_lsq_dev(const DevCtl* __restrict__ ctl, const double* __restri
 }
 
 template <typename ZT>
-__global__ void k_gemv_add_dev(long long n, const ZT* __restrict__ Z, const DevCtl* __restrict__ ctl,
+__global__ void k_gemv_add_dev(long long n, long long ld, const ZT* __restrict__ Z, const DevCtl* __restrict__ ctl,
                                const double* __restrict__ y, double* __restrict__ x) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int k = ctl->k;
   double s = x[r];
-  for (int c = 0; c < k; ++c) s += (double)Z[(long long)c * n + r] * y[c];
+  for (int c = 0; c < k; ++c) s += (double)Z[(long long)c * ld + r] * y[c];
   x[r] = s;
 }
 
@@ -954,9 +957,9 @@ cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool trans
     k_lsq_dev<<<1, 32, 0, c.stream>>>(ctl, c.H, c.g, c.yv);
     MHFP_LAUNCH_CHECK();
     if (ff_krylov(c))
-      k_gemv_add_dev<float><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Zf, ctl, c.yv, c.xcur);
+      k_gemv_add_dev<float><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.ldz, c.Zf, ctl, c.yv, c.xcur);
     else
-      k_gemv_add_dev<double><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.Z, ctl, c.yv, c.xcur);
+      k_gemv_add_dev<double><<<grid_for(n, 256), 256, 0, c.stream>>>(n, n, c.Z, ctl, c.yv, c.xcur);
     MHFP_LAUNCH_CHECK();
     k_cycle_end<<<1, 32, 0, c.stream>>>(ctl);
     MHFP_LAUNCH_CHECK();
