@@ -714,19 +714,28 @@ __global__ void __launch_bounds__(256) k_prolong_faces(FaceTopo32 t, const T* __
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_mv(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
                                                   T* __restrict__ y) {
-  __shared__ double sh[8];
-  const int row = blockIdx.x;
-  const double* a = Ainv + (long long)row * n;
+  // y = Ainv b (the coarsest level's dense FP64 inverse): a block of 8 warps
+  // takes 2 rows, each row's columns split in quarters, one warp per
+  // quarter, so that about 40 warps per SM keep the inverse streaming; the
+  // four partial sums of a row are added in a fixed order
+  __shared__ double part[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 2 + (warp >> 2);
+  const int chunk = (n + 3) / 4;
+  const int c0 = (warp & 3) * chunk, c1 = min(n, c0 + chunk);
   double s = 0.0;
+  if (row < n) {
+    const double* a = Ainv + (long long)row * n;
 #pragma unroll 4
-  for (int c = threadIdx.x; c < n; c += 256) s += a[c] * (double)b[c];
+    for (int c = c0 + lane; c < c1; c += 32) s += a[c] * (double)b[c];
+  }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  if (lane == 0) part[warp] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += sh[w];
-    y[row] = (T)t;
+  if (threadIdx.x < 2) {
+    const int r = blockIdx.x * 2 + threadIdx.x;
+    if (r < n) y[r] = (T)(((part[4 * threadIdx.x] + part[4 * threadIdx.x + 1]) + part[4 * threadIdx.x + 2]) +
+                          part[4 * threadIdx.x + 3]);
   }
 }
 
@@ -735,7 +744,6 @@ __global__ void k_cast_f32(long long n, const double* __restrict__ x, float* __r
   if (i < n) y[i] = (float)x[i];
 }
 
-// rows x n FP64 values (row stride n) to FP32 with row stride ld >= n
 // rows 0..125 of the FP64 offset-major values ([row][n]) into the
 // node-blocked FP32 layout of the symmetric sweep
 __global__ void k_cast_f32_sym(long long n, const double* __restrict__ x, float* __restrict__ y) {
@@ -1886,7 +1894,7 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   const LV<T> v = view(c, L, T());
   if (L.dense_inv) {
     const int n = (int)L.n;
-    k_dense_mv<T><<<n, 256, 0, c.stream>>>(n, L.dense_inv, b, x);
+    k_dense_mv<T><<<(n + 1) / 2, 256, 0, c.stream>>>(n, L.dense_inv, b, x);
     MHFP_LAUNCH_CHECK();
     return;
   }
