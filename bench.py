@@ -40,13 +40,13 @@ FALLBACK_HBM_GBS = 6800.0
 # (measured; the CPU legs scale their samples to it, the oracle being the
 # same algorithm)
 WORKLOADS = {
-    "lognormal64": dict(n=64, restart=12, gpu_iters=32,
+    "lognormal64": dict(n=64, restart=12, gpu_iters=35,
                         desc="64^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
     "lognormal32": dict(n=32, gpu_iters=28,
                         desc="32^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
     "lognormal96": dict(n=96, gpu_iters=36,
                         desc="96^3 hex, log-normal kappa (sigma 2, corr. 8 cells, seed 2), S_eps=0, dt=1e-3 s"),
-    "layered128": dict(n=128, gen="layered", restart=20, gpu_iters=54,
+    "layered128": dict(n=128, gen="layered", restart=20, gpu_iters=56,
                        desc="128^3 hex, interior node jitter U(+-0.2h), 8 z-layers: kappa log-U[1e-18,1e-12] m^2, "
                             "E log-U[1e8,1e10] Pa, nu U[0.2,0.35]; S_eps=0, dt=0.1 s (seed 3)"),
     "adjoint48": dict(n=48, desc="48^3 hex, log-normal ln kappa (sigma 1, seed 5), 10 backward-Euler steps dt=0.1 s, "
