@@ -169,3 +169,42 @@ def test_hybrid_only_calls_are_refused():
     s.close()
     with pytest.raises(MhfpError):
         _solver(prob, precision=1)
+
+
+def test_mixed_form_at_the_table_grid_64():
+    """The 1/h = 64 cantilever of Table tab:can_3 (1,884,739 unknowns,
+    dt = 1e-5) in the mixed form, at full size against the oracle: every
+    operator row (1e-12), D_s and C~_p's diagonal (1e-12), C~_p itself (the
+    first level of its hierarchy, 1e-12), and the solution of the bench's
+    configuration (FGMRES(30), tolerance 1e-6 and 1e-8) checked by the
+    residual recomputed with the oracle's assembled mixed matrix."""
+    prob = mi.cantilever_cube(64, dt=1e-5)
+    B = oracle.assemble(prob)
+    M = mixed.assemble_mixed(B, prob.face_bc)
+    A = mixed.mixed_matrix(M)
+    Cp = mixed.ctilde_p(M)
+    from paper_2002_09603_gb300 import Solver, default_options
+    opt = default_options()
+    opt.formulation = 1
+    opt.restart = 30
+    s = Solver(prob)
+    s.assemble_condense()
+    s.setup_precond(opt)
+    rng = np.random.default_rng(64)
+    x = rng.standard_normal(s.n)
+    _blockwise(s.apply_operator(_gpu(x)).cpu().numpy(), A @ x, B.sizes, 1e-12)
+    bt, ds = s.scalings()
+    _close(bt.cpu().numpy(), Cp.diagonal(), 1e-12, "diag C~_p")
+    _blockwise(ds.cpu().numpy(), mixed.equilibration(M, Cp), B.sizes, 1e-12)
+    xp = rng.standard_normal(B.sizes[1])
+    _close(s.level_apply(1, 0, _gpu(xp)).cpu().numpy(), Cp @ xp, 1e-12, "C~_p")
+    b = s.build_rhs()
+    bref = system.rhs(B)
+    _blockwise(b.cpu().numpy(), bref, B.sizes, 1e-12)
+    d = ds.cpu().numpy()
+    for tol in (1e-6, 1e-8):
+        xs, st = s.solve(b, tol=tol)
+        assert st["converged"]
+        r = d * (bref - A @ xs.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.05 * tol * np.linalg.norm(d * bref), (tol, np.linalg.norm(r) / np.linalg.norm(d * bref))
+    s.close()
