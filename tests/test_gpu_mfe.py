@@ -177,7 +177,10 @@ def test_mixed_form_at_the_table_grid_64():
     operator row (1e-12), D_s and C~_p's diagonal (1e-12), C~_p itself (the
     first level of its hierarchy, 1e-12), and the solution of the bench's
     configuration (FGMRES(30), tolerance 1e-6 and 1e-8) checked by the
-    residual recomputed with the oracle's assembled mixed matrix."""
+    residual recomputed with the oracle's assembled mixed matrix.  The same
+    problem in the hybrid form with M_II^(h) and M_III^(h) (the table's other
+    columns): operator rows and the solutions' residuals recomputed with the
+    oracle's assembled hybrid matrix."""
     prob = mi.cantilever_cube(64, dt=1e-5)
     B = oracle.assemble(prob)
     M = mixed.assemble_mixed(B, prob.face_bc)
@@ -208,3 +211,20 @@ def test_mixed_form_at_the_table_grid_64():
         r = d * (bref - A @ xs.cpu().numpy())
         assert np.linalg.norm(r) <= 1.05 * tol * np.linalg.norm(d * bref), (tol, np.linalg.norm(r) / np.linalg.norm(d * bref))
     s.close()
+    AH = system.system_matrix(B)
+    for nk in (0, 1):
+        opt = default_options()
+        opt.near_kernel = nk
+        opt.restart = 30
+        s = Solver(prob)
+        s.assemble_condense()
+        s.setup_precond(opt)
+        _blockwise(s.apply_operator(_gpu(x)).cpu().numpy(), AH @ x, B.sizes, 1e-12)
+        d = s.scalings()[1].cpu().numpy()
+        b = s.build_rhs()
+        _blockwise(b.cpu().numpy(), bref, B.sizes, 1e-12)
+        xs, st = s.solve(b, tol=1e-8)
+        assert st["converged"]
+        r = d * (bref - AH @ xs.cpu().numpy())
+        assert np.linalg.norm(r) <= 1.05e-8 * np.linalg.norm(d * bref), (nk, np.linalg.norm(r) / np.linalg.norm(d * bref))
+        s.close()
