@@ -228,3 +228,30 @@ def test_mixed_form_at_the_table_grid_64():
         r = d * (bref - AH @ xs.cpu().numpy())
         assert np.linalg.norm(r) <= 1.05e-8 * np.linalg.norm(d * bref), (nk, np.linalg.norm(r) / np.linalg.norm(d * bref))
         s.close()
+
+
+def test_mixed_form_with_rigid_body_modes_and_in_a_batch():
+    """formulation = 1 combined with the rigid-body-mode displacement
+    multigrid (near_kernel = 1) reaches the mixed system's direct solution,
+    and mixed-form handles solved together (mhfp_solve_batch) give the same
+    solutions as one at a time."""
+    from paper_2002_09603_gb300 import solve_batch
+    prob = mi.cantilever_cube(8, dt=1e-5)
+    B = oracle.assemble(prob)
+    M = mixed.assemble_mixed(B, prob.face_bc)
+    bref = system.rhs(B)
+    xd = mixed.solve_direct(M, bref)
+    s = _solver(prob, near_kernel=1)
+    assert s.hierarchy(0)["block"][1:] == [6] * (s.hierarchy(0)["levels"] - 1)
+    x, st = s.solve(s.build_rhs(), tol=1e-10)
+    assert st["converged"]
+    assert np.linalg.norm(x.cpu().numpy() - xd) <= 1e-7 * np.linalg.norm(xd)
+    s2 = _solver(mi.random_small(10, 9, 8, seed=12, jitter=0.15))
+    bs = [s.build_rhs(), s2.build_rhs()]
+    xs, stats, codes = solve_batch([s, s2], bs, tol=1e-10)
+    assert list(codes) == [0, 0]
+    for h, b, xb in zip((s, s2), bs, xs):
+        x1, _ = h.solve(b, tol=1e-10)
+        assert torch.equal(x1, xb)
+    s.close()
+    s2.close()
