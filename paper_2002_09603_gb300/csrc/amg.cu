@@ -506,7 +506,9 @@ constexpr int prolong_chunk() { return BF * BC == 1 ? 9 : (BF * BC <= 9 ? 4 : 1)
 template <int BF, int BC, int R, typename T>
 __global__ void __launch_bounds__(256) k_prolong_f(Lat32 F, Lat32 C, const T* __restrict__ P,
                                                    const T* __restrict__ xc, T* __restrict__ x) {
-  const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+  // blocks take the fine points in descending order: the restriction just
+  // streamed P in ascending order, so its tail is still in L2
+  const unsigned p = (gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
   if (p >= (unsigned)F.N) return;
   T acc[BF];
 #pragma unroll
@@ -696,7 +698,8 @@ __global__ void __launch_bounds__(256) k_restrict_faces(FaceTopo32 t, const T* _
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_faces(FaceTopo32 t, const T* __restrict__ pw,
                                                        const T* __restrict__ xc, T* __restrict__ x) {
-  const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
+  // descending block order, as k_prolong_f
+  const unsigned f = (gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
   if (f >= t.nF) return;
   int c[2][3], lf[2];
   bool ok[2];

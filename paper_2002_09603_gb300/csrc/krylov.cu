@@ -32,31 +32,31 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // SM) bounds these passes, so they are written for occupancy: few registers
 // per thread, many rows in flight, independent FMA chains.
 constexpr int GS_BLOCKS = 1216;   // 8 x 152 SMs
-constexpr int GS_COLS = 4;        // columns per block in the dot kernel
+constexpr int GS_COLS = 8;        // columns per block in the dot kernel (w is read once per 8 columns)
 constexpr int GS_DOT_BLOCKS = 608;  // 4 x 152 SMs: about 12 rows per thread, so the
                                     // block reductions' FP64 adds stay small
 
 // partials[c][block] = sum over this block's rows of V[:,c] . w for the
 // GS_COLS columns of blockIdx.y; block column 0 also sums w . w into slot
 // `ncols` when with_norm.  Skipped entirely when skip && *skip.
-// Sum of (a0, a1, a2, a3) over the warp by a transposed butterfly: each
-// exchange halves the number of live columns per lane, so the four sums
-// cost 6 FP64 adds and 6 shuffles per lane instead of 20 and 20.  Lane
-// 8q + r (r = 0..7) returns the warp's sum for column q.
-__device__ __forceinline__ double warp_sum4(double a0, double a1, double a2, double a3) {
+// Sum of a[0..7] over the warp by a transposed butterfly: each exchange
+// halves the number of live columns per lane, so the eight sums cost 7 + 2
+// FP64 adds and shuffles per lane instead of 40.  Lane 4q + r (r = 0..3)
+// returns the warp's sum for column q.
+__device__ __forceinline__ double warp_sum8(const double (&a)[GS_COLS]) {
   const unsigned lane = threadIdx.x & 31u;
-  const bool h16 = lane & 16u;
-  double k0 = h16 ? a2 : a0, k1 = h16 ? a3 : a1;
-  const double s0 = h16 ? a0 : a2, s1 = h16 ? a1 : a3;
-  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);  // columns 2*h16, 2*h16 + 1
-  const bool h8 = lane & 8u;
-  double k = h8 ? k1 : k0;
-  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);  // column lane >> 3
-  k += __shfl_xor_sync(0xffffffffu, k, 4);
-  k += __shfl_xor_sync(0xffffffffu, k, 2);
-  k += __shfl_xor_sync(0xffffffffu, k, 1);
-  return k;
+  const bool h16 = lane & 16u, h8 = lane & 8u, h4 = lane & 4u;
+  double k[4], m[2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)  // columns 4 h16 + q
+    k[q] = (h16 ? a[4 + q] : a[q]) + __shfl_xor_sync(0xffffffffu, h16 ? a[q] : a[4 + q], 16);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)  // columns 4 h16 + 2 h8 + q
+    m[q] = (h8 ? k[2 + q] : k[q]) + __shfl_xor_sync(0xffffffffu, h8 ? k[q] : k[2 + q], 8);
+  double t = (h4 ? m[1] : m[0]) + __shfl_xor_sync(0xffffffffu, h4 ? m[0] : m[1], 4);  // column lane >> 2
+  t += __shfl_xor_sync(0xffffffffu, t, 2);
+  t += __shfl_xor_sync(0xffffffffu, t, 1);
+  return t;
 }
 
 // acc[q] += V[:, c0 + q] . w over this thread's rows for q < NC (the
@@ -75,32 +75,40 @@ __device__ __forceinline__ void gs_rows(long long n, const double* __restrict__ 
   }
 }
 
-__global__ void __launch_bounds__(RED_THREADS, 8) k_gs_dots(long long n, const double* __restrict__ V, int ncols,
+__global__ void __launch_bounds__(RED_THREADS, 4) k_gs_dots(long long n, const double* __restrict__ V, int ncols,
                                                              const double* __restrict__ w,
                                                              double* __restrict__ partials,
                                                              const int* __restrict__ skip, int with_norm) {
-  static_assert(GS_COLS == 4, "warp_sum4 reduces four columns");
+  static_assert(GS_COLS == 8, "warp_sum8 reduces eight columns");
   if (skip && *skip) return;
   __shared__ double sh[RED_THREADS / 32][GS_COLS];
   __shared__ double shn[RED_THREADS / 32];
   const int c0 = blockIdx.y * GS_COLS;
   const bool do_norm = with_norm && blockIdx.y == 0;
-  double acc[GS_COLS] = {0.0, 0.0, 0.0, 0.0}, nw = 0.0;
+  double acc[GS_COLS] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, nw = 0.0;
   // block-uniform branch on the number of valid columns in this group
-  switch ((ncols - c0 < GS_COLS ? ncols - c0 : GS_COLS) + (do_norm ? 8 : 0)) {
+  switch ((ncols - c0 < GS_COLS ? ncols - c0 : GS_COLS) + (do_norm ? 16 : 0)) {
     case 1: gs_rows<1, false>(n, V, c0, w, acc, nw); break;
     case 2: gs_rows<2, false>(n, V, c0, w, acc, nw); break;
     case 3: gs_rows<3, false>(n, V, c0, w, acc, nw); break;
     case 4: gs_rows<4, false>(n, V, c0, w, acc, nw); break;
-    case 9: gs_rows<1, true>(n, V, c0, w, acc, nw); break;
-    case 10: gs_rows<2, true>(n, V, c0, w, acc, nw); break;
-    case 11: gs_rows<3, true>(n, V, c0, w, acc, nw); break;
-    case 12: gs_rows<4, true>(n, V, c0, w, acc, nw); break;
+    case 5: gs_rows<5, false>(n, V, c0, w, acc, nw); break;
+    case 6: gs_rows<6, false>(n, V, c0, w, acc, nw); break;
+    case 7: gs_rows<7, false>(n, V, c0, w, acc, nw); break;
+    case 8: gs_rows<8, false>(n, V, c0, w, acc, nw); break;
+    case 17: gs_rows<1, true>(n, V, c0, w, acc, nw); break;
+    case 18: gs_rows<2, true>(n, V, c0, w, acc, nw); break;
+    case 19: gs_rows<3, true>(n, V, c0, w, acc, nw); break;
+    case 20: gs_rows<4, true>(n, V, c0, w, acc, nw); break;
+    case 21: gs_rows<5, true>(n, V, c0, w, acc, nw); break;
+    case 22: gs_rows<6, true>(n, V, c0, w, acc, nw); break;
+    case 23: gs_rows<7, true>(n, V, c0, w, acc, nw); break;
+    case 24: gs_rows<8, true>(n, V, c0, w, acc, nw); break;
     default: break;
   }
   const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-  const double t = warp_sum4(acc[0], acc[1], acc[2], acc[3]);
-  if ((lane & 7u) == 0) sh[wid][lane >> 3] = t;
+  const double t = warp_sum8(acc);
+  if ((lane & 3u) == 0) sh[wid][lane >> 2] = t;
   if (do_norm) {
     for (int o = 16; o > 0; o >>= 1) nw += __shfl_xor_sync(0xffffffffu, nw, o);
     if (lane == 0) shn[wid] = nw;
