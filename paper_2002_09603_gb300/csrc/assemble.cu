@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(256, 4) k_apply_u_ff(Dims d, const float* __re
 
 // p rows in float-float: cpu A_pu z_u + (Abar + A_stab) z_p + cpi A_ppi z_pi,
 // each of the three sums carried as a pair and combined in FP64
-__global__ void __launch_bounds__(256) k_apply_p_ff(FaceTopo32 t, const float* __restrict__ aph,
+__global__ void __launch_bounds__(256, 2) k_apply_p_ff(FaceTopo32 t, const float* __restrict__ aph,
                                                     const float* __restrict__ apl, const float* __restrict__ pdh,
                                                     const float* __restrict__ pdl, const float* __restrict__ sth,
                                                     const float* __restrict__ stl, const float* __restrict__ pph,
@@ -809,14 +809,21 @@ __global__ void __launch_bounds__(256) k_apply_p_ff(FaceTopo32 t, const float* _
   const int i = (int)(T - q * (unsigned)t.nx), k = (int)t.d_ny.div(q), j = (int)(q - (unsigned)k * (unsigned)t.ny);
   const unsigned Lx = (unsigned)t.nx + 1, Ly = (unsigned)t.ny + 1;
   const unsigned nU = 3 * Lx * Ly * ((unsigned)t.nz + 1);
-  float uh = 0.f, ul = 0.f;  // A_up^T z_u (the row is its negative)
+  // every load of the row is issued before the (serial) pair accumulation
+  float va[24], vb[24], vz[24];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const unsigned n = (unsigned)(i + (a & 1)) + Lx * ((unsigned)(j + ((a >> 1) & 1)) + Ly * (unsigned)(k + (a >> 2)));
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      ff_mac(uh, ul, aph[(unsigned)(3 * a + c) * t.nT + T], apl[(unsigned)(3 * a + c) * t.nT + T], z[3 * n + c]);
+    for (int c = 0; c < 3; ++c) {
+      va[3 * a + c] = aph[(unsigned)(3 * a + c) * t.nT + T];
+      vb[3 * a + c] = apl[(unsigned)(3 * a + c) * t.nT + T];
+      vz[3 * a + c] = z[3 * n + c];
+    }
   }
+  float uh = 0.f, ul = 0.f;  // A_up^T z_u (the row is its negative)
+#pragma unroll
+  for (int e = 0; e < 24; ++e) ff_mac(uh, ul, va[e], vb[e], vz[e]);
   const float* zp = z + nU;
   float ph = 0.f, pl = 0.f;
   ff_mac(ph, pl, pdh[T], pdl[T], zp[T]);
@@ -827,16 +834,23 @@ __global__ void __launch_bounds__(256) k_apply_p_ff(FaceTopo32 t, const float* _
     if (ch != 0.f) ff_mac(ph, pl, -ch, -stl[d * t.nT + T], zp[nb[d]]);
   }
   const float* zpi = zp + t.nT;
+  float wa[6], wb[6], wz[6];
+#pragma unroll
+  for (int lf = 0; lf < 6; ++lf) {
+    wa[lf] = pph[lf * t.nT + T];
+    wb[lf] = ppl[lf * t.nT + T];
+    wz[lf] = zpi[t.face(i, j, k, lf)];
+  }
   float ch = 0.f, cl = 0.f;
 #pragma unroll
-  for (int lf = 0; lf < 6; ++lf) ff_mac(ch, cl, pph[lf * t.nT + T], ppl[lf * t.nT + T], zpi[t.face(i, j, k, lf)]);
+  for (int lf = 0; lf < 6; ++lf) ff_mac(ch, cl, wa[lf], wb[lf], wz[lf]);
   const double s = -cpu * ((double)uh + (double)ul) + ((double)ph + (double)pl) + cpi * ((double)ch + (double)cl);
   const long long r = (long long)nU + T;
   y[r] = finish(s, r, so, nullptr);
 }
 
 // pi rows in float-float: cpp A_pip z_p + A_pipi z_pi (ELL, 11 slots)
-__global__ void __launch_bounds__(256) k_apply_pi_ff(FaceTopo32 t, long long nU, const float* __restrict__ pph,
+__global__ void __launch_bounds__(256, 3) k_apply_pi_ff(FaceTopo32 t, long long nU, const float* __restrict__ pph,
                                                      const float* __restrict__ ppl, const float* __restrict__ eh,
                                                      const float* __restrict__ el, const float* __restrict__ z,
                                                      double* __restrict__ y, const double* __restrict__ so,
@@ -856,9 +870,16 @@ __global__ void __launch_bounds__(256) k_apply_pi_ff(FaceTopo32 t, long long nU,
     }
   unsigned col[11];
   t.ell_cols(f, col);
+  float va[11], vb[11], vz[11];  // every load issued before the pair accumulation
+#pragma unroll
+  for (int q = 0; q < 11; ++q) {
+    va[q] = eh[(long long)q * t.nF + f];
+    vb[q] = el[(long long)q * t.nF + f];
+    vz[q] = zpi[col[q]];
+  }
   float ah = 0.f, al = 0.f;
 #pragma unroll
-  for (int q = 0; q < 11; ++q) ff_mac(ah, al, eh[(long long)q * t.nF + f], el[(long long)q * t.nF + f], zpi[col[q]]);
+  for (int q = 0; q < 11; ++q) ff_mac(ah, al, va[q], vb[q], vz[q]);
   const double s = cpp * ((double)ph + (double)pl) + ((double)ah + (double)al);
   const long long r = nU + t.nT + f;
   y[r] = finish(s, r, so, nullptr);
