@@ -741,31 +741,40 @@ __global__ void __launch_bounds__(256, 4) k_apply_u_ff(Dims d, const float* __re
   for (int u = 0; u <= 13; ++u) {
     const int o = 13 + u, dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
     const long long s = dx + (long long)Lx * (dy + (long long)Ly * dz);
+    // both blocks' loads are issued before the pair accumulation (an
+    // absent neighbour's loads read the node's own rows and are not used)
+    const bool up = in(i + dx, j + dy, k + dz), lo = u > 0 && in(i - dx, j - dy, k - dz);
+    const long long qu = up ? p + s : p, ql = lo ? p - s : p;
+    const long long qb = sym_base(ql) + u * 9 * 32;
+    float oh[9], ol[9], th[9], tl[9], zu[3], zl[3];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      oh[e] = uh[ob + u * 9 * 32 + e * 32];
+      ol[e] = ul[ob + u * 9 * 32 + e * 32];
+      th[e] = uh[qb + e * 32];
+      tl[e] = ul[qb + e * 32];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      zu[c] = z[3 * qu + c];
+      zl[c] = z[3 * ql + c];
+    }
     // own block A(p, p + e_u): row a, column c at entry 3 a + c
-    if (in(i + dx, j + dy, k + dz)) {
-      const long long q = p + s;
-      const float z0 = z[3 * q], z1 = z[3 * q + 1], z2 = z[3 * q + 2];
-      const float* h = uh + ob + u * 9 * 32;
-      const float* l = ul + ob + u * 9 * 32;
+    if (up) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        ff_mac(sh[a], sl[a], h[(3 * a) * 32], l[(3 * a) * 32], z0);
-        ff_mac(sh[a], sl[a], h[(3 * a + 1) * 32], l[(3 * a + 1) * 32], z1);
-        ff_mac(sh[a], sl[a], h[(3 * a + 2) * 32], l[(3 * a + 2) * 32], z2);
+        ff_mac(sh[a], sl[a], oh[3 * a], ol[3 * a], zu[0]);
+        ff_mac(sh[a], sl[a], oh[3 * a + 1], ol[3 * a + 1], zu[1]);
+        ff_mac(sh[a], sl[a], oh[3 * a + 2], ol[3 * a + 2], zu[2]);
       }
     }
     // lower block A(p, p - e_u) = A(p - e_u, p)^T: row a, column c at entry 3 c + a
-    if (u > 0 && in(i - dx, j - dy, k - dz)) {
-      const long long q = p - s;
-      const float z0 = z[3 * q], z1 = z[3 * q + 1], z2 = z[3 * q + 2];
-      const long long qb = sym_base(q) + u * 9 * 32;
-      const float* h = uh + qb;
-      const float* l = ul + qb;
+    if (lo) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        ff_mac(sh[a], sl[a], h[a * 32], l[a * 32], z0);
-        ff_mac(sh[a], sl[a], h[(3 + a) * 32], l[(3 + a) * 32], z1);
-        ff_mac(sh[a], sl[a], h[(6 + a) * 32], l[(6 + a) * 32], z2);
+        ff_mac(sh[a], sl[a], th[a], tl[a], zl[0]);
+        ff_mac(sh[a], sl[a], th[3 + a], tl[3 + a], zl[1]);
+        ff_mac(sh[a], sl[a], th[6 + a], tl[6 + a], zl[2]);
       }
     }
   }
