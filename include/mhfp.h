@@ -232,6 +232,27 @@ mhfp_status mhfp_solve_batch(int count, const mhfp_handle* hs, const double* con
 typedef struct mhfp_batch_s* mhfp_batch;
 mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
                               double tol, mhfp_batch* out);
+/* The same batch with several right-hand sides of one handle solved in
+ * lockstep (multi-right-hand-side kernels; not in the paper: its solve
+ * batched over the loads of one discretisation, as with the four load
+ * scales of one mesh).  Entries of one handle are taken, in list order, in
+ * sets of at most max_lanes (1 <= max_lanes <= MHFP_MAX_LANES; 1 gives
+ * mhfp_batch_create).  A set of K > 1 entries is one FGMRES run for all K:
+ * each kernel of the solve is launched once with the K right-hand sides as
+ * its third grid dimension, reading the handle's matrices for all of them
+ * at once; each right-hand side keeps its own Krylov basis, Hessenberg
+ * matrix, restarts and stopping decision, and its result is bit-identical to
+ * the same entry in mhfp_batch_create.  The set runs until its last member
+ * has stopped; a member that stops earlier keeps its solution and
+ * statistics.  Sets of one handle run one after another in its branch;
+ * different handles concurrently.  The batch allocates, for each (handle,
+ * set size K) it uses, a workspace of K copies of the handle's solve vectors
+ * (about (1.5 restart + 14) n doubles per right-hand side), freed by
+ * mhfp_batch_destroy.  Only for handles set up with precision = 1 and
+ * formulation = 0 (otherwise MHFP_ERR_STATE). */
+#define MHFP_MAX_LANES 16
+mhfp_status mhfp_batch_create_lanes(int count, const mhfp_handle* hs, const double* const* d_rhs,
+                                    double* const* d_x, double tol, int max_lanes, mhfp_batch* out);
 mhfp_status mhfp_batch_run(mhfp_batch b, void* stream, mhfp_stats* stats, mhfp_status* statuses);
 void mhfp_batch_destroy(mhfp_batch b);
 

@@ -25,7 +25,7 @@ EXPORTS = ["mhfp_default_options", "mhfp_create", "mhfp_assemble_condense", "mhf
            "mhfp_grad_logk", "mhfp_misfit", "mhfp_adjoint_rhs", "mhfp_apply_precond_t", "mhfp_apply_precond", "mhfp_vcycle",
            "mhfp_level_apply", "mhfp_hierarchy", "mhfp_get_scalings", "mhfp_sizes", "mhfp_timing",
            "mhfp_timing_read", "mhfp_solve_batch", "mhfp_residual_norm_noalloc", "mhfp_update_logk",
-           "mhfp_batch_create", "mhfp_batch_run", "mhfp_batch_destroy", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
+           "mhfp_batch_create", "mhfp_batch_create_lanes", "mhfp_batch_run", "mhfp_batch_destroy", "mhfp_launch_count", "mhfp_last_error", "mhfp_status_string", "mhfp_destroy"]
 
 
 class MhfpError(RuntimeError):
@@ -105,6 +105,7 @@ def load(path: str | None = None):
         "mhfp_residual_norm_noalloc": (i, [vp, vp, vp, vp]),
         "mhfp_update_logk": (i, [vp, vp]),
         "mhfp_batch_create": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, C.POINTER(vp)]),
+        "mhfp_batch_create_lanes": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, i, C.POINTER(vp)]),
         "mhfp_batch_run": (i, [vp, vp, C.POINTER(Stats), C.POINTER(i)]),
         "mhfp_batch_destroy": (None, [vp]),
         "mhfp_solve_batch": (i, [i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, C.POINTER(Stats),
@@ -386,9 +387,11 @@ def solve_batch(solvers, rhs, tol=1e-8, out=None):
 class Batch:
     """Many solves as one CUDA graph launch (mhfp_batch_*): entry i solves
     solvers[i] for rhs[i] into out[i]; entries of one solver run in order,
-    different solvers concurrently.  The tensors are bound at creation."""
+    different solvers concurrently.  The tensors are bound at creation.
+    lanes > 1: a solver's entries in sets of up to `lanes` right-hand sides
+    solved in lockstep (mhfp_batch_create_lanes)."""
 
-    def __init__(self, solvers, rhs, out, tol=1e-8):
+    def __init__(self, solvers, rhs, out, tol=1e-8, lanes=1):
         n = len(solvers)
         if n == 0 or len(rhs) != n or len(out) != n:
             raise ValueError("Batch: one right-hand side and one output per entry")
@@ -401,7 +404,10 @@ class Batch:
         R = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
         X = (C.c_void_p * n)(*[t.data_ptr() for t in out])
         b = C.c_void_p()
-        code = self.lib.mhfp_batch_create(n, H, R, X, float(tol), C.byref(b))
+        if lanes == 1:
+            code = self.lib.mhfp_batch_create(n, H, R, X, float(tol), C.byref(b))
+        else:
+            code = self.lib.mhfp_batch_create_lanes(n, H, R, X, float(tol), int(lanes), C.byref(b))
         if code != MHFP_OK:
             raise MhfpError(code, self.lib.mhfp_last_error(solvers[0].h).decode())
         self.b = b

@@ -1,9 +1,10 @@
 """Many independent systems solved together.
 
-Marshalling only: one handle per instance.  `solve_loads_one_launch` binds
+Marshalling only: one handle per instance.  `LoadBatch` binds
 every (instance, load) pair into one CUDA graph (mhfp_batch_create) and
 solves them all with one launch (mhfp_batch_run): the loads of an instance
-run one after another in its branch, the instances concurrently.
+run one after another in its branch, or, with lanes > 1, in lockstep
+(mhfp_batch_create_lanes), the instances concurrently.
 `solve_loads` is the earlier form: per load, one mhfp_solve_batch call that
 launches each instance's solve graph on its own stream.
 """
@@ -12,7 +13,9 @@ from __future__ import annotations
 from ._lib import Batch, Solver, default_options, solve_batch
 
 
-def prepare_batch(problems, precision=1, restart=12, autotune=1, reorth=1):
+def prepare_batch(problems, precision=1, restart=12, autotune=1, reorth=1, **options):
+    """One set-up handle per problem, each on a stream of its own; `options`
+    sets further mhfp_options fields by name."""
     import torch
     solvers = []
     for prob in problems:
@@ -21,6 +24,8 @@ def prepare_batch(problems, precision=1, restart=12, autotune=1, reorth=1):
         opt.restart = restart
         opt.autotune = autotune
         opt.reorth = reorth
+        for k, v in options.items():
+            setattr(opt, k, v)
         st = torch.cuda.Stream()
         s = Solver(prob, stream=st)
         s.assemble_condense()
@@ -46,9 +51,11 @@ def solve_loads(solvers, load_scales, tol=1e-8):
 
 class LoadBatch:
     """Every instance x every load scale as one graph launch.  The right-hand
-    sides are built once (mhfp_build_rhs); `run()` solves them all."""
+    sides are built once (mhfp_build_rhs); `run()` solves them all.  lanes > 1
+    solves up to `lanes` loads of an instance in lockstep (each kernel once
+    for all of them)."""
 
-    def __init__(self, solvers, load_scales, tol=1e-8):
+    def __init__(self, solvers, load_scales, tol=1e-8, lanes=1):
         import torch
         self.solvers = solvers
         self.scales = tuple(load_scales)
@@ -62,7 +69,7 @@ class LoadBatch:
             s.stream.synchronize()
         torch.cuda.synchronize()
         self.rhs, self.out = rhs, out
-        self.batch = Batch(entries, rhs, out, tol=tol)
+        self.batch = Batch(entries, rhs, out, tol=tol, lanes=lanes)
 
     def run(self, stream=None):
         """Returns (solutions, stats, statuses), entry order instance-major."""

@@ -182,7 +182,10 @@ __device__ __forceinline__ void sym_residual(const Lat& L, long long p, const T*
 template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_resid_u0_sym(Lat L, const T* __restrict__ up,
                                                             const T* __restrict__ x, const T* __restrict__ b,
-                                                            T* __restrict__ y) {
+                                                            T* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  b = lane_ptr(b, lb);
+  y = lane_ptr(y, lb);
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
@@ -195,7 +198,11 @@ template <typename T, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_cheb_u0_sym(Lat L, const T* __restrict__ up,
                                                            const T* __restrict__ dinv, const T* __restrict__ b,
                                                            const T* __restrict__ xin, T* __restrict__ xout,
-                                                           T* __restrict__ d, T cd, T cr) {
+                                                           T* __restrict__ d, T cd, T cr, long long lb) {
+  b = lane_ptr(b, lb);
+  xin = lane_ptr(xin, lb);
+  xout = lane_ptr(xout, lb);
+  d = lane_ptr(d, lb);
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= L.N) return;
   T r[3] = {b[3 * p], b[3 * p + 1], b[3 * p + 2]};
@@ -330,7 +337,13 @@ __device__ __forceinline__ void sym_x(const Lat& L, const float* __restrict__ x,
 }
 
 template <bool CHEB>
-__global__ void __launch_bounds__(TMA_THREADS, 3) k_sym_tma(Lat L, TmaSweep a) {
+__global__ void __launch_bounds__(TMA_THREADS, 3) k_sym_tma(Lat L, TmaSweep a0, long long lb) {
+  // lane blockIdx.z's vectors (the matrix rows are shared)
+  TmaSweep a = a0;
+  a.b = lane_ptr(a.b, lb);
+  a.xin = lane_ptr(a.xin, lb);
+  a.xout = lane_ptr(a.xout, lb);
+  a.d = lane_ptr(a.d, lb);
   extern __shared__ __align__(128) unsigned char tma_smem[];
   float* stage = (float*)tma_smem;
   unsigned long long* full = (unsigned long long*)(tma_smem + (size_t)TMA_S * TMA_STAGE * sizeof(float));
@@ -505,7 +518,9 @@ constexpr int prolong_chunk() { return BF * BC == 1 ? 9 : (BF * BC <= 9 ? 4 : 1)
 // one fine point per thread
 template <int BF, int BC, int R, typename T>
 __global__ void __launch_bounds__(256) k_prolong_f(Lat32 F, Lat32 C, const T* __restrict__ P,
-                                                   const T* __restrict__ xc, T* __restrict__ x) {
+                                                   const T* __restrict__ xc, T* __restrict__ x, long long lb) {
+  xc = lane_ptr(xc, lb);
+  x = lane_ptr(x, lb);
   // blocks take the fine points in descending order: the restriction just
   // streamed P in ascending order, so its tail is still in L2
   const unsigned p = (gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
@@ -522,7 +537,9 @@ __global__ void __launch_bounds__(256) k_prolong_f(Lat32 F, Lat32 C, const T* __
 // points, partial sums added in a fixed order through shared memory
 template <int BF, int BC, int R, int W, typename T>
 __global__ void __launch_bounds__(32 * W) k_prolong_w(Lat32 F, Lat32 C, const T* __restrict__ P,
-                                                      const T* __restrict__ xc, T* __restrict__ x) {
+                                                      const T* __restrict__ xc, T* __restrict__ x, long long lb) {
+  xc = lane_ptr(xc, lb);
+  x = lane_ptr(x, lb);
   __shared__ T part[W][BF][32];
   const unsigned p = blockIdx.x * 32 + threadIdx.x;
   const bool valid = p < (unsigned)F.N;
@@ -548,7 +565,9 @@ __global__ void __launch_bounds__(32 * W) k_prolong_w(Lat32 F, Lat32 C, const T*
 // points before the sums, then a fixed-order xor reduction over the warp
 template <int BF, int BC, int R, typename T>
 __global__ void __launch_bounds__(256) k_restrict_f(Lat32 F, Lat32 C, const T* __restrict__ P,
-                                                    const T* __restrict__ r, T* __restrict__ bc) {
+                                                    const T* __restrict__ r, T* __restrict__ bc, long long lb) {
+  r = lane_ptr(r, lb);
+  bc = lane_ptr(bc, lb);
   constexpr int ns = (2 + 2 * R) / 3 + 1, w = 3 + 2 * R, NB = w * w * w, PER = (NB + 31) / 32;
   // blocks larger than 3 x 3 keep one box point's loads in flight at a time
   constexpr int KB = BF * BC > 9 ? 1 : PER;
@@ -609,7 +628,10 @@ __global__ void __launch_bounds__(256) k_restrict_f(Lat32 F, Lat32 C, const T* _
 // the values stream from memory
 template <typename T>
 __global__ void __launch_bounds__(256) k_spmv_ell(FaceTopo32 t, const T* __restrict__ val, const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y) {
+                                                  const T* __restrict__ b, T* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  b = lane_ptr(b, lb);
+  y = lane_ptr(y, lb);
   const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nF) return;
   unsigned col[11];
@@ -624,7 +646,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cheb_ell(FaceTopo32 t, const T* __restrict__ val,
                                                   const T* __restrict__ dinv, const T* __restrict__ b,
                                                   const T* __restrict__ xin, T* __restrict__ xout, T* __restrict__ d,
-                                                  T cd, T cr) {
+                                                  T cd, T cr, long long lb) {
+  b = lane_ptr(b, lb);
+  xin = lane_ptr(xin, lb);
+  xout = lane_ptr(xout, lb);
+  d = lane_ptr(d, lb);
   const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nF) return;
   T r = b[f];
@@ -680,7 +706,9 @@ __device__ __forceinline__ int ft_face_cells(const FaceTopo& d, long long f, int
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_faces(FaceTopo32 t, const T* __restrict__ pw,
-                                                        const T* __restrict__ r, T* __restrict__ bc) {
+                                                        const T* __restrict__ r, T* __restrict__ bc, long long lb) {
+  r = lane_ptr(r, lb);
+  bc = lane_ptr(bc, lb);
   const unsigned Tc = blockIdx.x * blockDim.x + threadIdx.x;
   if (Tc >= t.nT) return;
   const unsigned q = t.d_nx.div(Tc);
@@ -697,7 +725,9 @@ __global__ void __launch_bounds__(256) k_restrict_faces(FaceTopo32 t, const T* _
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_prolong_faces(FaceTopo32 t, const T* __restrict__ pw,
-                                                       const T* __restrict__ xc, T* __restrict__ x) {
+                                                       const T* __restrict__ xc, T* __restrict__ x, long long lb) {
+  xc = lane_ptr(xc, lb);
+  x = lane_ptr(x, lb);
   // descending block order, as k_prolong_f
   const unsigned f = (gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
   if (f >= t.nF) return;
@@ -716,7 +746,9 @@ __global__ void __launch_bounds__(256) k_prolong_faces(FaceTopo32 t, const T* __
 // inverse and the sums stay FP64 whatever the precision of the cycle's vectors
 template <typename T>
 __global__ void __launch_bounds__(256) k_dense_mv(int n, const double* __restrict__ Ainv, const T* __restrict__ b,
-                                                  T* __restrict__ y) {
+                                                  T* __restrict__ y, long long lb) {
+  b = lane_ptr(b, lb);
+  y = lane_ptr(y, lb);
   // y = Ainv b (the coarsest level's dense FP64 inverse): a block of 8 warps
   // takes 2 rows, each row's columns split in quarters, one warp per
   // quarter, so that about 40 warps per SM keep the inverse streaming; the
@@ -1200,7 +1232,8 @@ void launch_spmv(Ctx& c, const StructOp& A, int bs, const T* val, const T* x, co
 
 void level_spmv(Ctx& c, Level& L, const double* x, const double* b, double* y) {
   if (L.faces) {
-    k_spmv_ell<double><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), L.ell ? L.ell : c.Cpi, x, b, y);
+    k_spmv_ell<double><<<lgrid(grid_for(L.n, 256)), 256, 0, c.stream>>>(face_topo(c), L.ell ? L.ell : c.Cpi, x, b, y,
+                                                                         lbytes());
   } else {
     launch_spmv<double>(c, L.A, L.bs, L.A.val, x, b, y, default_schedule(L.A.N, L.bs));
   }
@@ -1658,7 +1691,7 @@ template <typename T>
 void level_spmv_t(Ctx& c, Level& L, const T* x, const T* b, T* y) {
   const LV<T> v = view(c, L, T());
   if (L.faces) {
-    k_spmv_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), v.ell, x, b, y);
+    k_spmv_ell<T><<<lgrid(grid_for(L.n, 256)), 256, 0, c.stream>>>(face_topo(c), v.ell, x, b, y, lbytes());
   } else {
     launch_spmv<T>(c, L.A, L.bs, v.val, x, b, y, L.tpp ? L.tpp : default_schedule(L.A.N, L.bs));
   }
@@ -1701,8 +1734,8 @@ void launch_sym_tma(Ctx& c, const Level& L, bool cheb, const float* b, const flo
     attr = true;
   }
   TmaSweep a{L.symf, L.dinvf, b, xin, xout, d, cd, cr, c.d_flag};
-  if (cheb) k_sym_tma<true><<<grid, TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a);
-  else k_sym_tma<false><<<grid, TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a);
+  if (cheb) k_sym_tma<true><<<lgrid(grid), TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a, lbytes());
+  else k_sym_tma<false><<<lgrid(grid), TMA_THREADS, TMA_SMEM, c.stream>>>(lat, a, lbytes());
 }
 void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, float* xout, float* d, float cd,
                      float cr) {
@@ -1716,17 +1749,17 @@ void launch_cheb_sym(Ctx& c, const Level& L, const float* b, const float* xin, f
   if (mb == 4)
     launch_sym_tma(c, L, true, b, xin, xout, d, cd, cr);
   else if (mb == 5)
-    k_cheb_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
-                                                                        d, cd, cr);
+    k_cheb_u0_sym<float, 5><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin,
+                                                                                xout, d, cd, cr, lbytes());
   else if (mb == 7)
-    k_cheb_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
-                                                                        d, cd, cr);
+    k_cheb_u0_sym<float, 7><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin,
+                                                                                xout, d, cd, cr, lbytes());
   else if (mb == 8)
-    k_cheb_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
-                                                                        d, cd, cr);
+    k_cheb_u0_sym<float, 8><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin,
+                                                                                xout, d, cd, cr, lbytes());
   else
-    k_cheb_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin, xout,
-                                                                        d, cd, cr);
+    k_cheb_u0_sym<float, 6><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, L.dinvf, b, xin,
+                                                                                xout, d, cd, cr, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, float* y) {
@@ -1735,13 +1768,17 @@ void launch_resid_sym(Ctx& c, const Level& L, const float* x, const float* b, fl
   if (mb == 4)
     launch_sym_tma(c, L, false, b, x, y, nullptr, 0.f, 0.f);
   else if (mb == 5)
-    k_resid_u0_sym<float, 5><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+    k_resid_u0_sym<float, 5><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, x, b, y,
+                                                                                 lbytes());
   else if (mb == 7)
-    k_resid_u0_sym<float, 7><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+    k_resid_u0_sym<float, 7><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, x, b, y,
+                                                                                 lbytes());
   else if (mb == 8)
-    k_resid_u0_sym<float, 8><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+    k_resid_u0_sym<float, 8><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, x, b, y,
+                                                                                 lbytes());
   else
-    k_resid_u0_sym<float, 6><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, L.symf, x, b, y);
+    k_resid_u0_sym<float, 6><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, L.symf, x, b, y,
+                                                                                 lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
@@ -1867,8 +1904,8 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
     }
     if (time_it && xin) timing_begin(c, 0);
     if (L.faces) {
-      k_cheb_ell<T><<<grid_for(L.n, 256), 256, 0, c.stream>>>(face_topo(c), v.ell, v.dinv, b, xin, out, v.d, (T)cd,
-                                                             (T)cr);
+      k_cheb_ell<T><<<lgrid(grid_for(L.n, 256)), 256, 0, c.stream>>>(face_topo(c), v.ell, v.dinv, b, xin, out, v.d,
+                                                                     (T)cd, (T)cr, lbytes());
     } else if (time_it) {
       if constexpr (std::is_same<T, float>::value) {
         launch_cheb_sym(c, L, b, xin, out, v.d, (T)cd, (T)cr);
@@ -1888,7 +1925,7 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
     xin = out;
     out = (out == x) ? other : x;
   }
-  if (xin != x) MHFP_CUDA(cudaMemcpyAsync(x, xin, L.n * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
+  if (xin != x) MHFP_CUDA(lane_copy(x, xin, L.n * sizeof(T), c.stream));
 }
 
 template <typename T>
@@ -1897,7 +1934,7 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   const LV<T> v = view(c, L, T());
   if (L.dense_inv) {
     const int n = (int)L.n;
-    k_dense_mv<T><<<(n + 1) / 2, 256, 0, c.stream>>>(n, L.dense_inv, b, x);
+    k_dense_mv<T><<<lgrid((n + 1) / 2), 256, 0, c.stream>>>(n, L.dense_inv, b, x, lbytes());
     MHFP_LAUNCH_CHECK();
     return;
   }
@@ -1918,30 +1955,31 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   T* cb = bvec(C, T());
   T* cx = xvec(C, T());
   if (L.faces) {
-    k_restrict_faces<T><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb);
+    k_restrict_faces<T><<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb, lbytes());
   } else {
     const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
     dispatch_pair(L.bs, C.bs, [&](auto BF, auto BC) {
       dispatch_r(L.R, [&](auto RR) {
-        k_restrict_f<BF.value, BC.value, RR.value, T><<<grid_for(C.A.N * 32, 256), 256, 0, c.stream>>>(F, Cc, v.P,
-                                                                                                       v.r, cb);
+        k_restrict_f<BF.value, BC.value, RR.value, T><<<lgrid(grid_for(C.A.N * 32, 256)), 256, 0, c.stream>>>(
+            F, Cc, v.P, v.r, cb, lbytes());
       });
     });
   }
   MHFP_LAUNCH_CHECK();
   vcycle_level<T>(c, H, l + 1, cb, cx);
   if (L.faces) {
-    k_prolong_faces<T><<<grid_for(c.nF, 256), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, x);
+    k_prolong_faces<T><<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, x, lbytes());
   } else {
     // one fine point per thread on large levels, slots split over 8 warps on small ones
     const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
     dispatch_pair(L.bs, C.bs, [&](auto BF, auto BC) {
       dispatch_r(L.R, [&](auto RR) {
         if (L.A.N >= 65536)
-          k_prolong_f<BF.value, BC.value, RR.value, T><<<grid_for(L.A.N, 256), 256, 0, c.stream>>>(F, Cc, v.P, cx, x);
+          k_prolong_f<BF.value, BC.value, RR.value, T><<<lgrid(grid_for(L.A.N, 256)), 256, 0, c.stream>>>(
+              F, Cc, v.P, cx, x, lbytes());
         else
-          k_prolong_w<BF.value, BC.value, RR.value, 8, T><<<grid_for(L.A.N, 32), dim3(32, 8), 0, c.stream>>>(
-              F, Cc, v.P, cx, x);
+          k_prolong_w<BF.value, BC.value, RR.value, 8, T><<<lgrid(grid_for(L.A.N, 32)), dim3(32, 8), 0, c.stream>>>(
+              F, Cc, v.P, cx, x, lbytes());
       });
     });
   }

@@ -10,6 +10,7 @@
 namespace mhfp {
 
 long long g_launches = 0;
+thread_local LaneCfg g_lane;
 
 void* dalloc(Ctx& c, size_t bytes) {
   void* p = nullptr;
@@ -580,9 +581,15 @@ struct mhfp_batch_s {
 
 mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* const* d_rhs, double* const* d_x,
                               double tol, mhfp_batch* out) {
+  return mhfp_batch_create_lanes(count, hs, d_rhs, d_x, tol, 1, out);
+}
+
+mhfp_status mhfp_batch_create_lanes(int count, const mhfp_handle* hs, const double* const* d_rhs,
+                                    double* const* d_x, double tol, int max_lanes, mhfp_batch* out) {
   if (!out) return MHFP_ERR_ARG;
   *out = nullptr;
   if (count < 1 || !hs || !d_rhs || !d_x || !(tol > 0.0) || !(tol < 1.0)) return MHFP_ERR_ARG;
+  if (max_lanes < 1 || max_lanes > MHFP_MAX_LANES) return MHFP_ERR_ARG;
   for (int i = 0; i < count; ++i) {
     if (!hs[i] || !d_rhs[i] || !d_x[i]) return MHFP_ERR_ARG;
     if (!hs[i]->c.prepared) return MHFP_ERR_STATE;
@@ -605,7 +612,7 @@ mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* co
   try {
     MHFP_CUDA(cudaSetDevice(b->device));
     for (Ctx* c : cs) MHFP_CUDA(cudaStreamSynchronize(c->stream));
-    mhfp::build_batch_graph(b->g, cs, r, x, tol);
+    mhfp::build_batch_graph(b->g, cs, r, x, tol, max_lanes);
   } catch (const Error& e) {
     hs[0]->c.err = e.msg;
     mhfp::destroy_batch_graph(b->g);

@@ -557,7 +557,11 @@ __global__ void __launch_bounds__(APPLY_U_NODES * 3) k_apply_u(Dims d, const dou
                                                               const double* __restrict__ Aup,
                                                               const double* __restrict__ x, double* __restrict__ y,
                                                               const double* __restrict__ so,
-                                                              const double* __restrict__ bsub, double cup) {
+                                                              const double* __restrict__ bsub, double cup,
+                                                              long long lb) {
+  x = lane_ptr(x, lb);
+  y = lane_ptr(y, lb);
+  bsub = lane_ptr(bsub, lb);
   const long long n = (long long)blockIdx.x * APPLY_U_NODES + threadIdx.x;
   if (n >= d.nN) return;
   const int comp = threadIdx.y;
@@ -610,7 +614,10 @@ __global__ void __launch_bounds__(256) k_apply_p(FaceTopo32 t, const double* __r
                                                  const double* __restrict__ ApPi, double cpi,
                                                  const double* __restrict__ x, double* __restrict__ y,
                                                  const double* __restrict__ so, const double* __restrict__ bsub,
-                                                 double cpu) {
+                                                 double cpu, long long lb) {
+  x = lane_ptr(x, lb);
+  y = lane_ptr(y, lb);
+  bsub = lane_ptr(bsub, lb);
   // 32-bit cell and node decoding; the same sums in the same order as the
   // definition: A_pu x_u, then the p block, then A_ppi x_pi
   const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
@@ -648,7 +655,10 @@ __global__ void __launch_bounds__(256) k_apply_p(FaceTopo32 t, const double* __r
 __global__ void __launch_bounds__(256) k_apply_pi(FaceTopo32 t, long long nU, const double* __restrict__ ApPi,
                                                   const double* __restrict__ Apipi, const double* __restrict__ x,
                                                   double* __restrict__ y, const double* __restrict__ so,
-                                                  const double* __restrict__ bsub, double cpp) {
+                                                  const double* __restrict__ bsub, double cpp, long long lb) {
+  x = lane_ptr(x, lb);
+  y = lane_ptr(y, lb);
+  bsub = lane_ptr(bsub, lb);
   const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nF) return;
   int c[2][3], lf[2];
@@ -729,7 +739,10 @@ __global__ void __launch_bounds__(256, 4) k_apply_u_ff(Dims d, const float* __re
                                                        const float* __restrict__ ul, const float* __restrict__ aph,
                                                        const float* __restrict__ apl, const float* __restrict__ z,
                                                        double* __restrict__ y, const double* __restrict__ so,
-                                                       const double* __restrict__ bsub, float cup) {
+                                                       const double* __restrict__ bsub, float cup, long long lb) {
+  z = lane_ptr(z, lb);
+  y = lane_ptr(y, lb);
+  bsub = lane_ptr(bsub, lb);
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= d.nN) return;
   const int Lx = d.nx + 1, Ly = d.ny + 1, Lz = d.nz + 1;
@@ -811,7 +824,9 @@ __global__ void __launch_bounds__(256, 2) k_apply_p_ff(FaceTopo32 t, const float
                                                     const float* __restrict__ stl, const float* __restrict__ pph,
                                                     const float* __restrict__ ppl, double cpi,
                                                     const float* __restrict__ z, double* __restrict__ y,
-                                                    const double* __restrict__ so, double cpu) {
+                                                    const double* __restrict__ so, double cpu, long long lb) {
+  z = lane_ptr(z, lb);
+  y = lane_ptr(y, lb);
   const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= t.nT) return;
   const unsigned q = t.d_nx.div(T);
@@ -863,7 +878,9 @@ __global__ void __launch_bounds__(256, 3) k_apply_pi_ff(FaceTopo32 t, long long 
                                                      const float* __restrict__ ppl, const float* __restrict__ eh,
                                                      const float* __restrict__ el, const float* __restrict__ z,
                                                      double* __restrict__ y, const double* __restrict__ so,
-                                                     double cpp) {
+                                                     double cpp, long long lb) {
+  z = lane_ptr(z, lb);
+  y = lane_ptr(y, lb);
   const unsigned f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= t.nF) return;
   int c[2][3], lf[2];
@@ -932,7 +949,10 @@ __global__ void k_split_lo(long long n, const double* __restrict__ x, const floa
 template <typename R>
 __global__ void __launch_bounds__(256) k_prec_p(FaceTopo32 t, const R* __restrict__ ApPi,
                                                 const R* __restrict__ btilde, R dt, const R* __restrict__ vp,
-                                                const R* __restrict__ zpi, R* __restrict__ zp) {
+                                                const R* __restrict__ zpi, R* __restrict__ zp, long long lb) {
+  vp = lane_ptr(vp, lb);
+  zpi = lane_ptr(zpi, lb);
+  zp = lane_ptr(zp, lb);
   const unsigned T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= t.nT) return;
   const unsigned q = t.d_nx.div(T);
@@ -953,7 +973,10 @@ __global__ void __launch_bounds__(256) k_prec_p(FaceTopo32 t, const R* __restric
 // node decoding, every cell's loads issued before the sums
 template <typename R>
 __global__ void __launch_bounds__(256) k_prec_u(FaceTopo32 t, const R* __restrict__ Aup, const R* __restrict__ vu,
-                                                const R* __restrict__ zp, R* __restrict__ tu) {
+                                                const R* __restrict__ zp, R* __restrict__ tu, long long lb) {
+  vu = lane_ptr(vu, lb);
+  zp = lane_ptr(zp, lb);
+  tu = lane_ptr(tu, lb);
   const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nN = (unsigned)(t.nx + 1) * (unsigned)(t.ny + 1) * (unsigned)(t.nz + 1);
   if (n >= nN) return;
@@ -1415,13 +1438,13 @@ void build_mixed_blocks(Ctx& c) {
 void apply_operator_mixed(Ctx& c, const double* x, double* y, const double* so, const double* bsub) {
   const Dims d = dims_of(c);
   timing_begin(c, 1);
-  k_apply_u<<<grid_for(c.nN, APPLY_U_NODES), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
-                                                                                    bsub, 1.0);
+  k_apply_u<<<lgrid(grid_for(c.nN, APPLY_U_NODES)), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
+                                                                                    bsub, 1.0, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Spp, c.stabc, c.Apq_c, c.dt, x, y, so,
-                                                       bsub, 1.0);
+  k_apply_p<<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Spp, c.stabc, c.Apq_c, c.dt, x, y, so,
+                                                       bsub, 1.0, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(topo32(c), 3 * c.nN, c.Aqp_c, c.Aqq, x, y, so, bsub, 1.0);
+  k_apply_pi<<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(topo32(c), 3 * c.nN, c.Aqp_c, c.Aqq, x, y, so, bsub, 1.0, lbytes());
   MHFP_LAUNCH_CHECK();
   const double bytes = 27.0 * 9 * 8 * c.nN + 2.0 * 24 * 8 * c.nT + 11.0 * 8 * c.nF + 17.0 * 8 * c.nT + 16.0 * c.n;
   timing_end(c, 1, bytes);
@@ -1449,15 +1472,15 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
   const Dims d = dims_of(c);
   timing_begin(c, 1);
   const double sgn = transpose ? -1.0 : 1.0;
-  k_apply_u<<<grid_for(c.nN, APPLY_U_NODES), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
-                                                                                    bsub, sgn);
+  k_apply_u<<<lgrid(grid_for(c.nN, APPLY_U_NODES)), dim3(APPLY_U_NODES, 3), 0, c.stream>>>(d, c.Auu.val, c.Aup, x, y, so,
+                                                                                    bsub, sgn, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_apply_p<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Abar, c.stabc, c.ApPi,
-                                                       transpose ? 1.0 : c.dt, x, y, so, bsub, sgn);
+  k_apply_p<<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(topo32(c), c.Aup, c.Abar, c.stabc, c.ApPi,
+                                                       transpose ? 1.0 : c.dt, x, y, so, bsub, sgn, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_apply_pi<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy),
+  k_apply_pi<<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(FaceTopo32::make(c.nx, c.ny, c.nz, c.nT, c.nF, c.nFx, c.nFy),
                                                         3 * c.nN, c.ApPi, c.Apipi, x, y, so, bsub,
-                                                        transpose ? c.dt : 1.0);
+                                                        transpose ? c.dt : 1.0, lbytes());
   MHFP_LAUNCH_CHECK();
   // algorithmic bytes: A_uu values (27*9 doubles/node) + A_up read twice
   // (24 doubles/cell) + ELL values (11 doubles/face; the columns are
@@ -1469,26 +1492,26 @@ void apply_operator(Ctx& c, const double* x, double* y, const double* so, const 
 
 void precond_p_step(Ctx& c, const double* vp, const double* zpi, double* zp) {
   const Dims d = dims_of(c);
-  k_prec_p<double><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.ApPi, c.btilde, c.dt, vp, zpi, zp);
+  k_prec_p<double><<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(topo32(c), c.ApPi, c.btilde, c.dt, vp, zpi, zp, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_u_rhs(Ctx& c, const double* vu, const double* zp, double* tu) {
   const Dims d = dims_of(c);
-  k_prec_u<double><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(topo32(c), c.Aup, vu, zp, tu);
+  k_prec_u<double><<<lgrid(grid_for(c.nN, 256)), 256, 0, c.stream>>>(topo32(c), c.Aup, vu, zp, tu, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_p_step(Ctx& c, const float* vp, const float* zpi, float* zp) {
   const Dims d = dims_of(c);
-  k_prec_p<float><<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.ApPif, c.btildef, (float)c.dt, vp, zpi,
-                                                             zp);
+  k_prec_p<float><<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(topo32(c), c.ApPif, c.btildef, (float)c.dt, vp, zpi,
+                                                             zp, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
 void precond_u_rhs(Ctx& c, const float* vu, const float* zp, float* tu) {
   const Dims d = dims_of(c);
-  k_prec_u<float><<<grid_for(c.nN, 256), 256, 0, c.stream>>>(topo32(c), c.Aupf, vu, zp, tu);
+  k_prec_u<float><<<lgrid(grid_for(c.nN, 256)), 256, 0, c.stream>>>(topo32(c), c.Aupf, vu, zp, tu, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
@@ -1610,15 +1633,15 @@ void apply_operator_arnoldi(Ctx& c, const double* z, const float* zf, double* y,
   }
   const Dims d = dims_of(c);
   timing_begin(c, 6);
-  k_apply_u_ff<<<grid_for(c.nN, 256), 256, 0, c.stream>>>(d, c.auu_h, c.auu_l, c.Aupf, c.aup_l, zf, y, so, nullptr,
-                                                           transpose ? -1.f : 1.f);
+  k_apply_u_ff<<<lgrid(grid_for(c.nN, 256)), 256, 0, c.stream>>>(d, c.auu_h, c.auu_l, c.Aupf, c.aup_l, zf, y, so, nullptr,
+                                                           transpose ? -1.f : 1.f, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_apply_p_ff<<<grid_for(c.nT, 256), 256, 0, c.stream>>>(topo32(c), c.Aupf, c.aup_l, c.pd_h, c.pd_l, c.st_h, c.st_l,
+  k_apply_p_ff<<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(topo32(c), c.Aupf, c.aup_l, c.pd_h, c.pd_l, c.st_h, c.st_l,
                                                           c.appi_h, c.appi_l, transpose ? 1.0 : c.dt, zf, y, so,
-                                                          transpose ? -1.0 : 1.0);
+                                                          transpose ? -1.0 : 1.0, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_apply_pi_ff<<<grid_for(c.nF, 256), 256, 0, c.stream>>>(topo32(c), 3 * c.nN, c.appi_h, c.appi_l, c.apipi_h,
-                                                           c.apipi_l, zf, y, so, transpose ? c.dt : 1.0);
+  k_apply_pi_ff<<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(topo32(c), 3 * c.nN, c.appi_h, c.appi_l, c.apipi_h,
+                                                           c.apipi_l, zf, y, so, transpose ? c.dt : 1.0, lbytes());
   MHFP_LAUNCH_CHECK();
   // algorithmic bytes, every coefficient a hi + lo pair (8 B): A_uu's
   // symmetric half (126 per node) and A_up (24 per cell) by the u rows, A_up

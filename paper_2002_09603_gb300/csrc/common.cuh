@@ -46,6 +46,59 @@ inline unsigned grid_for(long long n, int block) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// ------------------------------------------------------------ lanes
+// Several right-hand sides of one handle solved in lockstep ("lanes"): every
+// kernel of the solve runs once for all of them, lane l in blockIdx.z.  A
+// lane's work vectors sit at the same offset inside its slice of one arena,
+// the slices `bytes` apart, so a kernel finds lane l's copy of a work vector
+// at p + l * bytes; matrices are shared and never offset.  g_lane is set
+// while a lockstep solve is captured into a graph (one host thread captures
+// at a time); otherwise it is {1, 0} and every launch is the single-vector
+// one.
+struct LaneCfg {
+  int k = 1;
+  long long bytes = 0;
+};
+extern thread_local LaneCfg g_lane;
+inline dim3 lgrid(unsigned x, unsigned y = 1) { return dim3(x, y, (unsigned)g_lane.k); }
+inline long long lbytes() { return g_lane.bytes; }
+// lane blockIdx.z's copy of work vector p (null stays null)
+template <class T>
+__device__ __forceinline__ T* lane_ptr(T* p, long long lb) {
+  return p ? (T*)((char*)p + (long long)blockIdx.z * lb) : p;
+}
+template <class T>
+__device__ __forceinline__ const T* lane_ptr(const T* p, long long lb) {
+  return p ? (const T*)((const char*)p + (long long)blockIdx.z * lb) : p;
+}
+// lanes for the launches queued while it lives (restores the previous ones)
+struct LaneScope {
+  LaneCfg saved;
+  LaneScope(int k, long long bytes) : saved(g_lane) {
+    g_lane.k = k;
+    g_lane.bytes = bytes;
+  }
+  ~LaneScope() { g_lane = saved; }
+  LaneScope(const LaneScope&) = delete;
+  LaneScope& operator=(const LaneScope&) = delete;
+};
+// a copy or a fill of a work vector in every lane
+inline cudaError_t lane_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  for (int l = 0; l < g_lane.k; ++l) {
+    const cudaError_t e = cudaMemcpyAsync((char*)dst + l * g_lane.bytes, (const char*)src + l * g_lane.bytes, bytes,
+                                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+inline cudaError_t lane_memset(void* dst, int v, size_t bytes, cudaStream_t s) {
+  for (int l = 0; l < g_lane.k; ++l) {
+    const cudaError_t e = cudaMemsetAsync((char*)dst + l * g_lane.bytes, v, bytes, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Row blocks that mhfp_residual_norm_noalloc needs for a mesh of nx*ny*nz
 // cells: one partial-sum slot per block of 256 rows in each of its three row
 // kernels (displacement nodes, cells, faces).  The call accepts a mesh when
@@ -272,9 +325,13 @@ struct TimedPair {
 constexpr int TIMING_CLASSES = 7;
 
 // FGMRES control block kept in device memory by the device-driven solve
+// (several lanes: one block per lane; fin = the lane's solve has ended,
+// live = it takes part in the current cycle's steps; lane 0 also counts the
+// set's cycle starts and Arnoldi steps, decides and steps)
 struct DevCtl {
   double tol, bnorm, tolb, est, true_rel, pad0, pad1, pad2;
   int maxit, m, total, cycles, k, converged, status, pad3;
+  int fin, live, decides, steps;
 };
 
 // one captured FGMRES iteration (Arnoldi step j of a cycle)
@@ -391,6 +448,11 @@ struct Ctx {
   DevCtl* ctl = nullptr;                 // device control block
   DevCtl* host_ctl = nullptr;            // pinned copy
   double *bcur = nullptr, *xcur = nullptr;
+  // lockstep workspaces (several right-hand sides of one handle): the
+  // handle they belong to, their lane count and the bytes between lanes
+  const Ctx* lane_of = nullptr;
+  int lanes = 1;
+  long long lane_bytes = 0;
 };
 
 // resumable FGMRES: each advance consumes one scalar read back from the
@@ -478,9 +540,15 @@ struct BatchGraph {
   DevCtl* host_ctl = nullptr;                        // pinned, one per entry
   std::vector<cudaGraphConditionalHandle*> d_hif;    // per entry
   std::vector<std::array<long long, 3>> counts;      // kernels: start, per cycle, per step
+  std::vector<int> lanes;                            // per entry: lanes of its set (1: a single solve)
+  std::vector<int> lead;                             // per entry: the entry holding its set's counters
+  std::vector<Ctx*> lane_ctx;                        // owned: lockstep workspaces
 };
+// max_lanes: entries of one handle are taken, in list order, in sets of at
+// most max_lanes right-hand sides solved in lockstep (one launch per kernel
+// for the whole set); sets of one handle run one after another
 void build_batch_graph(BatchGraph& B, const std::vector<Ctx*>& cs, const std::vector<const double*>& rhs,
-                       const std::vector<double*>& x, double tol);
+                       const std::vector<double*>& x, double tol, int max_lanes = 1);
 void run_batch_graph(BatchGraph& B, cudaStream_t stream);
 void autotune_cheb_degree(Ctx& c);
 void destroy_batch_graph(BatchGraph& B);

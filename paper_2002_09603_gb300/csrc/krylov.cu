@@ -78,8 +78,13 @@ __device__ __forceinline__ void gs_rows(long long n, const double* __restrict__ 
 __global__ void __launch_bounds__(RED_THREADS, 4) k_gs_dots(long long n, const double* __restrict__ V, int ncols,
                                                              const double* __restrict__ w,
                                                              double* __restrict__ partials,
-                                                             const int* __restrict__ skip, int with_norm) {
+                                                             const int* __restrict__ skip, int with_norm,
+                                                             long long lb) {
   static_assert(GS_COLS == 8, "warp_sum8 reduces eight columns");
+  V = lane_ptr(V, lb);
+  w = lane_ptr(w, lb);
+  partials = lane_ptr(partials, lb);
+  skip = lane_ptr(skip, lb);
   if (skip && *skip) return;
   __shared__ double sh[RED_THREADS / 32][GS_COLS];
   __shared__ double shn[RED_THREADS / 32];
@@ -128,14 +133,17 @@ __global__ void __launch_bounds__(RED_THREADS, 4) k_gs_dots(long long n, const d
 
 // same reduction, skipped when *skip != 0
 __global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partials, double* __restrict__ out,
-                                       const int* __restrict__ skip);
+                                       const int* __restrict__ skip, long long lb);
 
 
 // out[col] (+)= sum_b partials[col * nb + b] in a fixed order
 // the ncols dot products into hout[0..ncols) and, when nrm2 is given, the
 // norm partials (row ncols) into *nrm2; same fixed-order sums as below
 __global__ void k_reduce_dots(int nb, const double* __restrict__ partials, double* __restrict__ hout, int ncols,
-                              double* __restrict__ nrm2) {
+                              double* __restrict__ nrm2, long long lb) {
+  partials = lane_ptr(partials, lb);
+  hout = lane_ptr(hout, lb);
+  nrm2 = lane_ptr(nrm2, lb);
   __shared__ double sh[RED_THREADS / 32];
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[(long long)blockIdx.x * nb + b];
@@ -146,7 +154,10 @@ __global__ void k_reduce_dots(int nb, const double* __restrict__ partials, doubl
   }
 }
 
-__global__ void k_reduce_partials(int nb, const double* __restrict__ partials, double* __restrict__ out, int accumulate) {
+__global__ void k_reduce_partials(int nb, const double* __restrict__ partials, double* __restrict__ out, int accumulate,
+                                  long long lb) {
+  partials = lane_ptr(partials, lb);
+  out = lane_ptr(out, lb);
   __shared__ double sh[RED_THREADS / 32];
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[(long long)blockIdx.x * nb + b];
@@ -155,7 +166,10 @@ __global__ void k_reduce_partials(int nb, const double* __restrict__ partials, d
 }
 
 __global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partials, double* __restrict__ out,
-                                       const int* __restrict__ skip) {
+                                       const int* __restrict__ skip, long long lb) {
+  partials = lane_ptr(partials, lb);
+  out = lane_ptr(out, lb);
+  skip = lane_ptr(skip, lb);
   if (*skip) return;
   __shared__ double sh[RED_THREADS / 32];
   double v = 0.0;
@@ -170,7 +184,12 @@ __global__ void k_reduce_partials_flag(int nb, const double* __restrict__ partia
 __global__ void __launch_bounds__(RED_THREADS, 8) k_gemv_sub(long long n, const double* __restrict__ V, int ncols,
                                                               const double* __restrict__ h, double* __restrict__ w,
                                                               double* __restrict__ partials,
-                                                              const int* __restrict__ skip) {
+                                                              const int* __restrict__ skip, long long lb) {
+  V = lane_ptr(V, lb);
+  h = lane_ptr(h, lb);
+  w = lane_ptr(w, lb);
+  partials = lane_ptr(partials, lb);
+  skip = lane_ptr(skip, lb);
   if (skip && *skip) return;
   __shared__ double sh[RED_THREADS / 32];
   __shared__ double nh[64];
@@ -202,7 +221,9 @@ __global__ void __launch_bounds__(RED_THREADS, 8) k_gemv_sub(long long n, const 
 }
 
 __global__ void __launch_bounds__(RED_THREADS) k_norm_partials(long long n, const double* __restrict__ x,
-                                                                double* __restrict__ partials) {
+                                                                double* __restrict__ partials, long long lb) {
+  x = lane_ptr(x, lb);
+  partials = lane_ptr(partials, lb);
   __shared__ double sh[RED_THREADS / 32];
   double acc = 0.0;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
@@ -233,7 +254,10 @@ __global__ void k_gemv_add(long long n, const double* __restrict__ Z, int ncols,
 }
 
 __global__ void k_scale_dev(long long n, const double* __restrict__ x, const double* __restrict__ s,
-                            double* __restrict__ y) {
+                            double* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  s = lane_ptr(s, lb);
+  y = lane_ptr(y, lb);
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) y[r] = x[r] * s[0];
 }
@@ -243,8 +267,11 @@ __global__ void k_scale_host(long long n, const double* __restrict__ x, double s
   if (r < n) y[r] = x[r] * s;
 }
 
+// s is a shared elementwise scaling (not a work vector)
 __global__ void k_ewise(long long n, const double* __restrict__ x, const double* __restrict__ s, int divide,
-                        double* __restrict__ y) {
+                        double* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  y = lane_ptr(y, lb);
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) y[r] = divide ? x[r] / s[r] : x[r] * s[r];
 }
@@ -256,7 +283,11 @@ __global__ void k_ewise(long long n, const double* __restrict__ x, const double*
 // when it is skipped h2 is zeroed and the norm after the first pass is
 // carried into nrm[2], which the second pass overwrites otherwise.
 __global__ void k_dgks(int ncols, const double* __restrict__ nrm, int* __restrict__ flag, double* __restrict__ h2,
-                       double* __restrict__ nrm_final) {
+                       double* __restrict__ nrm_final, long long lb) {
+  nrm = lane_ptr(nrm, lb);
+  flag = lane_ptr(flag, lb);
+  h2 = lane_ptr(h2, lb);
+  nrm_final = lane_ptr(nrm_final, lb);
   const int i = threadIdx.x;
   const bool skip = nrm[1] > 0.5 * nrm[0];
   if (i == 0) {
@@ -273,8 +304,16 @@ __global__ void k_dgks(int ncols, const double* __restrict__ nrm, int* __restric
 // one, update g.  scal[0] = |g_{j+1}|, scal[1] = 1/||w|| (0 on breakdown).
 __global__ void k_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
                          const double* __restrict__ nrm2, double* __restrict__ H, double* __restrict__ cs,
-                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal) {
+                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ scal, long long lb) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  h1 = lane_ptr(h1, lb);
+  h2 = lane_ptr(h2, lb);
+  nrm2 = lane_ptr(nrm2, lb);
+  H = lane_ptr(H, lb);
+  cs = lane_ptr(cs, lb);
+  sn = lane_ptr(sn, lb);
+  g = lane_ptr(g, lb);
+  scal = lane_ptr(scal, lb);
   double* col = H + (long long)j * (m + 1);
   for (int i = 0; i <= j; ++i) col[i] = h2 ? h1[i] + h2[i] : h1[i];
   const double hn = sqrt(nrm2[0]);
@@ -318,22 +357,22 @@ __global__ void k_set_g(int m, double beta, double* __restrict__ g) {
 // with skip non-null nothing happens when *skip != 0
 void gs_dots(Ctx& c, int ncols, double* hout, double* nrm2, const int* skip) {
   const int wn = nrm2 ? 1 : 0;
-  dim3 grid(GS_DOT_BLOCKS, (ncols + GS_COLS - 1) / GS_COLS);
-  k_gs_dots<<<grid, RED_THREADS, 0, c.stream>>>(c.n, c.V, ncols, c.w, c.partials, skip, wn);
+  const dim3 grid = lgrid(GS_DOT_BLOCKS, (ncols + GS_COLS - 1) / GS_COLS);
+  k_gs_dots<<<grid, RED_THREADS, 0, c.stream>>>(c.n, c.V, ncols, c.w, c.partials, skip, wn, lbytes());
   MHFP_LAUNCH_CHECK();
   if (skip) {
-    k_reduce_partials_flag<<<ncols, RED_THREADS, 0, c.stream>>>(GS_DOT_BLOCKS, c.partials, hout, skip);
+    k_reduce_partials_flag<<<lgrid(ncols), RED_THREADS, 0, c.stream>>>(GS_DOT_BLOCKS, c.partials, hout, skip, lbytes());
   } else {
-    k_reduce_dots<<<ncols + wn, RED_THREADS, 0, c.stream>>>(GS_DOT_BLOCKS, c.partials, hout, ncols, nrm2);
+    k_reduce_dots<<<lgrid(ncols + wn), RED_THREADS, 0, c.stream>>>(GS_DOT_BLOCKS, c.partials, hout, ncols, nrm2, lbytes());
   }
   MHFP_LAUNCH_CHECK();
 }
 
 // norm^2 into dst (device)
 void norm2_dev(Ctx& c, const double* x, long long n, double* dst) {
-  k_norm_partials<<<RED_BLOCKS, RED_THREADS, 0, c.stream>>>(n, x, c.partials);
+  k_norm_partials<<<lgrid(RED_BLOCKS), RED_THREADS, 0, c.stream>>>(n, x, c.partials, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials, dst, 0);
+  k_reduce_partials<<<lgrid(1), RED_THREADS, 0, c.stream>>>(RED_BLOCKS, c.partials, dst, 0, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
@@ -389,12 +428,15 @@ double device_norm2(Ctx& c, const double* x, long long n) {
 }
 
 void vec_scale(Ctx& c, const double* x, const double* s, bool divide, double* y, long long n) {
-  k_ewise<<<grid_for(n, 256), 256, 0, c.stream>>>(n, x, s, divide ? 1 : 0, y);
+  k_ewise<<<lgrid(grid_for(n, 256)), 256, 0, c.stream>>>(n, x, s, divide ? 1 : 0, y, lbytes());
   MHFP_LAUNCH_CHECK();
 }
 
+// mul is a shared elementwise scaling (not a work vector)
 __global__ void k_to_f32(long long n, const double* __restrict__ x, const double* __restrict__ mul,
-                         float* __restrict__ y) {
+                         float* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  y = lane_ptr(y, lb);
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) y[r] = (float)(mul ? x[r] * mul[r] : x[r]);
 }
@@ -437,7 +479,7 @@ void apply_precond_mixed(Ctx& c, const double* v, const double* mul, double* z, 
   const long long n = c.n;
   float* zo = zf_out ? zf_out : c.zf;
   timing_begin(c, 3);
-  k_to_f32<<<grid_for(n, 256), 256, 0, c.stream>>>(n, v, mul, c.tf);
+  k_to_f32<<<lgrid(grid_for(n, 256)), 256, 0, c.stream>>>(n, v, mul, c.tf, lbytes());
   MHFP_LAUNCH_CHECK();
   // level-0 right-hand-side buffers are free at the finest levels
   precond_blocks<float>(c, c.tf, zo, c.hu[0].bf, c.hpi[0].bf, transpose);
@@ -511,29 +553,29 @@ void enqueue_arnoldi_step(Ctx& c, int j, bool transpose, bool host_copy = true) 
   // (reorth = 0: the first pass alone, the second is not even queued)
   const bool reorth = c.opt.reorth != 0;
   gs_dots(c, j + 1, c.h, c.scal + 4, nullptr);
-  k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
-                                                     nullptr);
+  k_gemv_sub<<<lgrid(GS_BLOCKS), RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h, c.w, c.partials + (size_t)m * GS_BLOCKS,
+                                                     nullptr, lbytes());
   MHFP_LAUNCH_CHECK();
   // one pass: the new norm goes straight to the slot the Givens step reads
-  k_reduce_partials<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
-                                                     reorth ? c.scal + 5 : c.scal + 2, 0);
+  k_reduce_partials<<<lgrid(1), RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
+                                                     reorth ? c.scal + 5 : c.scal + 2, 0, lbytes());
   MHFP_LAUNCH_CHECK();
   if (reorth) {
-    k_dgks<<<1, 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2);
+    k_dgks<<<lgrid(1), 64, 0, c.stream>>>(j + 1, c.scal + 4, c.dflag, c.h + (m + 1), c.scal + 2, lbytes());
     MHFP_LAUNCH_CHECK();
     gs_dots(c, j + 1, c.h + (m + 1), nullptr, c.dflag);
-    k_gemv_sub<<<GS_BLOCKS, RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
-                                                       c.partials + (size_t)m * GS_BLOCKS, c.dflag);
+    k_gemv_sub<<<lgrid(GS_BLOCKS), RED_THREADS, 0, c.stream>>>(n, c.V, j + 1, c.h + (m + 1), c.w,
+                                                       c.partials + (size_t)m * GS_BLOCKS, c.dflag, lbytes());
     MHFP_LAUNCH_CHECK();
-    k_reduce_partials_flag<<<1, RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
-                                                           c.scal + 2, c.dflag);
+    k_reduce_partials_flag<<<lgrid(1), RED_THREADS, 0, c.stream>>>(GS_BLOCKS, c.partials + (size_t)m * GS_BLOCKS,
+                                                           c.scal + 2, c.dflag, lbytes());
     MHFP_LAUNCH_CHECK();
   }
   timing_end(c, 2, 8.0 * n * (2.0 * (j + 1) + 4.0));
-  k_givens<<<1, 32, 0, c.stream>>>(j, m, c.h, reorth ? c.h + (m + 1) : nullptr, c.scal + 2, c.H, c.cs, c.sn, c.g,
-                                   c.scal);
+  k_givens<<<lgrid(1), 32, 0, c.stream>>>(j, m, c.h, reorth ? c.h + (m + 1) : nullptr, c.scal + 2, c.H, c.cs, c.sn, c.g,
+                                   c.scal, lbytes());
   MHFP_LAUNCH_CHECK();
-  k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n);
+  k_scale_dev<<<lgrid(grid_for(n, 256)), 256, 0, c.stream>>>(n, c.w, c.scal + 1, c.V + (long long)(j + 1) * n, lbytes());
   MHFP_LAUNCH_CHECK();
   if (host_copy) MHFP_CUDA(cudaMemcpyAsync(c.host_scal, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
 }
@@ -714,91 +756,150 @@ void fgmres_advance(Ctx& c, FgState& f) {
 // bounded: a cycle runs at most m steps and the WHILE ends once maxit steps
 // have run.
 
-__global__ void k_ctl_init(DevCtl* __restrict__ ctl, const double* __restrict__ nrm2, cudaGraphConditionalHandle hw) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double bn = sqrt(nrm2[0]);
-  ctl->bnorm = bn;
-  ctl->tolb = ctl->tol * bn;
-  ctl->est = 1.0;
-  ctl->true_rel = 0.0;
-  ctl->total = 0;
-  ctl->cycles = 0;
-  ctl->k = 0;
-  ctl->converged = 0;
-  ctl->status = 0;
-  ctl->pad3 = 0;  // cycle starts, a second bound on the WHILE loop
-  if (!isfinite(bn)) {
-    ctl->status = (int)MHFP_ERR_NONFINITE;
-    cudaGraphSetConditional(hw, 0);
-  } else if (bn == 0.0) {
-    ctl->converged = 1;
-    ctl->est = 0.0;
-    cudaGraphSetConditional(hw, 0);
-  } else {
-    cudaGraphSetConditional(hw, 1);
-  }
+// Several lanes (right-hand sides of one handle in lockstep): the control
+// kernels run in one thread and walk the lanes, lane l's control block,
+// scalars and Hessenberg data lb bytes after lane l - 1's.  A lane whose
+// solve has ended (fin) is skipped; the set goes on while any lane has not
+// ended, and a cycle's next step opens while any lane is live in it.  With
+// one lane every decision is the single solve's.
+template <class T>
+__device__ __forceinline__ T* lane_at(T* p, int l, long long lb) {
+  return (T*)((char*)p + (long long)l * lb);
 }
 
-// start of a cycle: beta = ||D_s (b - A x)||; stop, or open step 0
+__global__ void k_ctl_init(DevCtl* __restrict__ ctl, const double* __restrict__ nrm2, cudaGraphConditionalHandle hw,
+                           int K, long long lb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bool any = false;
+  for (int l = 0; l < K; ++l) {
+    DevCtl* c = lane_at(ctl, l, lb);
+    const double bn = sqrt(lane_at(nrm2, l, lb)[0]);
+    c->bnorm = bn;
+    c->tolb = c->tol * bn;
+    c->est = 1.0;
+    c->true_rel = 0.0;
+    c->total = 0;
+    c->cycles = 0;
+    c->k = 0;
+    c->converged = 0;
+    c->status = 0;
+    c->pad3 = 0;  // cycle starts, a second bound on the WHILE loop
+    c->fin = 0;
+    c->live = 0;
+    if (!isfinite(bn)) {
+      c->status = (int)MHFP_ERR_NONFINITE;
+      c->fin = 1;
+    } else if (bn == 0.0) {
+      c->converged = 1;
+      c->est = 0.0;
+      c->fin = 1;
+    } else {
+      any = true;
+    }
+  }
+  ctl->decides = 0;
+  ctl->steps = 0;
+  cudaGraphSetConditional(hw, any ? 1 : 0);
+}
+
+// start of a cycle: beta = ||D_s (b - A x)|| per lane; a lane stops, or
+// takes part in the cycle; step 0 opens while any lane takes part
 __global__ void k_cycle_decide(DevCtl* __restrict__ ctl, const double* __restrict__ nrm2, double* __restrict__ scal,
                                double* __restrict__ g, cudaGraphConditionalHandle hw,
-                               const cudaGraphConditionalHandle* __restrict__ hif) {
+                               const cudaGraphConditionalHandle* __restrict__ hif, int K, long long lb) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int m = ctl->m;
-  const double beta = sqrt(nrm2[0]);
-  ctl->k = 0;
-  ctl->pad3 += 1;
-  // every cycle either runs at least one step (total grows by one) or
-  // stops; the count of cycle starts bounds the loop even if a step did not
-  // run, so the WHILE node always terminates
-  bool stop = ctl->pad3 > ctl->maxit + 1;
-  if (stop) {
-    ctl->true_rel = beta / ctl->bnorm;
-  } else if (!isfinite(beta)) {
-    ctl->status = (int)MHFP_ERR_NONFINITE;
-    stop = true;
-  } else if (beta <= 1.05 * ctl->tolb) {
-    ctl->converged = 1;
-    ctl->est = beta / ctl->bnorm;
-    ctl->true_rel = beta / ctl->bnorm;
-    stop = true;
-  } else if (ctl->total >= ctl->maxit) {
-    ctl->true_rel = beta / ctl->bnorm;
-    stop = true;
+  ctl->decides += 1;
+  bool any = false;
+  for (int l = 0; l < K; ++l) {
+    DevCtl* c = lane_at(ctl, l, lb);
+    double* sc = lane_at(scal, l, lb);
+    c->k = 0;
+    c->live = 0;
+    if (c->fin) {
+      sc[6] = 0.0;
+      continue;
+    }
+    const double beta = sqrt(lane_at(nrm2, l, lb)[0]);
+    c->pad3 += 1;
+    // every cycle either runs at least one step (total grows by one) or
+    // stops; the count of cycle starts bounds the loop even if a step did
+    // not run, so the WHILE node always terminates
+    bool stop = c->pad3 > c->maxit + 1;
+    if (stop) {
+      c->true_rel = beta / c->bnorm;
+    } else if (!isfinite(beta)) {
+      c->status = (int)MHFP_ERR_NONFINITE;
+      stop = true;
+    } else if (beta <= 1.05 * c->tolb) {
+      c->converged = 1;
+      c->est = beta / c->bnorm;
+      c->true_rel = beta / c->bnorm;
+      stop = true;
+    } else if (c->total >= c->maxit) {
+      c->true_rel = beta / c->bnorm;
+      stop = true;
+    }
+    if (stop) {
+      c->fin = 1;
+      sc[6] = 0.0;
+      continue;
+    }
+    c->live = 1;
+    any = true;
+    double* gl = lane_at(g, l, lb);
+    sc[6] = 1.0 / beta;
+    gl[0] = beta;
+    for (int i = 1; i <= m; ++i) gl[i] = 0.0;
   }
-  if (stop) {
-    scal[6] = 0.0;
+  if (!any) {
     cudaGraphSetConditional(hw, 0);
     for (int j = 0; j < m; ++j) cudaGraphSetConditional(hif[j], 0);
     return;
   }
-  scal[6] = 1.0 / beta;
-  g[0] = beta;
-  for (int i = 1; i <= m; ++i) g[i] = 0.0;
   cudaGraphSetConditional(hif[0], 1);
   for (int j = 1; j < m; ++j) cudaGraphSetConditional(hif[j], 0);
 }
 
-// after Arnoldi step j: count it and open step j+1 unless converged / done
+// after Arnoldi step j: count it for every live lane, and open step j+1
+// unless no lane is live any more (converged in the Arnoldi estimate, maxit
+// or a non-finite residual); a lane that leaves keeps k, its step count of
+// this cycle, for the update x += Z y
 __global__ void k_step_done(DevCtl* __restrict__ ctl, const double* __restrict__ scal, int j,
-                            cudaGraphConditionalHandle hnext, int has_next, cudaGraphConditionalHandle hw) {
+                            cudaGraphConditionalHandle hnext, int has_next, cudaGraphConditionalHandle hw, int K,
+                            long long lb) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double resid = scal[0];
-  ctl->total += 1;
-  ctl->k = j + 1;
-  ctl->est = resid / ctl->bnorm;
-  bool next = has_next && resid > ctl->tolb && ctl->total < ctl->maxit;
-  if (!isfinite(resid)) {
-    ctl->status = (int)MHFP_ERR_NONFINITE;
-    next = false;
-    cudaGraphSetConditional(hw, 0);
+  ctl->steps += 1;
+  bool any_next = false, all_fin = true;
+  for (int l = 0; l < K; ++l) {
+    DevCtl* c = lane_at(ctl, l, lb);
+    if (c->live) {
+      const double resid = lane_at(scal, l, lb)[0];
+      c->total += 1;
+      c->k = j + 1;
+      c->est = resid / c->bnorm;
+      bool next = has_next && resid > c->tolb && c->total < c->maxit;
+      if (!isfinite(resid)) {
+        c->status = (int)MHFP_ERR_NONFINITE;
+        c->fin = 1;
+        next = false;
+      }
+      if (!next) c->live = 0;
+      any_next = any_next || next;
+    }
+    all_fin = all_fin && c->fin;
   }
-  if (has_next) cudaGraphSetConditional(hnext, next ? 1 : 0);
+  if (all_fin) cudaGraphSetConditional(hw, 0);
+  if (has_next) cudaGraphSetConditional(hnext, any_next ? 1 : 0);
 }
 
 __global__ void k_lsq_dev(const DevCtl* __restrict__ ctl, const double* __restrict__ H, const double* __restrict__ g,
-                          double* __restrict__ y) {
+                          double* __restrict__ y, long long lb) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl = lane_ptr(ctl, lb);
+  H = lane_ptr(H, lb);
+  g = lane_ptr(g, lb);
+  y = lane_ptr(y, lb);
   const int k = ctl->k, m = ctl->m;
   for (int i = k - 1; i >= 0; --i) {
     double s = g[i];
@@ -810,16 +911,21 @@ __global__ void k_lsq_dev(const DevCtl* __restrict__ ctl, const double* __restri
 
 template <typename ZT>
 __global__ void k_gemv_add_dev(long long n, long long ld, const ZT* __restrict__ Z, const DevCtl* __restrict__ ctl,
-                               const double* __restrict__ y, double* __restrict__ x) {
+                               const double* __restrict__ y, double* __restrict__ x, long long lb) {
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
+  Z = lane_ptr(Z, lb);
+  ctl = lane_ptr(ctl, lb);
+  y = lane_ptr(y, lb);
+  x = lane_ptr(x, lb);
   const int k = ctl->k;
   double s = x[r];
   for (int c = 0; c < k; ++c) s += (double)Z[(long long)c * ld + r] * y[c];
   x[r] = s;
 }
 
-__global__ void k_cycle_end(DevCtl* __restrict__ ctl) {
+__global__ void k_cycle_end(DevCtl* __restrict__ ctl, long long lb) {
+  ctl = lane_ptr(ctl, lb);
   if (threadIdx.x == 0 && blockIdx.x == 0 && ctl->k > 0) ctl->cycles += 1;
 }
 
@@ -886,8 +992,9 @@ cudaGraphNode_t add_conditional(cudaGraph_t parent, cudaGraphNode_t dep, cudaGra
   return node;
 }
 
-__global__ void k_ctl_reset(DevCtl* __restrict__ ctl, double tol, int maxit, int m) {
+__global__ void k_ctl_reset(DevCtl* __restrict__ ctl, double tol, int maxit, int m, long long lb) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl = lane_ptr(ctl, lb);
   DevCtl h{};
   h.tol = tol;
   h.maxit = maxit;
@@ -901,17 +1008,21 @@ __global__ void k_ctl_reset(DevCtl* __restrict__ ctl, double tol, int maxit, int
 // [xcur -> x] and the control block -> host_slot.  The bracketed parts are
 // added when rhs / x are given (batched graphs); the single-solve graph
 // leaves them to the host.  d_hif: device array of `restart` IF handles for
-// this solve.  Returns the last node; the kernel counts go to *cnt.
+// this solve.  With K lanes (c a lane workspace, lane l's work vectors lb
+// bytes after lane l - 1's) the solve takes K right-hand sides rhs[0..K)
+// in lockstep into x[0..K), control blocks to host_slot[0..K).  Returns the
+// last node; the kernel counts go to *cnt.
 struct SolveCounts {
   long long start = 0, cycle = 0, step = 0;
 };
 
 cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool transpose,
-                          cudaGraphConditionalHandle* d_hif, const double* rhs, double* x, double tol,
-                          DevCtl* host_slot, SolveCounts* cnt) {
+                          cudaGraphConditionalHandle* d_hif, const double* const* rhs, double* const* x, double tol,
+                          DevCtl* const* host_slot, SolveCounts* cnt, int K = 1, long long lb = 0) {
   const int m = c.opt.restart;
   const long long n = c.n;
   const long long l0 = g_launches;
+  LaneScope lanes(K, lb);
   // the WHILE node sits in G, the IF nodes in the WHILE body: each handle is
   // created on the graph that contains its node
   cudaGraphConditionalHandle hw;
@@ -919,18 +1030,22 @@ cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool trans
   DevCtl* ctl = c.ctl;
   cudaGraphNode_t last = dep;
   if (rhs) {
-    cudaGraphNode_t cp;
-    MHFP_CUDA(cudaGraphAddMemcpyNode1D(&cp, G, last ? &last : nullptr, last ? 1 : 0, c.bcur, rhs,
-                                       n * sizeof(double), cudaMemcpyDeviceToDevice));
-    last = add_kernel(G, cp, k_ctl_reset, dim3(1), dim3(32), ctl, tol, c.opt.maxit, m);
+    for (int l = 0; l < K; ++l) {
+      cudaGraphNode_t cp;
+      MHFP_CUDA(cudaGraphAddMemcpyNode1D(&cp, G, last ? &last : nullptr, last ? 1 : 0,
+                                         (char*)c.bcur + (long long)l * lb, rhs[l], n * sizeof(double),
+                                         cudaMemcpyDeviceToDevice));
+      last = cp;
+    }
+    last = add_kernel(G, last, k_ctl_reset, lgrid(1), dim3(32), ctl, tol, c.opt.maxit, m, lb);
   }
   // x = 0, ||D_s b|| and the control block
   last = add_child(G, last, capture_piece(c, [&] {
-    MHFP_CUDA(cudaMemsetAsync(c.xcur, 0, n * sizeof(double), c.stream));
+    MHFP_CUDA(lane_memset(c.xcur, 0, n * sizeof(double), c.stream));
     vec_scale(c, c.bcur, c.ds, false, c.tmp, n);
     norm2_dev(c, c.tmp, n, c.scal + 4);
   }));
-  last = add_kernel(G, last, k_ctl_init, dim3(1), dim3(32), ctl, (const double*)(c.scal + 4), hw);
+  last = add_kernel(G, last, k_ctl_init, dim3(1), dim3(32), ctl, (const double*)(c.scal + 4), hw, K, lb);
   const long long nk_start = g_launches - l0;
   cudaGraph_t W;
   cudaGraphNode_t wnode = add_conditional(G, last, hw, cudaGraphCondTypeWhile, &W);
@@ -944,9 +1059,9 @@ cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool trans
     norm2_dev(c, c.tmp, n, c.scal + 4);
   }));
   b = add_kernel(W, b, k_cycle_decide, dim3(1), dim3(32), ctl, (const double*)(c.scal + 4), c.scal, c.g, hw,
-                 (const cudaGraphConditionalHandle*)d_hif);
+                 (const cudaGraphConditionalHandle*)d_hif, K, lb);
   b = add_child(W, b, capture_piece(c, [&] {
-    k_scale_dev<<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.tmp, c.scal + 6, c.V);
+    k_scale_dev<<<lgrid(grid_for(n, 256)), 256, 0, c.stream>>>(n, c.tmp, c.scal + 6, c.V, lbytes());
     MHFP_LAUNCH_CHECK();
   }));
   const long long nk_cycle = g_launches - l1;
@@ -957,35 +1072,44 @@ cudaGraphNode_t add_solve(Ctx& c, cudaGraph_t G, cudaGraphNode_t dep, bool trans
     const long long l2 = g_launches;
     cudaGraphNode_t s = add_child(body, nullptr, capture_piece(c, [&] { enqueue_arnoldi_step(c, j, transpose, false); }));
     add_kernel(body, s, k_step_done, dim3(1), dim3(32), ctl, (const double*)c.scal, j,
-               j + 1 < m ? hif[j + 1] : hif[j], j + 1 < m ? 1 : 0, hw);
+               j + 1 < m ? hif[j + 1] : hif[j], j + 1 < m ? 1 : 0, hw, K, lb);
     nk_step = g_launches - l2;
   }
   const long long l3 = g_launches;
   b = add_child(W, b, capture_piece(c, [&] {
-    k_lsq_dev<<<1, 32, 0, c.stream>>>(ctl, c.H, c.g, c.yv);
+    k_lsq_dev<<<lgrid(1), 32, 0, c.stream>>>(ctl, c.H, c.g, c.yv, lbytes());
     MHFP_LAUNCH_CHECK();
     if (ff_krylov(c))
-      k_gemv_add_dev<float><<<grid_for(n, 256), 256, 0, c.stream>>>(n, c.ldz, c.Zf, ctl, c.yv, c.xcur);
+      k_gemv_add_dev<float><<<lgrid(grid_for(n, 256)), 256, 0, c.stream>>>(n, c.ldz, c.Zf, ctl, c.yv, c.xcur,
+                                                                           lbytes());
     else
-      k_gemv_add_dev<double><<<grid_for(n, 256), 256, 0, c.stream>>>(n, n, c.Z, ctl, c.yv, c.xcur);
+      k_gemv_add_dev<double><<<lgrid(grid_for(n, 256)), 256, 0, c.stream>>>(n, n, c.Z, ctl, c.yv, c.xcur,
+                                                                            lbytes());
     MHFP_LAUNCH_CHECK();
-    k_cycle_end<<<1, 32, 0, c.stream>>>(ctl);
+    k_cycle_end<<<lgrid(1), 32, 0, c.stream>>>(ctl, lbytes());
     MHFP_LAUNCH_CHECK();
   }));
   const long long nk_end = g_launches - l3;
   last = wnode;
   if (x) {
-    cudaGraphNode_t cp;
-    MHFP_CUDA(cudaGraphAddMemcpyNode1D(&cp, G, &last, 1, x, c.xcur, n * sizeof(double), cudaMemcpyDeviceToDevice));
-    last = cp;
+    for (int l = 0; l < K; ++l) {
+      cudaGraphNode_t cp;
+      MHFP_CUDA(cudaGraphAddMemcpyNode1D(&cp, G, &last, 1, x[l], (const char*)c.xcur + (long long)l * lb,
+                                         n * sizeof(double), cudaMemcpyDeviceToDevice));
+      last = cp;
+    }
   }
-  // after the loop: the control block back to pinned host memory
-  cudaGraphNode_t fin;
-  MHFP_CUDA(cudaGraphAddMemcpyNode1D(&fin, G, &last, 1, host_slot, ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost));
+  // after the loop: the control blocks back to pinned host memory
+  for (int l = 0; l < K; ++l) {
+    cudaGraphNode_t fin;
+    MHFP_CUDA(cudaGraphAddMemcpyNode1D(&fin, G, &last, 1, host_slot[l], (const char*)ctl + (long long)l * lb,
+                                       sizeof(DevCtl), cudaMemcpyDeviceToHost));
+    last = fin;
+  }
   cnt->start = nk_start;
   cnt->cycle = nk_cycle + nk_end;
   cnt->step = nk_step;
-  return fin;
+  return last;
 }
 
 // the handle's device-side solve state (control block, current b and x)
@@ -1007,8 +1131,9 @@ void build_solve_graph(Ctx& c, bool transpose) {
   cudaGraph_t G;
   MHFP_CUDA(cudaGraphCreate(&G, 0));
   SolveCounts cnt;
+  DevCtl* slot = c.host_ctl;
   try {
-    add_solve(c, G, nullptr, transpose, c.d_hif[ti], nullptr, nullptr, 0.0, c.host_ctl, &cnt);
+    add_solve(c, G, nullptr, transpose, c.d_hif[ti], nullptr, nullptr, 0.0, &slot, &cnt);
   } catch (...) {
     g_launches = l0;
     cudaGraphDestroy(G);
@@ -1026,23 +1151,133 @@ void build_solve_graph(Ctx& c, bool transpose) {
   c.solve_step_kernels[ti] = cnt.step;
 }
 
+// A lockstep workspace for K right-hand sides of handle `base`: a copy of
+// the handle that shares every matrix, hierarchy and launch schedule, with
+// its own work vectors (Krylov basis, Hessenberg data, control block, the
+// levels' vectors) carved from one arena: lane 0's at the start, lane l's
+// l * lane_bytes further.
+Ctx* make_lane_ctx(Ctx& base, int K) {
+  if (!ff_krylov(base))
+    throw Error{MHFP_ERR_STATE, "right-hand sides in lockstep need the mixed-precision solve of the hybrid system"};
+  ensure_solve_state(base);
+  Ctx* lc = new Ctx(base);
+  lc->allocs.clear();
+  lc->timing = Timing{};
+  lc->suppress_events = false;
+  lc->cap_stream = nullptr;
+  lc->graphs[0].clear();
+  lc->graphs[1].clear();
+  lc->solve_exec[0] = lc->solve_exec[1] = nullptr;
+  lc->d_hif[0] = lc->d_hif[1] = nullptr;
+  lc->host_scal = nullptr;
+  lc->host_ctl = nullptr;
+  // the lane layout: every work vector at a 256-byte aligned offset
+  struct Slot {
+    void** p;
+    size_t bytes;
+  };
+  std::vector<Slot> slots;
+  const int m = base.opt.restart;
+  const size_t n = (size_t)base.n;
+  auto add = [&](auto*& p, size_t bytes) { slots.push_back({(void**)&p, bytes}); };
+  add(lc->V, (size_t)(m + 1) * n * sizeof(double));
+  add(lc->w, n * sizeof(double));
+  add(lc->t, n * sizeof(double));
+  add(lc->tmp, n * sizeof(double));
+  add(lc->h, 2 * (size_t)(m + 1) * sizeof(double));
+  add(lc->H, (size_t)(m + 1) * m * sizeof(double));
+  add(lc->cs, (size_t)m * sizeof(double));
+  add(lc->sn, (size_t)m * sizeof(double));
+  add(lc->g, (size_t)(m + 1) * sizeof(double));
+  add(lc->yv, (size_t)m * sizeof(double));
+  add(lc->partials, (size_t)(m + 2) * GS_BLOCKS * sizeof(double));
+  add(lc->scal, 8 * sizeof(double));
+  add(lc->dflag, 4 * sizeof(int));
+  add(lc->Zf, (size_t)m * (size_t)base.ldz * sizeof(float));
+  add(lc->tf, n * sizeof(float));
+  add(lc->zf, n * sizeof(float));
+  add(lc->ctl, sizeof(DevCtl));
+  add(lc->bcur, n * sizeof(double));
+  add(lc->xcur, n * sizeof(double));
+  lc->Z = nullptr;
+  for (auto* H : {&lc->hu, &lc->hpi})
+    for (Level& L : *H) {
+      const size_t ld = (size_t)L.n * sizeof(double), lf = (size_t)L.n * sizeof(float);
+      for (double** v : {&L.x, &L.b, &L.r, &L.d, &L.y})
+        if (*v) add(*v, ld);
+      for (float** v : {&L.xf, &L.bf, &L.rf, &L.df, &L.yf})
+        if (*v) add(*v, lf);
+    }
+  size_t lane = 0;
+  std::vector<size_t> off(slots.size());
+  for (size_t i = 0; i < slots.size(); ++i) {
+    off[i] = lane;
+    lane += (slots[i].bytes + 255) & ~(size_t)255;
+  }
+  try {
+    char* arena = (char*)dalloc(*lc, lane * (size_t)K);
+    MHFP_CUDA(cudaMemsetAsync(arena, 0, lane * (size_t)K, base.stream));
+    for (size_t i = 0; i < slots.size(); ++i) *slots[i].p = arena + off[i];
+    lc->lane_bytes = (long long)lane;
+    lc->lanes = K;
+  } catch (...) {
+    dfree_all(*lc);
+    delete lc;
+    throw;
+  }
+  return lc;
+}
+
+void destroy_lane_ctx(Ctx* lc) {
+  if (!lc) return;
+  if (lc->cap_stream) cudaStreamDestroy(lc->cap_stream);
+  dfree_all(*lc);
+  delete lc;
+}
+
 }  // namespace
 
 // One CUDA graph for many solves: every handle's entries run in list order
 // in a branch of their own (they share its Krylov workspace); branches of
-// different handles are independent, so one launch runs them all.
+// different handles are independent, so one launch runs them all.  With
+// max_lanes > 1 a handle's entries are taken in sets of up to max_lanes
+// right-hand sides, each set one lockstep solve in a workspace of its own.
 void build_batch_graph(BatchGraph& B, const std::vector<Ctx*>& cs, const std::vector<const double*>& rhs,
-                       const std::vector<double*>& x, double tol) {
+                       const std::vector<double*>& x, double tol, int max_lanes) {
   const long long l0 = g_launches;
   MHFP_CUDA(cudaGraphCreate(&B.graph, 0));
   const int count = (int)cs.size();
   B.counts.assign(count, {0, 0, 0});
+  B.lanes.assign(count, 1);
+  B.lead.assign(count, 0);
   MHFP_CUDA(cudaMallocHost(&B.host_ctl, (size_t)std::max(count, 1) * sizeof(DevCtl)));
   std::vector<std::pair<Ctx*, cudaGraphNode_t>> tail;  // last node of each handle's branch
+  std::vector<bool> taken(count, false);
   try {
     for (int i = 0; i < count; ++i) {
+      if (taken[i]) continue;
       Ctx& c = *cs[i];
+      // this entry and the next entries of the same handle, up to max_lanes
+      std::vector<int> set{i};
+      for (int k = i + 1; k < count && (int)set.size() < max_lanes; ++k)
+        if (cs[k] == &c && !taken[k]) set.push_back(k);
+      for (int e : set) taken[e] = true;
+      const int K = (int)set.size();
       ensure_solve_state(c);
+      Ctx* run = &c;
+      if (K > 1) {
+        // one lockstep workspace per (handle, lane count), reused by the
+        // handle's later sets, which run after this one in its branch
+        Ctx* found = nullptr;
+        for (Ctx* lc : B.lane_ctx)
+          if (lc->lane_of == &c && lc->lanes == K) found = lc;
+        if (!found) {
+          found = make_lane_ctx(c, K);
+          found->lane_of = &c;
+          B.lane_ctx.push_back(found);
+        }
+        run = found;
+      }
       cudaGraphConditionalHandle* d_hif = nullptr;
       MHFP_CUDA(cudaMalloc(&d_hif, (size_t)c.opt.restart * sizeof(cudaGraphConditionalHandle)));
       B.d_hif.push_back(d_hif);
@@ -1051,8 +1286,19 @@ void build_batch_graph(BatchGraph& B, const std::vector<Ctx*>& cs, const std::ve
       for (size_t t = 0; t < tail.size(); ++t)
         if (tail[t].first == &c) slot = t;
       if (slot < tail.size()) dep = tail[slot].second;
+      std::vector<const double*> r;
+      std::vector<double*> xs;
+      std::vector<DevCtl*> hs;
+      for (int e : set) {
+        r.push_back(rhs[e]);
+        xs.push_back(x[e]);
+        hs.push_back(&B.host_ctl[e]);
+        B.lanes[e] = K;
+        B.lead[e] = i;
+      }
       SolveCounts cnt;
-      const cudaGraphNode_t last = add_solve(c, B.graph, dep, false, d_hif, rhs[i], x[i], tol, &B.host_ctl[i], &cnt);
+      const cudaGraphNode_t last = add_solve(*run, B.graph, dep, false, d_hif, r.data(), xs.data(), tol, hs.data(),
+                                             &cnt, K, K > 1 ? run->lane_bytes : 0);
       B.counts[i] = {cnt.start + 1, cnt.cycle, cnt.step};  // + the control-block reset
       if (slot < tail.size()) tail[slot].second = last;
       else tail.push_back({&c, last});
@@ -1069,8 +1315,12 @@ void run_batch_graph(BatchGraph& B, cudaStream_t stream) {
   MHFP_CUDA(cudaGraphLaunch(B.exec, stream));
   MHFP_CUDA(cudaStreamSynchronize(stream));
   for (size_t i = 0; i < B.counts.size(); ++i) {
+    if ((int)i != B.lead[i]) continue;  // a set's launches are counted once, at its first entry
     const DevCtl& h = B.host_ctl[i];
-    g_launches += B.counts[i][0] + (long long)(h.cycles + 1) * B.counts[i][1] + (long long)h.total * B.counts[i][2];
+    if (B.lanes[i] == 1)
+      g_launches += B.counts[i][0] + (long long)(h.cycles + 1) * B.counts[i][1] + (long long)h.total * B.counts[i][2];
+    else  // lane 0 counts the set's cycle starts and steps
+      g_launches += B.counts[i][0] + (long long)h.decides * B.counts[i][1] + (long long)h.steps * B.counts[i][2];
   }
 }
 
@@ -1079,6 +1329,7 @@ void destroy_batch_graph(BatchGraph& B) {
   if (B.graph) cudaGraphDestroy(B.graph);
   for (auto* p : B.d_hif) cudaFree(p);
   if (B.host_ctl) cudaFreeHost(B.host_ctl);
+  for (Ctx* lc : B.lane_ctx) destroy_lane_ctx(lc);
   B = BatchGraph{};
 }
 

@@ -73,7 +73,10 @@ constexpr int f_chunk() { return BS == 6 ? 1 : (sizeof(T) == 4 ? (BS == 1 ? 25 :
 // y = b - A x, or y = A x when b is null
 template <int BS, int KIND, typename T>
 __global__ void __launch_bounds__(256) k_spmv_f(Lat32 L, const T* __restrict__ val, const T* __restrict__ x,
-                                                const T* __restrict__ b, T* __restrict__ y) {
+                                                const T* __restrict__ b, T* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  b = lane_ptr(b, lb);
+  y = lane_ptr(y, lb);
   const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (unsigned)L.N) return;
   T r[BS];
@@ -103,7 +106,11 @@ __device__ __forceinline__ void cheb_update(unsigned p, unsigned N, const T r[BS
 template <int BS, int KIND, typename T>
 __global__ void __launch_bounds__(256) k_cheb_f(Lat32 L, const T* __restrict__ val, const T* __restrict__ dinv,
                                                 const T* __restrict__ b, const T* __restrict__ xin,
-                                                T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+                                                T* __restrict__ xout, T* __restrict__ d, T cd, T cr, long long lb) {
+  b = lane_ptr(b, lb);
+  xin = lane_ptr(xin, lb);
+  xout = lane_ptr(xout, lb);
+  d = lane_ptr(d, lb);
   const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (unsigned)L.N) return;
   T r[BS];
@@ -117,7 +124,10 @@ __global__ void __launch_bounds__(256) k_cheb_f(Lat32 L, const T* __restrict__ v
 template <int BS, typename T>
 __global__ void __launch_bounds__(256) k_cheb_zero(long long npts, const T* __restrict__ dinv,
                                                    const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ d,
-                                                   T cr) {
+                                                   T cr, long long lb) {
+  b = lane_ptr(b, lb);
+  xout = lane_ptr(xout, lb);
+  d = lane_ptr(d, lb);
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npts) return;
   T r[BS];
@@ -165,7 +175,10 @@ __device__ __forceinline__ bool wsplit_residual(const Lat32& L, const T* __restr
 
 template <int BS, int KIND, int W, typename T>
 __global__ void __launch_bounds__(32 * W) k_spmv_w(Lat32 L, const T* __restrict__ val, const T* __restrict__ x,
-                                                   const T* __restrict__ b, T* __restrict__ y) {
+                                                   const T* __restrict__ b, T* __restrict__ y, long long lb) {
+  x = lane_ptr(x, lb);
+  b = lane_ptr(b, lb);
+  y = lane_ptr(y, lb);
   __shared__ T part[W][BS][32];
   unsigned p;
   T r[BS];
@@ -177,7 +190,11 @@ __global__ void __launch_bounds__(32 * W) k_spmv_w(Lat32 L, const T* __restrict_
 template <int BS, int KIND, int W, typename T>
 __global__ void __launch_bounds__(32 * W) k_cheb_w(Lat32 L, const T* __restrict__ val, const T* __restrict__ dinv,
                                                    const T* __restrict__ b, const T* __restrict__ xin,
-                                                   T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
+                                                   T* __restrict__ xout, T* __restrict__ d, T cd, T cr, long long lb) {
+  b = lane_ptr(b, lb);
+  xin = lane_ptr(xin, lb);
+  xout = lane_ptr(xout, lb);
+  d = lane_ptr(d, lb);
   __shared__ T part[W][BS][32];
   unsigned p;
   T r[BS];
@@ -197,10 +214,10 @@ void sweep_spmv(cudaStream_t stream, const StructOp& A, int bs, const T* val, co
     dispatch_kind_bs<BS.value>(A.kind, [&](auto K) {
       dispatch_sched(sched, [&](auto S) {
         if constexpr (S.value == 1)
-          k_spmv_f<BS.value, K.value, T><<<grid_for(A.N, 256), 256, 0, stream>>>(L, val, x, b, y);
+          k_spmv_f<BS.value, K.value, T><<<lgrid(grid_for(A.N, 256)), 256, 0, stream>>>(L, val, x, b, y, lbytes());
         else
-          k_spmv_w<BS.value, K.value, S.value, T><<<grid_for(A.N, 32), dim3(32, S.value), 0, stream>>>(L, val, x, b,
-                                                                                                        y);
+          k_spmv_w<BS.value, K.value, S.value, T><<<lgrid(grid_for(A.N, 32)), dim3(32, S.value), 0, stream>>>(
+              L, val, x, b, y, lbytes());
       });
     });
   });
@@ -214,11 +231,11 @@ void sweep_cheb(cudaStream_t stream, const StructOp& A, int bs, const T* val, co
     dispatch_kind_bs<BS.value>(A.kind, [&](auto K) {
       dispatch_sched(sched, [&](auto S) {
         if constexpr (S.value == 1)
-          k_cheb_f<BS.value, K.value, T><<<grid_for(A.N, 256), 256, 0, stream>>>(lat, val, dinv, b, xin, out, d, cd,
-                                                                                 cr);
+          k_cheb_f<BS.value, K.value, T><<<lgrid(grid_for(A.N, 256)), 256, 0, stream>>>(lat, val, dinv, b, xin, out, d,
+                                                                                         cd, cr, lbytes());
         else
-          k_cheb_w<BS.value, K.value, S.value, T><<<grid_for(A.N, 32), dim3(32, S.value), 0, stream>>>(
-              lat, val, dinv, b, xin, out, d, cd, cr);
+          k_cheb_w<BS.value, K.value, S.value, T><<<lgrid(grid_for(A.N, 32)), dim3(32, S.value), 0, stream>>>(
+              lat, val, dinv, b, xin, out, d, cd, cr, lbytes());
       });
     });
   });
@@ -227,7 +244,7 @@ void sweep_cheb(cudaStream_t stream, const StructOp& A, int bs, const T* val, co
 template <typename T>
 void sweep_cheb_zero(cudaStream_t stream, long long npts, int bs, const T* dinv, const T* b, T* out, T* d, T cr) {
   dispatch_bs(bs, [&](auto BS) {
-    k_cheb_zero<BS.value, T><<<grid_for(npts, 256), 256, 0, stream>>>(npts, dinv, b, out, d, cr);
+    k_cheb_zero<BS.value, T><<<lgrid(grid_for(npts, 256)), 256, 0, stream>>>(npts, dinv, b, out, d, cr, lbytes());
   });
 }
 

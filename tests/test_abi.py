@@ -82,3 +82,23 @@ def test_create_rejects_invalid_inputs_on_the_host(field, value):
     trac = (ctypes.c_double * 3)(0.0, 0.0, -1.0)
     assert L.load().mhfp_create(ctypes.byref(mesh), ctypes.byref(mats), 0.1, trac, None, ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_lockstep_batch_rejects_lane_counts_on_the_host():
+    """mhfp_batch_create_lanes rejects a lane count outside 1..MHFP_MAX_LANES
+    before it reads a handle (dummy pointers, no GPU)."""
+    import paper_2002_09603_gb300._lib as L
+    from paper_2002_09603_gb300 import build
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    src = open(os.path.join(ROOT, "include", "mhfp.h")).read()
+    max_lanes = int(re.search(r"#define MHFP_MAX_LANES (\d+)", src).group(1))
+    lib = L.load()
+    dummy = (ctypes.c_void_p * 1)(ctypes.c_void_p(8))
+    out = ctypes.c_void_p()
+    for lanes in (0, -1, max_lanes + 1):
+        assert lib.mhfp_batch_create_lanes(1, dummy, dummy, dummy, 1e-8, lanes, ctypes.byref(out)) == 1
+        assert not out.value
+    assert lib.mhfp_batch_create_lanes(1, dummy, dummy, dummy, 0.0, 2, ctypes.byref(out)) == 1

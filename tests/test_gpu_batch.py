@@ -65,3 +65,84 @@ def test_one_launch_matches_single_solves_and_the_oracle(precision):
     lb.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("lanes,fine_blocks", [(4, 0), (3, 0), (4, 4)])
+def test_lockstep_loads_match_single_solves_and_the_oracle(lanes, fine_blocks):
+    """The loads of each instance solved in lockstep (mhfp_batch_create_lanes:
+    every kernel launched once for a set of right-hand sides): each member's
+    solution and statistics bit-identical to the single solve of the same
+    right-hand side on the same handle, and each solution against the
+    oracle's direct solution (energy norm).  The right-hand sides of a set
+    differ in their previous state as well as in the load, so members stop
+    at different iterations, and one is zero (stops before the first cycle);
+    with lanes = 3 the fourth load of an instance is a set of its own, which
+    runs as a single solve; fine_blocks = 4 forces the bulk-copy finest sweep.
+    The sets run fewer kernels than the same solves one after another."""
+    from paper_2002_09603_gb300 import launch_count
+    from paper_2002_09603_gb300._lib import Batch
+    from paper_2002_09603_gb300.batch import prepare_batch
+    probs = _instances()
+    solvers = prepare_batch(probs, precision=1, restart=12, reorth=1, fine_blocks=fine_blocks)
+    rng = np.random.default_rng(11)
+    entries, rhs, out, host = [], [], [], []
+    for i, (s, prob) in enumerate(zip(solvers, probs)):
+        nU, nP, nPi = s.sizes
+        for q, scale in enumerate(mi.LOAD_SCALES):
+            if i == 2 and q == 1:
+                xp, scale = None, 0.0  # b = 0
+            elif q == 0:
+                xp = None
+            else:  # a seeded previous state [u | p | pi]
+                xp = np.concatenate([1e-4 * q * rng.standard_normal(nU), rng.standard_normal(nP + nPi)])
+            b = s.build_rhs(None if xp is None else torch.as_tensor(xp, device=s.device), load_scale=scale)
+            entries.append(s)
+            rhs.append(b)
+            out.append(s.empty())
+            host.append((prob, xp, scale))
+    for s in solvers:
+        s.stream.synchronize()
+    lbatch = Batch(entries, rhs, out, tol=1e-10, lanes=lanes)
+    plain = Batch(entries, rhs, [s.empty() for s in entries], tol=1e-10)
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    stats, codes = lbatch.run()
+    k_lanes = launch_count() - l0
+    assert codes == [0] * len(entries)
+    first = [x.clone() for x in out]
+    stats2, _ = lbatch.run()
+    assert all(torch.equal(a, b) for a, b in zip(first, out))
+    l1 = launch_count()
+    pstats, pcodes = plain.run()
+    k_plain = launch_count() - l1
+    assert pcodes == [0] * len(entries)
+    assert all(torch.equal(a, b) for a, b in zip(first, plain.out))
+    assert k_lanes < k_plain, (k_lanes, k_plain)
+    per_set = {}
+    cache = {}
+    for k, (s, (prob, xp, scale)) in enumerate(zip(entries, host)):
+        x1, st1 = s.solve(rhs[k], tol=1e-10)
+        assert torch.equal(x1, first[k]), (prob.nx, k)
+        for key in ("iterations", "restarts", "converged", "true_rel_residual", "rel_residual"):
+            assert st1[key] == stats[k][key] == pstats[k][key], (key, st1[key], stats[k][key], pstats[k][key])
+        per_set.setdefault((id(s), (k % len(mi.LOAD_SCALES)) // lanes), []).append(stats[k]["iterations"])
+        if id(prob) not in cache:
+            B = oracle.assemble(prob)
+            cache[id(prob)] = (B, precond.build(B, "amg"))
+        B, pc = cache[id(prob)]
+        nU, nP, _ = B.sizes
+        bo = system.rhs(B, None if xp is None else xp[:nU], None if xp is None else xp[nU:nU + nP],
+                        load_scale=scale)
+        xd = oracle.solve_direct(B, bo)
+        e = first[k].cpu().numpy() - xd
+
+        def en(v):
+            return np.sqrt(v[:nU] @ (B.Auu @ v[:nU]) + v[nU:nU + nP] @ (pc.Bt * v[nU:nU + nP])
+                           + v[nU + nP:] @ (pc.C @ v[nU + nP:]))
+        assert en(e) <= 1e-8 * en(xd), (prob.nx, k, en(e), en(xd))
+    # the members of some set stopped at different iterations
+    assert any(len(set(v)) > 1 for v in per_set.values() if len(v) > 1), per_set
+    lbatch.close()
+    plain.close()
+    for s in solvers:
+        s.close()
