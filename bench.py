@@ -790,9 +790,13 @@ def run_batch(args):
 
     probs = mi.batch_instances()
     t0 = time.perf_counter()
-    solvers = prepare_batch(probs, precision=1, restart=args.restart, reorth=args.reorth)
+    # the headline's solver options: the coarsening limit and the set-up
+    # autotuner's Chebyshev degree (chosen per instance)
+    solvers = prepare_batch(probs, precision=1, restart=args.restart, reorth=args.reorth,
+                            cheb_degree=args.cheb_degree, coarse_max=args.coarse_max)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    degrees = [sv.hierarchy(0)["cheb_degree"] for sv in solvers]
     for _ in range(max(1, args.warmup)):
         solve_loads(solvers, (1.0,))
     torch.cuda.synchronize()
@@ -849,7 +853,9 @@ def run_batch(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 (FGMRES, operator, Gram-Schmidt) + f32 (V-cycles, Schur steps)", "data": "synthetic",
             "config": {"workload": WORKLOADS["batch48"]["desc"], "instances": len(solvers), "systems": nsys,
-                       "restart": args.restart, "reorth": args.reorth,
+                       "restart": args.restart, "reorth": args.reorth, "coarse_max": args.coarse_max,
+                       "cheb_degree": ("set-up autotuner, per instance: " if args.cheb_degree == 0 else "option: ")
+                       + ", ".join(f"{d} x{degrees.count(d)}" for d in sorted(set(degrees))),
                        "unknowns_per_load": unknowns, "sizes": [p.nx for p in probs], "all_converged": ok,
                        "iterations_min_max": [min(iters), max(iters)], "setup_s": setup_s,
                        "serial_ms_per_system": serial * 1e3 / nsys,

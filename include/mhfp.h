@@ -248,8 +248,8 @@ mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* co
  * different handles concurrently.  The batch allocates, for each (handle,
  * set size K) it uses, a workspace of K copies of the handle's solve vectors
  * (about (1.5 restart + 14) n doubles per right-hand side), freed by
- * mhfp_batch_destroy.  Only for handles set up with precision = 1 and
- * formulation = 0 (otherwise MHFP_ERR_STATE). */
+ * mhfp_batch_destroy.  Only for handles of the hybrid system (formulation
+ * = 0, either precision); otherwise MHFP_ERR_STATE. */
 #define MHFP_MAX_LANES 16
 mhfp_status mhfp_batch_create_lanes(int count, const mhfp_handle* hs, const double* const* d_rhs,
                                     double* const* d_x, double tol, int max_lanes, mhfp_batch* out);

@@ -81,14 +81,15 @@ __global__ void __launch_bounds__(256) k_cheb(Lat L, const T* __restrict__ val, 
 // the finest displacement level (the dominant sweeps) under names of their own
 template <typename T>
 __global__ void __launch_bounds__(256) k_resid_u0(Lat L, const T* __restrict__ val, const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y) {
-  spmv_body<3, ST_BOX1, T>(L, val, x, b, y);
+                                                  const T* __restrict__ b, T* __restrict__ y, long long lb) {
+  spmv_body<3, ST_BOX1, T>(L, val, lane_ptr(x, lb), lane_ptr(b, lb), lane_ptr(y, lb));
 }
 template <typename T>
 __global__ void __launch_bounds__(256) k_cheb_u0(Lat L, const T* __restrict__ val, const T* __restrict__ dinv,
                                                  const T* __restrict__ b, const T* __restrict__ xin,
-                                                 T* __restrict__ xout, T* __restrict__ d, T cd, T cr) {
-  cheb_body<3, ST_BOX1, T>(L, val, dinv, b, xin, xout, d, cd, cr);
+                                                 T* __restrict__ xout, T* __restrict__ d, T cd, T cr, long long lb) {
+  cheb_body<3, ST_BOX1, T>(L, val, dinv, lane_ptr(b, lb), lane_ptr(xin, lb), lane_ptr(xout, lb), lane_ptr(d, lb), cd,
+                           cr);
 }
 // </hot:k_cheb_u0>
 
@@ -1911,7 +1912,8 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
         launch_cheb_sym(c, L, b, xin, out, v.d, (T)cd, (T)cr);
       } else {
         const Lat lat = lat_of(L.A);
-        k_cheb_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd, (T)cr);
+        k_cheb_u0<T><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, v.val, v.dinv, b, xin, out, v.d, (T)cd,
+                                                                         (T)cr, lbytes());
       }
     } else {
       launch_cheb<T>(c, L, v, b, xin, out, (T)cd, (T)cr, L.tpp ? L.tpp : default_schedule(L.A.N, L.bs));
@@ -1945,7 +1947,7 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
       launch_resid_sym(c, L, x, b, v.r);
     } else {
       const Lat lat = lat_of(L.A);
-      k_resid_u0<T><<<grid_for(lat.N, 256), 256, 0, c.stream>>>(lat, v.val, x, b, v.r);
+      k_resid_u0<T><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, v.val, x, b, v.r, lbytes());
       MHFP_LAUNCH_CHECK();
     }
   } else {

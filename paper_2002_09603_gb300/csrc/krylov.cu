@@ -1157,8 +1157,8 @@ void build_solve_graph(Ctx& c, bool transpose) {
 // levels' vectors) carved from one arena: lane 0's at the start, lane l's
 // l * lane_bytes further.
 Ctx* make_lane_ctx(Ctx& base, int K) {
-  if (!ff_krylov(base))
-    throw Error{MHFP_ERR_STATE, "right-hand sides in lockstep need the mixed-precision solve of the hybrid system"};
+  if (base.opt.formulation != 0)
+    throw Error{MHFP_ERR_STATE, "right-hand sides in lockstep are solved for the hybrid system only"};
   ensure_solve_state(base);
   Ctx* lc = new Ctx(base);
   lc->allocs.clear();
@@ -1193,13 +1193,13 @@ Ctx* make_lane_ctx(Ctx& base, int K) {
   add(lc->partials, (size_t)(m + 2) * GS_BLOCKS * sizeof(double));
   add(lc->scal, 8 * sizeof(double));
   add(lc->dflag, 4 * sizeof(int));
-  add(lc->Zf, (size_t)m * (size_t)base.ldz * sizeof(float));
-  add(lc->tf, n * sizeof(float));
-  add(lc->zf, n * sizeof(float));
+  if (base.Zf) add(lc->Zf, (size_t)m * (size_t)base.ldz * sizeof(float));  // mixed precision: FP32 Z
+  if (base.Z) add(lc->Z, (size_t)m * n * sizeof(double));                  // FP64 throughout
+  if (base.tf) add(lc->tf, n * sizeof(float));
+  if (base.zf) add(lc->zf, n * sizeof(float));
   add(lc->ctl, sizeof(DevCtl));
   add(lc->bcur, n * sizeof(double));
   add(lc->xcur, n * sizeof(double));
-  lc->Z = nullptr;
   for (auto* H : {&lc->hu, &lc->hpi})
     for (Level& L : *H) {
       const size_t ld = (size_t)L.n * sizeof(double), lf = (size_t)L.n * sizeof(float);

@@ -67,8 +67,8 @@ def test_one_launch_matches_single_solves_and_the_oracle(precision):
         s.close()
 
 
-@pytest.mark.parametrize("lanes,fine_blocks", [(4, 0), (3, 0), (4, 4)])
-def test_lockstep_loads_match_single_solves_and_the_oracle(lanes, fine_blocks):
+@pytest.mark.parametrize("lanes,fine_blocks,precision", [(4, 0, 1), (3, 0, 1), (4, 4, 1), (4, 0, 0)])
+def test_lockstep_loads_match_single_solves_and_the_oracle(lanes, fine_blocks, precision):
     """The loads of each instance solved in lockstep (mhfp_batch_create_lanes:
     every kernel launched once for a set of right-hand sides): each member's
     solution and statistics bit-identical to the single solve of the same
@@ -77,13 +77,14 @@ def test_lockstep_loads_match_single_solves_and_the_oracle(lanes, fine_blocks):
     differ in their previous state as well as in the load, so members stop
     at different iterations, and one is zero (stops before the first cycle);
     with lanes = 3 the fourth load of an instance is a set of its own, which
-    runs as a single solve; fine_blocks = 4 forces the bulk-copy finest sweep.
+    runs as a single solve; fine_blocks = 4 forces the bulk-copy finest sweep;
+    precision 0 is the FP64-throughout solve.
     The sets run fewer kernels than the same solves one after another."""
     from paper_2002_09603_gb300 import launch_count
     from paper_2002_09603_gb300._lib import Batch
     from paper_2002_09603_gb300.batch import prepare_batch
     probs = _instances()
-    solvers = prepare_batch(probs, precision=1, restart=12, reorth=1, fine_blocks=fine_blocks)
+    solvers = prepare_batch(probs, precision=precision, restart=12, reorth=1, fine_blocks=fine_blocks)
     rng = np.random.default_rng(11)
     entries, rhs, out, host = [], [], [], []
     for i, (s, prob) in enumerate(zip(solvers, probs)):
