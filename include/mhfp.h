@@ -239,8 +239,7 @@ mhfp_status mhfp_batch_create(int count, const mhfp_handle* hs, const double* co
  * sets of at most max_lanes (1 <= max_lanes <= MHFP_MAX_LANES; 1 gives
  * mhfp_batch_create).  A set of K > 1 entries is one FGMRES run for all K:
  * each kernel of the solve is launched once with the K right-hand sides as
- * its third grid dimension, reading the handle's matrices for all of them
- * at once; each right-hand side keeps its own Krylov basis, Hessenberg
+ * its third grid dimension, the handle's matrices shared by all of them; each right-hand side keeps its own Krylov basis, Hessenberg
  * matrix, restarts and stopping decision, and its result is bit-identical to
  * the same entry in mhfp_batch_create.  The set runs until its last member
  * has stopped; a member that stops earlier keeps its solution and
