@@ -1883,19 +1883,22 @@ void autotune_level(Ctx& c, Level& L) {
   L.sweep_us = best;
 }
 
+// Chebyshev smoothing of level l from x0 (null: from zero) into dst.  Each
+// step reads neighbours of its input, so it cannot update in place: the
+// steps write dst and alt in turn, chosen so that the last one writes dst
+// (the first step's output differs from x0 when alt is the buffer that x0
+// is not, or x0 is null).
 template <typename T>
-void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_zero, bool time_it) {
+void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, const T* x0, T* dst, T* alt, bool time_it) {
   Level& L = H[l];
   const LV<T> v = view(c, L, T());
-  T* other = v.y;
+  const int deg = c.opt.cheb_degree;
   const double lmax = L.lmax, lmin = lmax / c.opt.cheb_ratio;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
-  // ping-pong so that the last step writes x (each step reads neighbours of
-  // its input, so it cannot update in place)
-  const T* xin = from_zero ? nullptr : x;
-  T* out = (from_zero && c.opt.cheb_degree % 2 == 1) ? x : other;
-  for (int s = 0; s < c.opt.cheb_degree; ++s) {
+  const T* xin = x0;
+  for (int s = 0; s < deg; ++s) {
+    T* out = ((deg - 1 - s) % 2 == 0) ? dst : alt;
     double cd = 0.0, cr = 1.0 / theta;
     if (s > 0) {
       const double rn = 1.0 / (2.0 * sigma - rho);
@@ -1925,9 +1928,7 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool from_ze
     const double blocks = std::is_same<T, float>::value ? 14.0 : 27.0;
     if (time_it && xin) timing_end(c, 0, (blocks * 9 + 9) * sizeof(T) * L.npts + 5.0 * sizeof(T) * L.n);
     xin = out;
-    out = (out == x) ? other : x;
   }
-  if (xin != x) MHFP_CUDA(lane_copy(x, xin, L.n * sizeof(T), c.stream));
 }
 
 template <typename T>
@@ -1941,17 +1942,21 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
     return;
   }
   const bool fine_u = (&H == &c.hu) && l == 0;
-  smooth<T>(c, H, l, b, x, true, fine_u);
+  // the pre-smoothed and corrected iterate lives in s_buf, chosen so that the
+  // post-smoothing's last step writes x: the level's other work vector when
+  // the degree is odd, x itself when it is even (no copy back)
+  T* s_buf = (c.opt.cheb_degree % 2 == 1) ? v.y : x;
+  smooth<T>(c, H, l, b, nullptr, s_buf, s_buf == x ? v.y : x, fine_u);
   if (fine_u) {
     if constexpr (std::is_same<T, float>::value) {
-      launch_resid_sym(c, L, x, b, v.r);
+      launch_resid_sym(c, L, s_buf, b, v.r);
     } else {
       const Lat lat = lat_of(L.A);
-      k_resid_u0<T><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, v.val, x, b, v.r, lbytes());
+      k_resid_u0<T><<<lgrid(grid_for(lat.N, 256)), 256, 0, c.stream>>>(lat, v.val, s_buf, b, v.r, lbytes());
       MHFP_LAUNCH_CHECK();
     }
   } else {
-    level_spmv_t<T>(c, L, x, b, v.r);
+    level_spmv_t<T>(c, L, s_buf, b, v.r);
   }
   Level& C = H[l + 1];
   T* cb = bvec(C, T());
@@ -1970,7 +1975,7 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   MHFP_LAUNCH_CHECK();
   vcycle_level<T>(c, H, l + 1, cb, cx);
   if (L.faces) {
-    k_prolong_faces<T><<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, x, lbytes());
+    k_prolong_faces<T><<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, s_buf, lbytes());
   } else {
     // one fine point per thread on large levels, slots split over 8 warps on small ones
     const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
@@ -1978,15 +1983,15 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
       dispatch_r(L.R, [&](auto RR) {
         if (L.A.N >= 65536)
           k_prolong_f<BF.value, BC.value, RR.value, T><<<lgrid(grid_for(L.A.N, 256)), 256, 0, c.stream>>>(
-              F, Cc, v.P, cx, x, lbytes());
+              F, Cc, v.P, cx, s_buf, lbytes());
         else
           k_prolong_w<BF.value, BC.value, RR.value, 8, T><<<lgrid(grid_for(L.A.N, 32)), dim3(32, 8), 0, c.stream>>>(
-              F, Cc, v.P, cx, x, lbytes());
+              F, Cc, v.P, cx, s_buf, lbytes());
       });
     });
   }
   MHFP_LAUNCH_CHECK();
-  smooth<T>(c, H, l, b, x, false, fine_u);
+  smooth<T>(c, H, l, b, s_buf, x, v.y, fine_u);
 }
 
 float* cast_copy(Ctx& c, const double* src, size_t n) {
@@ -2161,7 +2166,7 @@ void build_mixed_hierarchies(Ctx& c) {
 // x = the Chebyshev smoother of level 0 of H applied to b from x = 0 (the
 // mixed formulation's A_qq solve)
 void chebyshev_from_zero(Ctx& c, std::vector<Level>& H, const double* b, double* x) {
-  smooth<double>(c, H, 0, b, x, true, false);
+  smooth<double>(c, H, 0, b, nullptr, x, view(c, H[0], double()).y, false);
 }
 
 int level_schedule(Ctx& c, std::vector<Level>& H, int l) {
