@@ -566,9 +566,13 @@ __global__ void __launch_bounds__(32 * W) k_prolong_w(Lat32 F, Lat32 C, const T*
 // points before the sums, then a fixed-order xor reduction over the warp
 template <int BF, int BC, int R, typename T>
 __global__ void __launch_bounds__(256) k_restrict_f(Lat32 F, Lat32 C, const T* __restrict__ P,
-                                                    const T* __restrict__ r, T* __restrict__ bc, long long lb) {
+                                                    const T* __restrict__ r, T* __restrict__ bc,
+                                                    const T* __restrict__ dinvc, T cr, T* __restrict__ xc,
+                                                    T* __restrict__ dc, long long lb) {
   r = lane_ptr(r, lb);
   bc = lane_ptr(bc, lb);
+  xc = lane_ptr(xc, lb);
+  dc = lane_ptr(dc, lb);
   constexpr int ns = (2 + 2 * R) / 3 + 1, w = 3 + 2 * R, NB = w * w * w, PER = (NB + 31) / 32;
   // blocks larger than 3 x 3 keep one box point's loads in flight at a time
   constexpr int KB = BF * BC > 9 ? 1 : PER;
@@ -620,6 +624,19 @@ __global__ void __launch_bounds__(256) k_restrict_f(Lat32 F, Lat32 C, const T* _
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], m);
     if (valid && lane == 0) bc[BC * J + q] = acc[q];
+  }
+  // the coarse level's first Chebyshev step from zero (with dinvc): d = cr
+  // D^-1 b, x = d, the same sums as its own kernel would form from bc
+  if (dinvc && valid && lane == 0) {
+    const unsigned Nc = (unsigned)C.N;
+#pragma unroll
+    for (int a = 0; a < BC; ++a) {
+      T z = T(0);
+#pragma unroll
+      for (int t = 0; t < BC; ++t) z += dinvc[(unsigned)(a * BC + t) * Nc + J] * acc[t];
+      dc[BC * J + a] = cr * z;
+      xc[BC * J + a] = cr * z;
+    }
   }
 }
 
@@ -707,9 +724,13 @@ __device__ __forceinline__ int ft_face_cells(const FaceTopo& d, long long f, int
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_faces(FaceTopo32 t, const T* __restrict__ pw,
-                                                        const T* __restrict__ r, T* __restrict__ bc, long long lb) {
+                                                        const T* __restrict__ r, T* __restrict__ bc,
+                                                        const T* __restrict__ dinvc, T cr, T* __restrict__ xc,
+                                                        T* __restrict__ dc, long long lb) {
   r = lane_ptr(r, lb);
   bc = lane_ptr(bc, lb);
+  xc = lane_ptr(xc, lb);
+  dc = lane_ptr(dc, lb);
   const unsigned Tc = blockIdx.x * blockDim.x + threadIdx.x;
   if (Tc >= t.nT) return;
   const unsigned q = t.d_nx.div(Tc);
@@ -722,6 +743,12 @@ __global__ void __launch_bounds__(256) k_restrict_faces(FaceTopo32 t, const T* _
     s += pw[f] * r[f];
   }
   bc[Tc] = s;
+  if (dinvc) {  // the cell level's first Chebyshev step from zero, as k_restrict_f
+    T z = T(0);
+    z += dinvc[Tc] * s;
+    dc[Tc] = cr * z;
+    xc[Tc] = cr * z;
+  }
 }
 
 template <typename T>
@@ -1888,17 +1915,33 @@ void autotune_level(Ctx& c, Level& L) {
 // steps write dst and alt in turn, chosen so that the last one writes dst
 // (the first step's output differs from x0 when alt is the buffer that x0
 // is not, or x0 is null).
+// the centre of level L's Chebyshev interval [lmax / ratio, lmax]
+double cheb_theta(const Ctx& c, const Level& L) {
+  const double lmax = L.lmax, lmin = lmax / c.opt.cheb_ratio;
+  return 0.5 * (lmax + lmin);
+}
+
+// output buffer of step s of a smoothing into dst that alternates with alt
 template <typename T>
-void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, const T* x0, T* dst, T* alt, bool time_it) {
+T* step_out(int deg, int s, T* dst, T* alt) {
+  return ((deg - 1 - s) % 2 == 0) ? dst : alt;
+}
+
+// With first_done the first step (from zero, x0 null) was already taken by
+// the restriction that produced b (its output in that step's buffer, its
+// direction in the level's d): the smoothing goes on from the second step.
+template <typename T>
+void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, const T* x0, T* dst, T* alt, bool time_it,
+            bool first_done = false) {
   Level& L = H[l];
   const LV<T> v = view(c, L, T());
   const int deg = c.opt.cheb_degree;
   const double lmax = L.lmax, lmin = lmax / c.opt.cheb_ratio;
-  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  const double theta = cheb_theta(c, L), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rho = 1.0 / sigma;
-  const T* xin = x0;
-  for (int s = 0; s < deg; ++s) {
-    T* out = ((deg - 1 - s) % 2 == 0) ? dst : alt;
+  const T* xin = first_done ? step_out(deg, 0, dst, alt) : x0;
+  for (int s = first_done ? 1 : 0; s < deg; ++s) {
+    T* out = step_out(deg, s, dst, alt);
     double cd = 0.0, cr = 1.0 / theta;
     if (s > 0) {
       const double rn = 1.0 / (2.0 * sigma - rho);
@@ -1932,7 +1975,7 @@ void smooth(Ctx& c, std::vector<Level>& H, int l, const T* b, const T* x0, T* ds
 }
 
 template <typename T>
-void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
+void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x, bool pre_done = false) {
   Level& L = H[l];
   const LV<T> v = view(c, L, T());
   if (L.dense_inv) {
@@ -1946,7 +1989,7 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   // post-smoothing's last step writes x: the level's other work vector when
   // the degree is odd, x itself when it is even (no copy back)
   T* s_buf = (c.opt.cheb_degree % 2 == 1) ? v.y : x;
-  smooth<T>(c, H, l, b, nullptr, s_buf, s_buf == x ? v.y : x, fine_u);
+  smooth<T>(c, H, l, b, nullptr, s_buf, s_buf == x ? v.y : x, fine_u, pre_done);
   if (fine_u) {
     if constexpr (std::is_same<T, float>::value) {
       launch_resid_sym(c, L, s_buf, b, v.r);
@@ -1961,19 +2004,30 @@ void vcycle_level(Ctx& c, std::vector<Level>& H, int l, const T* b, T* x) {
   Level& C = H[l + 1];
   T* cb = bvec(C, T());
   T* cx = xvec(C, T());
+  // the restriction also takes the coarse level's first Chebyshev step from
+  // zero (d = cr D^-1 b into that step's buffer), unless it is the dense one
+  const bool fuse = !C.dense_inv;
+  const LV<T> cv = view(c, C, T());
+  const int deg = c.opt.cheb_degree;
+  T* cs_buf = (deg % 2 == 1) ? cv.y : cx;
+  const T* fdinv = fuse ? cv.dinv : nullptr;
+  const T fcr = fuse ? (T)(1.0 / cheb_theta(c, C)) : T(0);
+  T* fx = fuse ? step_out(deg, 0, cs_buf, cs_buf == cx ? cv.y : cx) : nullptr;
+  T* fd = fuse ? cv.d : nullptr;
   if (L.faces) {
-    k_restrict_faces<T><<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb, lbytes());
+    k_restrict_faces<T><<<lgrid(grid_for(c.nT, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, v.r, cb, fdinv, fcr,
+                                                                          fx, fd, lbytes());
   } else {
     const Lat32 F = lat32_of(L.A), Cc = lat32_of(C.A);
     dispatch_pair(L.bs, C.bs, [&](auto BF, auto BC) {
       dispatch_r(L.R, [&](auto RR) {
         k_restrict_f<BF.value, BC.value, RR.value, T><<<lgrid(grid_for(C.A.N * 32, 256)), 256, 0, c.stream>>>(
-            F, Cc, v.P, v.r, cb, lbytes());
+            F, Cc, v.P, v.r, cb, fdinv, fcr, fx, fd, lbytes());
       });
     });
   }
   MHFP_LAUNCH_CHECK();
-  vcycle_level<T>(c, H, l + 1, cb, cx);
+  vcycle_level<T>(c, H, l + 1, cb, cx, fuse);
   if (L.faces) {
     k_prolong_faces<T><<<lgrid(grid_for(c.nF, 256)), 256, 0, c.stream>>>(face_topo(c), v.pw, cx, s_buf, lbytes());
   } else {
